@@ -1,0 +1,231 @@
+/*
+ * he_lr.h -- C ABI of the GB300 library for encrypted logistic-regression
+ * training with quadratic-gradient NAG (arXiv 2406.13221).
+ *
+ * The paper trains logistic regression on data encrypted under an approximate
+ * homomorphic scheme (Sec. 2.1: Enc, Dec, Add, cAdd, Mul, cMul, rotation and
+ * rescaling), with the client preparing Z and Bbar, encrypting Z, Bbar and the
+ * initial weights, and the cloud running the iterations (Sec. 4.3, Steps 1-8).
+ * This library implements the scheme in residue-number-system form (limbs
+ * modulo NTT-friendly primes below 2^60, hybrid key switching with one special
+ * prime P) on one GPU.
+ *
+ * Conventions for every call:
+ *   - Return value: HE_OK (0) or one of the HE_E* codes below; no call throws.
+ *     he_last_error(ctx) returns a message for the last failure on ctx
+ *     (owned by ctx, valid until the next call on ctx).
+ *   - Handles are opaque.  The library owns all device memory it allocates
+ *     (stream-ordered allocations on the stream given at he_ctx_create);
+ *     the caller owns every host buffer it passes and keeps it valid for the
+ *     duration of the call only.  Calls on one context are not thread-safe.
+ *   - "Slots": N/2 complex values per plaintext; slot j is the value of the
+ *     message polynomial at zeta^(5^j), zeta = exp(i pi / N).
+ *   - Levels: a ciphertext at level l has limbs q_0..q_l; fresh encryptions
+ *     sit at level n_q - 1.
+ *   - Words exchanged with the host (he_ct_export / he_ct_import) are in
+ *     coefficient form, layout [2][level+1][N], limb j reduced modulo q_j.
+ *   - The library fails loudly: there is no CPU fallback for any call that
+ *     computes on ciphertexts; without a usable CUDA device they return
+ *     HE_ECUDA.
+ */
+#ifndef HE_LR_H
+#define HE_LR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    HE_OK = 0,
+    HE_EINVAL = 1,    /* bad argument (null pointer, size, parameter range) */
+    HE_ENOMEM = 2,    /* device or host allocation failed */
+    HE_ELEVEL = 3,    /* not enough levels left for the operation */
+    HE_ESCALE = 4,    /* scales of the operands do not match */
+    HE_ECUDA = 5,     /* CUDA runtime error or no device */
+    HE_ETIMEOUT = 6,  /* a bounded device-side wait expired */
+    HE_EINTERNAL = 7, /* internal invariant violated */
+    HE_EKEY = 8       /* a required key (secret, relinearisation or rotation) is missing */
+};
+
+typedef struct he_ctx he_ctx;
+typedef struct he_ct he_ct;
+typedef struct he_pt he_pt;
+
+/* Scheme parameters (Sec. 5: the paper's runs use N = 2^16; the chain here is
+ * one q0_bits prime, n_q - 1 primes of qi_bits, one special prime of p_bits,
+ * all = 1 mod 2N; the secret is ternary and errors are discrete Gaussians of
+ * width sigma). log_n in [10, 16], 2 <= n_q <= 39, bit widths in [30, 60]. */
+typedef struct {
+    int log_n;
+    int n_q;
+    int q0_bits;
+    int qi_bits;
+    int p_bits;
+    double sigma;
+} he_params;
+
+/* Create a context: generates the prime chain, transform tables and the
+ * encoder tables on the device.  cuda_stream: a cudaStream_t (NULL = legacy
+ * default stream); every kernel of this context runs on it. */
+int he_ctx_create(const he_params *p, void *cuda_stream, he_ctx **out);
+int he_ctx_destroy(he_ctx *ctx);
+const char *he_last_error(const he_ctx *ctx);
+/* Prime chain q_0..q_{n_q-1}, P (n >= n_q + 1 entries). */
+int he_ctx_primes(const he_ctx *ctx, uint64_t *out, size_t n);
+/* Host-only: the Gaussian sampler's cumulative table for width sigma
+ * (floor(2^63 P(|x| <= k)), last entry 2^63); returns its length via *len. */
+int he_gauss_table(double sigma, uint64_t *out, size_t cap, size_t *len);
+/* Host-only: the canonical-embedding root table zeta^k = exp(i pi k / N),
+ * k < 2N, as re/im doubles (2N entries each). */
+int he_zeta_table(int log_n, double *re, double *im);
+
+/* Key generation (Sec. 2.1, Sec. 4.3: the third party issues the keys).
+ * The secret s is ternary, the public key is (-a s + e, a), the
+ * relinearisation key switches s^2 -> s and one rotation key per entry of
+ * `rotations` (a left rotation of the slot vector by r; negative r rotates
+ * right) switches s(X^(5^r)) -> s.  Randomness is the splitmix64 stream of
+ * `seed`.  May be called again to add rotation keys (same seed). */
+int he_keygen(he_ctx *ctx, uint64_t seed, const int64_t *rotations, size_t n_rot);
+
+/* Encode n_slots <= N/2 complex values (re, im; im may be NULL) at `level`
+ * with `scale`: the coefficients are round_half_away(scale * tau^-1(z)). */
+int he_encode(he_ctx *ctx, const double *re, const double *im, size_t n_slots, int level,
+              double scale, he_pt **out);
+/* Decode to n_slots values (im may be NULL).  Valid while |scale * z| < q_0/2. */
+int he_decode(he_ctx *ctx, const he_pt *pt, double *re, double *im, size_t n_slots);
+/* Enc_pk (Sec. 2.1): (v b + e0 + m, v a + e1), v ternary, e0, e1 Gaussian, all
+ * drawn from the splitmix64 stream of `seed`. */
+int he_encrypt(he_ctx *ctx, const he_pt *pt, uint64_t seed, he_ct **out);
+/* Dec_sk (Sec. 2.1): c0 + c1 s. */
+int he_decrypt(he_ctx *ctx, const he_ct *ct, he_pt **out);
+
+int he_ct_export(const he_ct *ct, uint64_t *words, size_t n_words, int *level, double *scale);
+int he_ct_import(he_ctx *ctx, const uint64_t *words, size_t n_words, int level, double scale,
+                 he_ct **out);
+/* Plaintext words in coefficient form, [level+1][N]. */
+int he_pt_export(const he_pt *pt, uint64_t *words, size_t n_words, int *level, double *scale);
+int he_ct_level(const he_ct *ct, int *level, double *scale);
+int he_ct_free(he_ct *ct);
+int he_pt_free(he_pt *pt);
+
+/* Homomorphic operations of Sec. 2.1; each returns a new ciphertext.
+ * Add/Sub need equal levels and scales (relative 2^-40).  Mul is the tensor
+ * product followed by relinearisation; its scale is the product of scales
+ * and it does not rescale.  Rescale divides by q_level with rounding.
+ * cMul multiplies by round_half_away(c * const_scale); cAdd adds
+ * round_half_away(c * scale) to every slot.  Rotate by r slots to the left. */
+int he_add(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
+int he_sub(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
+int he_mul(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
+int he_rescale(he_ctx *ctx, const he_ct *a, he_ct **out);
+int he_moddrop(he_ctx *ctx, const he_ct *a, int level, he_ct **out);
+int he_rotate(he_ctx *ctx, const he_ct *a, int64_t r, he_ct **out);
+int he_cmul(he_ctx *ctx, const he_ct *a, double c, double const_scale, he_ct **out);
+int he_cadd(he_ctx *ctx, const he_ct *a, double c, he_ct **out);
+int he_ptmul(he_ctx *ctx, const he_ct *a, const he_pt *pt, he_ct **out);
+/* Set the declared scale of a ciphertext (used to align scales that agree up
+ * to rounding of a constant, Sec. 2.1 rescaling). */
+int he_set_scale(he_ct *ct, double scale);
+
+/* Batched negacyclic NTT on device limbs (the transform under every ring
+ * product of the scheme).  d_limbs: device pointer, [n_limbs][N] words in
+ * [0, q); limb i is reduced modulo prime index prime_of[i % period]
+ * (index n_q is P).  Output: evaluation form in the library's internal order
+ * (bit-reversed evaluation index); he_ntt_inverse undoes it.  Runs on the
+ * context stream. */
+int he_ntt_forward(he_ctx *ctx, uint64_t *d_limbs, size_t n_limbs, const int *prime_of, int period);
+int he_ntt_inverse(he_ctx *ctx, uint64_t *d_limbs, size_t n_limbs, const int *prime_of, int period);
+
+/* Batched key switching of device polynomials, the hot primitive of every Mul
+ * and rotation.  d_in: [batch][level+1][N] NTT-form words (modulo q_j);
+ * d_out: [batch][2][level+1][N].  gal = 0 selects the relinearisation key,
+ * otherwise the rotation key of galois element gal.  Device scratch is
+ * allocated by the call. */
+int he_keyswitch_batch(he_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int batch, int level,
+                       uint64_t gal);
+/* Galois element of a left rotation by r. */
+uint64_t he_galois_elt(const he_ctx *ctx, int64_t r);
+
+/* ------------------------------------------------------------------ training */
+/* Learning-rate schedule F2(t) = max - (max - min) (t / T)^power (Sec. 3.2);
+ * the paper's runs use (2, 1, 81, 2.5). */
+typedef struct {
+    double max, min, T, power;
+} he_lr_sched;
+
+enum { HE_LR_FULL_BATCH = 0, HE_LR_MINI_BATCH = 1 };
+enum { HE_LR_G8 = 0, HE_LR_G16 = 1 };
+
+typedef struct {
+    double sec_setup;        /* client precompute + encryption + key generation */
+    double sec_iter_avg;     /* average seconds per iteration (update + refresh) */
+    double sec_update_avg;   /* average seconds of the update alone (Steps 4-6) */
+    uint64_t keyswitches;    /* key switches issued per iteration (last one) */
+    int n_blocks;            /* encrypted data blocks */
+    int g, m;                /* packing: g columns x m rows per block */
+    double max_abs_ip;       /* unused by the library (0) */
+} he_lr_stats;
+
+typedef struct he_lr_job he_lr_job;
+
+/* Client side of Sec. 4.3 Steps 1-3: build Z = y * [1 | X] (bias first),
+ * Bbar per mini-batch of batch_rows rows (Sec. 3.1, 1/(eps + 1/4 sum |Z^T Z|),
+ * eps = 1e-8) and the full-batch Bbar by the combination of Sec. 3.3, pack
+ * m x g blocks (g = next power of two >= f + 1, m g = N/2; Sec. 2.2),
+ * encrypt the blocks, n*Bbar (replicated per row) and W = V = 0 at the top
+ * level with scale 2^log_scale.  Object k of kind K is encrypted with seed
+ * enc_seed + (K << 48) + k (K: 1 block, 2 Bbar, 3 W0, 4 V0, 5 W refresh at
+ * iteration k, 6 V refresh).  X: n x f row-major doubles, y: n labels +/-1.
+ * Keys for the needed rotations are generated from key_seed if missing.
+ * batch_blocks: data blocks per kernel launch (0 = automatic). */
+int he_lr_job_create(he_ctx *ctx, const double *X, const double *y, size_t n, size_t f,
+                     int mode, size_t batch_rows, int poly, double log_scale, uint64_t enc_seed,
+                     uint64_t key_seed, int batch_blocks, he_lr_job **out);
+/* Cloud side, Sec. 4.3 Steps 4-7 for iteration t (t = 0, 1, ...): gradient,
+ * quadratic gradient, NAG update (Algorithm 1) and the refresh of W and V
+ * (decrypt + re-encrypt, standing in for bootstrapping). */
+int he_lr_job_step(he_lr_job *job, int t, he_lr_sched sched);
+/* Decrypted weights W (slots of row `row`, g values; padded columns are 0). */
+int he_lr_job_weights(he_lr_job *job, int row, double *w, size_t len);
+/* Access to the job's current W and V ciphertexts (owned by the job). */
+int he_lr_job_state(he_lr_job *job, const he_ct **W, const he_ct **V);
+/* A copy of one encrypted input of the job: kind 0 = data block `index`,
+ * kind 1 = Enc(n Bbar) of mini-batch `index` (index 0 in full-batch mode). */
+int he_lr_job_input(he_lr_job *job, int kind, int index, he_ct **out);
+/* Gradient ciphertext of one block for the job's current W (Steps 1-6 alone,
+ * computed in the same chunked launch that he_lr_job_step uses for the chunk
+ * holding the block); returns a new ciphertext. */
+int he_lr_job_block_grad(he_lr_job *job, int block, double alpha, he_ct **out);
+int he_lr_job_info(const he_lr_job *job, he_lr_stats *stats);
+int he_lr_job_free(he_lr_job *job);
+
+/* Whole training through one call: job_create + iters x job_step + weights
+ * of row 0 (w_out holds g values).  stats may be NULL. */
+int he_lr_train(he_ctx *ctx, const double *X, const double *y, size_t n, size_t f, int iters,
+                he_lr_sched sched, int mode, size_t batch_rows, int poly, uint64_t enc_seed,
+                uint64_t key_seed, double *w_out, size_t w_len, he_lr_stats *stats);
+
+/* One encrypted iteration on caller-supplied ciphertexts (cloud only):
+ * Z[0..n_blocks-1] data blocks at one level, B = Enc(n Bbar) at that level,
+ * W, V at that level; g x m packing; alpha = F2(t), eta from Algorithm 1,
+ * inv_n = 1/n; poly = (c0, c1, c3) of the sigmoid polynomial.  Returns
+ * W', V' seven levels down (before any refresh). */
+int he_lr_iteration(he_ctx *ctx, he_ct *const *Z, size_t n_blocks, const he_ct *B, const he_ct *W,
+                    const he_ct *V, int g, int m, double alpha, double eta, double inv_n,
+                    const double poly[3], he_ct **W_out, he_ct **V_out);
+/* The refresh used between iterations: decrypt, take the real part of every
+ * slot, re-encode at the top level with `scale`, encrypt with `seed`. */
+int he_refresh(he_ctx *ctx, const he_ct *in, double scale, uint64_t seed, he_ct **out);
+
+/* Host-only client precompute exposed for checking: Bbar (length g) for the
+ * rows [row0, row0 + rows) of Z = y * [1 | X]. */
+int he_lr_bbar(const double *X, const double *y, size_t n, size_t f, size_t row0, size_t rows,
+               size_t g, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

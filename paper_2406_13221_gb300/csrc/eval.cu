@@ -1,0 +1,389 @@
+// eval.cu -- batched homomorphic operations (Sec. 2.1) over many ciphertexts at
+// once, and the single-ciphertext C ABI built on them.
+//
+// Scale rule: Mul and plaintext products multiply scales; Rescale at level l
+// divides by q_l; cMul by the integer k at constant scale S multiplies by S;
+// cAdd adds round_half_away(c * scale); Add needs scales equal to 2^-40.
+#include <math.h>
+#include "helr_internal.cuh"
+
+#define GS_LOOP(i, n) for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (size_t)gridDim.x * blockDim.x)
+
+namespace {
+inline unsigned grid_for(size_t work, int threads = 256)
+{
+    size_t b = (work + threads - 1) / threads;
+    if (b > (size_t)152 * 64) b = (size_t)152 * 64;
+    return (unsigned)(b ? b : 1);
+}
+
+// acc[p][j][k] (+)= sum_b a[b][p][j][k]
+__global__ void k_sum_items_kernel(uint64_t *acc, const uint64_t *a, size_t item, int batch, size_t nwords, int logn,
+                                   int nl, const ModQ *mods, int accumulate)
+{
+    GS_LOOP(i, nwords) {
+        int j = (int)((i >> logn) % nl);
+        uint64_t q = mods[j].q;
+        uint64_t s = accumulate ? acc[i] : 0;
+        for (int b = 0; b < batch; b++) s = addmod(s, a[b * item + i], q);
+        acc[i] = s;
+    }
+}
+}  // namespace
+
+bool scales_match(double a, double b) { return fabs(a - b) <= a * 0x1p-40; }
+
+int64_t round_half_away(double x) { return llround(x); }
+
+static KP shoup_consts(const he_ctx *c, int nl, int64_t k)
+{
+    KP kp;
+    for (int j = 0; j < nl; j++) {
+        uint64_t q = c->q[j];
+        uint64_t v = k >= 0 ? (uint64_t)k % q : (q - (uint64_t)(-(k + 1)) % q - 1);
+        kp.w[j][0] = v;
+        kp.w[j][1] = (uint64_t)(((unsigned __int128)v << 64) / q);
+    }
+    return kp;
+}
+
+static inline Str S(const CtB &x, he_ctx *c) { return Str{x.d, x.item, (size_t)(x.level + 1) * c->n}; }
+
+int ev_init(he_ctx *c, Eval *ev, int maxb, int maxlevel)
+{
+    ev->c = c;
+    ev->maxb = maxb;
+    ev->maxlevel = maxlevel;
+    ev->keyswitches = 0;
+    const size_t nl = maxlevel + 1, N = c->n, B = maxb;
+    HELR_TRY(helr_ks_scratch_alloc(c, maxb, maxlevel, &ev->ks));
+    size_t words = 3 * B * nl * N + 2 * B * nl * N + B * nl * N + 2 * B * N + 2 * B * nl * N;
+    uint64_t *p = nullptr;
+    HELR_TRY(helr_alloc(c, (void **)&p, words * 8));
+    ev->tens = p;
+    ev->ksout = ev->tens + 3 * B * nl * N;
+    ev->rot1 = ev->ksout + 2 * B * nl * N;
+    ev->last = ev->rot1 + B * nl * N;
+    ev->lift = ev->last + 2 * B * N;
+    return HE_OK;
+}
+void ev_free(Eval *ev)
+{
+    if (!ev->c) return;
+    helr_ks_scratch_free(ev->c, &ev->ks);
+    helr_free(ev->c, ev->tens);
+    ev->tens = nullptr;
+}
+
+static int check_batch(Eval *ev, const CtB &a)
+{
+    if (a.batch > ev->maxb || a.level > ev->maxlevel)
+        return helr_fail(ev->c, HE_EINTERNAL, "batch %d / level %d exceeds evaluator capacity", a.batch, a.level);
+    return HE_OK;
+}
+
+// out = Relin(a (x) b); b may broadcast.  out.level = a.level, scale = product.
+int ev_mul_relin(Eval *ev, const CtB &a, const CtB &b, CtB &out)
+{
+    he_ctx *c = ev->c;
+    HELR_TRY(check_batch(ev, a));
+    if (a.level != b.level) return helr_fail(c, HE_ELEVEL, "Mul: levels %d and %d differ", a.level, b.level);
+    const int B = a.batch, lv = a.level, nl = lv + 1;
+    const size_t N = c->n, lw = (size_t)nl * N;
+    const uint64_t *key = helr_find_key(c, 0);
+    if (!key) return helr_fail(c, HE_EKEY, "no relinearisation key");
+    k_tensor(c, a.d, b.d, ev->tens, B, lv, a.item, b.item, lw, (size_t)B * lw, c->stream);
+    HELR_TRY(helr_keyswitch(c, ev->tens + 2 * (size_t)B * lw, ev->ksout, B, lv, key, &ev->ks));
+    ev->keyswitches += B;
+    Str d{ev->tens, lw, (size_t)B * lw}, k{ev->ksout, 2 * lw, lw};
+    out.level = lv;
+    out.batch = B;
+    out.scale = a.scale * b.scale;
+    k_ew(c, EW_ADD, S(out, c), d, k, B, 2, nl, nullptr, c->stream);
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
+
+// divide by q_level with rounding: out at level - 1
+int ev_rescale(Eval *ev, const CtB &a, CtB &out)
+{
+    he_ctx *c = ev->c;
+    HELR_TRY(check_batch(ev, a));
+    const int lv = a.level;
+    if (lv < 1) return helr_fail(c, HE_ELEVEL, "Rescale: no level left");
+    const int B = a.batch, nl = lv + 1;
+    const size_t N = c->n;
+    cudaStream_t s = c->stream;
+    for (int p = 0; p < 2; p++)
+        HELR_CUDA(c, cudaMemcpy2DAsync(ev->last + p * N, 2 * N * 8, a.d + (size_t)p * nl * N + (size_t)lv * N,
+                                       (a.item ? a.item : 2 * nl * N) * 8, N * 8, B, cudaMemcpyDeviceToDevice, s));
+    HELR_TRY(helr_ntt_inv(c, ev->last, 2 * (size_t)B, limbmap_single(lv), s));
+    k_lift(c, ev->last, ev->lift, 2 * B, lv, N, limbmap_ct(lv - 1), (size_t)lv * N, s);
+    HELR_TRY(helr_ntt_fwd(c, ev->lift, 2 * (size_t)B * lv, limbmap_ct(lv - 1), s));
+    KP kp;
+    std::vector<uint64_t> h(2);
+    for (int j = 0; j < lv; j++) {
+        uint64_t x = 0, q = c->q[j], ql = c->q[lv] % q;
+        // q_l^-1 mod q_j by Fermat
+        unsigned __int128 r = 1, b = ql;
+        for (uint64_t e = q - 2; e; e >>= 1, b = b * b % q)
+            if (e & 1) r = r * b % q;
+        x = (uint64_t)r;
+        kp.w[j][0] = x;
+        kp.w[j][1] = (uint64_t)(((unsigned __int128)x << 64) / q);
+    }
+    out.level = lv - 1;
+    out.batch = B;
+    out.scale = a.scale / (double)c->q[lv];
+    Str in{a.d, a.item, (size_t)nl * N}, corr{ev->lift, 2 * (size_t)lv * N, (size_t)lv * N};
+    k_ew(c, EW_SUBMUL, S(out, c), in, corr, B, 2, lv, &kp, s);
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
+
+// left rotation by r slots; out must not alias a
+int ev_rotate(Eval *ev, const CtB &a, int64_t r, CtB &out)
+{
+    he_ctx *c = ev->c;
+    HELR_TRY(check_batch(ev, a));
+    const uint64_t gal = he_galois_elt(c, r);
+    const uint64_t *key = helr_find_key(c, gal);
+    if (!key) return helr_fail(c, HE_EKEY, "no rotation key for %lld", (long long)r);
+    const int B = a.batch, lv = a.level, nl = lv + 1;
+    const size_t N = c->n, lw = (size_t)nl * N;
+    cudaStream_t s = c->stream;
+    k_automorph_items(c, ev->rot1, lw, a.d + lw, a.item, B, nl, gal, s);
+    k_automorph_items(c, out.d, out.item, a.d, a.item, B, nl, gal, s);
+    HELR_TRY(helr_keyswitch(c, ev->rot1, ev->ksout, B, lv, key, &ev->ks));
+    ev->keyswitches += B;
+    Str o0{out.d, out.item, lw}, k0{ev->ksout, 2 * lw, lw};
+    k_ew(c, EW_ADD, o0, o0, k0, B, 1, nl, nullptr, s);
+    Str o1{out.d + lw, out.item, lw}, k1{ev->ksout + lw, 2 * lw, lw};
+    k_ew(c, EW_COPY, o1, k1, k1, B, 1, nl, nullptr, s);
+    out.level = lv;
+    out.batch = B;
+    out.scale = a.scale;
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
+
+int ev_add(Eval *ev, const CtB &a, const CtB &b, CtB &out, int sub)
+{
+    he_ctx *c = ev->c;
+    if (a.level != b.level) return helr_fail(c, HE_ELEVEL, "Add: levels %d and %d differ", a.level, b.level);
+    if (!scales_match(a.scale, b.scale)) return helr_fail(c, HE_ESCALE, "Add: scales %.17g and %.17g differ", a.scale, b.scale);
+    out.level = a.level;
+    out.batch = a.batch;
+    out.scale = a.scale;
+    k_ew(c, sub ? EW_SUB : EW_ADD, S(out, c), S(a, c), S(b, c), a.batch, 2, a.level + 1, nullptr, c->stream);
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
+
+int ev_cmul_int(Eval *ev, const CtB &a, int64_t k, double out_scale, CtB &out)
+{
+    he_ctx *c = ev->c;
+    KP kp = shoup_consts(c, a.level + 1, k);
+    out.level = a.level;
+    out.batch = a.batch;
+    out.scale = out_scale;
+    k_ew(c, EW_CMUL, S(out, c), S(a, c), S(a, c), a.batch, 2, a.level + 1, &kp, c->stream);
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
+
+// c0 += k (the constant polynomial k is k in every evaluation)
+int ev_cadd_int(Eval *ev, CtB &a, int64_t k)
+{
+    he_ctx *c = ev->c;
+    KP kp = shoup_consts(c, a.level + 1, k);
+    Str x{a.d, a.item, 0};
+    k_ew(c, EW_CADD, x, x, x, a.batch, 1, a.level + 1, &kp, c->stream);
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
+
+int ev_ptmul(Eval *ev, const CtB &a, const uint64_t *pt, double pt_scale, CtB &out)
+{
+    he_ctx *c = ev->c;
+    out.level = a.level;
+    out.batch = a.batch;
+    out.scale = a.scale * pt_scale;
+    Str p{const_cast<uint64_t *>(pt), 0, 0};
+    k_ew(c, EW_MUL, S(out, c), S(a, c), p, a.batch, 2, a.level + 1, nullptr, c->stream);
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
+
+int ev_moddrop(Eval *ev, const CtB &a, int target, CtB &out)
+{
+    he_ctx *c = ev->c;
+    if (target > a.level || target < 0) return helr_fail(c, HE_ELEVEL, "ModDrop to %d from %d", target, a.level);
+    Str in{a.d, a.item, (size_t)(a.level + 1) * c->n};
+    out.level = target;
+    out.batch = a.batch;
+    out.scale = a.scale;
+    k_ew(c, EW_COPY, S(out, c), in, in, a.batch, 2, target + 1, nullptr, c->stream);
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
+
+int ev_sum_items(Eval *ev, const CtB &a, uint64_t *acc, int accumulate)
+{
+    he_ctx *c = ev->c;
+    const int nl = a.level + 1;
+    size_t nw = 2 * (size_t)nl * c->n;
+    k_sum_items_kernel<<<grid_for(nw), 256, 0, c->stream>>>(acc, a.d, a.item, a.batch, nw, c->logn, nl, c->t.mod, accumulate);
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
+
+// ------------------------------------------------------------------ single-ciphertext C ABI
+static int one_eval(he_ctx *c, int level, Eval *ev) { return ev_init(c, ev, 1, level); }
+
+static CtB view(const he_ct *x) { return CtB{x->d, 1, x->level, x->scale, 0}; }
+
+extern "C" int he_add(he_ctx *c, const he_ct *a, const he_ct *b, he_ct **out)
+{
+    if (!c || !a || !b || !out) return HE_EINVAL;
+    Eval ev{};
+    ev.c = c;
+    he_ct *o = nullptr;
+    HELR_TRY(helr_new_ct(c, a->level, a->scale, &o));
+    CtB ob{o->d, 1, a->level, a->scale, 0};
+    int rc = ev_add(&ev, view(a), view(b), ob, 0);
+    if (rc) { he_ct_free(o); return rc; }
+    *out = o;
+    return HE_OK;
+}
+extern "C" int he_sub(he_ctx *c, const he_ct *a, const he_ct *b, he_ct **out)
+{
+    if (!c || !a || !b || !out) return HE_EINVAL;
+    Eval ev{};
+    ev.c = c;
+    he_ct *o = nullptr;
+    HELR_TRY(helr_new_ct(c, a->level, a->scale, &o));
+    CtB ob{o->d, 1, a->level, a->scale, 0};
+    int rc = ev_add(&ev, view(a), view(b), ob, 1);
+    if (rc) { he_ct_free(o); return rc; }
+    *out = o;
+    return HE_OK;
+}
+
+extern "C" int he_mul(he_ctx *c, const he_ct *a, const he_ct *b, he_ct **out)
+{
+    if (!c || !a || !b || !out) return HE_EINVAL;
+    Eval ev{};
+    HELR_TRY(one_eval(c, a->level, &ev));
+    he_ct *o = nullptr;
+    int rc = helr_new_ct(c, a->level, a->scale * b->scale, &o);
+    if (!rc) {
+        CtB ob{o->d, 1, a->level, 0, 0};
+        rc = ev_mul_relin(&ev, view(a), view(b), ob);
+        if (!rc) o->scale = ob.scale;
+    }
+    ev_free(&ev);
+    if (rc) { if (o) he_ct_free(o); return rc; }
+    *out = o;
+    return HE_OK;
+}
+
+extern "C" int he_rescale(he_ctx *c, const he_ct *a, he_ct **out)
+{
+    if (!c || !a || !out) return HE_EINVAL;
+    if (a->level < 1) return helr_fail(c, HE_ELEVEL, "Rescale: no level left");
+    Eval ev{};
+    HELR_TRY(one_eval(c, a->level, &ev));
+    he_ct *o = nullptr;
+    int rc = helr_new_ct(c, a->level - 1, 0, &o);
+    if (!rc) {
+        CtB ob{o->d, 1, a->level - 1, 0, 0};
+        rc = ev_rescale(&ev, view(a), ob);
+        o->scale = ob.scale;
+    }
+    ev_free(&ev);
+    if (rc) { if (o) he_ct_free(o); return rc; }
+    *out = o;
+    return HE_OK;
+}
+
+extern "C" int he_moddrop(he_ctx *c, const he_ct *a, int level, he_ct **out)
+{
+    if (!c || !a || !out) return HE_EINVAL;
+    if (level < 0 || level > a->level) return helr_fail(c, HE_ELEVEL, "ModDrop to %d from %d", level, a->level);
+    Eval ev{};
+    ev.c = c;
+    he_ct *o = nullptr;
+    HELR_TRY(helr_new_ct(c, level, a->scale, &o));
+    CtB ob{o->d, 1, level, a->scale, 0};
+    int rc = ev_moddrop(&ev, view(a), level, ob);
+    if (rc) { he_ct_free(o); return rc; }
+    *out = o;
+    return HE_OK;
+}
+
+extern "C" int he_rotate(he_ctx *c, const he_ct *a, int64_t r, he_ct **out)
+{
+    if (!c || !a || !out) return HE_EINVAL;
+    Eval ev{};
+    HELR_TRY(one_eval(c, a->level, &ev));
+    he_ct *o = nullptr;
+    int rc = helr_new_ct(c, a->level, a->scale, &o);
+    if (!rc) {
+        CtB ob{o->d, 1, a->level, a->scale, 0};
+        rc = ev_rotate(&ev, view(a), r, ob);
+    }
+    ev_free(&ev);
+    if (rc) { if (o) he_ct_free(o); return rc; }
+    *out = o;
+    return HE_OK;
+}
+
+extern "C" int he_cmul(he_ctx *c, const he_ct *a, double v, double const_scale, he_ct **out)
+{
+    if (!c || !a || !out || !(const_scale > 0)) return HE_EINVAL;
+    double x = v * const_scale;
+    if (!(fabs(x) < 9.2e18)) return helr_fail(c, HE_EINVAL, "cMul constant out of range");
+    Eval ev{};
+    ev.c = c;
+    he_ct *o = nullptr;
+    HELR_TRY(helr_new_ct(c, a->level, a->scale * const_scale, &o));
+    CtB ob{o->d, 1, a->level, 0, 0};
+    int rc = ev_cmul_int(&ev, view(a), round_half_away(x), a->scale * const_scale, ob);
+    if (rc) { he_ct_free(o); return rc; }
+    *out = o;
+    return HE_OK;
+}
+
+extern "C" int he_cadd(he_ctx *c, const he_ct *a, double v, he_ct **out)
+{
+    if (!c || !a || !out) return HE_EINVAL;
+    double x = v * a->scale;
+    if (!(fabs(x) < 9.2e18)) return helr_fail(c, HE_EINVAL, "cAdd constant out of range");
+    Eval ev{};
+    ev.c = c;
+    he_ct *o = nullptr;
+    HELR_TRY(helr_new_ct(c, a->level, a->scale, &o));
+    HELR_CUDA(c, cudaMemcpyAsync(o->d, a->d, sizeof(uint64_t) * 2 * (a->level + 1) * (size_t)c->n,
+                                 cudaMemcpyDeviceToDevice, c->stream));
+    CtB ob{o->d, 1, a->level, a->scale, 0};
+    int rc = ev_cadd_int(&ev, ob, round_half_away(x));
+    if (rc) { he_ct_free(o); return rc; }
+    *out = o;
+    return HE_OK;
+}
+
+extern "C" int he_ptmul(he_ctx *c, const he_ct *a, const he_pt *pt, he_ct **out)
+{
+    if (!c || !a || !pt || !out) return HE_EINVAL;
+    if (pt->level != a->level) return helr_fail(c, HE_ELEVEL, "plaintext level %d vs %d", pt->level, a->level);
+    Eval ev{};
+    ev.c = c;
+    he_ct *o = nullptr;
+    HELR_TRY(helr_new_ct(c, a->level, a->scale * pt->scale, &o));
+    CtB ob{o->d, 1, a->level, 0, 0};
+    int rc = ev_ptmul(&ev, view(a), pt->d, pt->scale, ob);
+    if (rc) { he_ct_free(o); return rc; }
+    *out = o;
+    return HE_OK;
+}

@@ -1,0 +1,618 @@
+// helr_ctx.cu -- context, tables, keys and the C ABI of the scheme operations
+// (Sec. 2.1: Enc, Dec, Add, cAdd, Mul, cMul, rotation, rescaling).
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+#include <math.h>
+#include <algorithm>
+
+#include "helr_internal.cuh"
+
+typedef unsigned __int128 u128;
+
+// ------------------------------------------------------------------ errors / memory
+int helr_fail(he_ctx *c, int code, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err.code = code;
+        c->err.msg = buf;
+    }
+    return code;
+}
+
+int helr_alloc(he_ctx *c, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return helr_fail(c, e == cudaErrorMemoryAllocation ? HE_ENOMEM : HE_ECUDA, "device allocation of %zu bytes: %s",
+                         bytes, cudaGetErrorString(e));
+    }
+    return HE_OK;
+}
+void helr_free(he_ctx *c, void *p)
+{
+    if (p) cudaFreeAsync(p, c->stream);
+}
+
+// ------------------------------------------------------------------ host number theory
+static uint64_t h_mulmod(uint64_t a, uint64_t b, uint64_t q) { return (uint64_t)((u128)a * b % q); }
+static uint64_t h_pow(uint64_t a, uint64_t e, uint64_t q)
+{
+    uint64_t r = 1 % q;
+    a %= q;
+    for (; e; e >>= 1, a = h_mulmod(a, a, q))
+        if (e & 1) r = h_mulmod(r, a, q);
+    return r;
+}
+static uint64_t h_inv(uint64_t a, uint64_t q) { return h_pow(a % q, q - 2, q); }
+static uint64_t h_shoup(uint64_t w, uint64_t q) { return (uint64_t)(((u128)w << 64) / q); }
+
+// Miller-Rabin with the prime bases below 40 (deterministic for 64-bit inputs)
+static bool h_is_prime(uint64_t n)
+{
+    const uint64_t B[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    if (n < 2) return false;
+    for (uint64_t b : B)
+        if (n % b == 0) return n == b;
+    uint64_t d = n - 1;
+    int s = 0;
+    while ((d & 1) == 0) d >>= 1, s++;
+    for (uint64_t b : B) {
+        uint64_t x = h_pow(b, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool comp = true;
+        for (int i = 1; i < s && comp; i++) {
+            x = h_mulmod(x, x, n);
+            if (x == n - 1) comp = false;
+        }
+        if (comp) return false;
+    }
+    return true;
+}
+
+// largest unused prime below 2^bits (and at least 2^(bits-1)) that is 1 mod 2N
+static uint64_t h_next_prime(int bits, uint64_t twon, const std::vector<uint64_t> &used)
+{
+    uint64_t top = (1ull << bits) - 1;
+    uint64_t cand = top - (top % twon) + 1;
+    if (cand > top) cand -= twon;
+    for (; cand >= (1ull << (bits - 1)); cand -= twon) {
+        if (std::find(used.begin(), used.end(), cand) != used.end()) continue;
+        if (h_is_prime(cand)) return cand;
+    }
+    return 0;
+}
+
+static unsigned bitrev(unsigned x, int bits)
+{
+    unsigned r = 0;
+    for (int i = 0; i < bits; i++) r |= ((x >> i) & 1u) << (bits - 1 - i);
+    return r;
+}
+
+int helr_build_cdt(double sigma, uint64_t *out, int cap)
+{
+    int K = (int)ceil(6.0 * sigma);
+    if (K + 1 > cap) return -1;
+    const double two_s2 = 2.0 * sigma * sigma;
+    double z = 0.0;
+    for (int k = 0; k <= K; k++) {
+        double p = exp(-(double)(k * k) / two_s2);
+        z += k ? 2.0 * p : p;
+    }
+    double run = 0.0;
+    for (int k = 0; k < K; k++) {
+        double p = exp(-(double)(k * k) / two_s2);
+        run += k ? 2.0 * p : p;
+        out[k] = (uint64_t)(run / z * 9223372036854775808.0);
+    }
+    out[K] = 1ull << 63;
+    return K + 1;
+}
+
+static void zeta_table(int logn, double *re, double *im)
+{
+    const int n = 1 << logn;
+    for (int k = 0; k < 2 * n; k++) {
+        double th = (M_PI * (double)k) / (double)n;
+        re[k] = cos(th);
+        im[k] = sin(th);
+    }
+}
+
+// ------------------------------------------------------------------ context
+static int upload(he_ctx *c, void **dst, const void *src, size_t bytes)
+{
+    HELR_TRY(helr_alloc(c, dst, bytes));
+    HELR_CUDA(c, cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    return HE_OK;
+}
+
+static int ctx_init(he_ctx *c, const he_params *p)
+{
+    c->logn = p->log_n;
+    c->n = 1 << p->log_n;
+    c->nslots = c->n / 2;
+    c->nq = p->n_q;
+    c->nprime = p->n_q + 1;
+    c->sigma = p->sigma;
+    const uint64_t twon = 2ull * c->n;
+    std::vector<uint64_t> used;
+    uint64_t v = h_next_prime(p->q0_bits, twon, used);
+    if (!v) return helr_fail(c, HE_EINVAL, "no %d-bit prime = 1 mod 2N", p->q0_bits);
+    used.push_back(v);
+    for (int i = 1; i < c->nq; i++) {
+        v = h_next_prime(p->qi_bits, twon, used);
+        if (!v) return helr_fail(c, HE_EINVAL, "not enough %d-bit primes", p->qi_bits);
+        used.push_back(v);
+    }
+    v = h_next_prime(p->p_bits, twon, used);
+    if (!v) return helr_fail(c, HE_EINVAL, "no special prime");
+    used.push_back(v);
+    for (int i = 0; i < c->nprime; i++) {
+        uint64_t q = used[i];
+        c->q[i] = q;
+        int bits = 64 - __builtin_clzll(q);
+        c->modh[i].q = q;
+        c->modh[i].s = (uint32_t)(bits - 2);
+        c->modh[i].mu = (uint64_t)(((u128)1 << (bits - 2 + 64)) / q);
+        c->modh[i].pad = 0;
+        // primitive 2N-th root: first h >= 2 whose (q-1)/2N-th power has order exactly 2N
+        for (uint64_t h = 2;; h++) {
+            uint64_t psi = h_pow(h, (q - 1) / twon, q);
+            if (h_pow(psi, c->n, q) == q - 1) {
+                c->psi[i] = psi;
+                break;
+            }
+        }
+    }
+    c->cdt_len = helr_build_cdt(c->sigma, c->cdt_host, 64);
+    if (c->cdt_len < 0) return helr_fail(c, HE_EINVAL, "sigma too large");
+
+    // transform tables: psi^(bitrev(k)) and psi^-(bitrev(k)), k < N, Shoup pairs
+    const int n = c->n, np = c->nprime;
+    std::vector<uint64_t> tw((size_t)np * n * 2), itw((size_t)np * n * 2), ninv((size_t)np * 2);
+    std::vector<uint64_t> pw(n), ipw(n);
+    for (int i = 0; i < np; i++) {
+        uint64_t q = c->q[i], psi = c->psi[i], ipsi = h_inv(psi, q);
+        pw[0] = 1;
+        ipw[0] = 1;
+        for (int k = 1; k < n; k++) {
+            pw[k] = h_mulmod(pw[k - 1], psi, q);
+            ipw[k] = h_mulmod(ipw[k - 1], ipsi, q);
+        }
+        for (int k = 0; k < n; k++) {
+            unsigned e = bitrev((unsigned)k, c->logn);
+            size_t o = ((size_t)i * n + k) * 2;
+            tw[o] = pw[e];
+            tw[o + 1] = h_shoup(pw[e], q);
+            itw[o] = ipw[e];
+            itw[o + 1] = h_shoup(ipw[e], q);
+        }
+        uint64_t ni = h_inv((uint64_t)n % q, q);
+        ninv[2 * i] = ni;
+        ninv[2 * i + 1] = h_shoup(ni, q);
+    }
+    std::vector<double> zr(2 * n), zi(2 * n), zeta(4 * (size_t)n);
+    zeta_table(c->logn, zr.data(), zi.data());
+    for (int k = 0; k < 2 * n; k++) zeta[2 * k] = zr[k], zeta[2 * k + 1] = zi[k];
+    std::vector<int> sidx(c->nslots);
+    uint64_t g = 1;
+    for (int j = 0; j < c->nslots; j++) {
+        sidx[j] = (int)((g - 1) / 4);
+        g = g * 5 % twon;
+    }
+    // rescale and ModDown inverses
+    const int nq = c->nq;
+    std::vector<uint64_t> qinv((size_t)nq * nq * 2, 0), pinv((size_t)nq * 2);
+    for (int l = 0; l < nq; l++)
+        for (int j = 0; j < l; j++) {
+            uint64_t x = h_inv(c->q[l] % c->q[j], c->q[j]);
+            qinv[((size_t)l * nq + j) * 2] = x;
+            qinv[((size_t)l * nq + j) * 2 + 1] = h_shoup(x, c->q[j]);
+        }
+    for (int j = 0; j < nq; j++) {
+        uint64_t x = h_inv(c->q[nq] % c->q[j], c->q[j]);
+        pinv[2 * j] = x;
+        pinv[2 * j + 1] = h_shoup(x, c->q[j]);
+    }
+    HELR_TRY(upload(c, (void **)&c->t.mod, c->modh, sizeof(ModQ) * np));
+    HELR_TRY(upload(c, (void **)&c->t.tw, tw.data(), tw.size() * 8));
+    HELR_TRY(upload(c, (void **)&c->t.itw, itw.data(), itw.size() * 8));
+    HELR_TRY(upload(c, (void **)&c->t.ninv, ninv.data(), ninv.size() * 8));
+    HELR_TRY(upload(c, (void **)&c->t.zeta, zeta.data(), zeta.size() * 8));
+    HELR_TRY(upload(c, (void **)&c->t.sidx, sidx.data(), sidx.size() * sizeof(int)));
+    HELR_TRY(upload(c, (void **)&c->t.cdt, c->cdt_host, sizeof(uint64_t) * c->cdt_len));
+    HELR_TRY(upload(c, (void **)&c->d_qinv, qinv.data(), qinv.size() * 8));
+    HELR_TRY(upload(c, (void **)&c->d_pinv, pinv.data(), pinv.size() * 8));
+    HELR_TRY(helr_alloc(c, (void **)&c->d_sk, sizeof(uint64_t) * np * n));
+    HELR_TRY(helr_alloc(c, (void **)&c->d_pk, sizeof(uint64_t) * 2 * nq * n));
+    c->h_sk = (int64_t *)calloc(n, sizeof(int64_t));
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HE_OK;
+}
+
+extern "C" int he_ctx_create(const he_params *p, void *stream, he_ctx **out)
+{
+    if (!out) return HE_EINVAL;
+    *out = nullptr;
+    if (!p || p->log_n < HELR_MIN_LOGN || p->log_n > HELR_MAX_LOGN || p->n_q < 2 || p->n_q + 1 > HELR_MAXQ ||
+        p->q0_bits < 30 || p->q0_bits > 60 || p->qi_bits < 30 || p->qi_bits > 60 || p->p_bits < 30 || p->p_bits > 60 ||
+        !(p->sigma > 0.0))
+        return HE_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return HE_ECUDA;
+    }
+    he_ctx *c = new he_ctx();
+    c->stream = (cudaStream_t)stream;
+    // keep freed stream-ordered memory in the pool between iterations
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    int rc = ctx_init(c, p);
+    if (rc != HE_OK) {
+        fprintf(stderr, "he_ctx_create: %s\n", c->err.msg.c_str());
+        he_ctx_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return HE_OK;
+}
+
+extern "C" int he_ctx_destroy(he_ctx *c)
+{
+    if (!c) return HE_EINVAL;
+    cudaStreamSynchronize(c->stream);
+    void *ptrs[] = {c->t.mod, c->t.tw, c->t.itw, c->t.ninv, c->t.zeta, c->t.sidx, c->t.cdt, c->d_qinv, c->d_pinv, c->d_sk, c->d_pk};
+    for (void *p : ptrs) helr_free(c, p);
+    for (auto &k : c->ksk) helr_free(c, k.d);
+    cudaStreamSynchronize(c->stream);
+    free(c->h_sk);
+    delete c;
+    return HE_OK;
+}
+
+extern "C" const char *he_last_error(const he_ctx *c) { return c ? c->err.msg.c_str() : "null context"; }
+
+extern "C" int he_ctx_primes(const he_ctx *c, uint64_t *out, size_t n)
+{
+    if (!c || !out || n < (size_t)c->nprime) return HE_EINVAL;
+    memcpy(out, c->q, sizeof(uint64_t) * c->nprime);
+    return HE_OK;
+}
+
+extern "C" int he_gauss_table(double sigma, uint64_t *out, size_t cap, size_t *len)
+{
+    if (!out || !len || !(sigma > 0)) return HE_EINVAL;
+    int k = helr_build_cdt(sigma, out, (int)std::min(cap, (size_t)1 << 20));
+    if (k < 0) return HE_EINVAL;
+    *len = (size_t)k;
+    return HE_OK;
+}
+
+extern "C" int he_zeta_table(int log_n, double *re, double *im)
+{
+    if (!re || !im || log_n < 1 || log_n > 20) return HE_EINVAL;
+    zeta_table(log_n, re, im);
+    return HE_OK;
+}
+
+extern "C" uint64_t he_galois_elt(const he_ctx *c, int64_t r)
+{
+    const int64_t ns = c->nslots;
+    int64_t rr = ((r % ns) + ns) % ns;
+    return h_pow(5, (uint64_t)rr, 2ull * c->n);
+}
+
+// ------------------------------------------------------------------ keys
+const uint64_t *helr_find_key(const he_ctx *c, uint64_t gal)
+{
+    for (auto &k : c->ksk)
+        if (k.gal == gal) return k.d;
+    return nullptr;
+}
+
+int helr_add_key(he_ctx *c, uint64_t gal)
+{
+    if (helr_find_key(c, gal)) return HE_OK;
+    const int n = c->n, np = c->nprime, nq = c->nq;
+    const size_t lw = (size_t)np * n;
+    uint64_t *sp = nullptr, *key = nullptr;
+    HELR_TRY(helr_alloc(c, (void **)&sp, sizeof(uint64_t) * lw));
+    HELR_TRY(helr_alloc(c, (void **)&key, sizeof(uint64_t) * (size_t)nq * 2 * lw));
+    if (gal == 0) HELR_TRY(helr_square_dev(c, sp, c->d_sk, np));
+    else k_automorph(c, sp, c->d_sk, np, gal, c->stream);
+    HELR_TRY(helr_make_ksk(c, gal, sp, key));
+    HELR_CUDA(c, cudaGetLastError());
+    helr_free(c, sp);
+    c->ksk.push_back({gal, key});
+    return HE_OK;
+}
+
+extern "C" int he_keygen(he_ctx *c, uint64_t seed, const int64_t *rot, size_t nrot)
+{
+    if (!c || (nrot && !rot)) return HE_EINVAL;
+    if (!c->have_keys || c->key_seed != seed) {
+        for (auto &k : c->ksk) helr_free(c, k.d);
+        c->ksk.clear();
+        HELR_TRY(helr_keygen_base(c, seed));
+        HELR_TRY(helr_add_key(c, 0));
+    }
+    for (size_t i = 0; i < nrot; i++) HELR_TRY(helr_add_key(c, he_galois_elt(c, rot[i])));
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HE_OK;
+}
+
+// ------------------------------------------------------------------ handles
+int helr_new_ct(he_ctx *c, int level, double scale, he_ct **out)
+{
+    he_ct *ct = new he_ct();
+    ct->ctx = c;
+    ct->level = level;
+    ct->scale = scale;
+    int rc = helr_alloc(c, (void **)&ct->d, sizeof(uint64_t) * 2 * (level + 1) * (size_t)c->n);
+    if (rc) {
+        delete ct;
+        return rc;
+    }
+    *out = ct;
+    return HE_OK;
+}
+static int new_pt(he_ctx *c, int level, double scale, he_pt **out)
+{
+    he_pt *pt = new he_pt();
+    pt->ctx = c;
+    pt->level = level;
+    pt->scale = scale;
+    int rc = helr_alloc(c, (void **)&pt->d, sizeof(uint64_t) * (level + 1) * (size_t)c->n);
+    if (rc) {
+        delete pt;
+        return rc;
+    }
+    *out = pt;
+    return HE_OK;
+}
+
+extern "C" int he_ct_free(he_ct *ct)
+{
+    if (!ct) return HE_EINVAL;
+    helr_free(ct->ctx, ct->d);
+    delete ct;
+    return HE_OK;
+}
+extern "C" int he_pt_free(he_pt *pt)
+{
+    if (!pt) return HE_EINVAL;
+    helr_free(pt->ctx, pt->d);
+    delete pt;
+    return HE_OK;
+}
+extern "C" int he_ct_level(const he_ct *ct, int *level, double *scale)
+{
+    if (!ct) return HE_EINVAL;
+    if (level) *level = ct->level;
+    if (scale) *scale = ct->scale;
+    return HE_OK;
+}
+extern "C" int he_set_scale(he_ct *ct, double scale)
+{
+    if (!ct || !(scale > 0)) return HE_EINVAL;
+    ct->scale = scale;
+    return HE_OK;
+}
+
+extern "C" int he_encode(he_ctx *c, const double *re, const double *im, size_t nslots, int level, double scale, he_pt **out)
+{
+    if (!c || !out || !re || nslots > (size_t)c->nslots || level < 0 || level >= c->nq || !(scale > 0)) return HE_EINVAL;
+    *out = nullptr;
+    double *d = nullptr;
+    HELR_TRY(helr_alloc(c, (void **)&d, sizeof(double) * 2 * c->nslots));
+    HELR_CUDA(c, cudaMemsetAsync(d, 0, sizeof(double) * 2 * c->nslots, c->stream));
+    HELR_CUDA(c, cudaMemcpyAsync(d, re, sizeof(double) * nslots, cudaMemcpyHostToDevice, c->stream));
+    if (im) HELR_CUDA(c, cudaMemcpyAsync(d + c->nslots, im, sizeof(double) * nslots, cudaMemcpyHostToDevice, c->stream));
+    he_pt *pt = nullptr;
+    HELR_TRY(new_pt(c, level, scale, &pt));
+    int rc = helr_encode_dev(c, d, d + c->nslots, 1, 0, level, scale, pt->d, 0);
+    helr_free(c, d);
+    if (rc) {
+        he_pt_free(pt);
+        return rc;
+    }
+    *out = pt;
+    return HE_OK;
+}
+
+extern "C" int he_decode(he_ctx *c, const he_pt *pt, double *re, double *im, size_t nslots)
+{
+    if (!c || !pt || !re || nslots > (size_t)c->nslots) return HE_EINVAL;
+    double *d = nullptr;
+    HELR_TRY(helr_alloc(c, (void **)&d, sizeof(double) * 2 * c->nslots));
+    HELR_TRY(helr_decode_dev(c, pt->d, pt->scale, d, d + c->nslots));
+    HELR_CUDA(c, cudaMemcpyAsync(re, d, sizeof(double) * nslots, cudaMemcpyDeviceToHost, c->stream));
+    if (im) HELR_CUDA(c, cudaMemcpyAsync(im, d + c->nslots, sizeof(double) * nslots, cudaMemcpyDeviceToHost, c->stream));
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    helr_free(c, d);
+    return HE_OK;
+}
+
+extern "C" int he_encrypt(he_ctx *c, const he_pt *pt, uint64_t seed, he_ct **out)
+{
+    if (!c || !pt || !out) return HE_EINVAL;
+    he_ct *ct = nullptr;
+    HELR_TRY(helr_new_ct(c, pt->level, pt->scale, &ct));
+    int rc = helr_encrypt_dev(c, pt->d, pt->level, seed, ct->d);
+    if (rc) {
+        he_ct_free(ct);
+        return rc;
+    }
+    *out = ct;
+    return HE_OK;
+}
+
+extern "C" int he_decrypt(he_ctx *c, const he_ct *ct, he_pt **out)
+{
+    if (!c || !ct || !out) return HE_EINVAL;
+    he_pt *pt = nullptr;
+    HELR_TRY(new_pt(c, ct->level, ct->scale, &pt));
+    int rc = helr_decrypt_dev(c, ct->d, ct->level, pt->d);
+    if (rc) {
+        he_pt_free(pt);
+        return rc;
+    }
+    *out = pt;
+    return HE_OK;
+}
+
+extern "C" int he_ct_export(const he_ct *ct, uint64_t *words, size_t nw, int *level, double *scale)
+{
+    if (!ct || !words) return HE_EINVAL;
+    he_ctx *c = ct->ctx;
+    const size_t need = 2 * (size_t)(ct->level + 1) * c->n;
+    if (nw < need) return helr_fail(c, HE_EINVAL, "export buffer too small");
+    uint64_t *tmp = nullptr;
+    HELR_TRY(helr_alloc(c, (void **)&tmp, need * 8));
+    LimbMap lm = limbmap_ct(ct->level);
+    HELR_TRY(helr_ntt_inv_oop(c, ct->d, tmp, 2 * (size_t)(ct->level + 1), lm, c->stream));
+    HELR_CUDA(c, cudaMemcpyAsync(words, tmp, need * 8, cudaMemcpyDeviceToHost, c->stream));
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    helr_free(c, tmp);
+    if (level) *level = ct->level;
+    if (scale) *scale = ct->scale;
+    return HE_OK;
+}
+
+extern "C" int he_pt_export(const he_pt *pt, uint64_t *words, size_t nw, int *level, double *scale)
+{
+    if (!pt || !words) return HE_EINVAL;
+    he_ctx *c = pt->ctx;
+    const size_t need = (size_t)(pt->level + 1) * c->n;
+    if (nw < need) return helr_fail(c, HE_EINVAL, "export buffer too small");
+    uint64_t *tmp = nullptr;
+    HELR_TRY(helr_alloc(c, (void **)&tmp, need * 8));
+    HELR_TRY(helr_ntt_inv_oop(c, pt->d, tmp, pt->level + 1, limbmap_ct(pt->level), c->stream));
+    HELR_CUDA(c, cudaMemcpyAsync(words, tmp, need * 8, cudaMemcpyDeviceToHost, c->stream));
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    helr_free(c, tmp);
+    if (level) *level = pt->level;
+    if (scale) *scale = pt->scale;
+    return HE_OK;
+}
+
+extern "C" int he_ct_import(he_ctx *c, const uint64_t *words, size_t nw, int level, double scale, he_ct **out)
+{
+    if (!c || !words || !out || level < 0 || level >= c->nq) return HE_EINVAL;
+    const size_t need = 2 * (size_t)(level + 1) * c->n;
+    if (nw < need) return helr_fail(c, HE_EINVAL, "import buffer too small");
+    he_ct *ct = nullptr;
+    HELR_TRY(helr_new_ct(c, level, scale, &ct));
+    HELR_CUDA(c, cudaMemcpyAsync(ct->d, words, need * 8, cudaMemcpyHostToDevice, c->stream));
+    HELR_TRY(helr_ntt_fwd(c, ct->d, 2 * (size_t)(level + 1), limbmap_ct(level), c->stream));
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    *out = ct;
+    return HE_OK;
+}
+
+// ------------------------------------------------------------------ key switching
+// d_in: [batch][nl][N] evaluation form; d_out: [batch][2][nl][N].
+int helr_keyswitch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, int level, const uint64_t *key,
+                   KsScratch *ws)
+{
+    const int nl = level + 1, nt = nl + 1;
+    const size_t N = c->n;
+    const size_t in_items = (size_t)batch * nl;
+    KsScratch local;
+    if (!ws) {
+        HELR_TRY(helr_ks_scratch_alloc(c, batch, level, &local));
+        ws = &local;
+    }
+    cudaStream_t s = c->stream;
+    // 1. coefficient form of every limb
+    HELR_TRY(helr_ntt_inv_oop(c, d_in, ws->dcoef, in_items, limbmap_ct(level), s));
+    // 2. ModUp: each digit lifted to all nl + 1 moduli, then transformed
+    k_modup(c, ws->dcoef, d_in, ws->ext, batch, level, nl * N, (size_t)nl * nt * N, s);
+    LimbMap lt;
+    lt.period = nt;
+    for (int t = 0; t < nl; t++) lt.p[t] = (unsigned char)t;
+    lt.p[nl] = (unsigned char)c->nq;
+    HELR_TRY(helr_ntt_fwd(c, ws->ext, (size_t)batch * nl * nt, lt, s));
+    // 3. inner product with the key digits
+    k_ks_inner(c, ws->ext, key, ws->acc, batch, level, (size_t)nl * nt * N, 2 * (size_t)nt * N, s);
+    // 4. ModDown: subtract the centred P-part and divide by P
+    HELR_CUDA(c, cudaMemcpy2DAsync(ws->pl, N * 8, ws->acc + (size_t)nl * N, (size_t)nt * N * 8, N * 8, (size_t)batch * 2,
+                                   cudaMemcpyDeviceToDevice, s));
+    HELR_TRY(helr_ntt_inv(c, ws->pl, (size_t)batch * 2, limbmap_single(c->nq), s));
+    k_lift(c, ws->pl, ws->lift, batch * 2, c->nq, N, limbmap_ct(level), (size_t)nl * N, s);
+    HELR_TRY(helr_ntt_fwd(c, ws->lift, (size_t)batch * 2 * nl, limbmap_ct(level), s));
+    k_rescale_combine(c, d_out, ws->acc, ws->lift, batch * 2, nl, (size_t)nt * N, (size_t)nl * N, (size_t)nl * N, c->d_pinv, s);
+    HELR_CUDA(c, cudaGetLastError());
+    if (ws == &local) helr_ks_scratch_free(c, &local);
+    return HE_OK;
+}
+
+int helr_ks_scratch_alloc(he_ctx *c, int batch, int level, KsScratch *ws)
+{
+    const int nl = level + 1, nt = nl + 1;
+    const size_t N = c->n;
+    size_t words = (size_t)batch * (nl * N + (size_t)nl * nt * N + 2 * nt * N + 2 * N + 2 * (size_t)nl * N);
+    uint64_t *base = nullptr;
+    HELR_TRY(helr_alloc(c, (void **)&base, words * 8));
+    ws->base = base;
+    ws->dcoef = base;
+    ws->ext = ws->dcoef + (size_t)batch * nl * N;
+    ws->acc = ws->ext + (size_t)batch * nl * nt * N;
+    ws->pl = ws->acc + (size_t)batch * 2 * nt * N;
+    ws->lift = ws->pl + (size_t)batch * 2 * N;
+    ws->batch = batch;
+    ws->level = level;
+    return HE_OK;
+}
+void helr_ks_scratch_free(he_ctx *c, KsScratch *ws)
+{
+    helr_free(c, ws->base);
+    ws->base = nullptr;
+}
+
+extern "C" int he_keyswitch_batch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, int level, uint64_t gal)
+{
+    if (!c || !d_in || !d_out || batch <= 0 || level < 0 || level >= c->nq) return HE_EINVAL;
+    const uint64_t *key = helr_find_key(c, gal);
+    if (!key) return helr_fail(c, HE_EKEY, "no key-switching key for galois element %llu", (unsigned long long)gal);
+    return helr_keyswitch(c, d_in, d_out, batch, level, key, nullptr);
+}
+
+static int limbmap_from(const he_ctx *c, const int *prime_of, int period, LimbMap *m)
+{
+    if (!prime_of || period <= 0 || period > HELR_MAXQ + 1) return HE_EINVAL;
+    m->period = period;
+    for (int i = 0; i < period; i++) {
+        if (prime_of[i] < 0 || prime_of[i] >= c->nprime) return HE_EINVAL;
+        m->p[i] = (unsigned char)prime_of[i];
+    }
+    return HE_OK;
+}
+extern "C" int he_ntt_forward(he_ctx *c, uint64_t *d, size_t nlimbs, const int *prime_of, int period)
+{
+    LimbMap m;
+    if (!c || !d || limbmap_from(c, prime_of, period, &m)) return HE_EINVAL;
+    return helr_ntt_fwd(c, d, nlimbs, m, c->stream);
+}
+extern "C" int he_ntt_inverse(he_ctx *c, uint64_t *d, size_t nlimbs, const int *prime_of, int period)
+{
+    LimbMap m;
+    if (!c || !d || limbmap_from(c, prime_of, period, &m)) return HE_EINVAL;
+    return helr_ntt_inv(c, d, nlimbs, m, c->stream);
+}

@@ -1,0 +1,284 @@
+// helr_internal.cuh -- shared declarations of the GB300 library (not installed).
+//
+// Ciphertexts live on the device in evaluation (NTT) form, limb-major:
+// [poly][limb][N] uint64 words, limb j reduced modulo q_j.  All ciphertext
+// arithmetic is exact modular integer arithmetic on 64-bit words with primes
+// below 2^60.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <string>
+#include <vector>
+#include <map>
+#include <memory>
+
+#include "../../include/he_lr.h"
+
+#define HELR_MAXQ 40      // ciphertext primes + special prime
+#define HELR_MAX_LOGN 16
+#define HELR_MIN_LOGN 10
+
+// ------------------------------------------------------------------ modular arithmetic
+// Per-prime constants.  Barrett: s = bits(q) - 2, mu = floor(2^(s+64) / q) < 2^63.
+struct ModQ {
+    uint64_t q;
+    uint64_t mu;
+    uint32_t s;
+    uint32_t pad;
+};
+
+__host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b)
+{
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+// x mod q for x = hi*2^64 + lo < q^2 (or any x < 2^64 with hi = 0); result in [0, q).
+__host__ __device__ __forceinline__ uint64_t barrett_reduce(uint64_t hi, uint64_t lo, const ModQ m)
+{
+    uint64_t y = m.s ? ((hi << (64 - m.s)) | (lo >> m.s)) : lo;
+    uint64_t qh = mulhi64(y, m.mu);
+    uint64_t r = lo - qh * m.q;
+    if (r >= m.q) r -= m.q;
+    if (r >= m.q) r -= m.q;
+    return r;
+}
+__host__ __device__ __forceinline__ uint64_t mulmod(uint64_t a, uint64_t b, const ModQ m)
+{
+    return barrett_reduce(mulhi64(a, b), a * b, m);
+}
+__host__ __device__ __forceinline__ uint64_t reduce64(uint64_t x, const ModQ m) { return barrett_reduce(0, x, m); }
+__host__ __device__ __forceinline__ uint64_t addmod(uint64_t a, uint64_t b, uint64_t q)
+{
+    uint64_t s = a + b;
+    return s >= q ? s - q : s;
+}
+__host__ __device__ __forceinline__ uint64_t submod(uint64_t a, uint64_t b, uint64_t q)
+{
+    return a >= b ? a - b : a + (q - b);
+}
+// Shoup product with a fixed operand w < q and wp = floor(w 2^64 / q):
+// returns w*y mod q up to one q, i.e. a value in [0, 2q), for any 64-bit y.
+__host__ __device__ __forceinline__ uint64_t shoup_lazy(uint64_t y, uint64_t w, uint64_t wp, uint64_t q)
+{
+    return w * y - mulhi64(wp, y) * q;
+}
+__host__ __device__ __forceinline__ uint64_t shoup(uint64_t y, uint64_t w, uint64_t wp, uint64_t q)
+{
+    uint64_t r = shoup_lazy(y, w, wp, q);
+    return r >= q ? r - q : r;
+}
+// centred representative of x in [0, qi) reduced into [0, qt)
+__host__ __device__ __forceinline__ uint64_t lift_centered(uint64_t x, uint64_t qi, const ModQ t)
+{
+    if (x > (qi >> 1)) {
+        uint64_t neg = reduce64(qi - x, t);
+        return neg ? t.q - neg : 0;
+    }
+    return reduce64(x, t);
+}
+
+// ------------------------------------------------------------------ limb maps
+// Limb i of a batch uses prime index p[i % period] (index nq means the special prime P).
+struct LimbMap {
+    int period;
+    unsigned char p[HELR_MAXQ + 2];
+};
+
+// ------------------------------------------------------------------ error state
+struct HeError {
+    int code;
+    std::string msg;
+};
+
+// ------------------------------------------------------------------ device tables per prime
+struct DevTables {
+    ModQ *mod;          // [nprime]
+    uint64_t *tw;       // [nprime][N][2]  forward (psi_rev, shoup)
+    uint64_t *itw;      // [nprime][N][2]  inverse (psi^-1 rev, shoup)
+    uint64_t *ninv;     // [nprime][2]     N^-1 and its Shoup companion
+    double *zeta;       // [2N][2]         exp(i pi k / N)
+    int *sidx;          // [N/2]           slot j -> DFT index
+    uint64_t *cdt;      // [cdt_len]
+};
+
+struct KeySwitchKey {
+    uint64_t gal;       // 0 = relinearisation
+    uint64_t *d;        // [nq digits][2][nq+1 limbs][N], NTT form
+};
+
+struct he_ctx {
+    int logn, n, nslots, nq;       // nq ciphertext primes q_0..q_{nq-1}
+    int nprime;                    // nq + 1 (index nq = P)
+    uint64_t q[HELR_MAXQ + 1];
+    ModQ modh[HELR_MAXQ + 1];
+    uint64_t psi[HELR_MAXQ + 1];
+    double sigma;
+    int cdt_len;
+    uint64_t cdt_host[64];
+    cudaStream_t stream;
+    DevTables t;
+    // inverse constants for rescale / ModDown (Shoup pairs), host copies
+    // qinv[l][j] = q_l^-1 mod q_j, pinv[j] = P^-1 mod q_j
+    uint64_t *d_qinv;              // [nq][nq][2]
+    uint64_t *d_pinv;              // [nq][2]
+    // keys
+    int have_keys;
+    uint64_t key_seed;
+    int64_t *h_sk;                 // host copy of the ternary secret (client side)
+    uint64_t *d_sk;                // [nprime][N] NTT form
+    uint64_t *d_pk;                // [2][nq][N] NTT form
+    std::vector<KeySwitchKey> ksk;
+    HeError err;
+};
+
+struct he_ct {
+    he_ctx *ctx;
+    int level;
+    double scale;
+    uint64_t *d;    // [2][level+1][N]
+};
+struct he_pt {
+    he_ctx *ctx;
+    int level;
+    double scale;
+    uint64_t *d;    // [level+1][N] NTT form
+};
+
+// ------------------------------------------------------------------ helpers (host)
+int helr_fail(he_ctx *c, int code, const char *fmt, ...);
+#define HELR_CUDA(c, call)                                                              \
+    do {                                                                                \
+        cudaError_t e__ = (call);                                                       \
+        if (e__ != cudaSuccess)                                                         \
+            return helr_fail((c), HE_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call,  \
+                             cudaGetErrorString(e__));                                  \
+    } while (0)
+#define HELR_TRY(x)                      \
+    do {                                 \
+        int rc__ = (x);                  \
+        if (rc__ != HE_OK) return rc__;  \
+    } while (0)
+
+int helr_alloc(he_ctx *c, void **p, size_t bytes);
+void helr_free(he_ctx *c, void *p);
+
+static inline LimbMap limbmap_ct(int level)
+{
+    LimbMap m;
+    m.period = level + 1;
+    for (int j = 0; j <= level; j++) m.p[j] = (unsigned char)j;
+    return m;
+}
+static inline LimbMap limbmap_single(int prime)
+{
+    LimbMap m;
+    m.period = 1;
+    m.p[0] = (unsigned char)prime;
+    return m;
+}
+
+// ------------------------------------------------------------------ kernels (launchers)
+// NTT over a batch of limbs: data [nlimbs][N]; values in [0, q) in and out.
+int helr_ntt_fwd(he_ctx *c, uint64_t *data, size_t nlimbs, const LimbMap &m, cudaStream_t s);
+int helr_ntt_inv(he_ctx *c, uint64_t *data, size_t nlimbs, const LimbMap &m, cudaStream_t s);
+// out-of-place variants (in may equal out)
+int helr_ntt_fwd_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s);
+int helr_ntt_inv_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s);
+
+// elementwise / structural kernels (ops.cu)
+void k_add(he_ctx *c, uint64_t *out, const uint64_t *a, const uint64_t *b, size_t nlimbs, const LimbMap &m, int sub, cudaStream_t s);
+void k_mul(he_ctx *c, uint64_t *out, const uint64_t *a, const uint64_t *b, size_t nlimbs, const LimbMap &m, cudaStream_t s);
+void k_tensor(he_ctx *c, const uint64_t *a, const uint64_t *b, uint64_t *d, int batch, int level,
+              size_t a_stride, size_t b_stride, size_t d_stride, size_t d_poly_stride, cudaStream_t s);
+void k_cmul_const(he_ctx *c, uint64_t *out, const uint64_t *in, const uint64_t *kpairs_dev,
+                  size_t nlimbs, int period, cudaStream_t s);
+void k_cadd_const(he_ctx *c, uint64_t *ct0, const uint64_t *kvals_dev, int batch, int level,
+                  size_t stride, cudaStream_t s);
+void k_automorph(he_ctx *c, uint64_t *out, const uint64_t *in, size_t nlimbs, uint64_t gal, cudaStream_t s);
+void k_lift(he_ctx *c, const uint64_t *in, uint64_t *out, int batch, int src_prime, size_t in_stride,
+            const LimbMap &dst, size_t out_stride, cudaStream_t s);
+void k_rescale_combine(he_ctx *c, uint64_t *out, const uint64_t *in, const uint64_t *corr, int batch,
+                       int level, size_t in_stride, size_t corr_stride, size_t out_stride,
+                       const uint64_t *inv_pairs, cudaStream_t s);
+void k_modup(he_ctx *c, const uint64_t *dcoef, const uint64_t *dntt, uint64_t *ext, int batch, int level,
+             size_t in_stride, size_t ext_stride, cudaStream_t s);
+void k_ks_inner(he_ctx *c, const uint64_t *ext, const uint64_t *key, uint64_t *acc, int batch, int level,
+                size_t ext_stride, size_t acc_stride, cudaStream_t s);
+
+// strided elementwise kernel: element (item b, poly p, limb j, k) of X lives at
+// X.p + b * X.item + p * X.poly + j * N + k (limb j reduced modulo q_j)
+struct Str {
+    uint64_t *p;
+    size_t item, poly;
+};
+enum { EW_ADD = 0, EW_SUB = 1, EW_MUL = 2, EW_CMUL = 3, EW_COPY = 4, EW_NEG = 5, EW_CADD = 6, EW_SUBMUL = 7 };
+// per-limb constants passed by value: Shoup pairs (w, w') for EW_CMUL / EW_SUBMUL, w alone for EW_CADD
+struct KP {
+    uint64_t w[HELR_MAXQ + 1][2];
+};
+void k_ew(he_ctx *c, int op, Str out, Str a, Str b, int batch, int npoly, int nl, const KP *kp, cudaStream_t s);
+void k_automorph_items(he_ctx *c, uint64_t *out, size_t out_item, const uint64_t *in, size_t in_item, int batch, int nl,
+                       uint64_t gal, cudaStream_t s);
+
+struct KsScratch {
+    uint64_t *base, *dcoef, *ext, *acc, *pl, *lift;
+    int batch, level;
+};
+int helr_ks_scratch_alloc(he_ctx *c, int batch, int level, KsScratch *ws);
+void helr_ks_scratch_free(he_ctx *c, KsScratch *ws);
+int helr_keyswitch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, int level, const uint64_t *key,
+                   KsScratch *ws);
+const uint64_t *helr_find_key(const he_ctx *c, uint64_t gal);
+int helr_add_key(he_ctx *c, uint64_t gal);
+int helr_new_ct(he_ctx *c, int level, double scale, he_ct **out);
+
+int helr_build_cdt(double sigma, uint64_t *out, int cap);
+int helr_sample(he_ctx *c, uint64_t *out, size_t nlimbs, const LimbMap &lm, uint64_t seed, uint64_t stream, int kind);
+int helr_encode_dev(he_ctx *c, const double *d_re, const double *d_im, int batch, size_t in_stride, int level,
+                    double scale, uint64_t *d_out, size_t out_stride);
+int helr_decode_dev(he_ctx *c, const uint64_t *d_pt, double scale, double *d_re, double *d_im);
+int helr_encrypt_dev(he_ctx *c, const uint64_t *d_pt, int level, uint64_t seed, uint64_t *d_ct);
+int helr_decrypt_dev(he_ctx *c, const uint64_t *d_ct, int level, uint64_t *d_pt);
+int helr_keygen_base(he_ctx *c, uint64_t seed);
+int helr_make_ksk(he_ctx *c, uint64_t gal, const uint64_t *sprime, uint64_t *out);
+int helr_square_dev(he_ctx *c, uint64_t *out, const uint64_t *in, size_t nlimbs);
+
+// ------------------------------------------------------------------ batched evaluator (eval.cu)
+// A batch of ciphertexts: item i at d + i * item, polynomials [2][level+1][N];
+// item == 0 broadcasts one ciphertext to every item.
+struct CtB {
+    uint64_t *d;
+    int batch;
+    int level;
+    double scale;
+    size_t item;
+};
+struct Eval {
+    he_ctx *c;
+    int maxb, maxlevel;
+    KsScratch ks;
+    uint64_t *tens;   // [3][maxb][nl][N]
+    uint64_t *ksout;  // [maxb][2][nl][N]
+    uint64_t *rot1;   // [maxb][nl][N]
+    uint64_t *last;   // [maxb][2][N]
+    uint64_t *lift;   // [maxb][2][nl][N]
+    uint64_t keyswitches;
+};
+int ev_init(he_ctx *c, Eval *ev, int maxb, int maxlevel);
+void ev_free(Eval *ev);
+int ev_mul_relin(Eval *ev, const CtB &a, const CtB &b, CtB &out);
+int ev_rescale(Eval *ev, const CtB &a, CtB &out);
+int ev_rotate(Eval *ev, const CtB &a, int64_t r, CtB &out);
+int ev_add(Eval *ev, const CtB &a, const CtB &b, CtB &out, int sub);
+int ev_cmul_int(Eval *ev, const CtB &a, int64_t k, double out_scale, CtB &out);
+int ev_cadd_int(Eval *ev, CtB &a, int64_t k);
+int ev_ptmul(Eval *ev, const CtB &a, const uint64_t *pt, double pt_scale, CtB &out);
+int ev_moddrop(Eval *ev, const CtB &a, int target, CtB &out);
+int ev_sum_items(Eval *ev, const CtB &a, uint64_t *acc, int accumulate);
+bool scales_match(double a, double b);
+int64_t round_half_away(double x);

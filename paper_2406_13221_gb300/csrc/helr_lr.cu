@@ -1,0 +1,647 @@
+// helr_lr.cu -- encrypted logistic-regression training with quadratic-gradient
+// NAG (arXiv 2406.13221): client precompute (Sec. 4.3 Steps 1-3), the encrypted
+// iteration (Steps 4-6: gradient, quadratic gradient, NAG update of
+// Algorithm 1) and the refresh between iterations (Step 7).
+//
+// Circuit per data block Z_i (all at the top level L, scale Delta):
+//  1  t  = Rescale(Relin(Z_i (x) W))                   z_rc w_c
+//  2  t += Rot(t, 2^k), k < log2 g                     row sums into column 0
+//  3  t  = Rescale(t * M)                              mask with ones in column 0
+//  4  t += Rot(t, -2^k), k < log2 g                    ip_r in every column
+//  5  s  = alpha (1 - g(ip)): ip^2 and (k3 ip) in parallel, then their product,
+//          plus k1 ip and the constant k0            sigmoid polynomial (Sec. 4.1)
+//  6  grad_i = Rescale(Relin(s (x) Z_i))               s_r z_rc
+// then once:
+//  7  acc = sum_i grad_i; acc += Rot(acc, g 2^k), k < log2 m   column sums
+//  8  nG = Rescale(Relin(acc (x) B))                   n Bbar_c g_c (quadratic gradient)
+//  9  V' = W + nG/n,  W' = (1 - eta) V' + eta V        Algorithm 1 update
+// The multiplier on G is alpha = F2(t) (the learning rate 2 - (t/81)^2.5 of the
+// experiments); Bbar and g are unnormalised sums, n Bbar is encrypted and 1/n
+// is a public scalar.
+#include <math.h>
+#include <string.h>
+#include <thread>
+#include <chrono>
+#include <algorithm>
+#include "helr_internal.cuh"
+
+static const double G8[3] = {0.5, 0.15, -0.0015};
+static const double G16[3] = {0.5, 0.0843, -0.0002};
+static const double BBAR_EPS = 1e-8;
+
+static uint64_t obj_seed(uint64_t base, uint64_t kind, uint64_t index) { return base + (kind << 48) + index; }
+
+// ------------------------------------------------------------------ client precompute
+// Bbar_c = 1 / (eps + 1/4 sum_k |(Z^T Z)_ck|) over rows [r0, r0 + rows) of Z = y [1 | X]
+static void bbar_rows(const double *X, const double *y, size_t f, size_t r0, size_t rows, size_t g, double *out)
+{
+    const size_t f1 = f + 1;
+    std::vector<double> H(f1 * f1, 0.0), z(f1);
+    for (size_t r = r0; r < r0 + rows; r++) {
+        z[0] = y[r];
+        for (size_t c = 0; c < f; c++) z[c + 1] = y[r] * X[r * f + c];
+        for (size_t a = 0; a < f1; a++) {
+            double za = z[a];
+            double *h = &H[a * f1];
+            for (size_t b = a; b < f1; b++) h[b] += za * z[b];
+        }
+    }
+    for (size_t a = 0; a < g; a++) out[a] = 0.0;
+    for (size_t a = 0; a < f1; a++) {
+        double s = 0.0;
+        for (size_t b = 0; b < f1; b++) s += fabs(a <= b ? H[a * f1 + b] : H[b * f1 + a]);
+        out[a] = 1.0 / (BBAR_EPS + 0.25 * s);
+    }
+}
+
+extern "C" int he_lr_bbar(const double *X, const double *y, size_t n, size_t f, size_t row0, size_t rows, size_t g,
+                          double *out)
+{
+    if (!X || !y || !out || g < f + 1 || row0 + rows > n) return HE_EINVAL;
+    bbar_rows(X, y, f, row0, rows, g, out);
+    return HE_OK;
+}
+
+// ------------------------------------------------------------------ job
+struct he_lr_job {
+    he_ctx *c;
+    int mode;
+    double poly[3];
+    size_t n, f;
+    int g, m, lg, lm, L;
+    int nblocks, bpb, nbatch;
+    size_t batch_rows;
+    double scale0;
+    uint64_t enc_seed;
+    size_t ctw;                 // words per top-level ciphertext
+    uint64_t *Z;                // [nblocks][2][L+1][N]
+    std::vector<he_ct *> B;     // Enc(n Bbar) per mini-batch, or one for the full batch
+    std::vector<double> inv_n;
+    he_ct *W, *V;
+    uint64_t *mask;             // plaintext M at level L-1, scale q_(L-1), evaluation form
+    double mask_scale;
+    Eval ev;
+    int chunk;
+    uint64_t *buf;              // work ciphertexts
+    uint64_t *T0, *T1, *T2, *T3, *T4, *acc;
+    he_lr_stats st;
+    double upd_total, iter_total;
+    int iters_done;
+};
+
+static double f2(const he_lr_sched &s, double t) { return s.max - (s.max - s.min) * pow(t / s.T, s.power); }
+
+// Algorithm 1: eta_t from the alpha recurrence started at alpha_0 = 0.01
+static double nag_eta(int t)
+{
+    double a0 = 0.01, a1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * a0 * a0)), eta = 0;
+    for (int k = 0; k <= t; k++) {
+        eta = (1.0 - a0) / a1;
+        a0 = a1;
+        a1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * a0 * a0));
+    }
+    return eta;
+}
+
+static int encrypt_slots(he_ctx *c, const double *h_slots, int count, int level, double scale, uint64_t seed_base_kind,
+                         uint64_t enc_seed, int first_index, uint64_t *dst, size_t dst_item)
+{
+    const size_t ns = c->nslots, N = c->n, nl = level + 1;
+    const int step = 32;
+    double *d = nullptr;
+    uint64_t *pt = nullptr;
+    HELR_TRY(helr_alloc(c, (void **)&d, sizeof(double) * ns * step));
+    HELR_TRY(helr_alloc(c, (void **)&pt, sizeof(uint64_t) * nl * N * step));
+    for (int b0 = 0; b0 < count; b0 += step) {
+        int cnt = std::min(step, count - b0);
+        HELR_CUDA(c, cudaMemcpyAsync(d, h_slots + (size_t)b0 * ns, sizeof(double) * ns * cnt, cudaMemcpyHostToDevice, c->stream));
+        HELR_TRY(helr_encode_dev(c, d, nullptr, cnt, ns, level, scale, pt, nl * N));
+        for (int b = 0; b < cnt; b++)
+            HELR_TRY(helr_encrypt_dev(c, pt + (size_t)b * nl * N, level, obj_seed(enc_seed, seed_base_kind, first_index + b0 + b),
+                                      dst + (size_t)(b0 + b) * dst_item));
+    }
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    helr_free(c, d);
+    helr_free(c, pt);
+    return HE_OK;
+}
+
+extern "C" int he_lr_job_free(he_lr_job *j)
+{
+    if (!j) return HE_EINVAL;
+    he_ctx *c = j->c;
+    cudaStreamSynchronize(c->stream);
+    helr_free(c, j->Z);
+    for (auto *b : j->B) he_ct_free(b);
+    if (j->W) he_ct_free(j->W);
+    if (j->V) he_ct_free(j->V);
+    helr_free(c, j->mask);
+    helr_free(c, j->buf);
+    ev_free(&j->ev);
+    cudaStreamSynchronize(c->stream);
+    delete j;
+    return HE_OK;
+}
+
+extern "C" int he_lr_job_create(he_ctx *c, const double *X, const double *y, size_t n, size_t f, int mode,
+                                size_t batch_rows, int poly, double log_scale, uint64_t enc_seed, uint64_t key_seed,
+                                int batch_blocks, he_lr_job **out)
+{
+    if (!c || !X || !y || !out || n == 0 || f == 0 || (mode != HE_LR_FULL_BATCH && mode != HE_LR_MINI_BATCH) ||
+        (poly != HE_LR_G8 && poly != HE_LR_G16) || !(log_scale > 0 && log_scale < 62))
+        return HE_EINVAL;
+    *out = nullptr;
+    auto t0 = std::chrono::steady_clock::now();
+    const int L = c->nq - 1;
+    if (L < 7) return helr_fail(c, HE_ELEVEL, "the iteration needs 7 levels (n_q >= 8)");
+    int g = 1;
+    while ((size_t)g < f + 1) g <<= 1;
+    if (g > c->nslots) return helr_fail(c, HE_EINVAL, "too many features for N/2 slots");
+    const int m = c->nslots / g;
+    if (batch_rows == 0) batch_rows = 1024;
+    if (batch_rows % m) return helr_fail(c, HE_EINVAL, "batch_rows must be a multiple of the %d rows per block", m);
+
+    he_lr_job *j = new he_lr_job();
+    j->c = c;
+    j->mode = mode;
+    memcpy(j->poly, poly == HE_LR_G8 ? G8 : G16, sizeof j->poly);
+    j->n = n;
+    j->f = f;
+    j->g = g;
+    j->m = m;
+    j->lg = __builtin_ctz(g);
+    j->lm = __builtin_ctz(m);
+    j->L = L;
+    j->nblocks = (int)((n + m - 1) / m);
+    j->batch_rows = batch_rows;
+    j->bpb = (int)(batch_rows / m);
+    j->nbatch = (int)((n + batch_rows - 1) / batch_rows);
+    j->scale0 = ldexp(1.0, 0) * pow(2.0, log_scale);
+    j->enc_seed = enc_seed;
+    const size_t N = c->n, ns = c->nslots;
+    j->ctw = 2 * (size_t)(L + 1) * N;
+    int rc = HE_OK;
+#define JTRY(x)                       \
+    do {                              \
+        rc = (x);                     \
+        if (rc) {                     \
+            he_lr_job_free(j);        \
+            return rc;                \
+        }                             \
+    } while (0)
+
+    // keys for the rotations of Steps 2, 4 and 7
+    std::vector<int64_t> rots;
+    for (int k = 0; k < j->lg; k++) rots.push_back(1 << k), rots.push_back(-(1 << k));
+    for (int k = 0; k < j->lm; k++) rots.push_back((int64_t)g << k);
+    JTRY(he_keygen(c, key_seed, rots.data(), rots.size()));
+
+    // Step 1: Z = y [1 | X], blocks of m rows x g columns, row-major in the slots
+    std::vector<double> slots((size_t)j->nblocks * ns, 0.0);
+    for (size_t r = 0; r < n; r++) {
+        double *row = &slots[(r / m) * ns + (r % m) * g];
+        row[0] = y[r];
+        for (size_t k = 0; k < f; k++) row[k + 1] = y[r] * X[r * f + k];
+    }
+    // Bbar per mini-batch (threads over batches), full batch by 1 / sum_k (1 / Bbar_k)
+    std::vector<double> bk((size_t)j->nbatch * g);
+    {
+        unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nth; t++)
+            th.emplace_back([&, t]() {
+                for (int k = (int)t; k < j->nbatch; k += (int)nth) {
+                    size_t r0 = (size_t)k * batch_rows, rows = std::min(batch_rows, n - r0);
+                    bbar_rows(X, y, f, r0, rows, g, &bk[(size_t)k * g]);
+                }
+            });
+        for (auto &x : th) x.join();
+    }
+    std::vector<std::vector<double>> bvec;
+    if (mode == HE_LR_FULL_BATCH) {
+        std::vector<double> full(g, 0.0);
+        for (size_t a = 0; a <= f; a++) {
+            double s = 0.0;
+            for (int k = 0; k < j->nbatch; k++) s += 1.0 / bk[(size_t)k * g + a];
+            full[a] = 1.0 / s;
+        }
+        std::vector<double> v(ns);
+        for (size_t i = 0; i < ns; i++) v[i] = (double)n * full[i % g];
+        bvec.push_back(v);
+        j->inv_n.push_back(1.0 / (double)n);
+    } else {
+        for (int k = 0; k < j->nbatch; k++) {
+            double nk = (double)std::min(batch_rows, n - (size_t)k * batch_rows);
+            std::vector<double> v(ns);
+            for (size_t i = 0; i < ns; i++) v[i] = nk * bk[(size_t)k * g + (i % g)];
+            bvec.push_back(v);
+            j->inv_n.push_back(1.0 / nk);
+        }
+    }
+    // Step 2: encrypt blocks, n Bbar, W0 = V0 = 0
+    JTRY(helr_alloc(c, (void **)&j->Z, sizeof(uint64_t) * j->ctw * j->nblocks));
+    JTRY(encrypt_slots(c, slots.data(), j->nblocks, L, j->scale0, 1, enc_seed, 0, j->Z, j->ctw));
+    slots.clear();
+    slots.shrink_to_fit();
+    for (size_t k = 0; k < bvec.size(); k++) {
+        he_ct *ct = nullptr;
+        JTRY(helr_new_ct(c, L, j->scale0, &ct));
+        j->B.push_back(ct);
+        JTRY(encrypt_slots(c, bvec[k].data(), 1, L, j->scale0, 2, enc_seed, (int)k, ct->d, j->ctw));
+    }
+    std::vector<double> zero(ns, 0.0);
+    JTRY(helr_new_ct(c, L, j->scale0, &j->W));
+    JTRY(encrypt_slots(c, zero.data(), 1, L, j->scale0, 3, enc_seed, 0, j->W->d, j->ctw));
+    JTRY(helr_new_ct(c, L, j->scale0, &j->V));
+    JTRY(encrypt_slots(c, zero.data(), 1, L, j->scale0, 4, enc_seed, 0, j->V->d, j->ctw));
+    // Step 3 mask: ones in column 0 of every row, at level L-1 with scale q_(L-1)
+    {
+        std::vector<double> msk(ns, 0.0);
+        for (size_t i = 0; i < ns; i += g) msk[i] = 1.0;
+        double *d = nullptr;
+        JTRY(helr_alloc(c, (void **)&d, sizeof(double) * ns));
+        JTRY(helr_alloc(c, (void **)&j->mask, sizeof(uint64_t) * L * N));
+        HELR_CUDA(c, cudaMemcpyAsync(d, msk.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, c->stream));
+        j->mask_scale = (double)c->q[L - 1];
+        JTRY(helr_encode_dev(c, d, nullptr, 1, 0, L - 1, j->mask_scale, j->mask, 0));
+        helr_free(c, d);
+    }
+    // work buffers: chunk of blocks per launch
+    int chunk = batch_blocks > 0 ? batch_blocks : (c->logn >= 16 ? 16 : 32);
+    chunk = std::min(chunk, mode == HE_LR_FULL_BATCH ? j->nblocks : j->bpb);
+    j->chunk = std::max(1, chunk);
+    JTRY(ev_init(c, &j->ev, j->chunk, L));
+    JTRY(helr_alloc(c, (void **)&j->buf, sizeof(uint64_t) * j->ctw * (5 * (size_t)j->chunk + 3)));
+    j->T0 = j->buf;
+    j->T1 = j->T0 + j->ctw * j->chunk;
+    j->T2 = j->T1 + j->ctw * j->chunk;
+    j->T3 = j->T2 + j->ctw * j->chunk;
+    j->T4 = j->T3 + j->ctw * j->chunk;
+    j->acc = j->T4 + j->ctw * j->chunk;
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    j->st.sec_setup = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    j->st.n_blocks = j->nblocks;
+    j->st.g = g;
+    j->st.m = m;
+    *out = j;
+    return HE_OK;
+#undef JTRY
+}
+
+// cMul by c at the constant scale that makes the rescaled result carry `target`
+static int cmul_to(Eval *ev, const CtB &a, double cval, double target, CtB &tmp, CtB &out)
+{
+    he_ctx *c = ev->c;
+    double q = (double)c->q[a.level];
+    double S = (target * q) / a.scale;
+    HELR_TRY(ev_cmul_int(ev, a, round_half_away(cval * S), a.scale * S, tmp));
+    HELR_TRY(ev_rescale(ev, tmp, out));
+    out.scale = target;
+    return HE_OK;
+}
+
+// Steps 1-6 on `cnt` blocks starting at Z; result (level L-5) in g_out
+static int block_grads(he_lr_job *j, const uint64_t *Z, int cnt, const CtB &W, double alpha, CtB &g_out)
+{
+    Eval *ev = &j->ev;
+    he_ctx *c = j->c;
+    const int L = j->L;
+    const size_t w = j->ctw;
+    CtB Zc{const_cast<uint64_t *>(Z), cnt, L, j->scale0, w};
+    CtB A{j->T0, cnt, 0, 0, w}, Bt{j->T1, cnt, 0, 0, w}, R{j->T2, cnt, 0, 0, w};
+    // 1
+    HELR_TRY(ev_mul_relin(ev, Zc, W, A));
+    HELR_TRY(ev_rescale(ev, A, Bt));
+    // 2
+    for (int k = 0; k < j->lg; k++) {
+        HELR_TRY(ev_rotate(ev, Bt, 1 << k, R));
+        HELR_TRY(ev_add(ev, Bt, R, Bt, 0));
+    }
+    // 3
+    HELR_TRY(ev_ptmul(ev, Bt, j->mask, j->mask_scale, A));
+    HELR_TRY(ev_rescale(ev, A, Bt));
+    // 4
+    for (int k = 0; k < j->lg; k++) {
+        HELR_TRY(ev_rotate(ev, Bt, -(1 << k), R));
+        HELR_TRY(ev_add(ev, Bt, R, Bt, 0));
+    }
+    CtB ip = Bt;  // level L-2
+    // 5
+    const double k0 = alpha * (1.0 - j->poly[0]), k1 = -(alpha * j->poly[1]), k3 = -(alpha * j->poly[2]);
+    CtB sq{j->T3, cnt, 0, 0, w}, c3{j->T4, cnt, 0, 0, w};
+    HELR_TRY(ev_mul_relin(ev, ip, ip, A));
+    HELR_TRY(ev_rescale(ev, A, sq));
+    HELR_TRY(ev_cmul_int(ev, ip, round_half_away(k3 * j->scale0), ip.scale * j->scale0, A));
+    HELR_TRY(ev_rescale(ev, A, c3));
+    CtB cube{j->T0, cnt, 0, 0, w};
+    HELR_TRY(ev_mul_relin(ev, sq, c3, R));
+    HELR_TRY(ev_rescale(ev, R, cube));
+    CtB lin{j->T3, cnt, 0, 0, w}, lind{j->T4, cnt, 0, 0, w};
+    HELR_TRY(cmul_to(ev, ip, k1, cube.scale, R, lin));
+    HELR_TRY(ev_moddrop(ev, lin, cube.level, lind));
+    CtB s{j->T1, cnt, 0, 0, w};
+    HELR_TRY(ev_add(ev, cube, lind, s, 0));
+    HELR_TRY(ev_cadd_int(ev, s, round_half_away(k0 * s.scale)));
+    // 6
+    CtB zd{j->T3, cnt, 0, 0, w};
+    HELR_TRY(ev_moddrop(ev, Zc, s.level, zd));
+    HELR_TRY(ev_mul_relin(ev, s, zd, A));
+    g_out.d = j->T2;
+    g_out.item = w;
+    HELR_TRY(ev_rescale(ev, A, g_out));
+    (void)c;
+    return HE_OK;
+}
+
+// Steps 7-9 on the accumulated gradient; W', V' at level L-7 into Wn, Vn
+static int finish(he_lr_job *j, CtB acc, const he_ct *Bct, double eta, double inv_n, CtB &Wn, CtB &Vn)
+{
+    Eval *ev = &j->ev;
+    const size_t w = j->ctw;
+    CtB R{j->T0, 1, 0, 0, w}, A{j->T1, 1, 0, 0, w}, Bd{j->T2, 1, 0, 0, w};
+    // 7
+    for (int k = 0; k < j->lm; k++) {
+        HELR_TRY(ev_rotate(ev, acc, (int64_t)j->g << k, R));
+        HELR_TRY(ev_add(ev, acc, R, acc, 0));
+    }
+    // 8
+    CtB Bv{Bct->d, 1, Bct->level, Bct->scale, 0};
+    HELR_TRY(ev_moddrop(ev, Bv, acc.level, Bd));
+    HELR_TRY(ev_mul_relin(ev, acc, Bd, A));
+    CtB nG{j->T3, 1, 0, 0, w};
+    HELR_TRY(ev_rescale(ev, A, nG));
+    // 9
+    const int lv = nG.level;
+    const double tgt = j->W->scale;
+    CtB Wv{j->W->d, 1, j->W->level, j->W->scale, 0}, Vv{j->V->d, 1, j->V->level, j->V->scale, 0};
+    CtB G{j->T4, 1, 0, 0, w}, Wd{j->T0, 1, 0, 0, w};
+    HELR_TRY(cmul_to(ev, nG, inv_n, tgt, A, G));
+    HELR_TRY(ev_moddrop(ev, Wv, lv - 1, Wd));
+    HELR_TRY(ev_add(ev, Wd, G, Vn, 0));
+    CtB x1{j->T4, 1, 0, 0, w}, x2{j->T0, 1, 0, 0, w};
+    HELR_TRY(ev_moddrop(ev, Wv, lv, Bd));
+    HELR_TRY(cmul_to(ev, Bd, 1.0 - eta, tgt, A, x1));
+    HELR_TRY(ev_moddrop(ev, Vv, lv, Bd));
+    HELR_TRY(cmul_to(ev, Bd, eta, tgt, A, x2));
+    HELR_TRY(ev_add(ev, x1, x2, x1, 0));
+    HELR_TRY(cmul_to(ev, nG, (1.0 - eta) * inv_n, tgt, A, x2));
+    HELR_TRY(ev_add(ev, x1, x2, Wn, 0));
+    return HE_OK;
+}
+
+// decrypt, keep the real part of every slot, re-encode at the top level, encrypt
+static int refresh_dev(he_ctx *c, const uint64_t *ct, int level, double scale, double new_scale, uint64_t seed, uint64_t *dst)
+{
+    const size_t N = c->n, ns = c->nslots;
+    uint64_t *pt = nullptr, *pt2 = nullptr;
+    double *z = nullptr;
+    HELR_TRY(helr_alloc(c, (void **)&pt, sizeof(uint64_t) * (level + 1) * N));
+    HELR_TRY(helr_alloc(c, (void **)&pt2, sizeof(uint64_t) * c->nq * N));
+    HELR_TRY(helr_alloc(c, (void **)&z, sizeof(double) * 2 * ns));
+    HELR_TRY(helr_decrypt_dev(c, ct, level, pt));
+    HELR_TRY(helr_decode_dev(c, pt, scale, z, z + ns));
+    HELR_TRY(helr_encode_dev(c, z, nullptr, 1, 0, c->nq - 1, new_scale, pt2, 0));
+    HELR_TRY(helr_encrypt_dev(c, pt2, c->nq - 1, seed, dst));
+    helr_free(c, pt);
+    helr_free(c, pt2);
+    helr_free(c, z);
+    return HE_OK;
+}
+
+extern "C" int he_lr_job_step(he_lr_job *j, int t, he_lr_sched sched)
+{
+    if (!j || t < 0 || !(sched.T > 0)) return HE_EINVAL;
+    he_ctx *c = j->c;
+    auto t0 = std::chrono::steady_clock::now();
+    const double alpha = f2(sched, (double)t), eta = nag_eta(t);
+    int b0 = 0, b1 = j->nblocks, k = 0;
+    if (j->mode == HE_LR_MINI_BATCH) {
+        k = t % j->nbatch;
+        b0 = k * j->bpb;
+        b1 = std::min(j->nblocks, b0 + j->bpb);
+    }
+    j->ev.keyswitches = 0;
+    const CtB W{j->W->d, 1, j->L, j->W->scale, 0};
+    double gscale = 0;
+    int glevel = 0;
+    for (int b = b0; b < b1; b += j->chunk) {
+        int cnt = std::min(j->chunk, b1 - b);
+        CtB g{};
+        HELR_TRY(block_grads(j, j->Z + (size_t)b * j->ctw, cnt, W, alpha, g));
+        HELR_TRY(ev_sum_items(&j->ev, g, j->acc, b != b0));
+        gscale = g.scale;
+        glevel = g.level;
+    }
+    CtB acc{j->acc, 1, glevel, gscale, 0};
+    CtB Wn{j->acc + j->ctw, 1, 0, 0, 0}, Vn{j->acc + 2 * j->ctw, 1, 0, 0, 0};
+    HELR_TRY(finish(j, acc, j->B[k], eta, j->inv_n[k], Wn, Vn));
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    auto t1 = std::chrono::steady_clock::now();
+    // Step 7: refresh W and V
+    HELR_TRY(refresh_dev(c, Wn.d, Wn.level, Wn.scale, j->scale0, obj_seed(j->enc_seed, 5, t), j->W->d));
+    HELR_TRY(refresh_dev(c, Vn.d, Vn.level, Vn.scale, j->scale0, obj_seed(j->enc_seed, 6, t), j->V->d));
+    j->W->scale = j->scale0;
+    j->V->scale = j->scale0;
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    auto t2 = std::chrono::steady_clock::now();
+    j->upd_total += std::chrono::duration<double>(t1 - t0).count();
+    j->iter_total += std::chrono::duration<double>(t2 - t0).count();
+    j->iters_done++;
+    j->st.keyswitches = j->ev.keyswitches;
+    j->st.sec_update_avg = j->upd_total / j->iters_done;
+    j->st.sec_iter_avg = j->iter_total / j->iters_done;
+    return HE_OK;
+}
+
+extern "C" int he_lr_job_weights(he_lr_job *j, int row, double *w, size_t len)
+{
+    if (!j || !w || row < 0 || row >= j->m || len < (size_t)j->g) return HE_EINVAL;
+    he_ctx *c = j->c;
+    he_pt *pt = nullptr;
+    HELR_TRY(he_decrypt(c, j->W, &pt));
+    std::vector<double> re(c->nslots);
+    int rc = he_decode(c, pt, re.data(), nullptr, c->nslots);
+    he_pt_free(pt);
+    if (rc) return rc;
+    memcpy(w, &re[(size_t)row * j->g], sizeof(double) * j->g);
+    return HE_OK;
+}
+
+extern "C" int he_lr_job_state(he_lr_job *j, const he_ct **W, const he_ct **V)
+{
+    if (!j) return HE_EINVAL;
+    if (W) *W = j->W;
+    if (V) *V = j->V;
+    return HE_OK;
+}
+
+extern "C" int he_lr_job_input(he_lr_job *j, int kind, int index, he_ct **out)
+{
+    if (!j || !out) return HE_EINVAL;
+    he_ctx *c = j->c;
+    const uint64_t *src;
+    double scale = j->scale0;
+    if (kind == 0 && index >= 0 && index < j->nblocks) src = j->Z + (size_t)index * j->ctw;
+    else if (kind == 1 && index >= 0 && index < (int)j->B.size()) src = j->B[index]->d;
+    else return HE_EINVAL;
+    he_ct *o = nullptr;
+    HELR_TRY(helr_new_ct(c, j->L, scale, &o));
+    HELR_CUDA(c, cudaMemcpyAsync(o->d, src, sizeof(uint64_t) * j->ctw, cudaMemcpyDeviceToDevice, c->stream));
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    *out = o;
+    return HE_OK;
+}
+
+extern "C" int he_lr_job_block_grad(he_lr_job *j, int block, double alpha, he_ct **out)
+{
+    if (!j || !out || block < 0 || block >= j->nblocks) return HE_EINVAL;
+    he_ctx *c = j->c;
+    const CtB W{j->W->d, 1, j->L, j->W->scale, 0};
+    // the chunk of the step's launch sequence that holds `block`
+    int b0 = 0, b1 = j->nblocks;
+    if (j->mode == HE_LR_MINI_BATCH) {
+        b0 = (block / j->bpb) * j->bpb;
+        b1 = std::min(j->nblocks, b0 + j->bpb);
+    }
+    int start = b0 + ((block - b0) / j->chunk) * j->chunk;
+    int cnt = std::min(j->chunk, b1 - start);
+    CtB g{};
+    HELR_TRY(block_grads(j, j->Z + (size_t)start * j->ctw, cnt, W, alpha, g));
+    he_ct *o = nullptr;
+    HELR_TRY(helr_new_ct(c, g.level, g.scale, &o));
+    HELR_CUDA(c, cudaMemcpyAsync(o->d, g.d + (size_t)(block - start) * g.item, sizeof(uint64_t) * 2 * (g.level + 1) * c->n,
+                                 cudaMemcpyDeviceToDevice, c->stream));
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    *out = o;
+    return HE_OK;
+}
+
+extern "C" int he_lr_job_info(const he_lr_job *j, he_lr_stats *st)
+{
+    if (!j || !st) return HE_EINVAL;
+    *st = j->st;
+    return HE_OK;
+}
+
+extern "C" int he_lr_train(he_ctx *c, const double *X, const double *y, size_t n, size_t f, int iters, he_lr_sched sched,
+                           int mode, size_t batch_rows, int poly, uint64_t enc_seed, uint64_t key_seed, double *w_out,
+                           size_t w_len, he_lr_stats *stats)
+{
+    if (!c || iters < 0 || !w_out) return HE_EINVAL;
+    he_lr_job *j = nullptr;
+    HELR_TRY(he_lr_job_create(c, X, y, n, f, mode, batch_rows, poly, 40.0, enc_seed, key_seed, 0, &j));
+    int rc = HE_OK;
+    for (int t = 0; t < iters && !rc; t++) rc = he_lr_job_step(j, t, sched);
+    if (!rc) rc = he_lr_job_weights(j, 0, w_out, w_len);
+    if (!rc && stats) rc = he_lr_job_info(j, stats);
+    he_lr_job_free(j);
+    return rc;
+}
+
+// ------------------------------------------------------------------ cloud-only iteration / refresh
+extern "C" int he_lr_iteration(he_ctx *c, he_ct *const *Z, size_t nb, const he_ct *B, const he_ct *W, const he_ct *V, int g,
+                               int m, double alpha, double eta, double inv_n, const double poly[3], he_ct **W_out,
+                               he_ct **V_out)
+{
+    if (!c || !Z || !nb || !B || !W || !V || !poly || !W_out || !V_out || g * m != c->nslots || (g & (g - 1)) || g < 1)
+        return HE_EINVAL;
+    const int L = W->level;
+    if (L < 7) return helr_fail(c, HE_ELEVEL, "the iteration needs 7 levels");
+    for (size_t i = 0; i < nb; i++)
+        if (Z[i]->level != L) return helr_fail(c, HE_ELEVEL, "data blocks must share the level of W");
+    // a temporary job around the caller's ciphertexts
+    he_lr_job j{};
+    j.c = c;
+    memcpy(j.poly, poly, sizeof j.poly);
+    j.g = g;
+    j.m = m;
+    j.lg = __builtin_ctz(g);
+    j.lm = __builtin_ctz(m);
+    j.L = L;
+    j.scale0 = W->scale;
+    const size_t N = c->n;
+    j.ctw = 2 * (size_t)(L + 1) * N;
+    j.chunk = (int)std::min<size_t>(nb, c->logn >= 16 ? 16 : 32);
+    int rc = HE_OK;
+    uint64_t *zbuf = nullptr;
+    std::vector<double> msk(c->nslots, 0.0);
+    for (int i = 0; i < c->nslots; i += g) msk[i] = 1.0;
+    double *dm = nullptr;
+    he_ct *Wo = nullptr, *Vo = nullptr;
+    if ((rc = ev_init(c, &j.ev, std::max(j.chunk, 3), L))) goto out;
+    if ((rc = helr_alloc(c, (void **)&j.buf, sizeof(uint64_t) * j.ctw * (5 * (size_t)std::max(j.chunk, 3) + 3)))) goto out;
+    j.T0 = j.buf;
+    j.T1 = j.T0 + j.ctw * std::max(j.chunk, 3);
+    j.T2 = j.T1 + j.ctw * std::max(j.chunk, 3);
+    j.T3 = j.T2 + j.ctw * std::max(j.chunk, 3);
+    j.T4 = j.T3 + j.ctw * std::max(j.chunk, 3);
+    j.acc = j.T4 + j.ctw * std::max(j.chunk, 3);
+    if ((rc = helr_alloc(c, (void **)&j.mask, sizeof(uint64_t) * L * N))) goto out;
+    if ((rc = helr_alloc(c, (void **)&dm, sizeof(double) * c->nslots))) goto out;
+    if (cudaMemcpyAsync(dm, msk.data(), sizeof(double) * c->nslots, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+        rc = helr_fail(c, HE_ECUDA, "mask upload");
+        goto out;
+    }
+    j.mask_scale = (double)c->q[L - 1];
+    if ((rc = helr_encode_dev(c, dm, nullptr, 1, 0, L - 1, j.mask_scale, j.mask, 0))) goto out;
+    if ((rc = helr_alloc(c, (void **)&zbuf, sizeof(uint64_t) * j.ctw * j.chunk))) goto out;
+    j.W = const_cast<he_ct *>(W);
+    j.V = const_cast<he_ct *>(V);
+    {
+        const CtB Wb{W->d, 1, L, W->scale, 0};
+        double gscale = 0;
+        int glevel = 0;
+        for (size_t b = 0; b < nb && !rc; b += j.chunk) {
+            int cnt = (int)std::min<size_t>(j.chunk, nb - b);
+            for (int i = 0; i < cnt && !rc; i++)
+                if (cudaMemcpyAsync(zbuf + (size_t)i * j.ctw, Z[b + i]->d, j.ctw * 8, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+                    rc = helr_fail(c, HE_ECUDA, "gather");
+            CtB gg{};
+            if (!rc) rc = block_grads(&j, zbuf, cnt, Wb, alpha, gg);
+            if (!rc) rc = ev_sum_items(&j.ev, gg, j.acc, b != 0);
+            gscale = gg.scale;
+            glevel = gg.level;
+        }
+        if (rc) goto out;
+        if ((rc = helr_new_ct(c, L - 7, 0, &Wo))) goto out;
+        if ((rc = helr_new_ct(c, L - 7, 0, &Vo))) goto out;
+        CtB acc{j.acc, 1, glevel, gscale, 0};
+        CtB Wn{Wo->d, 1, 0, 0, 0}, Vn{Vo->d, 1, 0, 0, 0};
+        if ((rc = finish(&j, acc, B, eta, inv_n, Wn, Vn))) goto out;
+        Wo->level = Wn.level;
+        Wo->scale = Wn.scale;
+        Vo->level = Vn.level;
+        Vo->scale = Vn.scale;
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = helr_fail(c, HE_ECUDA, "iteration");
+    }
+out:
+    helr_free(c, zbuf);
+    helr_free(c, dm);
+    helr_free(c, j.mask);
+    helr_free(c, j.buf);
+    ev_free(&j.ev);
+    cudaStreamSynchronize(c->stream);
+    if (rc) {
+        if (Wo) he_ct_free(Wo);
+        if (Vo) he_ct_free(Vo);
+        return rc;
+    }
+    *W_out = Wo;
+    *V_out = Vo;
+    return HE_OK;
+}
+
+extern "C" int he_refresh(he_ctx *c, const he_ct *in, double scale, uint64_t seed, he_ct **out)
+{
+    if (!c || !in || !out || !(scale > 0)) return HE_EINVAL;
+    he_ct *o = nullptr;
+    HELR_TRY(helr_new_ct(c, c->nq - 1, scale, &o));
+    int rc = refresh_dev(c, in->d, in->level, in->scale, scale, seed, o->d);
+    if (!rc) rc = cudaStreamSynchronize(c->stream) == cudaSuccess ? HE_OK : helr_fail(c, HE_ECUDA, "refresh");
+    if (rc) {
+        he_ct_free(o);
+        return rc;
+    }
+    *out = o;
+    return HE_OK;
+}

@@ -1,0 +1,341 @@
+// ntt.cu -- batched negacyclic NTT over Z_q[X]/(X^N + 1) for N = 2^10 .. 2^16.
+//
+// Every ring product of the scheme (Sec. 2.1 Mul, cMul by a plaintext, key
+// switching inside Mul and rotation) is a pointwise product between forward
+// transforms.  Transform: A[p] = sum_j a_j psi^(j (2 bitrev(p) + 1)), i.e. the
+// evaluations at the odd powers of a primitive 2N-th root psi, stored in
+// bit-reversed order (merged-twist Cooley-Tukey forward, Gentleman-Sande
+// inverse; the inverse includes the factor N^-1).
+//
+// Layout: N = R1 * R2 with R1 = 2^K1, R2 = 2^K2, index j = j1 * R2 + j2.
+//  * pass 1: the first K1 butterfly stages act along j1 ("columns", stride R2);
+//    a CTA takes C adjacent columns so that global accesses are contiguous runs.
+//  * pass 2: the last K2 stages act inside each contiguous row of R2 words.
+// Inside a pass one column/row of R = 2^K words is held by T threads with E
+// words each (E = 2^ceil(K/2), T = 2^floor(K/2)): the first log2(E) stages run in
+// registers on the strided assignment j = l + T r, one shared-memory exchange
+// regroups the words as j = E l + r, and the remaining log2(T) stages run in
+// registers again.  Butterflies are Harvey's lazy forms (values in [0, 4q) in the
+// forward and [0, 2q) in the inverse) with Shoup twiddle products.
+#include "helr_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ void ct_bfly(uint64_t &x, uint64_t &y, uint64_t w, uint64_t wp, uint64_t q, uint64_t q2)
+{
+    uint64_t a = x >= q2 ? x - q2 : x;
+    uint64_t t = shoup_lazy(y, w, wp, q);
+    x = a + t;
+    y = a - t + q2;
+}
+
+__device__ __forceinline__ void gs_bfly(uint64_t &x, uint64_t &y, uint64_t w, uint64_t wp, uint64_t q, uint64_t q2)
+{
+    uint64_t a = x + y;
+    a = a >= q2 ? a - q2 : a;
+    uint64_t b = x - y + q2;
+    y = shoup_lazy(b, w, wp, q);
+    x = a;
+}
+
+__device__ __forceinline__ ulonglong2 ldtw(const uint64_t *tw, int idx)
+{
+    return __ldg(reinterpret_cast<const ulonglong2 *>(tw) + idx);
+}
+
+// padded shared-memory position of word j inside one column/row segment
+template <int LE>
+__device__ __forceinline__ int spad(int j) { return j + (j >> LE); }
+
+template <int K>
+struct Geo {
+    static constexpr int LE = (K + 1) / 2, LT = K / 2;
+    static constexpr int E = 1 << LE, T = 1 << LT, R = 1 << K;
+    static constexpr int SEG = R + (R >> LE) + 1;  // segment stride in words (odd)
+};
+
+// forward stages on the strided assignment (j = l + T r): local stages s < LE
+template <int K>
+__device__ __forceinline__ void fwd_strided(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, uint64_t q, uint64_t q2)
+{
+    constexpr int E = Geo<K>::E, LE = Geo<K>::LE;
+#pragma unroll
+    for (int s = 0; s < LE; s++) {
+        const int m = 1 << s, hr = E >> (s + 1);
+#pragma unroll
+        for (int g = 0; g < m; g++) {
+            ulonglong2 w = ldtw(tw, m * A + g);
+#pragma unroll
+            for (int k = 0; k < hr; k++) ct_bfly(x[g * 2 * hr + k], x[g * 2 * hr + k + hr], w.x, w.y, q, q2);
+        }
+    }
+}
+
+// forward stages on the contiguous assignment (j = E l + r): local stages s >= LE
+template <int K>
+__device__ __forceinline__ void fwd_contig(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, int l, uint64_t q, uint64_t q2)
+{
+    constexpr int E = Geo<K>::E, LE = Geo<K>::LE, R = Geo<K>::R;
+#pragma unroll
+    for (int s = LE; s < K; s++) {
+        const int m = 1 << s, h = R >> (s + 1), gpt = E / (2 * h);
+#pragma unroll
+        for (int g = 0; g < gpt; g++) {
+            ulonglong2 w = ldtw(tw, m * A + l * gpt + g);
+#pragma unroll
+            for (int k = 0; k < h; k++) ct_bfly(x[g * 2 * h + k], x[g * 2 * h + k + h], w.x, w.y, q, q2);
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void inv_contig(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, int l, uint64_t q, uint64_t q2)
+{
+    constexpr int E = Geo<K>::E, LE = Geo<K>::LE, R = Geo<K>::R;
+#pragma unroll
+    for (int s = K - 1; s >= LE; s--) {
+        const int m = 1 << s, h = R >> (s + 1), gpt = E / (2 * h);
+#pragma unroll
+        for (int g = 0; g < gpt; g++) {
+            ulonglong2 w = ldtw(tw, m * A + l * gpt + g);
+#pragma unroll
+            for (int k = 0; k < h; k++) gs_bfly(x[g * 2 * h + k], x[g * 2 * h + k + h], w.x, w.y, q, q2);
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void inv_strided(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, uint64_t q, uint64_t q2)
+{
+    constexpr int E = Geo<K>::E, LE = Geo<K>::LE;
+#pragma unroll
+    for (int s = LE - 1; s >= 0; s--) {
+        const int m = 1 << s, hr = E >> (s + 1);
+#pragma unroll
+        for (int g = 0; g < m; g++) {
+            ulonglong2 w = ldtw(tw, m * A + g);
+#pragma unroll
+            for (int k = 0; k < hr; k++) gs_bfly(x[g * 2 * hr + k], x[g * 2 * hr + k + hr], w.x, w.y, q, q2);
+        }
+    }
+}
+
+// exchange the E words of thread l inside one segment of shared memory
+template <int K>
+__device__ __forceinline__ void to_contig(uint64_t (&x)[Geo<K>::E], uint64_t *seg, int l)
+{
+    constexpr int E = Geo<K>::E, LE = Geo<K>::LE, T = Geo<K>::T;
+#pragma unroll
+    for (int r = 0; r < E; r++) seg[spad<LE>(l + T * r)] = x[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < E; r++) x[r] = seg[spad<LE>(E * l + r)];
+}
+template <int K>
+__device__ __forceinline__ void to_strided(uint64_t (&x)[Geo<K>::E], uint64_t *seg, int l)
+{
+    constexpr int E = Geo<K>::E, LE = Geo<K>::LE, T = Geo<K>::T;
+#pragma unroll
+    for (int r = 0; r < E; r++) seg[spad<LE>(E * l + r)] = x[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < E; r++) x[r] = seg[spad<LE>(l + T * r)];
+}
+
+// ---------------------------------------------------------------- forward
+// pass 1: columns. grid.x = nlimbs * (R2 / C); block = C * T1 threads.
+template <int K1, int K2, int C>
+__global__ void __launch_bounds__(C * Geo<K1>::T) k_ntt_fwd_cols(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
+                                                                 const uint64_t *__restrict__ twall, const ModQ *__restrict__ mods,
+                                                                 LimbMap lm)
+{
+    using G = Geo<K1>;
+    constexpr int R2 = 1 << K2, N = G::R * R2, NG = R2 / C;
+    extern __shared__ uint64_t smem[];
+    const int limb = blockIdx.x / NG, grp = blockIdx.x % NG;
+    const int jj = threadIdx.x % C, l = threadIdx.x / C;
+    const int pr = lm.p[limb % lm.period];
+    const uint64_t q = mods[pr].q, q2 = 2 * q;
+    const uint64_t *tw = twall + (size_t)pr * N * 2;
+    const size_t base = (size_t)limb * N + grp * C + jj;
+    uint64_t x[G::E];
+#pragma unroll
+    for (int r = 0; r < G::E; r++) x[r] = in[base + (size_t)(l + G::T * r) * R2];
+    fwd_strided<K1>(x, tw, 1, q, q2);
+    to_contig<K1>(x, smem + jj * G::SEG, l);
+    fwd_contig<K1>(x, tw, 1, l, q, q2);
+#pragma unroll
+    for (int r = 0; r < G::E; r++) out[base + (size_t)(G::E * l + r) * R2] = x[r];
+}
+
+// pass 2: rows. grid.x = nlimbs * (R1 / RPC); block = RPC * T2 threads.
+template <int K1, int K2, int RPC>
+__global__ void __launch_bounds__(RPC * Geo<K2>::T) k_ntt_fwd_rows(uint64_t *__restrict__ data, const uint64_t *__restrict__ twall,
+                                                                   const ModQ *__restrict__ mods, LimbMap lm)
+{
+    using G = Geo<K2>;
+    constexpr int R1 = 1 << K1, R2 = G::R, N = R1 * R2, NG = R1 / RPC;
+    extern __shared__ uint64_t smem[];
+    const int limb = blockIdx.x / NG, grp = blockIdx.x % NG;
+    const int l = threadIdx.x % G::T, rl = threadIdx.x / G::T;
+    const int row = grp * RPC + rl;
+    const int pr = lm.p[limb % lm.period];
+    const uint64_t q = mods[pr].q, q2 = 2 * q;
+    const uint64_t *tw = twall + (size_t)pr * N * 2;
+    uint64_t *rowp = data + (size_t)limb * N + (size_t)row * R2;
+    uint64_t *seg = smem + rl * G::SEG;
+    uint64_t x[G::E];
+#pragma unroll
+    for (int r = 0; r < G::E; r++) x[r] = rowp[l + G::T * r];
+    const int A = R1 + row;
+    fwd_strided<K2>(x, tw, A, q, q2);
+    to_contig<K2>(x, seg, l);
+    fwd_contig<K2>(x, tw, A, l, q, q2);
+#pragma unroll
+    for (int r = 0; r < G::E; r++) {
+        uint64_t v = x[r];
+        v = v >= q2 ? v - q2 : v;
+        x[r] = v >= q ? v - q : v;
+    }
+    __syncthreads();
+    to_strided<K2>(x, seg, l);
+#pragma unroll
+    for (int r = 0; r < G::E; r++) rowp[l + G::T * r] = x[r];
+}
+
+// ---------------------------------------------------------------- inverse
+// pass A: rows (last forward stages undone first).
+template <int K1, int K2, int RPC>
+__global__ void __launch_bounds__(RPC * Geo<K2>::T) k_ntt_inv_rows(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
+                                                                   const uint64_t *__restrict__ twall, const ModQ *__restrict__ mods,
+                                                                   LimbMap lm)
+{
+    using G = Geo<K2>;
+    constexpr int R1 = 1 << K1, R2 = G::R, N = R1 * R2, NG = R1 / RPC;
+    extern __shared__ uint64_t smem[];
+    const int limb = blockIdx.x / NG, grp = blockIdx.x % NG;
+    const int l = threadIdx.x % G::T, rl = threadIdx.x / G::T;
+    const int row = grp * RPC + rl;
+    const int pr = lm.p[limb % lm.period];
+    const uint64_t q = mods[pr].q, q2 = 2 * q;
+    const uint64_t *tw = twall + (size_t)pr * N * 2;
+    const uint64_t *rin = in + (size_t)limb * N + (size_t)row * R2;
+    uint64_t *rout = out + (size_t)limb * N + (size_t)row * R2;
+    uint64_t *seg = smem + rl * G::SEG;
+    uint64_t x[G::E];
+#pragma unroll
+    for (int r = 0; r < G::E; r++) x[r] = rin[l + G::T * r];
+    to_contig<K2>(x, seg, l);
+    const int A = R1 + row;
+    inv_contig<K2>(x, tw, A, l, q, q2);
+    __syncthreads();
+    to_strided<K2>(x, seg, l);
+    inv_strided<K2>(x, tw, A, q, q2);
+#pragma unroll
+    for (int r = 0; r < G::E; r++) rout[l + G::T * r] = x[r];
+}
+
+// pass B: columns, then the factor N^-1 and the final reduction to [0, q).
+template <int K1, int K2, int C>
+__global__ void __launch_bounds__(C * Geo<K1>::T) k_ntt_inv_cols(uint64_t *__restrict__ data, const uint64_t *__restrict__ twall,
+                                                                 const ModQ *__restrict__ mods, const uint64_t *__restrict__ ninv,
+                                                                 LimbMap lm)
+{
+    using G = Geo<K1>;
+    constexpr int R2 = 1 << K2, N = G::R * R2, NG = R2 / C;
+    extern __shared__ uint64_t smem[];
+    const int limb = blockIdx.x / NG, grp = blockIdx.x % NG;
+    const int jj = threadIdx.x % C, l = threadIdx.x / C;
+    const int pr = lm.p[limb % lm.period];
+    const uint64_t q = mods[pr].q, q2 = 2 * q;
+    const uint64_t *tw = twall + (size_t)pr * N * 2;
+    const size_t base = (size_t)limb * N + grp * C + jj;
+    uint64_t x[G::E];
+    // words of this column arrive as j1 = E l + r (contiguous assignment)
+#pragma unroll
+    for (int r = 0; r < G::E; r++) x[r] = data[base + (size_t)(G::E * l + r) * R2];
+    inv_contig<K1>(x, tw, 1, l, q, q2);
+    to_strided<K1>(x, smem + jj * G::SEG, l);
+    inv_strided<K1>(x, tw, 1, q, q2);
+    const uint64_t ni = ninv[2 * pr], nip = ninv[2 * pr + 1];
+#pragma unroll
+    for (int r = 0; r < G::E; r++) data[base + (size_t)(l + G::T * r) * R2] = shoup(x[r], ni, nip, q);
+}
+
+template <int K1, int K2>
+struct NttPlan {
+    static constexpr int T1 = Geo<K1>::T, T2 = Geo<K2>::T;
+    static constexpr int R1 = 1 << K1, R2 = 1 << K2;
+    static constexpr int C = (256 / T1) < R2 ? (256 / T1) : R2;
+    static constexpr int RPC = (256 / T2) < R1 ? (256 / T2) : R1;
+    static constexpr size_t SM1 = (size_t)C * Geo<K1>::SEG * 8;
+    static constexpr size_t SM2 = (size_t)RPC * Geo<K2>::SEG * 8;
+
+    static cudaError_t prepare()
+    {
+        cudaError_t e = cudaFuncSetAttribute(k_ntt_fwd_cols<K1, K2, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM1);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_inv_cols<K1, K2, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM1);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_fwd_rows<K1, K2, RPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM2);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_inv_rows<K1, K2, RPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM2);
+        return e;
+    }
+    static void fwd(const uint64_t *in, uint64_t *out, size_t nlimbs, const DevTables &t, const LimbMap &m, cudaStream_t s)
+    {
+        k_ntt_fwd_cols<K1, K2, C><<<(unsigned)(nlimbs * (R2 / C)), C * T1, SM1, s>>>(in, out, t.tw, t.mod, m);
+        k_ntt_fwd_rows<K1, K2, RPC><<<(unsigned)(nlimbs * (R1 / RPC)), RPC * T2, SM2, s>>>(out, t.tw, t.mod, m);
+    }
+    static void inv(const uint64_t *in, uint64_t *out, size_t nlimbs, const DevTables &t, const LimbMap &m, cudaStream_t s)
+    {
+        k_ntt_inv_rows<K1, K2, RPC><<<(unsigned)(nlimbs * (R1 / RPC)), RPC * T2, SM2, s>>>(in, out, t.itw, t.mod, m);
+        k_ntt_inv_cols<K1, K2, C><<<(unsigned)(nlimbs * (R2 / C)), C * T1, SM1, s>>>(out, t.itw, t.mod, t.ninv, m);
+    }
+};
+
+template <int K1, int K2>
+int run(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s, bool inverse)
+{
+    static bool prepared = false;
+    if (!prepared) {
+        HELR_CUDA(c, (NttPlan<K1, K2>::prepare()));
+        prepared = true;
+    }
+    if (nlimbs == 0) return HE_OK;
+    if (inverse) NttPlan<K1, K2>::inv(in, out, nlimbs, c->t, m, s);
+    else NttPlan<K1, K2>::fwd(in, out, nlimbs, c->t, m, s);
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
+
+int dispatch(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s, bool inv)
+{
+    if (nlimbs > (size_t)1 << 24) return helr_fail(c, HE_EINVAL, "too many limbs in one transform batch");
+    switch (c->logn) {
+    case 10: return run<5, 5>(c, in, out, nlimbs, m, s, inv);
+    case 11: return run<5, 6>(c, in, out, nlimbs, m, s, inv);
+    case 12: return run<6, 6>(c, in, out, nlimbs, m, s, inv);
+    case 13: return run<6, 7>(c, in, out, nlimbs, m, s, inv);
+    case 14: return run<7, 7>(c, in, out, nlimbs, m, s, inv);
+    case 15: return run<7, 8>(c, in, out, nlimbs, m, s, inv);
+    case 16: return run<8, 8>(c, in, out, nlimbs, m, s, inv);
+    default: return helr_fail(c, HE_EINVAL, "log_n %d unsupported", c->logn);
+    }
+}
+
+}  // namespace
+
+int helr_ntt_fwd(he_ctx *c, uint64_t *data, size_t nlimbs, const LimbMap &m, cudaStream_t s)
+{
+    return dispatch(c, data, data, nlimbs, m, s, false);
+}
+int helr_ntt_inv(he_ctx *c, uint64_t *data, size_t nlimbs, const LimbMap &m, cudaStream_t s)
+{
+    return dispatch(c, data, data, nlimbs, m, s, true);
+}
+int helr_ntt_fwd_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s)
+{
+    return dispatch(c, in, out, nlimbs, m, s, false);
+}
+int helr_ntt_inv_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s)
+{
+    return dispatch(c, in, out, nlimbs, m, s, true);
+}

@@ -1,0 +1,331 @@
+// ops.cu -- elementwise and structural kernels of the scheme (Sec. 2.1 operations)
+//
+// All ciphertext kernels work on evaluation-form limbs ([..][limb][N] words)
+// except the lifts, which read coefficient-form limbs produced by an inverse
+// transform.  Words move as 16-byte pairs (two coefficients per thread).
+#include "helr_internal.cuh"
+
+#define GS_LOOP(i, n) for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (size_t)gridDim.x * blockDim.x)
+
+namespace {
+
+inline unsigned grid_for(size_t work, int threads = 256)
+{
+    size_t b = (work + threads - 1) / threads;
+    if (b > (size_t)152 * 64) b = (size_t)152 * 64;
+    return (unsigned)(b ? b : 1);
+}
+
+__global__ void k_add_kernel(uint64_t *out, const uint64_t *a, const uint64_t *b, size_t npairs, int half_n,
+                             const ModQ *mods, LimbMap lm, int sub)
+{
+    GS_LOOP(i, npairs) {
+        size_t limb = i / half_n;
+        uint64_t q = mods[lm.p[limb % lm.period]].q;
+        ulonglong2 x = reinterpret_cast<const ulonglong2 *>(a)[i];
+        ulonglong2 y = reinterpret_cast<const ulonglong2 *>(b)[i];
+        ulonglong2 z;
+        if (sub) { z.x = submod(x.x, y.x, q); z.y = submod(x.y, y.y, q); }
+        else { z.x = addmod(x.x, y.x, q); z.y = addmod(x.y, y.y, q); }
+        reinterpret_cast<ulonglong2 *>(out)[i] = z;
+    }
+}
+
+__global__ void k_mul_kernel(uint64_t *out, const uint64_t *a, const uint64_t *b, size_t npairs, int half_n,
+                             const ModQ *mods, LimbMap lm)
+{
+    GS_LOOP(i, npairs) {
+        size_t limb = i / half_n;
+        ModQ m = mods[lm.p[limb % lm.period]];
+        ulonglong2 x = reinterpret_cast<const ulonglong2 *>(a)[i];
+        ulonglong2 y = reinterpret_cast<const ulonglong2 *>(b)[i];
+        ulonglong2 z;
+        z.x = mulmod(x.x, y.x, m);
+        z.y = mulmod(x.y, y.y, m);
+        reinterpret_cast<ulonglong2 *>(out)[i] = z;
+    }
+}
+
+// (d0, d1, d2) = (a0 b0, a0 b1 + a1 b0, a1 b1); a, b: items of [2][L][N]; d_i at d + item * d_stride + i * d_poly
+__global__ void k_tensor_kernel(const uint64_t *a, const uint64_t *b, uint64_t *d, size_t npairs, int half_n,
+                                int nl, size_t a_stride, size_t b_stride, size_t d_stride, size_t d_poly, const ModQ *mods)
+{
+    GS_LOOP(i, npairs) {
+        size_t per = (size_t)nl * half_n;
+        size_t bt = i / per, r = i % per;
+        int limb = (int)(r / half_n);
+        ModQ m = mods[limb];
+        const ulonglong2 *A = reinterpret_cast<const ulonglong2 *>(a + bt * a_stride);
+        const ulonglong2 *B = reinterpret_cast<const ulonglong2 *>(b + bt * b_stride);
+        ulonglong2 *D0 = reinterpret_cast<ulonglong2 *>(d + bt * d_stride);
+        ulonglong2 *D1 = reinterpret_cast<ulonglong2 *>(d + bt * d_stride + d_poly);
+        ulonglong2 *D2 = reinterpret_cast<ulonglong2 *>(d + bt * d_stride + 2 * d_poly);
+        ulonglong2 a0 = A[r], a1 = A[per + r], b0 = B[r], b1 = B[per + r];
+        ulonglong2 o0, o1, o2;
+        o0.x = mulmod(a0.x, b0.x, m); o0.y = mulmod(a0.y, b0.y, m);
+        o1.x = addmod(mulmod(a0.x, b1.x, m), mulmod(a1.x, b0.x, m), m.q);
+        o1.y = addmod(mulmod(a0.y, b1.y, m), mulmod(a1.y, b0.y, m), m.q);
+        o2.x = mulmod(a1.x, b1.x, m); o2.y = mulmod(a1.y, b1.y, m);
+        D0[r] = o0; D1[r] = o1; D2[r] = o2;
+    }
+}
+
+// out = in * k_j (Shoup pair per limb position j = limb % period)
+__global__ void k_cmul_kernel(uint64_t *out, const uint64_t *in, const uint64_t *kp, size_t npairs, int half_n,
+                              int period, const ModQ *mods)
+{
+    GS_LOOP(i, npairs) {
+        int j = (int)((i / half_n) % period);
+        uint64_t q = mods[j].q, w = kp[2 * j], wp = kp[2 * j + 1];
+        ulonglong2 x = reinterpret_cast<const ulonglong2 *>(in)[i];
+        x.x = shoup(x.x, w, wp, q);
+        x.y = shoup(x.y, w, wp, q);
+        reinterpret_cast<ulonglong2 *>(out)[i] = x;
+    }
+}
+
+// c0 += k_j in every evaluation (adding a constant polynomial)
+__global__ void k_cadd_kernel(uint64_t *c0, const uint64_t *kv, size_t npairs, int half_n, int nl, size_t stride,
+                              const ModQ *mods)
+{
+    GS_LOOP(i, npairs) {
+        size_t per = (size_t)nl * half_n;
+        size_t bt = i / per, r = i % per;
+        int j = (int)(r / half_n);
+        uint64_t q = mods[j].q, k = kv[j];
+        ulonglong2 *p = reinterpret_cast<ulonglong2 *>(c0 + bt * stride) + r;
+        ulonglong2 x = *p;
+        x.x = addmod(x.x, k, q);
+        x.y = addmod(x.y, k, q);
+        *p = x;
+    }
+}
+
+// evaluation-form automorphism X -> X^g: position p holds the evaluation at
+// psi^(2 bitrev(p) + 1); a(X^g) there equals a at psi^((2 bitrev(p) + 1) g).
+__global__ void k_automorph_kernel(uint64_t *out, const uint64_t *in, size_t nwords, int logn, uint64_t gal)
+{
+    const uint64_t mask2n = (2ull << logn) - 1;
+    const int n = 1 << logn;
+    GS_LOOP(i, nwords) {
+        size_t limb = i >> logn;
+        uint32_t p = (uint32_t)(i & (n - 1));
+        uint32_t k = __brev(p) >> (32 - logn);
+        uint64_t e = ((2ull * k + 1) * gal) & mask2n;
+        uint32_t ks = (uint32_t)((e - 1) >> 1);
+        uint32_t ps = __brev(ks) >> (32 - logn);
+        out[i] = in[(limb << logn) + ps];
+    }
+}
+
+// out[b][t][k] = centred(in[b][k] mod q_src) reduced mod prime(t), t < dst.period
+__global__ void k_lift_kernel(const uint64_t *in, uint64_t *out, size_t nwords, int logn, int ndst, int src_prime,
+                              size_t in_stride, size_t out_stride, const ModQ *mods, LimbMap dst)
+{
+    const int n = 1 << logn;
+    const uint64_t qs = mods[src_prime].q;
+    GS_LOOP(i, nwords) {
+        size_t per = (size_t)ndst << logn;
+        size_t bt = i / per, r = i % per;
+        int t = (int)(r >> logn), k = (int)(r & (n - 1));
+        uint64_t v = in[bt * in_stride + k];
+        out[bt * out_stride + r] = lift_centered(v, qs, mods[dst.p[t]]);
+    }
+}
+
+// out[b][j][k] = (in[b][j][k] - corr[b][j][k]) * inv_j mod q_j, j < nl
+__global__ void k_combine_kernel(uint64_t *out, const uint64_t *in, const uint64_t *corr, size_t npairs, int half_n,
+                                 int nl, size_t in_stride, size_t corr_stride, size_t out_stride,
+                                 const uint64_t *inv, const ModQ *mods)
+{
+    GS_LOOP(i, npairs) {
+        size_t per = (size_t)nl * half_n;
+        size_t bt = i / per, r = i % per;
+        int j = (int)(r / half_n);
+        uint64_t q = mods[j].q, w = inv[2 * j], wp = inv[2 * j + 1];
+        ulonglong2 x = reinterpret_cast<const ulonglong2 *>(in + bt * in_stride)[r];
+        ulonglong2 y = reinterpret_cast<const ulonglong2 *>(corr + bt * corr_stride)[r];
+        ulonglong2 z;
+        z.x = shoup(submod(x.x, y.x, q), w, wp, q);
+        z.y = shoup(submod(x.y, y.y, q), w, wp, q);
+        reinterpret_cast<ulonglong2 *>(out + bt * out_stride)[r] = z;
+    }
+}
+
+// ModUp: ext[b][i][t][k] = centred(dcoef[b][i][k] mod q_i) mod prime(t), t = 0..L (L = level+1 is P)
+__global__ void k_modup_kernel(const uint64_t *dcoef, uint64_t *ext, size_t nwords, int logn, int nl, int pidx,
+                               size_t in_stride, size_t ext_stride, const ModQ *mods)
+{
+    const int n = 1 << logn, nt = nl + 1;
+    GS_LOOP(i, nwords) {
+        size_t per = (size_t)nl * nt << logn;
+        size_t bt = i / per, r = i % per;
+        int k = (int)(r & (n - 1));
+        int it = (int)(r >> logn);
+        int dig = it / nt, t = it % nt;
+        uint64_t v = dcoef[bt * in_stride + ((size_t)dig << logn) + k];
+        int tp = t < nl ? t : pidx;
+        ext[bt * ext_stride + r] = lift_centered(v, mods[dig].q, mods[tp]);
+    }
+}
+
+// inner product with the key: acc[b][p][t][k] = sum_i ext[b][i][t][k] key[i][p][kl(t)][k]
+__global__ void k_ks_inner_kernel(const uint64_t *ext, const uint64_t *key, uint64_t *acc, size_t npairs, int half_n,
+                                  int nl, int nq, size_t ext_stride, size_t acc_stride, const ModQ *mods)
+{
+    const int nt = nl + 1;
+    GS_LOOP(i, npairs) {
+        size_t per = (size_t)nt * half_n;
+        size_t bt = i / per, r = i % per;
+        int t = (int)(r / half_n);
+        size_t kk = r % half_n;
+        int kl = t < nl ? t : nq;
+        ModQ m = mods[kl];
+        const ulonglong2 *E = reinterpret_cast<const ulonglong2 *>(ext + bt * ext_stride);
+        const ulonglong2 *Kp = reinterpret_cast<const ulonglong2 *>(key);
+        uint64_t s0x = 0, s0y = 0, s1x = 0, s1y = 0;
+        for (int dg = 0; dg < nl; dg++) {
+            ulonglong2 x = E[((size_t)dg * nt + t) * half_n + kk];
+            ulonglong2 k0 = __ldg(Kp + (((size_t)dg * 2 + 0) * (nq + 1) + kl) * half_n + kk);
+            ulonglong2 k1 = __ldg(Kp + (((size_t)dg * 2 + 1) * (nq + 1) + kl) * half_n + kk);
+            s0x = addmod(s0x, mulmod(x.x, k0.x, m), m.q);
+            s0y = addmod(s0y, mulmod(x.y, k0.y, m), m.q);
+            s1x = addmod(s1x, mulmod(x.x, k1.x, m), m.q);
+            s1y = addmod(s1y, mulmod(x.y, k1.y, m), m.q);
+        }
+        ulonglong2 *A = reinterpret_cast<ulonglong2 *>(acc + bt * acc_stride);
+        A[r] = make_ulonglong2(s0x, s0y);
+        A[(size_t)nt * half_n + r] = make_ulonglong2(s1x, s1y);
+    }
+}
+
+__global__ void k_ew_kernel(int op, Str out, Str a, Str b, size_t npairs, int half_n, int npoly, int nl,
+                            const KP kp, const ModQ *mods)
+{
+    GS_LOOP(i, npairs) {
+        size_t per_poly = (size_t)nl * half_n, per_item = per_poly * npoly;
+        size_t bt = i / per_item, r = i % per_item;
+        size_t pl = r / per_poly, w = r % per_poly;
+        int j = (int)(w / half_n);
+        ModQ m = mods[j];
+        size_t off = 2 * w;
+        ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(a.p + bt * a.item + pl * a.poly + off);
+        ulonglong2 z;
+        if (op == EW_COPY) {
+            z = x;
+        } else if (op == EW_NEG) {
+            z.x = x.x ? m.q - x.x : 0;
+            z.y = x.y ? m.q - x.y : 0;
+        } else if (op == EW_CMUL) {
+            uint64_t wv = kp.w[j][0], wp = kp.w[j][1];
+            z.x = shoup(x.x, wv, wp, m.q);
+            z.y = shoup(x.y, wv, wp, m.q);
+        } else if (op == EW_CADD) {
+            z.x = addmod(x.x, kp.w[j][0], m.q);
+            z.y = addmod(x.y, kp.w[j][0], m.q);
+        } else if (op == EW_SUBMUL) {
+            ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(b.p + bt * b.item + pl * b.poly + off);
+            uint64_t wv = kp.w[j][0], wp = kp.w[j][1];
+            z.x = shoup(submod(x.x, y.x, m.q), wv, wp, m.q);
+            z.y = shoup(submod(x.y, y.y, m.q), wv, wp, m.q);
+        } else {
+            ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(b.p + bt * b.item + pl * b.poly + off);
+            if (op == EW_ADD) { z.x = addmod(x.x, y.x, m.q); z.y = addmod(x.y, y.y, m.q); }
+            else if (op == EW_SUB) { z.x = submod(x.x, y.x, m.q); z.y = submod(x.y, y.y, m.q); }
+            else { z.x = mulmod(x.x, y.x, m); z.y = mulmod(x.y, y.y, m); }
+        }
+        *reinterpret_cast<ulonglong2 *>(out.p + bt * out.item + pl * out.poly + off) = z;
+    }
+}
+
+__global__ void k_automorph_items_kernel(uint64_t *out, size_t out_item, const uint64_t *in, size_t in_item, size_t nwords,
+                                         int logn, int nl, uint64_t gal)
+{
+    const uint64_t mask2n = (2ull << logn) - 1;
+    const int n = 1 << logn;
+    GS_LOOP(i, nwords) {
+        size_t per = (size_t)nl << logn;
+        size_t bt = i / per, r = i % per;
+        size_t limb = r >> logn;
+        uint32_t p = (uint32_t)(r & (n - 1));
+        uint32_t k = __brev(p) >> (32 - logn);
+        uint64_t e = ((2ull * k + 1) * gal) & mask2n;
+        uint32_t ks = (uint32_t)((e - 1) >> 1);
+        uint32_t ps = __brev(ks) >> (32 - logn);
+        out[bt * out_item + r] = in[bt * in_item + (limb << logn) + ps];
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+void k_ew(he_ctx *c, int op, Str out, Str a, Str b, int batch, int npoly, int nl, const KP *kp, cudaStream_t s)
+{
+    static const KP zero = {};
+    size_t np = (size_t)batch * npoly * nl * (c->n / 2);
+    if (np) k_ew_kernel<<<grid_for(np), 256, 0, s>>>(op, out, a, b, np, c->n / 2, npoly, nl, kp ? *kp : zero, c->t.mod);
+}
+void k_automorph_items(he_ctx *c, uint64_t *out, size_t out_item, const uint64_t *in, size_t in_item, int batch, int nl,
+                       uint64_t gal, cudaStream_t s)
+{
+    size_t nw = (size_t)batch * nl << c->logn;
+    if (nw) k_automorph_items_kernel<<<grid_for(nw), 256, 0, s>>>(out, out_item, in, in_item, nw, c->logn, nl, gal);
+}
+void k_add(he_ctx *c, uint64_t *out, const uint64_t *a, const uint64_t *b, size_t nlimbs, const LimbMap &m, int sub, cudaStream_t s)
+{
+    size_t np = nlimbs * (size_t)(c->n / 2);
+    if (np) k_add_kernel<<<grid_for(np), 256, 0, s>>>(out, a, b, np, c->n / 2, c->t.mod, m, sub);
+}
+void k_mul(he_ctx *c, uint64_t *out, const uint64_t *a, const uint64_t *b, size_t nlimbs, const LimbMap &m, cudaStream_t s)
+{
+    size_t np = nlimbs * (size_t)(c->n / 2);
+    if (np) k_mul_kernel<<<grid_for(np), 256, 0, s>>>(out, a, b, np, c->n / 2, c->t.mod, m);
+}
+void k_tensor(he_ctx *c, const uint64_t *a, const uint64_t *b, uint64_t *d, int batch, int level,
+              size_t a_stride, size_t b_stride, size_t d_stride, size_t d_poly, cudaStream_t s)
+{
+    size_t np = (size_t)batch * (level + 1) * (c->n / 2);
+    if (np) k_tensor_kernel<<<grid_for(np), 256, 0, s>>>(a, b, d, np, c->n / 2, level + 1, a_stride, b_stride, d_stride, d_poly, c->t.mod);
+}
+void k_cmul_const(he_ctx *c, uint64_t *out, const uint64_t *in, const uint64_t *kp, size_t nlimbs, int period, cudaStream_t s)
+{
+    size_t np = nlimbs * (size_t)(c->n / 2);
+    if (np) k_cmul_kernel<<<grid_for(np), 256, 0, s>>>(out, in, kp, np, c->n / 2, period, c->t.mod);
+}
+void k_cadd_const(he_ctx *c, uint64_t *ct0, const uint64_t *kv, int batch, int level, size_t stride, cudaStream_t s)
+{
+    size_t np = (size_t)batch * (level + 1) * (c->n / 2);
+    if (np) k_cadd_kernel<<<grid_for(np), 256, 0, s>>>(ct0, kv, np, c->n / 2, level + 1, stride, c->t.mod);
+}
+void k_automorph(he_ctx *c, uint64_t *out, const uint64_t *in, size_t nlimbs, uint64_t gal, cudaStream_t s)
+{
+    size_t nw = nlimbs << c->logn;
+    if (nw) k_automorph_kernel<<<grid_for(nw), 256, 0, s>>>(out, in, nw, c->logn, gal);
+}
+void k_lift(he_ctx *c, const uint64_t *in, uint64_t *out, int batch, int src_prime, size_t in_stride,
+            const LimbMap &dst, size_t out_stride, cudaStream_t s)
+{
+    size_t nw = (size_t)batch * dst.period << c->logn;
+    if (nw) k_lift_kernel<<<grid_for(nw), 256, 0, s>>>(in, out, nw, c->logn, dst.period, src_prime, in_stride, out_stride, c->t.mod, dst);
+}
+void k_rescale_combine(he_ctx *c, uint64_t *out, const uint64_t *in, const uint64_t *corr, int batch, int nl,
+                       size_t in_stride, size_t corr_stride, size_t out_stride, const uint64_t *inv_pairs, cudaStream_t s)
+{
+    size_t np = (size_t)batch * nl * (c->n / 2);
+    if (np) k_combine_kernel<<<grid_for(np), 256, 0, s>>>(out, in, corr, np, c->n / 2, nl, in_stride, corr_stride, out_stride, inv_pairs, c->t.mod);
+}
+void k_modup(he_ctx *c, const uint64_t *dcoef, const uint64_t *dntt, uint64_t *ext, int batch, int level,
+             size_t in_stride, size_t ext_stride, cudaStream_t s)
+{
+    (void)dntt;
+    int nl = level + 1;
+    size_t nw = (size_t)batch * nl * (nl + 1) << c->logn;
+    if (nw) k_modup_kernel<<<grid_for(nw), 256, 0, s>>>(dcoef, ext, nw, c->logn, nl, c->nq, in_stride, ext_stride, c->t.mod);
+}
+void k_ks_inner(he_ctx *c, const uint64_t *ext, const uint64_t *key, uint64_t *acc, int batch, int level,
+                size_t ext_stride, size_t acc_stride, cudaStream_t s)
+{
+    int nl = level + 1;
+    size_t np = (size_t)batch * (nl + 1) * (c->n / 2);
+    if (np) k_ks_inner_kernel<<<grid_for(np), 256, 0, s>>>(ext, key, acc, np, c->n / 2, nl, c->nq, ext_stride, acc_stride, c->t.mod);
+}

@@ -1,0 +1,277 @@
+"""Parity of the CUDA path with the CPU oracle, element by element.
+
+Ciphertext, plaintext and transform words must be identical (integer work is
+bit-exact); decoded doubles must be identical too, because both sides run the
+same FP64 butterfly network without contraction.  Inputs are seeded and
+synthetic.  All calls go through the C ABI (binding.py).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from oracle import qgnag  # noqa: E402
+from oracle.ckks import Ckks, Ct as OCt  # noqa: E402
+from paper_2406_13221_gb300 import binding, build, synth  # noqa: E402
+
+build.build()
+D = 2.0 ** 40
+
+
+def bitrev(x, bits):
+    return int(format(x, "0%db" % bits)[::-1], 2)
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
+
+
+def from_dev(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy().view(np.uint64)
+
+
+@pytest.mark.parametrize("logn", [10, 11, 12, 13, 14, 15, 16])
+@pytest.mark.parametrize("nlimbs", [1, 3, 37])
+def test_ntt_matches_oracle(logn, nlimbs):
+    nq = 3
+    ctx = binding.Context(logn, nq)
+    he = Ckks(logn, nq)
+    assert ctx.primes == he.primes
+    n = 1 << logn
+    rng = np.random.default_rng(logn * 100 + nlimbs)
+    period = nq + 1
+    prime_of = [(i * 3 + 1) % period for i in range(period)]
+    data = np.zeros((nlimbs, n), np.uint64)
+    for i in range(nlimbs):
+        q = he.primes[prime_of[i % period]]
+        data[i] = rng.integers(0, q, n, dtype=np.uint64)
+    dev = to_dev(data)
+    ctx.ntt_forward(dev.data_ptr(), nlimbs, prime_of)
+    got = from_dev(dev).reshape(nlimbs, n)
+    perm = np.array([bitrev(p, logn) for p in range(n)])
+    check = range(nlimbs) if n <= 8192 else [0, nlimbs - 1]
+    for i in check:
+        ref = data[i].copy()
+        he.L.orc_ntt(he.ctx, prime_of[i % period], ref.ctypes.data_as(__import__("ctypes").c_void_p))
+        assert np.array_equal(got[i], ref[perm]), "limb %d" % i
+    ctx.ntt_inverse(dev.data_ptr(), nlimbs, prime_of)
+    assert np.array_equal(from_dev(dev).reshape(nlimbs, n), data)
+
+
+@pytest.fixture(scope="module")
+def pair():
+    """GPU context and oracle with identical parameters and keys (N = 2^13)."""
+    logn, nq = 13, 9
+    ctx = binding.Context(logn, nq)
+    he = Ckks(logn, nq)
+    rots = [1, 2, 4, 8, -1, -2, -4, -8, 3, 100, -77] + [16 << k for k in range(8)]
+    ctx.keygen(2, rots)
+    he.keygen(2, rots)
+    return ctx, he
+
+
+def rand_slots(n, seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-scale, scale, n) + 1j * rng.uniform(-scale, scale, n)
+
+
+def test_secret_key_and_encode_bitwise(pair):
+    ctx, he = pair
+    z = rand_slots(ctx.nslots, 1, 3.0)
+    for level, scale in ((8, D), (3, 2.0 ** 35), (0, float(he.q[0]) / 7)):
+        words, lv, sc = ctx.encode(z, level, scale).export()
+        ref = he.encode(z, level, scale)
+        assert lv == level and sc == scale
+        assert np.array_equal(words, ref.data)
+
+
+def test_ragged_and_empty_slot_vectors(pair):
+    ctx, he = pair
+    for k in (0, 1, 1000, ctx.nslots):
+        z = rand_slots(k, 2) if k else np.zeros(0, complex)
+        words, _, _ = ctx.encode(z, 2, D).export()
+        assert np.array_equal(words, he.encode(z, 2, D).data)
+
+
+def test_decode_bitwise(pair):
+    ctx, he = pair
+    z = rand_slots(ctx.nslots, 3)
+    pt = ctx.encode(z, 4, D)
+    words, lv, sc = pt.export()
+    from oracle.ckks import Pt as OPt
+    ref = he.decode(OPt(words, lv, sc))
+    got = ctx.decode(pt)
+    assert np.array_equal(got.real.view(np.uint64), ref.real.view(np.uint64))
+    assert np.array_equal(got.imag.view(np.uint64), ref.imag.view(np.uint64))
+
+
+def test_encrypt_decrypt_bitwise(pair):
+    ctx, he = pair
+    z = rand_slots(ctx.nslots, 4)
+    for level in (8, 5):
+        ct = ctx.encrypt(ctx.encode(z, level, D), 11)
+        ref = he.encrypt(he.encode(z, level, D), 11)
+        assert np.array_equal(ct.export(), ref.data)
+        words, _, _ = ctx.decrypt(ct).export()
+        assert np.array_equal(words, he.decrypt(ref).data)
+
+
+def enc_pair(ctx, he, z, seed, level=8, scale=D):
+    ref = he.encrypt(he.encode(z, level, scale), seed)
+    return ctx.import_ct(ref.data, level, scale), ref
+
+
+def test_add_sub_mul_rescale_bitwise(pair):
+    ctx, he = pair
+    a, ra = enc_pair(ctx, he, rand_slots(ctx.nslots, 5), 21)
+    b, rb = enc_pair(ctx, he, rand_slots(ctx.nslots, 6), 22)
+    assert np.array_equal(ctx.add(a, b).export(), he.add(ra, rb).data)
+    assert np.array_equal(ctx.sub(a, b).export(), he.sub(ra, rb).data)
+    m = ctx.mul(a, b)
+    rm = he.mul(ra, rb)
+    assert np.array_equal(m.export(), rm.data)
+    assert m.scale == rm.scale
+    r = ctx.rescale(m)
+    rr = he.rescale(rm)
+    assert np.array_equal(r.export(), rr.data)
+    assert (r.level, r.scale) == (rr.level, rr.scale)
+    # a chain down to level 1 exercises every limb count of the key switch
+    x, rx = r, rr
+    while x.level > 1:
+        y = ctx.moddrop(b, x.level)
+        x = ctx.rescale(ctx.mul(x, y))
+        rx = he.rescale(he.mul(rx, he.moddrop(rb, rx.level)))
+        assert np.array_equal(x.export(), rx.data), x.level
+
+
+@pytest.mark.parametrize("r", [1, -1, 3, 100, -77, 16, 2048])
+def test_rotation_bitwise(pair, r):
+    ctx, he = pair
+    a, ra = enc_pair(ctx, he, rand_slots(ctx.nslots, 7), 23)
+    assert np.array_equal(ctx.rotate(a, r).export(), he.rotate(ra, r).data)
+    a3 = ctx.moddrop(a, 3)
+    assert np.array_equal(ctx.rotate(a3, r).export(), he.rotate(he.moddrop(ra, 3), r).data)
+
+
+def test_constants_and_plaintext_product_bitwise(pair):
+    ctx, he = pair
+    a, ra = enc_pair(ctx, he, rand_slots(ctx.nslots, 8), 24)
+    for c, s in ((-0.37, D), (0.0015 * 2, D), (1e-6, float(he.q[8]))):
+        x = ctx.cmul(a, c, s)
+        rx = he.cmul(ra, c, s)
+        assert np.array_equal(x.export(), rx.data)
+        assert x.scale == rx.scale
+    assert np.array_equal(ctx.cadd(a, 0.625).export(), he.cadd(ra, 0.625).data)
+    assert np.array_equal(ctx.cadd(a, -3.25).export(), he.cadd(ra, -3.25).data)
+    z = rand_slots(ctx.nslots, 9)
+    p = ctx.encode(z, 8, float(he.q[8]))
+    rp = he.encode(z, 8, float(he.q[8]))
+    assert np.array_equal(ctx.ptmul(a, p).export(), he.ptmul(ra, rp).data)
+
+
+def test_batched_keyswitch_bitwise(pair):
+    """he_keyswitch_batch on 5 polynomials (ragged batch) equals the oracle's key switch."""
+    ctx, he = pair
+    level, batch = 6, 5
+    rng = np.random.default_rng(10)
+    n = ctx.n
+    polys = np.zeros((batch, level + 1, n), np.uint64)
+    for b in range(batch):
+        for j in range(level + 1):
+            polys[b, j] = rng.integers(0, he.q[j], n, dtype=np.uint64)
+    gal = he.galois_elt(3)
+    dev = to_dev(polys)
+    ctx.ntt_forward(dev.data_ptr(), batch * (level + 1), list(range(level + 1)))
+    out = torch.zeros(batch * 2 * (level + 1) * n, dtype=torch.int64, device="cuda")
+    ctx.keyswitch_batch(dev.data_ptr(), out.data_ptr(), batch, level, gal)
+    ctx.ntt_inverse(out.data_ptr(), batch * 2 * (level + 1), list(range(level + 1)))
+    got = from_dev(out).reshape(batch, 2, level + 1, n)
+    for b in range(batch):
+        assert np.array_equal(got[b], he.keyswitch(level, gal, polys[b]))
+
+
+def test_errors_are_reported(pair):
+    ctx, he = pair
+    a, _ = enc_pair(ctx, he, rand_slots(ctx.nslots, 11), 25)
+    b = ctx.cmul(a, 1.0, 3.0)  # scale 3 * 2^40
+    with pytest.raises(binding.HeError) as e:
+        ctx.add(a, b)
+    assert e.value.code == binding.HE_ESCALE
+    with pytest.raises(binding.HeError) as e:
+        ctx.rotate(a, 5)  # no key for 5
+    assert e.value.code == binding.HE_EKEY
+    low = ctx.moddrop(a, 0)
+    with pytest.raises(binding.HeError) as e:
+        ctx.rescale(low)
+    assert e.value.code == binding.HE_ELEVEL
+    with pytest.raises(binding.HeError) as e:
+        ctx.add(a, low)
+    assert e.value.code == binding.HE_ELEVEL
+
+
+# ------------------------------------------------------------------ the iteration
+@pytest.fixture(scope="module")
+def small_job_inputs(pair):
+    ctx, he = pair
+    X, y = synth.small()
+    data = qgnag.TrainData(X, y, g=16, m=256, batch_rows=1024)
+    circ = qgnag.Circuit(he, 16, 256, D)
+    return ctx, he, data, circ
+
+
+def test_iteration_bitwise(small_job_inputs):
+    ctx, he, data, circ = small_job_inputs
+    L = 8
+    Z = [he.encrypt(he.encode(data.blocks[b], L, D), 100 + b) for b in range(data.blocks.shape[0])]
+    B = he.encrypt(he.encode(np.tile(data.n * data.bbar_full, circ.m), L, D), 200)
+    rng = np.random.default_rng(12)
+    w0 = np.tile(np.r_[rng.uniform(-0.5, 0.5, data.f1), np.zeros(16 - data.f1)], circ.m)
+    v0 = np.tile(np.r_[rng.uniform(-0.5, 0.5, data.f1), np.zeros(16 - data.f1)], circ.m)
+    W = he.encrypt(he.encode(w0, L, D), 201)
+    V = he.encrypt(he.encode(v0, L, D), 202)
+    alpha, eta = qgnag.schedule(1), qgnag.nag_scalars(2)[1]
+    Wn, Vn = circ.iteration(Z, B, W, V, alpha, eta, 1.0 / data.n)
+    g = lambda c: ctx.import_ct(c.data, c.level, c.scale)  # noqa: E731
+    gW, gV = binding.lr_iteration(ctx, [g(z) for z in Z], g(B), g(W), g(V), 16, 256, alpha, eta,
+                                  1.0 / data.n, qgnag.G8)
+    assert (gW.level, gW.scale) == (Wn.level, Wn.scale)
+    assert np.array_equal(gW.export(), Wn.data)
+    assert np.array_equal(gV.export(), Vn.data)
+    # refresh of both
+    for x, rx, seed in ((gW, Wn, 301), (gV, Vn, 302)):
+        assert np.array_equal(ctx.refresh(x, D, seed).export(), circ.refresh(rx, seed).data)
+
+
+def test_job_step_bitwise_and_weights(small_job_inputs):
+    ctx, he, data, circ = small_job_inputs
+    X, y = synth.small()
+    job = binding.Job(ctx, X, y, binding.FULL_BATCH, 1024, binding.G8, 40.0, enc_seed=3, key_seed=2)
+    st = job.stats()
+    assert (st.n_blocks, st.g, st.m) == (4, 16, 256)
+    # encrypted data blocks equal the oracle's encryption of the same packing
+    for b in range(4):
+        ref = he.encrypt(he.encode(data.blocks[b], 8, D), qgnag.obj_seed(3, qgnag.SEED_BLOCK, b))
+        assert np.array_equal(job.input(0, b).export(), ref.data)
+    Bg = job.input(1, 0)
+    Z = [OCt(job.input(0, b).export(), 8, D) for b in range(4)]
+    B = OCt(Bg.export(), 8, D)
+    (Ww, _, _), (Vw, _, _) = job.state_words()
+    W, V = OCt(Ww, 8, D), OCt(Vw, 8, D)
+    etas = qgnag.nag_scalars(2)
+    for t in range(2):
+        job.step(t)
+        Wn, Vn = circ.iteration(Z, B, W, V, qgnag.schedule(t), etas[t], 1.0 / data.n)
+        W = circ.refresh(Wn, qgnag.obj_seed(3, qgnag.SEED_WREF, t))
+        V = circ.refresh(Vn, qgnag.obj_seed(3, qgnag.SEED_VREF, t))
+        (Ww, _, _), (Vw, _, _) = job.state_words()
+        assert np.array_equal(Ww, W.data), t
+        assert np.array_equal(Vw, V.data), t
+    from oracle import plain
+    wp = plain.train(data, 2)
+    for row in (0, 255):
+        assert np.abs(job.weights(row) - wp).max() < 1e-3
