@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark: encrypted quadratic-gradient NAG logistic-regression training.
+
+One step = one full-batch QG-NAG iteration (gradient over every encrypted data
+block, quadratic gradient, NAG update, refresh of W and V) on synthetic data
+shaped like the paper's Financial workload: 422,108 samples x 200 features,
+N = 2^16, 9 ciphertext primes (one 60-bit, eight 40-bit) and a 60-bit special
+prime, scale 2^40, 128 x 256 packing (3,298 blocks).  Data blocks are resident
+in HBM (29 GiB, far larger than L2) before timing starts.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank trains an independent
+replica of the job on its GPU (the method shards into independent jobs; no
+collective on the data path); value = max-over-ranks time / (N * K).
+"""
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import signal
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "enc. QG-NAG sec/iter at 422,108x200 (N=2^16); keyswitch/s; batched vs plain GPU"
+N_SAMPLES, N_FEAT, LOGN, NQ, LOG_SCALE = 422108, 200, 16, 9, 40.0
+PAPER_CONTEXT = {"paper_full_batch_update_s": 60.0, "paper_full_batch_iter_s": 90.0,
+                 "paper_hardware": "8 vCPUs, HEAAN (non-RNS), Q=2^275, Delta=2^30"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--chunk", type=int, default=0, help="data blocks per launch (0 = library default)")
+    ap.add_argument("--rows", type=int, default=N_SAMPLES)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-twin", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ------------------------------------------------------------------ clocks
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def clocks_start(dev):
+    f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    try:
+        p = subprocess.Popen(["nvidia-smi", "-i", str(dev), "--query-gpu=" + CLOCK_Q, "--format=csv,noheader,nounits",
+                              "-lms", "200"], stdout=f, stderr=subprocess.DEVNULL)
+    except OSError:
+        p = None
+    return p, f.name
+
+
+def clocks_stop(handle):
+    p, path = handle
+    if p is not None:
+        p.send_signal(signal.SIGTERM)
+        try:
+            p.wait(5)
+        except subprocess.TimeoutExpired:
+            p.kill()
+    rows = []
+    try:
+        for line in open(path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                rows.append(parts)
+        os.unlink(path)
+    except OSError:
+        pass
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+    sm = sorted(float(r[1]) for r in rows)
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+    return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(rows[0][2]), "reasons": reasons, "samples": len(rows),
+            "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# ------------------------------------------------------------------ roofline inputs
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+def recorded_traffic(kernel):
+    """Bytes per launch recorded by an ncu capture (profiles/traffic.txt) for the
+    current source of the kernel; None when the kernel changed since."""
+    src = open(os.path.join(ROOT, "paper_2406_13221_gb300", "csrc", "ntt.cu"), "rb").read()
+    h = hashlib.sha256(src).hexdigest()[:12]
+    try:
+        for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
+            p = line.split()
+            if len(p) >= 3 and not line.startswith("#") and p[0] == kernel and p[1] == h:
+                return float(p[2])
+    except OSError:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args, rank, world):
+    import torch
+    from paper_2406_13221_gb300 import binding, build, synth
+
+    build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    dev = torch.cuda.current_device()
+    t0 = time.time()
+    X, y = synth.financial(seed=1, n=args.rows)
+    ctx = binding.Context(LOGN, NQ)
+    job = binding.Job(ctx, X, y, binding.FULL_BATCH, 1024, binding.G8, LOG_SCALE, enc_seed=3, key_seed=2,
+                      batch_blocks=args.chunk)
+    info = job.stats()
+    setup_s = time.time() - t0
+    sched = (2.0, 1.0, 81.0, 2.5)
+    t = 0
+    for _ in range(args.warmup):
+        job.step(t, sched)
+        t += 1
+    # ---------------- timed region (device-resident inputs)
+    ctx.prof_enable(True)
+    l0 = binding.launch_count()
+    clk = clocks_start(dev)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        job.step(t, sched)
+        t += 1
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clocks_stop(clk)
+    launches = binding.launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    prof = {name: ctx.prof_read(i) for i, name in enumerate(["ntt_fwd", "ntt_inv", "modup", "ks_inner"])}
+    ctx.prof_enable(False)
+    st = job.stats()
+    ms_max = allreduce_max(ms, world)
+    sec_iter = ms_max / 1000.0 / (args.steps * world)
+    ks_per_iter = int(st.keyswitches)
+    err = None
+    if not args.no_twin:
+        err = twin_error(X, y, job, t, sched)
+    # ---------------- batched vs plain one-ciphertext-per-launch
+    plain = None
+    if not args.no_plain:
+        job.set_batch(1)
+        job.step(t, sched)
+        t += 1
+        torch.cuda.synchronize()
+        p0 = time.time()
+        job.step(t, sched)
+        t += 1
+        torch.cuda.synchronize()
+        plain = time.time() - p0
+        job.set_batch(info_chunk(job, args))
+    # ---------------- end to end through the public API with host state
+    e2e = None
+    if not args.no_e2e:
+        ctw = 2 * NQ * (1 << LOGN)
+        sin = pinned_u64(2 * ctw)
+        sout = pinned_u64(2 * ctw)
+        job.step_io(t, None, sout, sched)
+        t += 1
+        sin[:] = sout
+        torch.cuda.synchronize()
+        h0 = time.time()
+        for _ in range(args.steps):
+            job.step_io(t, sin, sout, sched)
+            sin[:] = sout
+            t += 1
+        torch.cuda.synchronize()
+        e2e_s = allreduce_max(time.time() - h0, world) / (args.steps * world)
+        e2e = {"value": round(e2e_s, 5), "unit": "s/iter", "h2d_bytes_per_step": int(sin.nbytes),
+               "d2h_bytes_per_step": int(sout.nbytes)}
+    roof = roofline(prof, args.steps)
+    out = {
+        "metric": METRIC, "value": round(sec_iter, 5), "unit": "s/iter", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "full-batch QG-NAG, %d x %d synthetic Financial-shaped data, N=2^16, "
+                               "chain 60+8x40 bits + 60-bit P, scale 2^40, 128x256 packing, g8 sigmoid" % (args.rows, N_FEAT),
+                   "blocks": int(info.n_blocks), "blocks_per_launch": info_chunk(job, args),
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "no flush: %.1f GiB of encrypted data blocks > 129 MB L2" % (info.n_blocks * ctw_bytes() / 2 ** 30)},
+        "keyswitch_per_s": round(ks_per_iter / sec_iter / world, 1) if sec_iter else None,
+        "keyswitches_per_iter": ks_per_iter,
+        "ntt_limbs_per_s": round((prof["ntt_fwd"][1] + prof["ntt_inv"][1]) / args.steps / (sec_iter * world), 1),
+        "plain_one_ct_per_launch_s_per_iter": round(plain, 4) if plain else None,
+        "batched_speedup_vs_plain": round(plain / sec_iter / world, 2) if plain else None,
+        "setup_s": round(setup_s, 1),
+        "max_abs_err_vs_fp64_twin": err,
+        "clocks": clocks, "gpu_launches": int(launches), "roofline": roof, "e2e": e2e,
+        "context": PAPER_CONTEXT,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(X, y, samples=1)
+    return out
+
+
+def ctw_bytes():
+    return 2 * NQ * (1 << LOGN) * 8
+
+
+def info_chunk(job, args):
+    return args.chunk if args.chunk else 16
+
+
+_PINNED = []
+
+
+def pinned_u64(n):
+    import torch
+    t = torch.empty(n, dtype=torch.int64, pin_memory=True)
+    _PINNED.append(t)  # keep the pinned storage alive
+    return t.numpy().view(np.uint64)
+
+
+def roofline(prof, steps):
+    """Dominant kernel class by measured time; algorithmic bytes per launch over
+    its average launch-group duration against the measured HBM peak."""
+    peaks = measured_peaks()
+    n = 1 << LOGN
+    best = max(prof, key=lambda k: prof[k][0])
+    ms, units, launches = prof[best]
+    groups = launches / (2 if best.startswith("ntt") else 1)
+    if best.startswith("ntt"):
+        alg_bytes = 16.0 * n * units           # each limb read and written once
+    elif best == "modup":
+        alg_bytes = 8.0 * n * units * (1 + 1.0 / 10)  # write every lifted limb, read each digit once
+    else:
+        alg_bytes = 8.0 * n * units * (2 * 9 * 10 + 2 * 10)  # upper bound at 9 limbs
+    per_launch = alg_bytes / groups if groups else 0
+    dur = ms / 1000.0 / groups if groups else 0
+    achieved = per_launch / dur / 1e9 if dur else 0
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    tr = recorded_traffic(best)
+    return {"kernel": best, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": tr, "alg_bytes_per_launch": per_launch,
+            "avg_launch_ms": round(dur * 1000, 4), "launch_groups": int(groups),
+            "share_of_step": round(ms / sum(v[0] for v in prof.values()), 3) if ms else None,
+            "classes_ms_per_step": {k: round(v[0] / steps, 2) for k, v in prof.items()},
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "fallback" not in peaks else "fallback"}
+
+
+def twin_error(X, y, job, iters, sched):
+    """Decrypted W (rows 0 and m-1) against the FP64 plaintext run of the same iterations."""
+    from oracle import plain, qgnag
+    data = qgnag.TrainData(X, y, g=256, m=128, batch_rows=1024)
+    wp = plain.train(data, iters, sched=sched)
+    err = max(float(np.abs(job.weights(r) - wp).max()) for r in (0, 127))
+    return err
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_baseline(X, y, samples=1, steps=1, warmup=0):
+    """The CPU oracle on a bounded sample of the same workload: Steps 1-6 on
+    `samples` data blocks plus Steps 7-9 and the refresh once, at N = 2^16;
+    sec/iter extrapolated linearly to all blocks (key generation untimed)."""
+    from oracle import qgnag
+    from oracle.ckks import Ckks
+    cores = os.cpu_count()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    data = qgnag.TrainData(X, y, g=256, m=128, batch_rows=1024)
+    he = Ckks(LOGN, NQ)
+    circ = qgnag.Circuit(he, 256, 128, 2.0 ** LOG_SCALE)
+    k0 = time.time()
+    he.keygen(2, circ.rotations())
+    keygen_s = time.time() - k0
+    L, D = NQ - 1, 2.0 ** LOG_SCALE
+    Z = [he.encrypt(he.encode(data.blocks[b], L, D), qgnag.obj_seed(3, 1, b)) for b in range(samples)]
+    B = he.encrypt(he.encode(np.tile(data.n * data.bbar_full, 128), L, D), qgnag.obj_seed(3, 2, 0))
+    W = he.encrypt(he.encode(np.zeros(he.nslots), L, D), 5)
+    V = he.encrypt(he.encode(np.zeros(he.nslots), L, D), 6)
+    vals = []
+    for i in range(warmup + steps):
+        t0 = time.time()
+        acc = None
+        for z in Z:
+            g = circ.block_grad(z, W, 2.0)
+            acc = g if acc is None else he.add(acc, g)
+        t1 = time.time()
+        Wn, Vn = circ.finish(acc, B, W, V, 0.99, 1.0 / data.n)
+        circ.refresh(Wn, 7)
+        circ.refresh(Vn, 8)
+        t2 = time.time()
+        est = (t1 - t0) / samples * data.blocks.shape[0] + (t2 - t1)
+        if i >= warmup:
+            vals.append(est)
+    return {"value": round(float(np.mean(vals)), 1), "unit": "s/iter", "cores": cores, "kind": "oracle",
+            "sample": "Steps 1-6 on %d of %d blocks + Steps 7-9 and refresh once, N=2^16, extrapolated "
+                      "linearly to all blocks; keygen (%.0f s) untimed" % (samples, data.blocks.shape[0], keygen_s)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from paper_2406_13221_gb300 import synth
+    X, y = synth.financial(seed=1, n=args.rows)
+    cb = cpu_baseline(X, y, samples=1, steps=args.steps, warmup=args.warmup)
+    return {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "s/iter", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "full-batch QG-NAG, %d x %d synthetic Financial-shaped data, N=2^16, "
+                                   "chain 60+8x40 bits + 60-bit P, scale 2^40, 128x256 packing, g8 sigmoid" % (args.rows, N_FEAT)},
+            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "s/iter", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -146,6 +146,16 @@ int he_ntt_inverse(he_ctx *ctx, uint64_t *d_limbs, size_t n_limbs, const int *pr
  * allocated by the call. */
 int he_keyswitch_batch(he_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int batch, int level,
                        uint64_t gal);
+/* Number of kernels this library has launched since it was loaded. */
+uint64_t he_launch_count(void);
+/* Per-class kernel timing with CUDA events on the context stream (adds two
+ * event records per timed launch group).  Classes: 0 forward NTT, 1 inverse
+ * NTT, 2 ModUp lift, 3 key-switch inner product.  Enabling resets the sums;
+ * he_prof_read synchronises the stream and returns the summed milliseconds,
+ * the work units (limbs for transforms, digit x modulus limbs for ModUp,
+ * key switches for the inner product) and the kernel launches of the class. */
+int he_prof_enable(he_ctx *ctx, int on);
+int he_prof_read(he_ctx *ctx, int cls, double *ms, double *units, uint64_t *launches);
 /* Galois element of a left rotation by r. */
 uint64_t he_galois_elt(const he_ctx *ctx, int64_t r);
 
@@ -188,6 +198,15 @@ int he_lr_job_create(he_ctx *ctx, const double *X, const double *y, size_t n, si
  * quadratic gradient, NAG update (Algorithm 1) and the refresh of W and V
  * (decrypt + re-encrypt, standing in for bootstrapping). */
 int he_lr_job_step(he_lr_job *job, int t, he_lr_sched sched);
+/* he_lr_job_step with the job state on the host: when state_in is not NULL,
+ * W and V are first loaded from coefficient words [2 ciphertexts][2][n_q][N]
+ * (W then V, top level, scale 2^log_scale); when state_out is not NULL, the
+ * refreshed W and V are written back in the same layout.  Host buffers may be
+ * pinned; the copies run on the context stream inside the call. */
+int he_lr_job_step_io(he_lr_job *job, int t, he_lr_sched sched, const uint64_t *state_in, uint64_t *state_out);
+/* Data blocks per kernel launch for later steps: 1 = the plain
+ * one-ciphertext-per-launch form; at most the value the job was created with. */
+int he_lr_job_set_batch(he_lr_job *job, int blocks_per_launch);
 /* Decrypted weights W (slots of row `row`, g values; padded columns are 0). */
 int he_lr_job_weights(he_lr_job *job, int row, double *w, size_t len);
 /* Access to the job's current W and V ciphertexts (owned by the job). */

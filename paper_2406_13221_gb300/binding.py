@@ -86,6 +86,11 @@ SIGNATURES = {
     "he_lr_job_block_grad": (_i, [_vp, _i, _d, _pp]),
     "he_lr_job_input": (_i, [_vp, _i, _i, _pp]),
     "he_lr_job_info": (_i, [_vp, ctypes.POINTER(he_lr_stats)]),
+    "he_lr_job_step_io": (_i, [_vp, _i, he_lr_sched, _vp, _vp]),
+    "he_launch_count": (_u64, []),
+    "he_lr_job_set_batch": (_i, [_vp, _i]),
+    "he_prof_enable": (_i, [_vp, _i]),
+    "he_prof_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_u64)]),
     "he_lr_job_free": (_i, [_vp]),
     "he_lr_train": (_i, [_vp, _vp, _vp, _sz, _sz, _i, he_lr_sched, _i, _sz, _i, _u64, _u64, _vp, _sz,
                          ctypes.POINTER(he_lr_stats)]),
@@ -231,6 +236,14 @@ class Context:
         p = np.asarray(prime_of, np.int32)
         self.check(self.L.he_ntt_inverse(self.h, dptr, nlimbs, _ptr(p), len(p)))
 
+    def prof_enable(self, on=True):
+        self.check(self.L.he_prof_enable(self.h, int(on)))
+
+    def prof_read(self, cls):
+        ms, units, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
+        self.check(self.L.he_prof_read(self.h, cls, ctypes.byref(ms), ctypes.byref(units), ctypes.byref(n)))
+        return ms.value, units.value, n.value
+
     def keyswitch_batch(self, din, dout, batch, level, gal):
         self.check(self.L.he_keyswitch_batch(self.h, din, dout, batch, level, gal))
 
@@ -307,6 +320,15 @@ class Job:
     def step(self, t, sched=(2.0, 1.0, 81.0, 2.5)):
         self.ctx.check(self.ctx.L.he_lr_job_step(self.h, t, he_lr_sched(*sched)))
 
+    def step_io(self, t, state_in, state_out, sched=(2.0, 1.0, 81.0, 2.5)):
+        """One step with W, V loaded from / written to host words (numpy uint64)."""
+        pin = None if state_in is None else state_in.ctypes.data_as(ctypes.c_void_p)
+        pout = None if state_out is None else state_out.ctypes.data_as(ctypes.c_void_p)
+        self.ctx.check(self.ctx.L.he_lr_job_step_io(self.h, t, he_lr_sched(*sched), pin, pout))
+
+    def set_batch(self, blocks_per_launch):
+        self.ctx.check(self.ctx.L.he_lr_job_set_batch(self.h, int(blocks_per_launch)))
+
     def weights(self, row=0):
         w = np.zeros(self.info.g)
         self.ctx.check(self.ctx.L.he_lr_job_weights(self.h, row, _ptr(w), len(w)))
@@ -362,6 +384,10 @@ def lr_iteration(ctx, Z, B, W, V, g, m, alpha, eta, inv_n, poly):
     ctx.check(ctx.L.he_lr_iteration(ctx.h, arr, len(Z), B.h, W.h, V.h, g, m, float(alpha), float(eta),
                                     float(inv_n), _ptr(p), ctypes.byref(Wo), ctypes.byref(Vo)))
     return Ct(ctx, Wo), Ct(ctx, Vo)
+
+
+def launch_count():
+    return int(load().he_launch_count())
 
 
 def gauss_table(sigma):

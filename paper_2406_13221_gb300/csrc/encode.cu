@@ -216,8 +216,8 @@ int helr_sample(he_ctx *c, uint64_t *out, size_t nlimbs, const LimbMap &lm, uint
 {
     size_t nw = nlimbs << c->logn;
     if (!nw) return HE_OK;
-    k_sample_kernel<<<grid_for(nw), 256, 0, c->stream>>>(out, nw, c->logn, lm, mix64(seed), stream, kind, c->t.cdt,
-                                                        c->cdt_len, c->t.mod);
+    HELR_LAUNCH(k_sample_kernel<<<grid_for(nw), 256, 0, c->stream>>>(out, nw, c->logn, lm, mix64(seed), stream, kind, c->t.cdt,
+                                                        c->cdt_len, c->t.mod));
     HELR_CUDA(c, cudaGetLastError());
     return HE_OK;
 }
@@ -235,11 +235,11 @@ int helr_encode_dev(he_ctx *c, const double *d_re, const double *d_im, int batch
     double *vr = v, *vi = v + (size_t)batch * ns;
     HELR_CUDA(c, cudaMemsetAsync(err, 0, sizeof(int), c->stream));
     size_t work = (size_t)batch * ns;
-    k_enc_scatter<<<grid_for(work), 256, 0, c->stream>>>(d_re, d_im, vr, vi, ns, logns, c->t.sidx, batch, in_stride);
+    HELR_LAUNCH(k_enc_scatter<<<grid_for(work), 256, 0, c->stream>>>(d_re, d_im, vr, vi, ns, logns, c->t.sidx, batch, in_stride));
     for (int len = 2; len <= ns; len <<= 1)
-        k_fft_stage<<<grid_for(work / 2), 256, 0, c->stream>>>(vr, vi, ns, batch, len, 1, c->t.zeta);
-    k_enc_finish<<<grid_for(work), 256, 0, c->stream>>>(vr, vi, d_out, ns, c->logn, level + 1, scale, c->t.zeta,
-                                                       c->t.mod, batch, out_stride, err);
+        HELR_LAUNCH(k_fft_stage<<<grid_for(work / 2), 256, 0, c->stream>>>(vr, vi, ns, batch, len, 1, c->t.zeta));
+    HELR_LAUNCH(k_enc_finish<<<grid_for(work), 256, 0, c->stream>>>(vr, vi, d_out, ns, c->logn, level + 1, scale, c->t.zeta,
+                                                       c->t.mod, batch, out_stride, err));
     HELR_CUDA(c, cudaGetLastError());
     int herr = 0;
     HELR_CUDA(c, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -261,10 +261,10 @@ int helr_decode_dev(he_ctx *c, const uint64_t *d_pt, double scale, double *d_re,
     HELR_TRY(helr_alloc(c, (void **)&coef, sizeof(uint64_t) * c->n));
     HELR_TRY(helr_alloc(c, (void **)&v, sizeof(double) * 2 * ns));
     HELR_TRY(helr_ntt_inv_oop(c, d_pt, coef, 1, limbmap_single(0), c->stream));
-    k_dec_start<<<grid_for(ns), 256, 0, c->stream>>>(coef, v, v + ns, ns, logns, c->q[0], c->t.zeta);
+    HELR_LAUNCH(k_dec_start<<<grid_for(ns), 256, 0, c->stream>>>(coef, v, v + ns, ns, logns, c->q[0], c->t.zeta));
     for (int len = 2; len <= ns; len <<= 1)
-        k_fft_stage<<<grid_for(ns / 2), 256, 0, c->stream>>>(v, v + ns, ns, 1, len, 0, c->t.zeta);
-    k_dec_finish<<<grid_for(ns), 256, 0, c->stream>>>(v, v + ns, d_re, d_im, ns, c->t.sidx, scale);
+        HELR_LAUNCH(k_fft_stage<<<grid_for(ns / 2), 256, 0, c->stream>>>(v, v + ns, ns, 1, len, 0, c->t.zeta));
+    HELR_LAUNCH(k_dec_finish<<<grid_for(ns), 256, 0, c->stream>>>(v, v + ns, d_re, d_im, ns, c->t.sidx, scale));
     HELR_CUDA(c, cudaGetLastError());
     helr_free(c, coef);
     helr_free(c, v);
@@ -286,8 +286,8 @@ int helr_encrypt_dev(he_ctx *c, const uint64_t *d_pt, int level, uint64_t seed, 
     HELR_TRY(helr_sample(c, e1, nl, lm, seed, 6, 1));
     HELR_TRY(helr_ntt_fwd(c, tmp, 3 * (size_t)nl, lm, c->stream));
     const uint64_t *pk0 = c->d_pk, *pk1 = c->d_pk + ((size_t)c->nq << c->logn);
-    k_mul_add<<<grid_for(lw), 256, 0, c->stream>>>(d_ct, v, pk0, e0, d_pt, lw, c->logn, c->t.mod);
-    k_mul_add<<<grid_for(lw), 256, 0, c->stream>>>(d_ct + lw, v, pk1, e1, nullptr, lw, c->logn, c->t.mod);
+    HELR_LAUNCH(k_mul_add<<<grid_for(lw), 256, 0, c->stream>>>(d_ct, v, pk0, e0, d_pt, lw, c->logn, c->t.mod));
+    HELR_LAUNCH(k_mul_add<<<grid_for(lw), 256, 0, c->stream>>>(d_ct + lw, v, pk1, e1, nullptr, lw, c->logn, c->t.mod));
     HELR_CUDA(c, cudaGetLastError());
     helr_free(c, tmp);
     return HE_OK;
@@ -298,7 +298,7 @@ int helr_decrypt_dev(he_ctx *c, const uint64_t *d_ct, int level, uint64_t *d_pt)
 {
     if (!c->have_keys) return helr_fail(c, HE_EKEY, "no secret key");
     const size_t lw = (size_t)(level + 1) << c->logn;
-    k_mul_add<<<grid_for(lw), 256, 0, c->stream>>>(d_pt, d_ct + lw, c->d_sk, d_ct, nullptr, lw, c->logn, c->t.mod);
+    HELR_LAUNCH(k_mul_add<<<grid_for(lw), 256, 0, c->stream>>>(d_pt, d_ct + lw, c->d_sk, d_ct, nullptr, lw, c->logn, c->t.mod));
     HELR_CUDA(c, cudaGetLastError());
     return HE_OK;
 }
@@ -322,7 +322,7 @@ int helr_keygen_base(he_ctx *c, uint64_t seed)
     HELR_TRY(helr_sample(c, tmp, nq, lq, seed, 2, 2));        // a
     HELR_TRY(helr_sample(c, tmp + lw, nq, lq, seed, 3, 1));   // e
     HELR_TRY(helr_ntt_fwd(c, tmp, 2 * (size_t)nq, lq, c->stream));
-    k_e_minus_as<<<grid_for(lw), 256, 0, c->stream>>>(c->d_pk, tmp + lw, tmp, c->d_sk, lw, c->logn, lq, c->t.mod);
+    HELR_LAUNCH(k_e_minus_as<<<grid_for(lw), 256, 0, c->stream>>>(c->d_pk, tmp + lw, tmp, c->d_sk, lw, c->logn, lq, c->t.mod));
     HELR_CUDA(c, cudaMemcpyAsync(c->d_pk + lw, tmp, sizeof(uint64_t) * lw, cudaMemcpyDeviceToDevice, c->stream));
     HELR_CUDA(c, cudaGetLastError());
     HELR_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -352,9 +352,9 @@ int helr_make_ksk(he_ctx *c, uint64_t gal, const uint64_t *sprime, uint64_t *out
         HELR_TRY(helr_sample(c, e, np, all, c->key_seed, ste, 1));
         HELR_TRY(helr_ntt_fwd(c, a, np, all, c->stream));
         HELR_TRY(helr_ntt_fwd(c, e, np, all, c->stream));
-        k_e_minus_as<<<grid_for(lw), 256, 0, c->stream>>>(b, e, a, c->d_sk, lw, c->logn, all, c->t.mod);
+        HELR_LAUNCH(k_e_minus_as<<<grid_for(lw), 256, 0, c->stream>>>(b, e, a, c->d_sk, lw, c->logn, all, c->t.mod));
         uint64_t pmod = c->q[nq] % c->q[d];
-        k_add_scaled<<<grid_for(n), 256, 0, c->stream>>>(b + (size_t)d * n, sprime + (size_t)d * n, pmod, n, c->t.mod, d);
+        HELR_LAUNCH(k_add_scaled<<<grid_for(n), 256, 0, c->stream>>>(b + (size_t)d * n, sprime + (size_t)d * n, pmod, n, c->t.mod, d));
         HELR_CUDA(c, cudaGetLastError());
     }
     helr_free(c, e);
@@ -364,7 +364,7 @@ int helr_make_ksk(he_ctx *c, uint64_t gal, const uint64_t *sprime, uint64_t *out
 int helr_square_dev(he_ctx *c, uint64_t *out, const uint64_t *in, size_t nlimbs)
 {
     size_t nw = nlimbs << c->logn;
-    k_square<<<grid_for(nw), 256, 0, c->stream>>>(out, in, nw, c->logn, c->t.mod);
+    HELR_LAUNCH(k_square<<<grid_for(nw), 256, 0, c->stream>>>(out, in, nw, c->logn, c->t.mod));
     HELR_CUDA(c, cudaGetLastError());
     return HE_OK;
 }

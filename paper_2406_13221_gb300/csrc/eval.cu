@@ -233,7 +233,7 @@ int ev_sum_items(Eval *ev, const CtB &a, uint64_t *acc, int accumulate)
     he_ctx *c = ev->c;
     const int nl = a.level + 1;
     size_t nw = 2 * (size_t)nl * c->n;
-    k_sum_items_kernel<<<grid_for(nw), 256, 0, c->stream>>>(acc, a.d, a.item, a.batch, nw, c->logn, nl, c->t.mod, accumulate);
+    HELR_LAUNCH(k_sum_items_kernel<<<grid_for(nw), 256, 0, c->stream>>>(acc, a.d, a.item, a.batch, nw, c->logn, nl, c->t.mod, accumulate));
     HELR_CUDA(c, cudaGetLastError());
     return HE_OK;
 }

@@ -10,6 +10,58 @@
 
 typedef unsigned __int128 u128;
 
+std::atomic<unsigned long long> g_helr_launches{0};
+
+void prof_start(he_ctx *c, int cls, cudaStream_t s)
+{
+    if (!c->prof.on) return;
+    ProfClass &p = c->prof.cls[cls];
+    while (p.ev.size() < 2 * (p.used + 1)) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        p.ev.push_back(e);
+    }
+    cudaEventRecord(p.ev[2 * p.used], s);
+}
+void prof_stop(he_ctx *c, int cls, cudaStream_t s, double units, int launches)
+{
+    if (!c->prof.on) return;
+    ProfClass &p = c->prof.cls[cls];
+    if (p.ev.size() < 2 * (p.used + 1)) return;
+    cudaEventRecord(p.ev[2 * p.used + 1], s);
+    p.used++;
+    p.units += units;
+    p.launches += launches;
+}
+
+extern "C" uint64_t he_launch_count(void) { return g_helr_launches.load(); }
+
+extern "C" int he_prof_enable(he_ctx *c, int on)
+{
+    if (!c) return HE_EINVAL;
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->prof.on = on;
+    for (auto &p : c->prof.cls) p.used = 0, p.units = 0, p.launches = 0;
+    return HE_OK;
+}
+
+extern "C" int he_prof_read(he_ctx *c, int cls, double *ms, double *units, uint64_t *launches)
+{
+    if (!c || cls < 0 || cls >= PROF_NCLASS) return HE_EINVAL;
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    ProfClass &p = c->prof.cls[cls];
+    double tot = 0;
+    for (size_t i = 0; i < p.used; i++) {
+        float x = 0;
+        HELR_CUDA(c, cudaEventElapsedTime(&x, p.ev[2 * i], p.ev[2 * i + 1]));
+        tot += x;
+    }
+    if (ms) *ms = tot;
+    if (units) *units = p.units;
+    if (launches) *launches = p.launches;
+    return HE_OK;
+}
+
 // ------------------------------------------------------------------ errors / memory
 int helr_fail(he_ctx *c, int code, const char *fmt, ...)
 {
@@ -277,6 +329,8 @@ extern "C" int he_ctx_destroy(he_ctx *c)
 {
     if (!c) return HE_EINVAL;
     cudaStreamSynchronize(c->stream);
+    for (auto &p : c->prof.cls)
+        for (auto e : p.ev) cudaEventDestroy(e);
     void *ptrs[] = {c->t.mod, c->t.tw, c->t.itw, c->t.ninv, c->t.zeta, c->t.sidx, c->t.cdt, c->d_qinv, c->d_pinv, c->d_sk, c->d_pk};
     for (void *p : ptrs) helr_free(c, p);
     for (auto &k : c->ksk) helr_free(c, k.d);

@@ -12,6 +12,7 @@
 #include <vector>
 #include <map>
 #include <memory>
+#include <atomic>
 
 #include "../../include/he_lr.h"
 
@@ -89,6 +90,31 @@ struct LimbMap {
     unsigned char p[HELR_MAXQ + 2];
 };
 
+// ------------------------------------------------------------------ launch accounting
+// Every kernel launch of the library goes through HELR_LAUNCH, which counts it.
+extern std::atomic<unsigned long long> g_helr_launches;
+#define HELR_LAUNCH(...)                                                  \
+    do {                                                                  \
+        g_helr_launches.fetch_add(1, std::memory_order_relaxed);          \
+        __VA_ARGS__;                                                      \
+    } while (0)
+
+// Optional per-class kernel timing with CUDA events on the context stream.
+enum { PROF_NTT_FWD = 0, PROF_NTT_INV = 1, PROF_MODUP = 2, PROF_KS_INNER = 3, PROF_NCLASS = 4 };
+struct ProfClass {
+    std::vector<cudaEvent_t> ev;  // start/stop pairs
+    size_t used = 0;
+    double units = 0;             // work units (limbs for transforms)
+    unsigned long long launches = 0;
+};
+struct Prof {
+    int on = 0;
+    ProfClass cls[PROF_NCLASS];
+};
+struct he_ctx;
+void prof_start(he_ctx *c, int cls, cudaStream_t s);
+void prof_stop(he_ctx *c, int cls, cudaStream_t s, double units, int launches);
+
 // ------------------------------------------------------------------ error state
 struct HeError {
     int code;
@@ -134,6 +160,7 @@ struct he_ctx {
     uint64_t *d_pk;                // [2][nq][N] NTT form
     std::vector<KeySwitchKey> ksk;
     HeError err;
+    Prof prof;
 };
 
 struct he_ct {

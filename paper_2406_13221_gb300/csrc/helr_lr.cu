@@ -81,7 +81,7 @@ struct he_lr_job {
     uint64_t *mask;             // plaintext M at level L-1, scale q_(L-1), evaluation form
     double mask_scale;
     Eval ev;
-    int chunk;
+    int chunk, chunk_max;
     uint64_t *buf;              // work ciphertexts
     uint64_t *T0, *T1, *T2, *T3, *T4, *acc;
     he_lr_stats st;
@@ -270,6 +270,7 @@ extern "C" int he_lr_job_create(he_ctx *c, const double *X, const double *y, siz
     int chunk = batch_blocks > 0 ? batch_blocks : (c->logn >= 16 ? 16 : 32);
     chunk = std::min(chunk, mode == HE_LR_FULL_BATCH ? j->nblocks : j->bpb);
     j->chunk = std::max(1, chunk);
+    j->chunk_max = j->chunk;
     JTRY(ev_init(c, &j->ev, j->chunk, L));
     JTRY(helr_alloc(c, (void **)&j->buf, sizeof(uint64_t) * j->ctw * (5 * (size_t)j->chunk + 3)));
     j->T0 = j->buf;
@@ -450,6 +451,37 @@ extern "C" int he_lr_job_step(he_lr_job *j, int t, he_lr_sched sched)
     j->st.keyswitches = j->ev.keyswitches;
     j->st.sec_update_avg = j->upd_total / j->iters_done;
     j->st.sec_iter_avg = j->iter_total / j->iters_done;
+    return HE_OK;
+}
+
+extern "C" int he_lr_job_set_batch(he_lr_job *j, int b)
+{
+    if (!j || b < 1 || b > j->chunk_max) return HE_EINVAL;
+    j->chunk = b;
+    return HE_OK;
+}
+
+extern "C" int he_lr_job_step_io(he_lr_job *j, int t, he_lr_sched sched, const uint64_t *in, uint64_t *out)
+{
+    if (!j) return HE_EINVAL;
+    he_ctx *c = j->c;
+    const size_t nl = j->L + 1, lw = 2 * nl;  // limbs per ciphertext
+    if (in) {
+        HELR_CUDA(c, cudaMemcpyAsync(j->W->d, in, j->ctw * 8, cudaMemcpyHostToDevice, c->stream));
+        HELR_CUDA(c, cudaMemcpyAsync(j->V->d, in + j->ctw, j->ctw * 8, cudaMemcpyHostToDevice, c->stream));
+        HELR_TRY(helr_ntt_fwd(c, j->W->d, lw, limbmap_ct(j->L), c->stream));
+        HELR_TRY(helr_ntt_fwd(c, j->V->d, lw, limbmap_ct(j->L), c->stream));
+        j->W->scale = j->V->scale = j->scale0;
+    }
+    HELR_TRY(he_lr_job_step(j, t, sched));
+    if (out) {
+        uint64_t *tmp = j->acc;  // free after the step
+        HELR_TRY(helr_ntt_inv_oop(c, j->W->d, tmp, lw, limbmap_ct(j->L), c->stream));
+        HELR_CUDA(c, cudaMemcpyAsync(out, tmp, j->ctw * 8, cudaMemcpyDeviceToHost, c->stream));
+        HELR_TRY(helr_ntt_inv_oop(c, j->V->d, tmp, lw, limbmap_ct(j->L), c->stream));
+        HELR_CUDA(c, cudaMemcpyAsync(out + j->ctw, tmp, j->ctw * 8, cudaMemcpyDeviceToHost, c->stream));
+        HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
     return HE_OK;
 }
 

@@ -281,13 +281,13 @@ struct NttPlan {
     }
     static void fwd(const uint64_t *in, uint64_t *out, size_t nlimbs, const DevTables &t, const LimbMap &m, cudaStream_t s)
     {
-        k_ntt_fwd_cols<K1, K2, C><<<(unsigned)(nlimbs * (R2 / C)), C * T1, SM1, s>>>(in, out, t.tw, t.mod, m);
-        k_ntt_fwd_rows<K1, K2, RPC><<<(unsigned)(nlimbs * (R1 / RPC)), RPC * T2, SM2, s>>>(out, t.tw, t.mod, m);
+        HELR_LAUNCH(k_ntt_fwd_cols<K1, K2, C><<<(unsigned)(nlimbs * (R2 / C)), C * T1, SM1, s>>>(in, out, t.tw, t.mod, m));
+        HELR_LAUNCH(k_ntt_fwd_rows<K1, K2, RPC><<<(unsigned)(nlimbs * (R1 / RPC)), RPC * T2, SM2, s>>>(out, t.tw, t.mod, m));
     }
     static void inv(const uint64_t *in, uint64_t *out, size_t nlimbs, const DevTables &t, const LimbMap &m, cudaStream_t s)
     {
-        k_ntt_inv_rows<K1, K2, RPC><<<(unsigned)(nlimbs * (R1 / RPC)), RPC * T2, SM2, s>>>(in, out, t.itw, t.mod, m);
-        k_ntt_inv_cols<K1, K2, C><<<(unsigned)(nlimbs * (R2 / C)), C * T1, SM1, s>>>(out, t.itw, t.mod, t.ninv, m);
+        HELR_LAUNCH(k_ntt_inv_rows<K1, K2, RPC><<<(unsigned)(nlimbs * (R1 / RPC)), RPC * T2, SM2, s>>>(in, out, t.itw, t.mod, m));
+        HELR_LAUNCH(k_ntt_inv_cols<K1, K2, C><<<(unsigned)(nlimbs * (R2 / C)), C * T1, SM1, s>>>(out, t.itw, t.mod, t.ninv, m));
     }
 };
 
@@ -300,8 +300,11 @@ int run(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbM
         prepared = true;
     }
     if (nlimbs == 0) return HE_OK;
+    const int cls = inverse ? PROF_NTT_INV : PROF_NTT_FWD;
+    prof_start(c, cls, s);
     if (inverse) NttPlan<K1, K2>::inv(in, out, nlimbs, c->t, m, s);
     else NttPlan<K1, K2>::fwd(in, out, nlimbs, c->t, m, s);
+    prof_stop(c, cls, s, (double)nlimbs, 2);
     HELR_CUDA(c, cudaGetLastError());
     return HE_OK;
 }

@@ -263,56 +263,56 @@ void k_ew(he_ctx *c, int op, Str out, Str a, Str b, int batch, int npoly, int nl
 {
     static const KP zero = {};
     size_t np = (size_t)batch * npoly * nl * (c->n / 2);
-    if (np) k_ew_kernel<<<grid_for(np), 256, 0, s>>>(op, out, a, b, np, c->n / 2, npoly, nl, kp ? *kp : zero, c->t.mod);
+    if (np) HELR_LAUNCH(k_ew_kernel<<<grid_for(np), 256, 0, s>>>(op, out, a, b, np, c->n / 2, npoly, nl, kp ? *kp : zero, c->t.mod));
 }
 void k_automorph_items(he_ctx *c, uint64_t *out, size_t out_item, const uint64_t *in, size_t in_item, int batch, int nl,
                        uint64_t gal, cudaStream_t s)
 {
     size_t nw = (size_t)batch * nl << c->logn;
-    if (nw) k_automorph_items_kernel<<<grid_for(nw), 256, 0, s>>>(out, out_item, in, in_item, nw, c->logn, nl, gal);
+    if (nw) HELR_LAUNCH(k_automorph_items_kernel<<<grid_for(nw), 256, 0, s>>>(out, out_item, in, in_item, nw, c->logn, nl, gal));
 }
 void k_add(he_ctx *c, uint64_t *out, const uint64_t *a, const uint64_t *b, size_t nlimbs, const LimbMap &m, int sub, cudaStream_t s)
 {
     size_t np = nlimbs * (size_t)(c->n / 2);
-    if (np) k_add_kernel<<<grid_for(np), 256, 0, s>>>(out, a, b, np, c->n / 2, c->t.mod, m, sub);
+    if (np) HELR_LAUNCH(k_add_kernel<<<grid_for(np), 256, 0, s>>>(out, a, b, np, c->n / 2, c->t.mod, m, sub));
 }
 void k_mul(he_ctx *c, uint64_t *out, const uint64_t *a, const uint64_t *b, size_t nlimbs, const LimbMap &m, cudaStream_t s)
 {
     size_t np = nlimbs * (size_t)(c->n / 2);
-    if (np) k_mul_kernel<<<grid_for(np), 256, 0, s>>>(out, a, b, np, c->n / 2, c->t.mod, m);
+    if (np) HELR_LAUNCH(k_mul_kernel<<<grid_for(np), 256, 0, s>>>(out, a, b, np, c->n / 2, c->t.mod, m));
 }
 void k_tensor(he_ctx *c, const uint64_t *a, const uint64_t *b, uint64_t *d, int batch, int level,
               size_t a_stride, size_t b_stride, size_t d_stride, size_t d_poly, cudaStream_t s)
 {
     size_t np = (size_t)batch * (level + 1) * (c->n / 2);
-    if (np) k_tensor_kernel<<<grid_for(np), 256, 0, s>>>(a, b, d, np, c->n / 2, level + 1, a_stride, b_stride, d_stride, d_poly, c->t.mod);
+    if (np) HELR_LAUNCH(k_tensor_kernel<<<grid_for(np), 256, 0, s>>>(a, b, d, np, c->n / 2, level + 1, a_stride, b_stride, d_stride, d_poly, c->t.mod));
 }
 void k_cmul_const(he_ctx *c, uint64_t *out, const uint64_t *in, const uint64_t *kp, size_t nlimbs, int period, cudaStream_t s)
 {
     size_t np = nlimbs * (size_t)(c->n / 2);
-    if (np) k_cmul_kernel<<<grid_for(np), 256, 0, s>>>(out, in, kp, np, c->n / 2, period, c->t.mod);
+    if (np) HELR_LAUNCH(k_cmul_kernel<<<grid_for(np), 256, 0, s>>>(out, in, kp, np, c->n / 2, period, c->t.mod));
 }
 void k_cadd_const(he_ctx *c, uint64_t *ct0, const uint64_t *kv, int batch, int level, size_t stride, cudaStream_t s)
 {
     size_t np = (size_t)batch * (level + 1) * (c->n / 2);
-    if (np) k_cadd_kernel<<<grid_for(np), 256, 0, s>>>(ct0, kv, np, c->n / 2, level + 1, stride, c->t.mod);
+    if (np) HELR_LAUNCH(k_cadd_kernel<<<grid_for(np), 256, 0, s>>>(ct0, kv, np, c->n / 2, level + 1, stride, c->t.mod));
 }
 void k_automorph(he_ctx *c, uint64_t *out, const uint64_t *in, size_t nlimbs, uint64_t gal, cudaStream_t s)
 {
     size_t nw = nlimbs << c->logn;
-    if (nw) k_automorph_kernel<<<grid_for(nw), 256, 0, s>>>(out, in, nw, c->logn, gal);
+    if (nw) HELR_LAUNCH(k_automorph_kernel<<<grid_for(nw), 256, 0, s>>>(out, in, nw, c->logn, gal));
 }
 void k_lift(he_ctx *c, const uint64_t *in, uint64_t *out, int batch, int src_prime, size_t in_stride,
             const LimbMap &dst, size_t out_stride, cudaStream_t s)
 {
     size_t nw = (size_t)batch * dst.period << c->logn;
-    if (nw) k_lift_kernel<<<grid_for(nw), 256, 0, s>>>(in, out, nw, c->logn, dst.period, src_prime, in_stride, out_stride, c->t.mod, dst);
+    if (nw) HELR_LAUNCH(k_lift_kernel<<<grid_for(nw), 256, 0, s>>>(in, out, nw, c->logn, dst.period, src_prime, in_stride, out_stride, c->t.mod, dst));
 }
 void k_rescale_combine(he_ctx *c, uint64_t *out, const uint64_t *in, const uint64_t *corr, int batch, int nl,
                        size_t in_stride, size_t corr_stride, size_t out_stride, const uint64_t *inv_pairs, cudaStream_t s)
 {
     size_t np = (size_t)batch * nl * (c->n / 2);
-    if (np) k_combine_kernel<<<grid_for(np), 256, 0, s>>>(out, in, corr, np, c->n / 2, nl, in_stride, corr_stride, out_stride, inv_pairs, c->t.mod);
+    if (np) HELR_LAUNCH(k_combine_kernel<<<grid_for(np), 256, 0, s>>>(out, in, corr, np, c->n / 2, nl, in_stride, corr_stride, out_stride, inv_pairs, c->t.mod));
 }
 void k_modup(he_ctx *c, const uint64_t *dcoef, const uint64_t *dntt, uint64_t *ext, int batch, int level,
              size_t in_stride, size_t ext_stride, cudaStream_t s)
@@ -320,12 +320,16 @@ void k_modup(he_ctx *c, const uint64_t *dcoef, const uint64_t *dntt, uint64_t *e
     (void)dntt;
     int nl = level + 1;
     size_t nw = (size_t)batch * nl * (nl + 1) << c->logn;
-    if (nw) k_modup_kernel<<<grid_for(nw), 256, 0, s>>>(dcoef, ext, nw, c->logn, nl, c->nq, in_stride, ext_stride, c->t.mod);
+    prof_start(c, PROF_MODUP, s);
+    if (nw) HELR_LAUNCH(k_modup_kernel<<<grid_for(nw), 256, 0, s>>>(dcoef, ext, nw, c->logn, nl, c->nq, in_stride, ext_stride, c->t.mod));
+    prof_stop(c, PROF_MODUP, s, (double)batch * nl * (nl + 1), 1);
 }
 void k_ks_inner(he_ctx *c, const uint64_t *ext, const uint64_t *key, uint64_t *acc, int batch, int level,
                 size_t ext_stride, size_t acc_stride, cudaStream_t s)
 {
     int nl = level + 1;
     size_t np = (size_t)batch * (nl + 1) * (c->n / 2);
-    if (np) k_ks_inner_kernel<<<grid_for(np), 256, 0, s>>>(ext, key, acc, np, c->n / 2, nl, c->nq, ext_stride, acc_stride, c->t.mod);
+    prof_start(c, PROF_KS_INNER, s);
+    if (np) HELR_LAUNCH(k_ks_inner_kernel<<<grid_for(np), 256, 0, s>>>(ext, key, acc, np, c->n / 2, nl, c->nq, ext_stride, acc_stride, c->t.mod));
+    prof_stop(c, PROF_KS_INNER, s, (double)batch, 1);
 }
