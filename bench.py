@@ -228,7 +228,7 @@ def ctw_bytes():
 
 
 def info_chunk(job, args):
-    return args.chunk if args.chunk else 16
+    return min(args.chunk if args.chunk else 16, int(job.info.n_blocks))
 
 
 _PINNED = []
