@@ -185,8 +185,9 @@ typedef struct he_lr_job he_lr_job;
  * Bbar per mini-batch of batch_rows rows (Sec. 3.1, 1/(eps + 1/4 sum |Z^T Z|),
  * eps = 1e-8) and the full-batch Bbar by the combination of Sec. 3.3, pack
  * m x g blocks (g = next power of two >= f + 1, m g = N/2; Sec. 2.2),
- * encrypt the blocks, n*Bbar (replicated per row) and W = V = 0 at the top
- * level with scale 2^log_scale.  Object k of kind K is encrypted with seed
+ * encrypt the blocks, n*Bbar (replicated per row) and W = V = 0 at level 7
+ * (the depth of one iteration, which then ends at level 0; primes above q_7
+ * stay unused) with scale 2^log_scale.  Object k of kind K is encrypted with seed
  * enc_seed + (K << 48) + k (K: 1 block, 2 Bbar, 3 W0, 4 V0, 5 W refresh at
  * iteration k, 6 V refresh).  X: n x f row-major doubles, y: n labels +/-1.
  * Keys for the needed rotations are generated from key_seed if missing.
@@ -200,7 +201,7 @@ int he_lr_job_create(he_ctx *ctx, const double *X, const double *y, size_t n, si
 int he_lr_job_step(he_lr_job *job, int t, he_lr_sched sched);
 /* he_lr_job_step with the job state on the host: when state_in is not NULL,
  * W and V are first loaded from coefficient words [2 ciphertexts][2][n_q][N]
- * (W then V, top level, scale 2^log_scale); when state_out is not NULL, the
+ * (W then V, level 7, scale 2^log_scale; n_q is then 8 limbs); when state_out is not NULL, the
  * refreshed W and V are written back in the same layout.  Host buffers may be
  * pinned; the copies run on the context stream inside the call. */
 int he_lr_job_step_io(he_lr_job *job, int t, he_lr_sched sched, const uint64_t *state_in, uint64_t *state_out);
@@ -235,9 +236,10 @@ int he_lr_train(he_ctx *ctx, const double *X, const double *y, size_t n, size_t 
 int he_lr_iteration(he_ctx *ctx, he_ct *const *Z, size_t n_blocks, const he_ct *B, const he_ct *W,
                     const he_ct *V, int g, int m, double alpha, double eta, double inv_n,
                     const double poly[3], he_ct **W_out, he_ct **V_out);
-/* The refresh used between iterations: decrypt, take the real part of every
- * slot, re-encode at the top level with `scale`, encrypt with `seed`. */
-int he_refresh(he_ctx *ctx, const he_ct *in, double scale, uint64_t seed, he_ct **out);
+/* The refresh used between iterations (standing in for the bootstrapping of
+ * Sec. 4.3 Step 7): decrypt, take the real part of every slot, re-encode at
+ * `level` with `scale`, encrypt with `seed`. */
+int he_refresh(he_ctx *ctx, const he_ct *in, int level, double scale, uint64_t seed, he_ct **out);
 
 /* Host-only client precompute exposed for checking: Bbar (length g) for the
  * rows [row0, row0 + rows) of Z = y * [1 | X]. */

@@ -130,18 +130,22 @@ class TrainData:
 
 
 # ------------------------------------------------------------------ encrypted iteration
+DEPTH = 7  # levels one iteration consumes
+
+
 class Circuit:
     """The encrypted QG-NAG iteration on one parameter set.
 
-    Levels: inputs at L = he.max_level; the iteration consumes 7 levels and ends
-    at level L - 7 (the default chain has L = 8, ending at level 1)."""
+    Levels: fresh inputs sit at level L (default: the iteration depth, 7, so the
+    iteration ends at level 0; any higher primes of the chain stay unused); the
+    iteration consumes 7 levels and ends at level L - 7."""
 
-    def __init__(self, he: Ckks, g, m, scale, poly=G8):
+    def __init__(self, he: Ckks, g, m, scale, poly=G8, start_level=None):
         self.he, self.g, self.m, self.scale, self.poly = he, g, m, float(scale), poly
         if g * m != he.nslots:
             raise ValueError("m * g must equal N/2")
-        self.L = he.max_level
-        if self.L < 7:
+        self.L = min(DEPTH, he.max_level) if start_level is None else start_level
+        if self.L < DEPTH or self.L > he.max_level:
             raise ValueError("the iteration needs 7 levels")
         self.lg, self.lm = int(math.log2(g)), int(math.log2(m))
         mask = np.zeros(he.nslots)
@@ -218,7 +222,7 @@ class Circuit:
 
     def refresh(self, ct, seed):
         """Step 7 stand-in: decrypt, keep the real part of the slots, re-encode at
-        the top level with the initial scale, encrypt with fresh randomness."""
+        the start level with the initial scale, encrypt with fresh randomness."""
         he = self.he
         z = he.decode(he.decrypt(ct))
         return he.encrypt(he.encode(z.real, self.L, self.scale), seed)

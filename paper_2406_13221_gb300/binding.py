@@ -95,7 +95,7 @@ SIGNATURES = {
     "he_lr_train": (_i, [_vp, _vp, _vp, _sz, _sz, _i, he_lr_sched, _i, _sz, _i, _u64, _u64, _vp, _sz,
                          ctypes.POINTER(he_lr_stats)]),
     "he_lr_iteration": (_i, [_vp, _vp, _sz, _vp, _vp, _vp, _i, _i, _d, _d, _d, _vp, _pp, _pp]),
-    "he_refresh": (_i, [_vp, _vp, _d, _u64, _pp]),
+    "he_refresh": (_i, [_vp, _vp, _i, _d, _u64, _pp]),
     "he_lr_bbar": (_i, [_vp, _vp, _sz, _sz, _sz, _sz, _sz, _vp]),
 }
 
@@ -224,8 +224,8 @@ class Context:
     def ptmul(self, a, pt):
         return self._op("he_ptmul", a.h, pt.h)
 
-    def refresh(self, ct, scale, seed):
-        return self._op("he_refresh", ct.h, float(scale), seed)
+    def refresh(self, ct, level, scale, seed):
+        return self._op("he_refresh", ct.h, int(level), float(scale), seed)
 
     # device-pointer primitives
     def ntt_forward(self, dptr, nlimbs, prime_of):

@@ -51,7 +51,7 @@ __global__ void k_sample_kernel(uint64_t *out, size_t nwords, int logn, LimbMap 
     GS_LOOP(i, nwords) {
         size_t limb = i >> logn;
         uint64_t k = i & (n - 1);
-        int p = lm.p[limb % lm.period];
+        int p = limb_prime(lm, limb);
         ModQ m = mods[p];
         uint64_t v;
         if (kind == 0) {
@@ -80,7 +80,7 @@ __global__ void k_e_minus_as(uint64_t *out, const uint64_t *e, const uint64_t *a
 {
     GS_LOOP(i, nwords) {
         size_t limb = i >> logn;
-        int p = lm.p[limb % lm.period];
+        int p = limb_prime(lm, limb);
         ModQ m = mods[p];
         uint64_t k = i & ((1u << logn) - 1);
         uint64_t as = mulmod(a[i], s[((size_t)p << logn) + k], m);

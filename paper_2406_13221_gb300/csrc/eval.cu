@@ -83,6 +83,7 @@ static int check_batch(Eval *ev, const CtB &a)
 }
 
 // out = Relin(a (x) b); b may broadcast.  out.level = a.level, scale = product.
+// The relinearisation sum (d0, d1) + KS(d2) is formed in the key switch's output stage.
 int ev_mul_relin(Eval *ev, const CtB &a, const CtB &b, CtB &out)
 {
     he_ctx *c = ev->c;
@@ -93,13 +94,16 @@ int ev_mul_relin(Eval *ev, const CtB &a, const CtB &b, CtB &out)
     const uint64_t *key = helr_find_key(c, 0);
     if (!key) return helr_fail(c, HE_EKEY, "no relinearisation key");
     k_tensor(c, a.d, b.d, ev->tens, B, lv, a.item, b.item, lw, (size_t)B * lw, c->stream);
-    HELR_TRY(helr_keyswitch(c, ev->tens + 2 * (size_t)B * lw, ev->ksout, B, lv, key, &ev->ks));
-    ev->keyswitches += B;
-    Str d{ev->tens, lw, (size_t)B * lw}, k{ev->ksout, 2 * lw, lw};
     out.level = lv;
     out.batch = B;
     out.scale = a.scale * b.scale;
-    k_ew(c, EW_ADD, S(out, c), d, k, B, 2, nl, nullptr, c->stream);
+    KsOut o;
+    o.out = S(out, c);
+    o.rel = ev->tens;
+    o.rel_item = lw;
+    o.rel_poly = (size_t)B * lw;
+    HELR_TRY(helr_keyswitch(c, ev->tens + 2 * (size_t)B * lw, nullptr, B, lv, key, &ev->ks, &o));
+    ev->keyswitches += B;
     HELR_CUDA(c, cudaGetLastError());
     return HE_OK;
 }
@@ -141,8 +145,8 @@ int ev_rescale(Eval *ev, const CtB &a, CtB &out)
     return HE_OK;
 }
 
-// left rotation by r slots; out must not alias a
-int ev_rotate(Eval *ev, const CtB &a, int64_t r, CtB &out)
+// left rotation by r slots (accumulate: out = a + Rot(a, r)); out must not alias a
+int ev_rotate_acc(Eval *ev, const CtB &a, int64_t r, CtB &out, int accumulate)
 {
     he_ctx *c = ev->c;
     HELR_TRY(check_batch(ev, a));
@@ -153,19 +157,25 @@ int ev_rotate(Eval *ev, const CtB &a, int64_t r, CtB &out)
     const size_t N = c->n, lw = (size_t)nl * N;
     cudaStream_t s = c->stream;
     k_automorph_items(c, ev->rot1, lw, a.d + lw, a.item, B, nl, gal, s);
-    k_automorph_items(c, out.d, out.item, a.d, a.item, B, nl, gal, s);
-    HELR_TRY(helr_keyswitch(c, ev->rot1, ev->ksout, B, lv, key, &ev->ks));
-    ev->keyswitches += B;
-    Str o0{out.d, out.item, lw}, k0{ev->ksout, 2 * lw, lw};
-    k_ew(c, EW_ADD, o0, o0, k0, B, 1, nl, nullptr, s);
-    Str o1{out.d + lw, out.item, lw}, k1{ev->ksout + lw, 2 * lw, lw};
-    k_ew(c, EW_COPY, o1, k1, k1, B, 1, nl, nullptr, s);
     out.level = lv;
     out.batch = B;
     out.scale = a.scale;
+    KsOut o;
+    o.out = S(out, c);
+    o.rot = a.d;
+    o.rot_item = a.item;
+    o.gal = gal;
+    if (accumulate) {
+        o.acc = a.d;
+        o.acc_item = a.item;
+        o.acc_poly = lw;
+    }
+    HELR_TRY(helr_keyswitch(c, ev->rot1, nullptr, B, lv, key, &ev->ks, &o));
+    ev->keyswitches += B;
     HELR_CUDA(c, cudaGetLastError());
     return HE_OK;
 }
+int ev_rotate(Eval *ev, const CtB &a, int64_t r, CtB &out) { return ev_rotate_acc(ev, a, r, out, 0); }
 
 int ev_add(Eval *ev, const CtB &a, const CtB &b, CtB &out, int sub)
 {

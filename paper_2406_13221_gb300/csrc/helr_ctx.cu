@@ -5,6 +5,7 @@
 #include <string.h>
 #include <math.h>
 #include <algorithm>
+#include <stdlib.h>
 
 #include "helr_internal.cuh"
 
@@ -308,6 +309,7 @@ extern "C" int he_ctx_create(const he_params *p, void *stream, he_ctx **out)
     }
     he_ctx *c = new he_ctx();
     c->stream = (cudaStream_t)stream;
+    if (const char *w = getenv("HELR_KS_WAVE")) c->ks_wave = atoi(w);
     // keep freed stream-ordered memory in the pool between iterations
     int dev = 0;
     cudaMemPool_t pool;
@@ -583,7 +585,7 @@ extern "C" int he_ct_import(he_ctx *c, const uint64_t *words, size_t nw, int lev
 // ------------------------------------------------------------------ key switching
 // d_in: [batch][nl][N] evaluation form; d_out: [batch][2][nl][N].
 int helr_keyswitch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, int level, const uint64_t *key,
-                   KsScratch *ws)
+                   KsScratch *ws, const KsOut *o)
 {
     const int nl = level + 1, nt = nl + 1;
     const size_t N = c->n;
@@ -596,22 +598,25 @@ int helr_keyswitch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, 
     cudaStream_t s = c->stream;
     // 1. coefficient form of every limb
     HELR_TRY(helr_ntt_inv_oop(c, d_in, ws->dcoef, in_items, limbmap_ct(level), s));
-    // 2. ModUp: each digit lifted to all nl + 1 moduli, then transformed
-    k_modup(c, ws->dcoef, d_in, ws->ext, batch, level, nl * N, (size_t)nl * nt * N, s);
-    LimbMap lt;
-    lt.period = nt;
-    for (int t = 0; t < nl; t++) lt.p[t] = (unsigned char)t;
-    lt.p[nl] = (unsigned char)c->nq;
-    HELR_TRY(helr_ntt_fwd(c, ws->ext, (size_t)batch * nl * nt, lt, s));
-    // 3. inner product with the key digits
-    k_ks_inner(c, ws->ext, key, ws->acc, batch, level, (size_t)nl * nt * N, 2 * (size_t)nt * N, s);
+    // 2-3. ModUp fused with the transforms and the inner product, in waves
+    const int wave = std::min(ws->wave, batch);
+    for (int b0 = 0; b0 < batch; b0 += wave) {
+        int cnt = std::min(wave, batch - b0);
+        HELR_TRY(helr_ks_fused(c, d_in + (size_t)b0 * nl * N, ws->dcoef + (size_t)b0 * nl * N, ws->ext, key,
+                               ws->acc + (size_t)b0 * 2 * nt * N, cnt, nl, s));
+    }
     // 4. ModDown: subtract the centred P-part and divide by P
     HELR_CUDA(c, cudaMemcpy2DAsync(ws->pl, N * 8, ws->acc + (size_t)nl * N, (size_t)nt * N * 8, N * 8, (size_t)batch * 2,
                                    cudaMemcpyDeviceToDevice, s));
     HELR_TRY(helr_ntt_inv(c, ws->pl, (size_t)batch * 2, limbmap_single(c->nq), s));
     k_lift(c, ws->pl, ws->lift, batch * 2, c->nq, N, limbmap_ct(level), (size_t)nl * N, s);
     HELR_TRY(helr_ntt_fwd(c, ws->lift, (size_t)batch * 2 * nl, limbmap_ct(level), s));
-    k_rescale_combine(c, d_out, ws->acc, ws->lift, batch * 2, nl, (size_t)nt * N, (size_t)nl * N, (size_t)nl * N, c->d_pinv, s);
+    if (o) {
+        k_ks_out(c, *o, ws->acc, ws->lift, batch, nl, s);
+    } else {
+        k_rescale_combine(c, d_out, ws->acc, ws->lift, batch * 2, nl, (size_t)nt * N, (size_t)nl * N, (size_t)nl * N,
+                          c->d_pinv, s);
+    }
     HELR_CUDA(c, cudaGetLastError());
     if (ws == &local) helr_ks_scratch_free(c, &local);
     return HE_OK;
@@ -621,17 +626,19 @@ int helr_ks_scratch_alloc(he_ctx *c, int batch, int level, KsScratch *ws)
 {
     const int nl = level + 1, nt = nl + 1;
     const size_t N = c->n;
-    size_t words = (size_t)batch * (nl * N + (size_t)nl * nt * N + 2 * nt * N + 2 * N + 2 * (size_t)nl * N);
+    const int wave = std::min(helr_ks_wave(c, nl), batch);
+    size_t words = (size_t)batch * (nl * N + 2 * nt * N + 2 * N + 2 * (size_t)nl * N) + (size_t)wave * nl * nt * N;
     uint64_t *base = nullptr;
     HELR_TRY(helr_alloc(c, (void **)&base, words * 8));
     ws->base = base;
     ws->dcoef = base;
-    ws->ext = ws->dcoef + (size_t)batch * nl * N;
-    ws->acc = ws->ext + (size_t)batch * nl * nt * N;
+    ws->acc = ws->dcoef + (size_t)batch * nl * N;
     ws->pl = ws->acc + (size_t)batch * 2 * nt * N;
     ws->lift = ws->pl + (size_t)batch * 2 * N;
+    ws->ext = ws->lift + (size_t)batch * 2 * nl * N;
     ws->batch = batch;
     ws->level = level;
+    ws->wave = wave;
     return HE_OK;
 }
 void helr_ks_scratch_free(he_ctx *c, KsScratch *ws)

@@ -73,14 +73,16 @@ __host__ __device__ __forceinline__ uint64_t shoup(uint64_t y, uint64_t w, uint6
     uint64_t r = shoup_lazy(y, w, wp, q);
     return r >= q ? r - q : r;
 }
-// centred representative of x in [0, qi) reduced into [0, qt)
+// centred representative of x in [0, qi) reduced into [0, qt); the Barrett
+// reduction is skipped when the magnitude is already below qt
 __host__ __device__ __forceinline__ uint64_t lift_centered(uint64_t x, uint64_t qi, const ModQ t)
 {
     if (x > (qi >> 1)) {
-        uint64_t neg = reduce64(qi - x, t);
+        uint64_t neg = qi - x;
+        if (neg >= t.q) neg = reduce64(neg, t);
         return neg ? t.q - neg : 0;
     }
-    return reduce64(x, t);
+    return x < t.q ? x : reduce64(x, t);
 }
 
 // ------------------------------------------------------------------ limb maps
@@ -114,6 +116,26 @@ struct Prof {
 struct he_ctx;
 void prof_start(he_ctx *c, int cls, cudaStream_t s);
 void prof_stop(he_ctx *c, int cls, cudaStream_t s, double units, int launches);
+
+// prime index of limb `limb` (an unrolled select: a dynamic index into a kernel
+// parameter array would force the array into local memory)
+__device__ __forceinline__ int limb_prime(const LimbMap &lm, size_t limb)
+{
+    const int i = (int)(limb % (size_t)lm.period);
+    int v = lm.p[0];
+#pragma unroll
+    for (int k = 1; k < HELR_MAXQ + 2; k++)
+        if (k == i) v = lm.p[k];
+    return v;
+}
+__device__ __forceinline__ int map_prime(const LimbMap &lm, int i)
+{
+    int v = lm.p[0];
+#pragma unroll
+    for (int k = 1; k < HELR_MAXQ + 2; k++)
+        if (k == i) v = lm.p[k];
+    return v;
+}
 
 // ------------------------------------------------------------------ error state
 struct HeError {
@@ -161,6 +183,7 @@ struct he_ctx {
     std::vector<KeySwitchKey> ksk;
     HeError err;
     Prof prof;
+    int ks_wave = 0;               // items per fused key-switch wave (0 = sized for L2)
 };
 
 struct he_ct {
@@ -232,10 +255,6 @@ void k_lift(he_ctx *c, const uint64_t *in, uint64_t *out, int batch, int src_pri
 void k_rescale_combine(he_ctx *c, uint64_t *out, const uint64_t *in, const uint64_t *corr, int batch,
                        int level, size_t in_stride, size_t corr_stride, size_t out_stride,
                        const uint64_t *inv_pairs, cudaStream_t s);
-void k_modup(he_ctx *c, const uint64_t *dcoef, const uint64_t *dntt, uint64_t *ext, int batch, int level,
-             size_t in_stride, size_t ext_stride, cudaStream_t s);
-void k_ks_inner(he_ctx *c, const uint64_t *ext, const uint64_t *key, uint64_t *acc, int batch, int level,
-                size_t ext_stride, size_t acc_stride, cudaStream_t s);
 
 // strided elementwise kernel: element (item b, poly p, limb j, k) of X lives at
 // X.p + b * X.item + p * X.poly + j * N + k (limb j reduced modulo q_j)
@@ -254,12 +273,32 @@ void k_automorph_items(he_ctx *c, uint64_t *out, size_t out_item, const uint64_t
 
 struct KsScratch {
     uint64_t *base, *dcoef, *ext, *acc, *pl, *lift;
-    int batch, level;
+    int batch, level, wave;
 };
+int helr_ks_fused(he_ctx *c, const uint64_t *dntt, const uint64_t *dcoef, uint64_t *mid, const uint64_t *key, uint64_t *acc,
+                  int items, int nl, cudaStream_t s);
+int helr_ks_wave(const he_ctx *c, int nl);
 int helr_ks_scratch_alloc(he_ctx *c, int batch, int level, KsScratch *ws);
 void helr_ks_scratch_free(he_ctx *c, KsScratch *ws);
+// Output stage of a key switch (ModDown combined with the operation around it):
+//   out_0 = KS_0 + [rel: rel_0] + [rot: sigma_gal(rot_0)] + [acc: acc_0]
+//   out_1 = KS_1 + [rel: rel_1] + [acc: acc_1]
+// rel: polynomials (d0, d1) of a tensor; rot: c0 of the rotated ciphertext;
+// acc: a ciphertext added to the result (rotate-and-add). Views are strided
+// [item][poly][limb][N]; out must not alias rot or acc.
+struct KsOut {
+    Str out;
+    const uint64_t *rel = nullptr;
+    size_t rel_item = 0, rel_poly = 0;
+    const uint64_t *rot = nullptr;
+    size_t rot_item = 0;
+    uint64_t gal = 0;
+    const uint64_t *acc = nullptr;
+    size_t acc_item = 0, acc_poly = 0;
+};
 int helr_keyswitch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, int level, const uint64_t *key,
-                   KsScratch *ws);
+                   KsScratch *ws, const KsOut *o = nullptr);
+void k_ks_out(he_ctx *c, const KsOut &o, const uint64_t *acc, const uint64_t *lift, int batch, int nl, cudaStream_t s);
 const uint64_t *helr_find_key(const he_ctx *c, uint64_t gal);
 int helr_add_key(he_ctx *c, uint64_t gal);
 int helr_new_ct(he_ctx *c, int level, double scale, he_ct **out);
@@ -301,6 +340,7 @@ void ev_free(Eval *ev);
 int ev_mul_relin(Eval *ev, const CtB &a, const CtB &b, CtB &out);
 int ev_rescale(Eval *ev, const CtB &a, CtB &out);
 int ev_rotate(Eval *ev, const CtB &a, int64_t r, CtB &out);
+int ev_rotate_acc(Eval *ev, const CtB &a, int64_t r, CtB &out, int accumulate);
 int ev_add(Eval *ev, const CtB &a, const CtB &b, CtB &out, int sub);
 int ev_cmul_int(Eval *ev, const CtB &a, int64_t k, double out_scale, CtB &out);
 int ev_cadd_int(Eval *ev, CtB &a, int64_t k);

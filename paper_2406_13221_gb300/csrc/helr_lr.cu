@@ -28,6 +28,7 @@
 static const double G8[3] = {0.5, 0.15, -0.0015};
 static const double G16[3] = {0.5, 0.0843, -0.0002};
 static const double BBAR_EPS = 1e-8;
+static const int ITER_DEPTH = 7;  // levels one iteration consumes
 
 static uint64_t obj_seed(uint64_t base, uint64_t kind, uint64_t index) { return base + (kind << 48) + index; }
 
@@ -152,8 +153,10 @@ extern "C" int he_lr_job_create(he_ctx *c, const double *X, const double *y, siz
         return HE_EINVAL;
     *out = nullptr;
     auto t0 = std::chrono::steady_clock::now();
-    const int L = c->nq - 1;
-    if (L < 7) return helr_fail(c, HE_ELEVEL, "the iteration needs 7 levels (n_q >= 8)");
+    // fresh ciphertexts sit at the iteration depth: the iteration ends at level 0
+    // and any primes of the chain above level 7 stay unused
+    const int L = ITER_DEPTH;
+    if (c->nq - 1 < L) return helr_fail(c, HE_ELEVEL, "the iteration needs 7 levels (n_q >= 8)");
     int g = 1;
     while ((size_t)g < f + 1) g <<= 1;
     if (g > c->nslots) return helr_fail(c, HE_EINVAL, "too many features for N/2 slots");
@@ -313,20 +316,28 @@ static int block_grads(he_lr_job *j, const uint64_t *Z, int cnt, const CtB &W, d
     // 1
     HELR_TRY(ev_mul_relin(ev, Zc, W, A));
     HELR_TRY(ev_rescale(ev, A, Bt));
-    // 2
+    // 2: t += Rot(t, 2^k), ping-pong between T1 and T2
     for (int k = 0; k < j->lg; k++) {
-        HELR_TRY(ev_rotate(ev, Bt, 1 << k, R));
-        HELR_TRY(ev_add(ev, Bt, R, Bt, 0));
+        HELR_TRY(ev_rotate_acc(ev, Bt, 1 << k, R, 1));
+        std::swap(Bt, R);
     }
     // 3
     HELR_TRY(ev_ptmul(ev, Bt, j->mask, j->mask_scale, A));
+    Bt.d = j->T1;
+    R.d = j->T2;
     HELR_TRY(ev_rescale(ev, A, Bt));
     // 4
     for (int k = 0; k < j->lg; k++) {
-        HELR_TRY(ev_rotate(ev, Bt, -(1 << k), R));
-        HELR_TRY(ev_add(ev, Bt, R, Bt, 0));
+        HELR_TRY(ev_rotate_acc(ev, Bt, -(1 << k), R, 1));
+        std::swap(Bt, R);
     }
-    CtB ip = Bt;  // level L-2
+    if (Bt.d != j->T1) {
+        CtB t1{j->T1, cnt, 0, 0, w};
+        HELR_TRY(ev_moddrop(ev, Bt, Bt.level, t1));
+        Bt = t1;
+    }
+    R.d = j->T2;
+    CtB ip = Bt;  // level L-2, in T1
     // 5
     const double k0 = alpha * (1.0 - j->poly[0]), k1 = -(alpha * j->poly[1]), k3 = -(alpha * j->poly[2]);
     CtB sq{j->T3, cnt, 0, 0, w}, c3{j->T4, cnt, 0, 0, w};
@@ -360,10 +371,10 @@ static int finish(he_lr_job *j, CtB acc, const he_ct *Bct, double eta, double in
     Eval *ev = &j->ev;
     const size_t w = j->ctw;
     CtB R{j->T0, 1, 0, 0, w}, A{j->T1, 1, 0, 0, w}, Bd{j->T2, 1, 0, 0, w};
-    // 7
+    // 7: acc += Rot(acc, g 2^k), ping-pong between acc and R
     for (int k = 0; k < j->lm; k++) {
-        HELR_TRY(ev_rotate(ev, acc, (int64_t)j->g << k, R));
-        HELR_TRY(ev_add(ev, acc, R, acc, 0));
+        HELR_TRY(ev_rotate_acc(ev, acc, (int64_t)j->g << k, R, 1));
+        std::swap(acc, R);
     }
     // 8
     CtB Bv{Bct->d, 1, Bct->level, Bct->scale, 0};
@@ -390,19 +401,20 @@ static int finish(he_lr_job *j, CtB acc, const he_ct *Bct, double eta, double in
     return HE_OK;
 }
 
-// decrypt, keep the real part of every slot, re-encode at the top level, encrypt
-static int refresh_dev(he_ctx *c, const uint64_t *ct, int level, double scale, double new_scale, uint64_t seed, uint64_t *dst)
+// decrypt, keep the real part of every slot, re-encode at new_level, encrypt
+static int refresh_dev(he_ctx *c, const uint64_t *ct, int level, double scale, int new_level, double new_scale,
+                       uint64_t seed, uint64_t *dst)
 {
     const size_t N = c->n, ns = c->nslots;
     uint64_t *pt = nullptr, *pt2 = nullptr;
     double *z = nullptr;
     HELR_TRY(helr_alloc(c, (void **)&pt, sizeof(uint64_t) * (level + 1) * N));
-    HELR_TRY(helr_alloc(c, (void **)&pt2, sizeof(uint64_t) * c->nq * N));
+    HELR_TRY(helr_alloc(c, (void **)&pt2, sizeof(uint64_t) * (new_level + 1) * N));
     HELR_TRY(helr_alloc(c, (void **)&z, sizeof(double) * 2 * ns));
     HELR_TRY(helr_decrypt_dev(c, ct, level, pt));
     HELR_TRY(helr_decode_dev(c, pt, scale, z, z + ns));
-    HELR_TRY(helr_encode_dev(c, z, nullptr, 1, 0, c->nq - 1, new_scale, pt2, 0));
-    HELR_TRY(helr_encrypt_dev(c, pt2, c->nq - 1, seed, dst));
+    HELR_TRY(helr_encode_dev(c, z, nullptr, 1, 0, new_level, new_scale, pt2, 0));
+    HELR_TRY(helr_encrypt_dev(c, pt2, new_level, seed, dst));
     helr_free(c, pt);
     helr_free(c, pt2);
     helr_free(c, z);
@@ -439,8 +451,8 @@ extern "C" int he_lr_job_step(he_lr_job *j, int t, he_lr_sched sched)
     HELR_CUDA(c, cudaStreamSynchronize(c->stream));
     auto t1 = std::chrono::steady_clock::now();
     // Step 7: refresh W and V
-    HELR_TRY(refresh_dev(c, Wn.d, Wn.level, Wn.scale, j->scale0, obj_seed(j->enc_seed, 5, t), j->W->d));
-    HELR_TRY(refresh_dev(c, Vn.d, Vn.level, Vn.scale, j->scale0, obj_seed(j->enc_seed, 6, t), j->V->d));
+    HELR_TRY(refresh_dev(c, Wn.d, Wn.level, Wn.scale, j->L, j->scale0, obj_seed(j->enc_seed, 5, t), j->W->d));
+    HELR_TRY(refresh_dev(c, Vn.d, Vn.level, Vn.scale, j->L, j->scale0, obj_seed(j->enc_seed, 6, t), j->V->d));
     j->W->scale = j->scale0;
     j->V->scale = j->scale0;
     HELR_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -578,7 +590,7 @@ extern "C" int he_lr_iteration(he_ctx *c, he_ct *const *Z, size_t nb, const he_c
     if (!c || !Z || !nb || !B || !W || !V || !poly || !W_out || !V_out || g * m != c->nslots || (g & (g - 1)) || g < 1)
         return HE_EINVAL;
     const int L = W->level;
-    if (L < 7) return helr_fail(c, HE_ELEVEL, "the iteration needs 7 levels");
+    if (L < ITER_DEPTH) return helr_fail(c, HE_ELEVEL, "the iteration needs 7 levels");
     for (size_t i = 0; i < nb; i++)
         if (Z[i]->level != L) return helr_fail(c, HE_ELEVEL, "data blocks must share the level of W");
     // a temporary job around the caller's ciphertexts
@@ -635,8 +647,8 @@ extern "C" int he_lr_iteration(he_ctx *c, he_ct *const *Z, size_t nb, const he_c
             glevel = gg.level;
         }
         if (rc) goto out;
-        if ((rc = helr_new_ct(c, L - 7, 0, &Wo))) goto out;
-        if ((rc = helr_new_ct(c, L - 7, 0, &Vo))) goto out;
+        if ((rc = helr_new_ct(c, L - ITER_DEPTH, 0, &Wo))) goto out;
+        if ((rc = helr_new_ct(c, L - ITER_DEPTH, 0, &Vo))) goto out;
         CtB acc{j.acc, 1, glevel, gscale, 0};
         CtB Wn{Wo->d, 1, 0, 0, 0}, Vn{Vo->d, 1, 0, 0, 0};
         if ((rc = finish(&j, acc, B, eta, inv_n, Wn, Vn))) goto out;
@@ -663,12 +675,12 @@ out:
     return HE_OK;
 }
 
-extern "C" int he_refresh(he_ctx *c, const he_ct *in, double scale, uint64_t seed, he_ct **out)
+extern "C" int he_refresh(he_ctx *c, const he_ct *in, int level, double scale, uint64_t seed, he_ct **out)
 {
-    if (!c || !in || !out || !(scale > 0)) return HE_EINVAL;
+    if (!c || !in || !out || !(scale > 0) || level < 0 || level >= c->nq) return HE_EINVAL;
     he_ct *o = nullptr;
-    HELR_TRY(helr_new_ct(c, c->nq - 1, scale, &o));
-    int rc = refresh_dev(c, in->d, in->level, in->scale, scale, seed, o->d);
+    HELR_TRY(helr_new_ct(c, level, scale, &o));
+    int rc = refresh_dev(c, in->d, in->level, in->scale, level, scale, seed, o->d);
     if (!rc) rc = cudaStreamSynchronize(c->stream) == cudaSuccess ? HE_OK : helr_fail(c, HE_ECUDA, "refresh");
     if (rc) {
         he_ct_free(o);

@@ -1,0 +1,204 @@
+// ks.cu -- fused hybrid key switching (the relinearisation inside every Mul and
+// the key switch inside every rotation, Sec. 2.1).
+//
+// Key switching of d (level l, L = l + 1 limbs) with one special prime P and
+// one digit per ciphertext prime:
+//   ModUp    digit i = centred limb i of d in coefficient form, reduced into
+//            every target modulus t in {q_0..q_l, P};
+//   inner    acc_t = sum_i NTT_t(digit i) * key_(i,t)   (two key polynomials);
+//   ModDown  out_j = (acc_j - centred(acc_P) mod q_j) * P^-1.
+// The forward transforms of ModUp are fused with their neighbours:
+//   k_ks_modup_cols  lifts digit i into target t while loading and runs the
+//                    column pass of the transform (t = i is skipped: that limb
+//                    is the evaluation-form input itself);
+//   k_ks_inner_rows  finishes the row pass of every digit for one target and
+//                    multiplies-accumulates with the key rows in registers, so
+//                    the transformed digits are never written out.
+// Items run in waves small enough for the column-pass output to stay in L2.
+#include <stdlib.h>
+#include "ntt_core.cuh"
+
+namespace {
+using namespace nttc;
+
+template <int K1, int K2, int C>
+__global__ void __launch_bounds__(C * Geo<K1>::T)
+    k_ks_modup_cols(const uint64_t *__restrict__ dcoef, uint64_t *__restrict__ mid, const uint64_t *__restrict__ twall,
+                    const ModQ *__restrict__ mods, int nl, int pidx)
+{
+    using G = Geo<K1>;
+    constexpr int R2 = 1 << K2, N = G::R * R2, NG = R2 / C;
+    extern __shared__ uint64_t smem[];
+    int bid = blockIdx.x;
+    const int tt = bid % nl;  // targets of one digit column are adjacent: the column is read from L2
+    bid /= nl;
+    const int grp = bid % NG;
+    bid /= NG;
+    const int i = bid % nl, b = bid / nl;
+    const int t = tt < i ? tt : tt + 1;          // target 0..nl, never i
+    const int pt = t < nl ? t : pidx;
+    const ModQ mt = mods[pt];
+    const uint64_t qi = mods[i].q, q = mt.q, q2 = 2 * q;
+    const uint64_t *tw = twall + (size_t)pt * N * 2;
+    const int jj = threadIdx.x % C, l = threadIdx.x / C;
+    const uint64_t *src = dcoef + ((size_t)b * nl + i) * N + grp * C + jj;
+    uint64_t *dst = mid + (((size_t)b * nl + i) * (nl + 1) + t) * N + grp * C + jj;
+    uint64_t x[G::E];
+#pragma unroll
+    for (int r = 0; r < G::E; r++) x[r] = lift_centered(src[(size_t)(l + G::T * r) * R2], qi, mt);
+    fwd_strided<K1>(x, tw, 1, q, q2);
+    to_contig<K1>(x, smem + jj * G::SEG, l);
+    fwd_contig<K1>(x, tw, 1, l, q, q2);
+#pragma unroll
+    for (int r = 0; r < G::E; r++) dst[(size_t)(G::E * l + r) * R2] = x[r];
+}
+
+template <int E>
+__device__ __forceinline__ void load_contig(uint64_t (&x)[E], const uint64_t *p)
+{
+#pragma unroll
+    for (int r = 0; r < E; r += 2) {
+        ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p + r);
+        x[r] = v.x;
+        x[r + 1] = v.y;
+    }
+}
+
+template <int K1, int K2, int RPC>
+__global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
+    k_ks_inner_rows(const uint64_t *__restrict__ mid, const uint64_t *__restrict__ dntt, const uint64_t *__restrict__ key,
+                    uint64_t *__restrict__ acc, const uint64_t *__restrict__ twall, const ModQ *__restrict__ mods, int nl,
+                    int nq, int pidx, int items)
+{
+    using G = Geo<K2>;
+    constexpr int R1 = 1 << K1, R2 = G::R, N = R1 * R2, NG = R1 / RPC, E = G::E;
+    extern __shared__ uint64_t smem[];
+    int bid = blockIdx.x;
+    const int b = bid % items;  // items sharing one key row are adjacent: the key row is read from L2
+    bid /= items;
+    const int grp = bid % NG;
+    const int t = bid / NG;
+    const int pt = t < nl ? t : pidx, kl = t < nl ? t : nq;
+    const ModQ m = mods[pt];
+    const uint64_t q = m.q, q2 = 2 * q;
+    const uint64_t *tw = twall + (size_t)pt * N * 2;
+    const int l = threadIdx.x % G::T, rl = threadIdx.x / G::T;
+    const int row = grp * RPC + rl;
+    const size_t roff = (size_t)row * R2;
+    uint64_t *seg = smem + rl * G::SEG;
+    uint64_t a0[E], a1[E];
+#pragma unroll
+    for (int r = 0; r < E; r++) a0[r] = a1[r] = 0;
+    for (int i = 0; i < nl; i++) {
+        uint64_t x[E];
+        if (i == t) {
+            load_contig<E>(x, dntt + ((size_t)b * nl + i) * N + roff + E * l);
+        } else {
+            const uint64_t *src = mid + (((size_t)b * nl + i) * (nl + 1) + t) * N + roff;
+#pragma unroll
+            for (int r = 0; r < E; r++) x[r] = src[l + G::T * r];
+            const int A = R1 + row;
+            fwd_strided<K2>(x, tw, A, q, q2);
+            to_contig<K2>(x, seg, l);
+            fwd_contig<K2>(x, tw, A, l, q, q2);
+#pragma unroll
+            for (int r = 0; r < E; r++) {
+                uint64_t v = x[r];
+                v = v >= q2 ? v - q2 : v;
+                x[r] = v >= q ? v - q : v;
+            }
+            __syncthreads();  // seg is rewritten by the next digit
+        }
+        uint64_t k0[E], k1[E];
+        load_contig<E>(k0, key + (((size_t)i * 2 + 0) * (nq + 1) + kl) * N + roff + E * l);
+        load_contig<E>(k1, key + (((size_t)i * 2 + 1) * (nq + 1) + kl) * N + roff + E * l);
+#pragma unroll
+        for (int r = 0; r < E; r++) {
+            a0[r] = addmod(a0[r], mulmod(x[r], k0[r], m), q);
+            a1[r] = addmod(a1[r], mulmod(x[r], k1[r], m), q);
+        }
+    }
+    uint64_t *o0 = acc + (((size_t)b * 2 + 0) * (nl + 1) + t) * N + roff + E * l;
+    uint64_t *o1 = acc + (((size_t)b * 2 + 1) * (nl + 1) + t) * N + roff + E * l;
+#pragma unroll
+    for (int r = 0; r < E; r += 2) {
+        *reinterpret_cast<ulonglong2 *>(o0 + r) = make_ulonglong2(a0[r], a0[r + 1]);
+        *reinterpret_cast<ulonglong2 *>(o1 + r) = make_ulonglong2(a1[r], a1[r + 1]);
+    }
+}
+
+template <int K1, int K2>
+struct KsPlan {
+    static constexpr int T1 = Geo<K1>::T, T2 = Geo<K2>::T;
+    static constexpr int R1 = 1 << K1, R2 = 1 << K2;
+    static constexpr int C = (256 / T1) < R2 ? (256 / T1) : R2;
+    static constexpr int RPC = (128 / T2) < R1 ? (128 / T2) : R1;
+    static constexpr size_t SM1 = (size_t)C * Geo<K1>::SEG * 8;
+    static constexpr size_t SM2 = (size_t)RPC * Geo<K2>::SEG * 8;
+    static cudaError_t prepare()
+    {
+        cudaError_t e = cudaFuncSetAttribute(k_ks_modup_cols<K1, K2, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM1);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_ks_inner_rows<K1, K2, RPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM2);
+        return e;
+    }
+    static void modup(he_ctx *c, const uint64_t *dcoef, uint64_t *mid, int items, int nl, cudaStream_t s)
+    {
+        unsigned grid = (unsigned)((size_t)items * nl * nl * (R2 / C));
+        HELR_LAUNCH(k_ks_modup_cols<K1, K2, C><<<grid, C * T1, SM1, s>>>(dcoef, mid, c->t.tw, c->t.mod, nl, c->nq));
+    }
+    static void inner(he_ctx *c, const uint64_t *mid, const uint64_t *dntt, const uint64_t *key, uint64_t *acc, int items,
+                      int nl, cudaStream_t s)
+    {
+        unsigned grid = (unsigned)((size_t)items * (nl + 1) * (R1 / RPC));
+        HELR_LAUNCH(k_ks_inner_rows<K1, K2, RPC><<<grid, RPC * T2, SM2, s>>>(mid, dntt, key, acc, c->t.tw, c->t.mod, nl,
+                                                                              c->nq, c->nq, items));
+    }
+};
+
+template <int K1, int K2>
+int run_fused(he_ctx *c, const uint64_t *dntt, const uint64_t *dcoef, uint64_t *mid, const uint64_t *key, uint64_t *acc,
+              int items, int nl, cudaStream_t s)
+{
+    static bool prepared = false;
+    if (!prepared) {
+        HELR_CUDA(c, (KsPlan<K1, K2>::prepare()));
+        prepared = true;
+    }
+    prof_start(c, PROF_MODUP, s);
+    KsPlan<K1, K2>::modup(c, dcoef, mid, items, nl, s);
+    prof_stop(c, PROF_MODUP, s, (double)items * nl * nl, 1);
+    prof_start(c, PROF_KS_INNER, s);
+    KsPlan<K1, K2>::inner(c, mid, dntt, key, acc, items, nl, s);
+    prof_stop(c, PROF_KS_INNER, s, (double)items, 1);
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
+
+}  // namespace
+
+// ModUp + transforms + inner product for `items` polynomials: dntt / dcoef are
+// [items][nl][N] (evaluation and coefficient form of the same input); mid is
+// scratch of [items][nl][nl+1][N]; acc receives [items][2][nl+1][N].
+int helr_ks_fused(he_ctx *c, const uint64_t *dntt, const uint64_t *dcoef, uint64_t *mid, const uint64_t *key, uint64_t *acc,
+                  int items, int nl, cudaStream_t s)
+{
+    switch (c->logn) {
+    case 10: return run_fused<5, 5>(c, dntt, dcoef, mid, key, acc, items, nl, s);
+    case 11: return run_fused<5, 6>(c, dntt, dcoef, mid, key, acc, items, nl, s);
+    case 12: return run_fused<6, 6>(c, dntt, dcoef, mid, key, acc, items, nl, s);
+    case 13: return run_fused<6, 7>(c, dntt, dcoef, mid, key, acc, items, nl, s);
+    case 14: return run_fused<7, 7>(c, dntt, dcoef, mid, key, acc, items, nl, s);
+    case 15: return run_fused<7, 8>(c, dntt, dcoef, mid, key, acc, items, nl, s);
+    case 16: return run_fused<8, 8>(c, dntt, dcoef, mid, key, acc, items, nl, s);
+    default: return helr_fail(c, HE_EINVAL, "log_n %d unsupported", c->logn);
+    }
+}
+
+// items per fused wave: the column-pass output of one wave stays in L2
+int helr_ks_wave(const he_ctx *c, int nl)
+{
+    if (c->ks_wave > 0) return c->ks_wave;
+    (void)nl;
+    return 8;  // tuned on GB300 at N = 2^16 (overridable with HELR_KS_WAVE)
+}

@@ -19,128 +19,10 @@
 // forward and [0, 2q) in the inverse) with Shoup twiddle products.
 #include "helr_internal.cuh"
 
+#include "ntt_core.cuh"
+
 namespace {
-
-__device__ __forceinline__ void ct_bfly(uint64_t &x, uint64_t &y, uint64_t w, uint64_t wp, uint64_t q, uint64_t q2)
-{
-    uint64_t a = x >= q2 ? x - q2 : x;
-    uint64_t t = shoup_lazy(y, w, wp, q);
-    x = a + t;
-    y = a - t + q2;
-}
-
-__device__ __forceinline__ void gs_bfly(uint64_t &x, uint64_t &y, uint64_t w, uint64_t wp, uint64_t q, uint64_t q2)
-{
-    uint64_t a = x + y;
-    a = a >= q2 ? a - q2 : a;
-    uint64_t b = x - y + q2;
-    y = shoup_lazy(b, w, wp, q);
-    x = a;
-}
-
-__device__ __forceinline__ ulonglong2 ldtw(const uint64_t *tw, int idx)
-{
-    return __ldg(reinterpret_cast<const ulonglong2 *>(tw) + idx);
-}
-
-// padded shared-memory position of word j inside one column/row segment
-template <int LE>
-__device__ __forceinline__ int spad(int j) { return j + (j >> LE); }
-
-template <int K>
-struct Geo {
-    static constexpr int LE = (K + 1) / 2, LT = K / 2;
-    static constexpr int E = 1 << LE, T = 1 << LT, R = 1 << K;
-    static constexpr int SEG = R + (R >> LE) + 1;  // segment stride in words (odd)
-};
-
-// forward stages on the strided assignment (j = l + T r): local stages s < LE
-template <int K>
-__device__ __forceinline__ void fwd_strided(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, uint64_t q, uint64_t q2)
-{
-    constexpr int E = Geo<K>::E, LE = Geo<K>::LE;
-#pragma unroll
-    for (int s = 0; s < LE; s++) {
-        const int m = 1 << s, hr = E >> (s + 1);
-#pragma unroll
-        for (int g = 0; g < m; g++) {
-            ulonglong2 w = ldtw(tw, m * A + g);
-#pragma unroll
-            for (int k = 0; k < hr; k++) ct_bfly(x[g * 2 * hr + k], x[g * 2 * hr + k + hr], w.x, w.y, q, q2);
-        }
-    }
-}
-
-// forward stages on the contiguous assignment (j = E l + r): local stages s >= LE
-template <int K>
-__device__ __forceinline__ void fwd_contig(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, int l, uint64_t q, uint64_t q2)
-{
-    constexpr int E = Geo<K>::E, LE = Geo<K>::LE, R = Geo<K>::R;
-#pragma unroll
-    for (int s = LE; s < K; s++) {
-        const int m = 1 << s, h = R >> (s + 1), gpt = E / (2 * h);
-#pragma unroll
-        for (int g = 0; g < gpt; g++) {
-            ulonglong2 w = ldtw(tw, m * A + l * gpt + g);
-#pragma unroll
-            for (int k = 0; k < h; k++) ct_bfly(x[g * 2 * h + k], x[g * 2 * h + k + h], w.x, w.y, q, q2);
-        }
-    }
-}
-
-template <int K>
-__device__ __forceinline__ void inv_contig(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, int l, uint64_t q, uint64_t q2)
-{
-    constexpr int E = Geo<K>::E, LE = Geo<K>::LE, R = Geo<K>::R;
-#pragma unroll
-    for (int s = K - 1; s >= LE; s--) {
-        const int m = 1 << s, h = R >> (s + 1), gpt = E / (2 * h);
-#pragma unroll
-        for (int g = 0; g < gpt; g++) {
-            ulonglong2 w = ldtw(tw, m * A + l * gpt + g);
-#pragma unroll
-            for (int k = 0; k < h; k++) gs_bfly(x[g * 2 * h + k], x[g * 2 * h + k + h], w.x, w.y, q, q2);
-        }
-    }
-}
-
-template <int K>
-__device__ __forceinline__ void inv_strided(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, uint64_t q, uint64_t q2)
-{
-    constexpr int E = Geo<K>::E, LE = Geo<K>::LE;
-#pragma unroll
-    for (int s = LE - 1; s >= 0; s--) {
-        const int m = 1 << s, hr = E >> (s + 1);
-#pragma unroll
-        for (int g = 0; g < m; g++) {
-            ulonglong2 w = ldtw(tw, m * A + g);
-#pragma unroll
-            for (int k = 0; k < hr; k++) gs_bfly(x[g * 2 * hr + k], x[g * 2 * hr + k + hr], w.x, w.y, q, q2);
-        }
-    }
-}
-
-// exchange the E words of thread l inside one segment of shared memory
-template <int K>
-__device__ __forceinline__ void to_contig(uint64_t (&x)[Geo<K>::E], uint64_t *seg, int l)
-{
-    constexpr int E = Geo<K>::E, LE = Geo<K>::LE, T = Geo<K>::T;
-#pragma unroll
-    for (int r = 0; r < E; r++) seg[spad<LE>(l + T * r)] = x[r];
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < E; r++) x[r] = seg[spad<LE>(E * l + r)];
-}
-template <int K>
-__device__ __forceinline__ void to_strided(uint64_t (&x)[Geo<K>::E], uint64_t *seg, int l)
-{
-    constexpr int E = Geo<K>::E, LE = Geo<K>::LE, T = Geo<K>::T;
-#pragma unroll
-    for (int r = 0; r < E; r++) seg[spad<LE>(E * l + r)] = x[r];
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < E; r++) x[r] = seg[spad<LE>(l + T * r)];
-}
+using namespace nttc;
 
 // ---------------------------------------------------------------- forward
 // pass 1: columns. grid.x = nlimbs * (R2 / C); block = C * T1 threads.
@@ -154,7 +36,7 @@ __global__ void __launch_bounds__(C * Geo<K1>::T) k_ntt_fwd_cols(const uint64_t 
     extern __shared__ uint64_t smem[];
     const int limb = blockIdx.x / NG, grp = blockIdx.x % NG;
     const int jj = threadIdx.x % C, l = threadIdx.x / C;
-    const int pr = lm.p[limb % lm.period];
+    const int pr = limb_prime(lm, limb);
     const uint64_t q = mods[pr].q, q2 = 2 * q;
     const uint64_t *tw = twall + (size_t)pr * N * 2;
     const size_t base = (size_t)limb * N + grp * C + jj;
@@ -179,7 +61,7 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T) k_ntt_fwd_rows(uint64_t *__r
     const int limb = blockIdx.x / NG, grp = blockIdx.x % NG;
     const int l = threadIdx.x % G::T, rl = threadIdx.x / G::T;
     const int row = grp * RPC + rl;
-    const int pr = lm.p[limb % lm.period];
+    const int pr = limb_prime(lm, limb);
     const uint64_t q = mods[pr].q, q2 = 2 * q;
     const uint64_t *tw = twall + (size_t)pr * N * 2;
     uint64_t *rowp = data + (size_t)limb * N + (size_t)row * R2;
@@ -216,7 +98,7 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T) k_ntt_inv_rows(const uint64_
     const int limb = blockIdx.x / NG, grp = blockIdx.x % NG;
     const int l = threadIdx.x % G::T, rl = threadIdx.x / G::T;
     const int row = grp * RPC + rl;
-    const int pr = lm.p[limb % lm.period];
+    const int pr = limb_prime(lm, limb);
     const uint64_t q = mods[pr].q, q2 = 2 * q;
     const uint64_t *tw = twall + (size_t)pr * N * 2;
     const uint64_t *rin = in + (size_t)limb * N + (size_t)row * R2;
@@ -246,7 +128,7 @@ __global__ void __launch_bounds__(C * Geo<K1>::T) k_ntt_inv_cols(uint64_t *__res
     extern __shared__ uint64_t smem[];
     const int limb = blockIdx.x / NG, grp = blockIdx.x % NG;
     const int jj = threadIdx.x % C, l = threadIdx.x / C;
-    const int pr = lm.p[limb % lm.period];
+    const int pr = limb_prime(lm, limb);
     const uint64_t q = mods[pr].q, q2 = 2 * q;
     const uint64_t *tw = twall + (size_t)pr * N * 2;
     const size_t base = (size_t)limb * N + grp * C + jj;

@@ -1,0 +1,153 @@
+// ntt_core.cuh -- device building blocks of the negacyclic transform, shared by
+// the standalone transform kernels (ntt.cu) and the fused key-switch kernels
+// (ks.cu).  See ntt.cu for the layout and the butterfly forms.
+#pragma once
+#include "helr_internal.cuh"
+
+namespace nttc {
+
+
+__device__ __forceinline__ void ct_bfly(uint64_t &x, uint64_t &y, uint64_t w, uint64_t wp, uint64_t q, uint64_t q2)
+{
+    uint64_t a = x >= q2 ? x - q2 : x;
+    uint64_t t = shoup_lazy(y, w, wp, q);
+    x = a + t;
+    y = a - t + q2;
+}
+
+__device__ __forceinline__ void gs_bfly(uint64_t &x, uint64_t &y, uint64_t w, uint64_t wp, uint64_t q, uint64_t q2)
+{
+    uint64_t a = x + y;
+    a = a >= q2 ? a - q2 : a;
+    uint64_t b = x - y + q2;
+    y = shoup_lazy(b, w, wp, q);
+    x = a;
+}
+
+__device__ __forceinline__ ulonglong2 ldtw(const uint64_t *tw, int idx)
+{
+    return __ldg(reinterpret_cast<const ulonglong2 *>(tw) + idx);
+}
+
+// padded shared-memory position of word j inside one column/row segment
+template <int LE>
+__device__ __forceinline__ int spad(int j) { return j + (j >> LE); }
+
+template <int K>
+struct Geo {
+    static constexpr int LE = (K + 1) / 2, LT = K / 2;
+    static constexpr int E = 1 << LE, T = 1 << LT, R = 1 << K;
+    static constexpr int SEG = R + (R >> LE) + 1;  // segment stride in words (odd)
+};
+
+// Stage loops are template recursions over the stage index with one flattened
+// constant-trip loop per stage, so every index into x[] is a compile-time
+// constant and x[] stays in registers.
+//
+// forward stages on the strided assignment (j = l + T r): local stages s < LE;
+// at local stage m = 2^s the E words form m groups of 2 hr (hr = E / 2m).
+template <int K, int S>
+__device__ __forceinline__ void fwd_strided_st(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, uint64_t q, uint64_t q2)
+{
+    constexpr int E = Geo<K>::E, LE = Geo<K>::LE, m = 1 << S, hr = E >> (S + 1);
+    ulonglong2 w[m];
+#pragma unroll
+    for (int g = 0; g < m; g++) w[g] = ldtw(tw, m * A + g);
+#pragma unroll
+    for (int bf = 0; bf < E / 2; bf++) {
+        const int g = bf / hr, k = bf % hr;
+        ct_bfly(x[g * 2 * hr + k], x[g * 2 * hr + k + hr], w[g].x, w[g].y, q, q2);
+    }
+    if constexpr (S + 1 < LE) fwd_strided_st<K, S + 1>(x, tw, A, q, q2);
+}
+template <int K>
+__device__ __forceinline__ void fwd_strided(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, uint64_t q, uint64_t q2)
+{
+    fwd_strided_st<K, 0>(x, tw, A, q, q2);
+}
+
+// forward stages on the contiguous assignment (j = E l + r): local stages s >= LE;
+// half-span h = R / 2^(s+1) <= E/2, gpt = E / 2h groups per thread.
+template <int K, int S>
+__device__ __forceinline__ void fwd_contig_st(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, int l, uint64_t q, uint64_t q2)
+{
+    constexpr int E = Geo<K>::E, R = Geo<K>::R, m = 1 << S, h = R >> (S + 1), gpt = E / (2 * h);
+    ulonglong2 w[gpt];
+#pragma unroll
+    for (int g = 0; g < gpt; g++) w[g] = ldtw(tw, m * A + l * gpt + g);
+#pragma unroll
+    for (int bf = 0; bf < E / 2; bf++) {
+        const int g = bf / h, k = bf % h;
+        ct_bfly(x[g * 2 * h + k], x[g * 2 * h + k + h], w[g].x, w[g].y, q, q2);
+    }
+    if constexpr (S + 1 < K) fwd_contig_st<K, S + 1>(x, tw, A, l, q, q2);
+}
+template <int K>
+__device__ __forceinline__ void fwd_contig(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, int l, uint64_t q, uint64_t q2)
+{
+    fwd_contig_st<K, Geo<K>::LE>(x, tw, A, l, q, q2);
+}
+
+template <int K, int S>
+__device__ __forceinline__ void inv_contig_st(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, int l, uint64_t q, uint64_t q2)
+{
+    constexpr int E = Geo<K>::E, R = Geo<K>::R, m = 1 << S, h = R >> (S + 1), gpt = E / (2 * h);
+    ulonglong2 w[gpt];
+#pragma unroll
+    for (int g = 0; g < gpt; g++) w[g] = ldtw(tw, m * A + l * gpt + g);
+#pragma unroll
+    for (int bf = 0; bf < E / 2; bf++) {
+        const int g = bf / h, k = bf % h;
+        gs_bfly(x[g * 2 * h + k], x[g * 2 * h + k + h], w[g].x, w[g].y, q, q2);
+    }
+    if constexpr (S - 1 >= Geo<K>::LE) inv_contig_st<K, S - 1>(x, tw, A, l, q, q2);
+}
+template <int K>
+__device__ __forceinline__ void inv_contig(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, int l, uint64_t q, uint64_t q2)
+{
+    inv_contig_st<K, K - 1>(x, tw, A, l, q, q2);
+}
+
+template <int K, int S>
+__device__ __forceinline__ void inv_strided_st(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, uint64_t q, uint64_t q2)
+{
+    constexpr int E = Geo<K>::E, m = 1 << S, hr = E >> (S + 1);
+    ulonglong2 w[m];
+#pragma unroll
+    for (int g = 0; g < m; g++) w[g] = ldtw(tw, m * A + g);
+#pragma unroll
+    for (int bf = 0; bf < E / 2; bf++) {
+        const int g = bf / hr, k = bf % hr;
+        gs_bfly(x[g * 2 * hr + k], x[g * 2 * hr + k + hr], w[g].x, w[g].y, q, q2);
+    }
+    if constexpr (S > 0) inv_strided_st<K, S - 1>(x, tw, A, q, q2);
+}
+template <int K>
+__device__ __forceinline__ void inv_strided(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, uint64_t q, uint64_t q2)
+{
+    inv_strided_st<K, Geo<K>::LE - 1>(x, tw, A, q, q2);
+}
+
+// exchange the E words of thread l inside one segment of shared memory
+template <int K>
+__device__ __forceinline__ void to_contig(uint64_t (&x)[Geo<K>::E], uint64_t *seg, int l)
+{
+    constexpr int E = Geo<K>::E, LE = Geo<K>::LE, T = Geo<K>::T;
+#pragma unroll
+    for (int r = 0; r < E; r++) seg[spad<LE>(l + T * r)] = x[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < E; r++) x[r] = seg[spad<LE>(E * l + r)];
+}
+template <int K>
+__device__ __forceinline__ void to_strided(uint64_t (&x)[Geo<K>::E], uint64_t *seg, int l)
+{
+    constexpr int E = Geo<K>::E, LE = Geo<K>::LE, T = Geo<K>::T;
+#pragma unroll
+    for (int r = 0; r < E; r++) seg[spad<LE>(E * l + r)] = x[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < E; r++) x[r] = seg[spad<LE>(l + T * r)];
+}
+
+}  // namespace nttc

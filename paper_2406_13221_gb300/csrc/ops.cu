@@ -21,7 +21,7 @@ __global__ void k_add_kernel(uint64_t *out, const uint64_t *a, const uint64_t *b
 {
     GS_LOOP(i, npairs) {
         size_t limb = i / half_n;
-        uint64_t q = mods[lm.p[limb % lm.period]].q;
+        uint64_t q = mods[limb_prime(lm, limb)].q;
         ulonglong2 x = reinterpret_cast<const ulonglong2 *>(a)[i];
         ulonglong2 y = reinterpret_cast<const ulonglong2 *>(b)[i];
         ulonglong2 z;
@@ -36,7 +36,7 @@ __global__ void k_mul_kernel(uint64_t *out, const uint64_t *a, const uint64_t *b
 {
     GS_LOOP(i, npairs) {
         size_t limb = i / half_n;
-        ModQ m = mods[lm.p[limb % lm.period]];
+        ModQ m = mods[limb_prime(lm, limb)];
         ulonglong2 x = reinterpret_cast<const ulonglong2 *>(a)[i];
         ulonglong2 y = reinterpret_cast<const ulonglong2 *>(b)[i];
         ulonglong2 z;
@@ -46,28 +46,28 @@ __global__ void k_mul_kernel(uint64_t *out, const uint64_t *a, const uint64_t *b
     }
 }
 
-// (d0, d1, d2) = (a0 b0, a0 b1 + a1 b0, a1 b1); a, b: items of [2][L][N]; d_i at d + item * d_stride + i * d_poly
-__global__ void k_tensor_kernel(const uint64_t *a, const uint64_t *b, uint64_t *d, size_t npairs, int half_n,
-                                int nl, size_t a_stride, size_t b_stride, size_t d_stride, size_t d_poly, const ModQ *mods)
+// (d0, d1, d2) = (a0 b0, a0 b1 + a1 b0, a1 b1); a, b: items of [2][L][N]; d_i at d + item * d_stride + i * d_poly.
+// grid: (N/2 / 256, limbs, items)
+__global__ void k_tensor_kernel(const uint64_t *a, const uint64_t *b, uint64_t *d, int half_n, int nl, size_t a_stride,
+                                size_t b_stride, size_t d_stride, size_t d_poly, const ModQ *mods)
 {
-    GS_LOOP(i, npairs) {
-        size_t per = (size_t)nl * half_n;
-        size_t bt = i / per, r = i % per;
-        int limb = (int)(r / half_n);
-        ModQ m = mods[limb];
-        const ulonglong2 *A = reinterpret_cast<const ulonglong2 *>(a + bt * a_stride);
-        const ulonglong2 *B = reinterpret_cast<const ulonglong2 *>(b + bt * b_stride);
-        ulonglong2 *D0 = reinterpret_cast<ulonglong2 *>(d + bt * d_stride);
-        ulonglong2 *D1 = reinterpret_cast<ulonglong2 *>(d + bt * d_stride + d_poly);
-        ulonglong2 *D2 = reinterpret_cast<ulonglong2 *>(d + bt * d_stride + 2 * d_poly);
-        ulonglong2 a0 = A[r], a1 = A[per + r], b0 = B[r], b1 = B[per + r];
-        ulonglong2 o0, o1, o2;
-        o0.x = mulmod(a0.x, b0.x, m); o0.y = mulmod(a0.y, b0.y, m);
-        o1.x = addmod(mulmod(a0.x, b1.x, m), mulmod(a1.x, b0.x, m), m.q);
-        o1.y = addmod(mulmod(a0.y, b1.y, m), mulmod(a1.y, b0.y, m), m.q);
-        o2.x = mulmod(a1.x, b1.x, m); o2.y = mulmod(a1.y, b1.y, m);
-        D0[r] = o0; D1[r] = o1; D2[r] = o2;
-    }
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= half_n) return;
+    const int limb = blockIdx.y;
+    const size_t bt = blockIdx.z;
+    const ModQ m = mods[limb];
+    const size_t per = (size_t)nl * half_n, r = (size_t)limb * half_n + w;
+    const ulonglong2 *A = reinterpret_cast<const ulonglong2 *>(a + bt * a_stride);
+    const ulonglong2 *B = reinterpret_cast<const ulonglong2 *>(b + bt * b_stride);
+    ulonglong2 a0 = A[r], a1 = A[per + r], b0 = B[r], b1 = B[per + r];
+    ulonglong2 o0, o1, o2;
+    o0.x = mulmod(a0.x, b0.x, m); o0.y = mulmod(a0.y, b0.y, m);
+    o1.x = addmod(mulmod(a0.x, b1.x, m), mulmod(a1.x, b0.x, m), m.q);
+    o1.y = addmod(mulmod(a0.y, b1.y, m), mulmod(a1.y, b0.y, m), m.q);
+    o2.x = mulmod(a1.x, b1.x, m); o2.y = mulmod(a1.y, b1.y, m);
+    reinterpret_cast<ulonglong2 *>(d + bt * d_stride)[r] = o0;
+    reinterpret_cast<ulonglong2 *>(d + bt * d_stride + d_poly)[r] = o1;
+    reinterpret_cast<ulonglong2 *>(d + bt * d_stride + 2 * d_poly)[r] = o2;
 }
 
 // out = in * k_j (Shoup pair per limb position j = limb % period)
@@ -118,158 +118,144 @@ __global__ void k_automorph_kernel(uint64_t *out, const uint64_t *in, size_t nwo
     }
 }
 
-// out[b][t][k] = centred(in[b][k] mod q_src) reduced mod prime(t), t < dst.period
-__global__ void k_lift_kernel(const uint64_t *in, uint64_t *out, size_t nwords, int logn, int ndst, int src_prime,
-                              size_t in_stride, size_t out_stride, const ModQ *mods, LimbMap dst)
+// out[b][t][k] = centred(in[b][k] mod q_src) reduced mod prime(t), t < dst.period; grid (N / 256, ndst, items)
+__global__ void k_lift_kernel(const uint64_t *in, uint64_t *out, int n, int src_prime, size_t in_stride,
+                              size_t out_stride, const ModQ *mods, LimbMap dst)
 {
-    const int n = 1 << logn;
-    const uint64_t qs = mods[src_prime].q;
-    GS_LOOP(i, nwords) {
-        size_t per = (size_t)ndst << logn;
-        size_t bt = i / per, r = i % per;
-        int t = (int)(r >> logn), k = (int)(r & (n - 1));
-        uint64_t v = in[bt * in_stride + k];
-        out[bt * out_stride + r] = lift_centered(v, qs, mods[dst.p[t]]);
-    }
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int t = blockIdx.y;
+    const size_t bt = blockIdx.z;
+    const ModQ mt = mods[map_prime(dst, t)];
+    out[bt * out_stride + (size_t)t * n + k] = lift_centered(in[bt * in_stride + k], mods[src_prime].q, mt);
 }
 
-// out[b][j][k] = (in[b][j][k] - corr[b][j][k]) * inv_j mod q_j, j < nl
-__global__ void k_combine_kernel(uint64_t *out, const uint64_t *in, const uint64_t *corr, size_t npairs, int half_n,
-                                 int nl, size_t in_stride, size_t corr_stride, size_t out_stride,
-                                 const uint64_t *inv, const ModQ *mods)
+// out[b][j][k] = (in[b][j][k] - corr[b][j][k]) * inv_j mod q_j, j < nl; grid (N/2 / 256, nl, items)
+__global__ void k_combine_kernel(uint64_t *out, const uint64_t *in, const uint64_t *corr, int half_n, size_t in_stride,
+                                 size_t corr_stride, size_t out_stride, const uint64_t *inv, const ModQ *mods)
 {
-    GS_LOOP(i, npairs) {
-        size_t per = (size_t)nl * half_n;
-        size_t bt = i / per, r = i % per;
-        int j = (int)(r / half_n);
-        uint64_t q = mods[j].q, w = inv[2 * j], wp = inv[2 * j + 1];
-        ulonglong2 x = reinterpret_cast<const ulonglong2 *>(in + bt * in_stride)[r];
-        ulonglong2 y = reinterpret_cast<const ulonglong2 *>(corr + bt * corr_stride)[r];
-        ulonglong2 z;
-        z.x = shoup(submod(x.x, y.x, q), w, wp, q);
-        z.y = shoup(submod(x.y, y.y, q), w, wp, q);
-        reinterpret_cast<ulonglong2 *>(out + bt * out_stride)[r] = z;
-    }
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= half_n) return;
+    const int j = blockIdx.y;
+    const size_t bt = blockIdx.z, r = (size_t)j * half_n + w;
+    const uint64_t q = mods[j].q, wv = inv[2 * j], wp = inv[2 * j + 1];
+    ulonglong2 x = reinterpret_cast<const ulonglong2 *>(in + bt * in_stride)[r];
+    ulonglong2 y = reinterpret_cast<const ulonglong2 *>(corr + bt * corr_stride)[r];
+    ulonglong2 z;
+    z.x = shoup(submod(x.x, y.x, q), wv, wp, q);
+    z.y = shoup(submod(x.y, y.y, q), wv, wp, q);
+    reinterpret_cast<ulonglong2 *>(out + bt * out_stride)[r] = z;
 }
 
-// ModUp: ext[b][i][t][k] = centred(dcoef[b][i][k] mod q_i) mod prime(t), t = 0..L (L = level+1 is P)
-__global__ void k_modup_kernel(const uint64_t *dcoef, uint64_t *ext, size_t nwords, int logn, int nl, int pidx,
-                               size_t in_stride, size_t ext_stride, const ModQ *mods)
+// grid: (N/2 / 256, npoly * nl, items)
+__global__ void k_ew_kernel(int op, Str out, Str a, Str b, int half_n, int nl, const KP kp, const ModQ *mods)
 {
-    const int n = 1 << logn, nt = nl + 1;
-    GS_LOOP(i, nwords) {
-        size_t per = (size_t)nl * nt << logn;
-        size_t bt = i / per, r = i % per;
-        int k = (int)(r & (n - 1));
-        int it = (int)(r >> logn);
-        int dig = it / nt, t = it % nt;
-        uint64_t v = dcoef[bt * in_stride + ((size_t)dig << logn) + k];
-        int tp = t < nl ? t : pidx;
-        ext[bt * ext_stride + r] = lift_centered(v, mods[dig].q, mods[tp]);
-    }
-}
-
-// inner product with the key: acc[b][p][t][k] = sum_i ext[b][i][t][k] key[i][p][kl(t)][k]
-__global__ void k_ks_inner_kernel(const uint64_t *ext, const uint64_t *key, uint64_t *acc, size_t npairs, int half_n,
-                                  int nl, int nq, size_t ext_stride, size_t acc_stride, const ModQ *mods)
-{
-    const int nt = nl + 1;
-    GS_LOOP(i, npairs) {
-        size_t per = (size_t)nt * half_n;
-        size_t bt = i / per, r = i % per;
-        int t = (int)(r / half_n);
-        size_t kk = r % half_n;
-        int kl = t < nl ? t : nq;
-        ModQ m = mods[kl];
-        const ulonglong2 *E = reinterpret_cast<const ulonglong2 *>(ext + bt * ext_stride);
-        const ulonglong2 *Kp = reinterpret_cast<const ulonglong2 *>(key);
-        uint64_t s0x = 0, s0y = 0, s1x = 0, s1y = 0;
-        for (int dg = 0; dg < nl; dg++) {
-            ulonglong2 x = E[((size_t)dg * nt + t) * half_n + kk];
-            ulonglong2 k0 = __ldg(Kp + (((size_t)dg * 2 + 0) * (nq + 1) + kl) * half_n + kk);
-            ulonglong2 k1 = __ldg(Kp + (((size_t)dg * 2 + 1) * (nq + 1) + kl) * half_n + kk);
-            s0x = addmod(s0x, mulmod(x.x, k0.x, m), m.q);
-            s0y = addmod(s0y, mulmod(x.y, k0.y, m), m.q);
-            s1x = addmod(s1x, mulmod(x.x, k1.x, m), m.q);
-            s1y = addmod(s1y, mulmod(x.y, k1.y, m), m.q);
-        }
-        ulonglong2 *A = reinterpret_cast<ulonglong2 *>(acc + bt * acc_stride);
-        A[r] = make_ulonglong2(s0x, s0y);
-        A[(size_t)nt * half_n + r] = make_ulonglong2(s1x, s1y);
-    }
-}
-
-__global__ void k_ew_kernel(int op, Str out, Str a, Str b, size_t npairs, int half_n, int npoly, int nl,
-                            const KP kp, const ModQ *mods)
-{
-    GS_LOOP(i, npairs) {
-        size_t per_poly = (size_t)nl * half_n, per_item = per_poly * npoly;
-        size_t bt = i / per_item, r = i % per_item;
-        size_t pl = r / per_poly, w = r % per_poly;
-        int j = (int)(w / half_n);
-        ModQ m = mods[j];
-        size_t off = 2 * w;
-        ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(a.p + bt * a.item + pl * a.poly + off);
-        ulonglong2 z;
-        if (op == EW_COPY) {
-            z = x;
-        } else if (op == EW_NEG) {
-            z.x = x.x ? m.q - x.x : 0;
-            z.y = x.y ? m.q - x.y : 0;
-        } else if (op == EW_CMUL) {
-            uint64_t wv = kp.w[j][0], wp = kp.w[j][1];
-            z.x = shoup(x.x, wv, wp, m.q);
-            z.y = shoup(x.y, wv, wp, m.q);
-        } else if (op == EW_CADD) {
-            z.x = addmod(x.x, kp.w[j][0], m.q);
-            z.y = addmod(x.y, kp.w[j][0], m.q);
-        } else if (op == EW_SUBMUL) {
-            ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(b.p + bt * b.item + pl * b.poly + off);
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= half_n) return;
+    const int pl = blockIdx.y / nl, j = blockIdx.y % nl;
+    const size_t bt = blockIdx.z;
+    const ModQ m = mods[j];
+    const size_t off = 2 * ((size_t)j * half_n + w);
+    ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(a.p + bt * a.item + pl * a.poly + off);
+    ulonglong2 z;
+    if (op == EW_COPY) {
+        z = x;
+    } else if (op == EW_NEG) {
+        z.x = x.x ? m.q - x.x : 0;
+        z.y = x.y ? m.q - x.y : 0;
+    } else if (op == EW_CMUL) {
+        uint64_t wv = kp.w[j][0], wp = kp.w[j][1];
+        z.x = shoup(x.x, wv, wp, m.q);
+        z.y = shoup(x.y, wv, wp, m.q);
+    } else if (op == EW_CADD) {
+        z.x = addmod(x.x, kp.w[j][0], m.q);
+        z.y = addmod(x.y, kp.w[j][0], m.q);
+    } else {
+        ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(b.p + bt * b.item + pl * b.poly + off);
+        if (op == EW_SUBMUL) {
             uint64_t wv = kp.w[j][0], wp = kp.w[j][1];
             z.x = shoup(submod(x.x, y.x, m.q), wv, wp, m.q);
             z.y = shoup(submod(x.y, y.y, m.q), wv, wp, m.q);
+        } else if (op == EW_ADD) {
+            z.x = addmod(x.x, y.x, m.q);
+            z.y = addmod(x.y, y.y, m.q);
+        } else if (op == EW_SUB) {
+            z.x = submod(x.x, y.x, m.q);
+            z.y = submod(x.y, y.y, m.q);
         } else {
-            ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(b.p + bt * b.item + pl * b.poly + off);
-            if (op == EW_ADD) { z.x = addmod(x.x, y.x, m.q); z.y = addmod(x.y, y.y, m.q); }
-            else if (op == EW_SUB) { z.x = submod(x.x, y.x, m.q); z.y = submod(x.y, y.y, m.q); }
-            else { z.x = mulmod(x.x, y.x, m); z.y = mulmod(x.y, y.y, m); }
+            z.x = mulmod(x.x, y.x, m);
+            z.y = mulmod(x.y, y.y, m);
         }
-        *reinterpret_cast<ulonglong2 *>(out.p + bt * out.item + pl * out.poly + off) = z;
     }
+    *reinterpret_cast<ulonglong2 *>(out.p + bt * out.item + pl * out.poly + off) = z;
 }
 
-__global__ void k_automorph_items_kernel(uint64_t *out, size_t out_item, const uint64_t *in, size_t in_item, size_t nwords,
-                                         int logn, int nl, uint64_t gal)
+// grid: (N / 256, nl, items)
+__global__ void k_automorph_items_kernel(uint64_t *out, size_t out_item, const uint64_t *in, size_t in_item, int logn,
+                                         uint64_t gal)
 {
-    const uint64_t mask2n = (2ull << logn) - 1;
     const int n = 1 << logn;
-    GS_LOOP(i, nwords) {
-        size_t per = (size_t)nl << logn;
-        size_t bt = i / per, r = i % per;
-        size_t limb = r >> logn;
-        uint32_t p = (uint32_t)(r & (n - 1));
-        uint32_t k = __brev(p) >> (32 - logn);
-        uint64_t e = ((2ull * k + 1) * gal) & mask2n;
-        uint32_t ks = (uint32_t)((e - 1) >> 1);
-        uint32_t ps = __brev(ks) >> (32 - logn);
-        out[bt * out_item + r] = in[bt * in_item + (limb << logn) + ps];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const size_t limb = blockIdx.y, bt = blockIdx.z;
+    const uint64_t mask2n = (2ull << logn) - 1;
+    uint32_t k = __brev((uint32_t)p) >> (32 - logn);
+    uint64_t e = ((2ull * k + 1) * gal) & mask2n;
+    uint32_t ks = (uint32_t)((e - 1) >> 1);
+    uint32_t ps = __brev(ks) >> (32 - logn);
+    out[bt * out_item + (limb << logn) + p] = in[bt * in_item + (limb << logn) + ps];
+}
+
+// ModDown output stage fused with relinearisation / rotation / accumulation.
+// grid: (N / 256, nl, items * 2); ks = (accP - lift) * P^-1 per limb j.
+__global__ void k_ks_out_kernel(KsOut o, const uint64_t *acc, const uint64_t *lift, int logn, int nl, const uint64_t *pinv,
+                                const ModQ *mods)
+{
+    const int n = 1 << logn;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int j = blockIdx.y;
+    const int p = blockIdx.z & 1;
+    const size_t bt = blockIdx.z >> 1;
+    const uint64_t q = mods[j].q;
+    const size_t lk = ((size_t)j << logn) + k;
+    const size_t nt = (size_t)nl + 1;
+    uint64_t a = acc[(bt * 2 + p) * (nt << logn) + lk];
+    uint64_t l = lift[(bt * 2 + p) * ((size_t)nl << logn) + lk];
+    uint64_t v = shoup(submod(a, l, q), pinv[2 * j], pinv[2 * j + 1], q);
+    if (o.rel) v = addmod(v, o.rel[bt * o.rel_item + p * o.rel_poly + lk], q);
+    if (o.rot && p == 0) {
+        const uint64_t mask2n = (2ull << logn) - 1;
+        uint32_t kk = __brev((uint32_t)k) >> (32 - logn);
+        uint64_t e = ((2ull * kk + 1) * o.gal) & mask2n;
+        uint32_t ps = __brev((uint32_t)((e - 1) >> 1)) >> (32 - logn);
+        v = addmod(v, o.rot[bt * o.rot_item + ((size_t)j << logn) + ps], q);
     }
+    if (o.acc) v = addmod(v, o.acc[bt * o.acc_item + p * o.acc_poly + lk], q);
+    o.out.p[bt * o.out.item + p * o.out.poly + lk] = v;
 }
 
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
+void k_ks_out(he_ctx *c, const KsOut &o, const uint64_t *acc, const uint64_t *lift, int batch, int nl, cudaStream_t s)
+{
+    dim3 grid((c->n + 255) / 256, nl, 2 * batch);
+    if (batch) HELR_LAUNCH(k_ks_out_kernel<<<grid, 256, 0, s>>>(o, acc, lift, c->logn, nl, c->d_pinv, c->t.mod));
+}
+
 void k_ew(he_ctx *c, int op, Str out, Str a, Str b, int batch, int npoly, int nl, const KP *kp, cudaStream_t s)
 {
     static const KP zero = {};
-    size_t np = (size_t)batch * npoly * nl * (c->n / 2);
-    if (np) HELR_LAUNCH(k_ew_kernel<<<grid_for(np), 256, 0, s>>>(op, out, a, b, np, c->n / 2, npoly, nl, kp ? *kp : zero, c->t.mod));
+    const int hn = c->n / 2;
+    dim3 grid((hn + 255) / 256, npoly * nl, batch);
+    if (batch && npoly && nl) HELR_LAUNCH(k_ew_kernel<<<grid, 256, 0, s>>>(op, out, a, b, hn, nl, kp ? *kp : zero, c->t.mod));
 }
 void k_automorph_items(he_ctx *c, uint64_t *out, size_t out_item, const uint64_t *in, size_t in_item, int batch, int nl,
                        uint64_t gal, cudaStream_t s)
 {
-    size_t nw = (size_t)batch * nl << c->logn;
-    if (nw) HELR_LAUNCH(k_automorph_items_kernel<<<grid_for(nw), 256, 0, s>>>(out, out_item, in, in_item, nw, c->logn, nl, gal));
+    dim3 grid((c->n + 255) / 256, nl, batch);
+    if (batch && nl) HELR_LAUNCH(k_automorph_items_kernel<<<grid, 256, 0, s>>>(out, out_item, in, in_item, c->logn, gal));
 }
 void k_add(he_ctx *c, uint64_t *out, const uint64_t *a, const uint64_t *b, size_t nlimbs, const LimbMap &m, int sub, cudaStream_t s)
 {
@@ -284,8 +270,9 @@ void k_mul(he_ctx *c, uint64_t *out, const uint64_t *a, const uint64_t *b, size_
 void k_tensor(he_ctx *c, const uint64_t *a, const uint64_t *b, uint64_t *d, int batch, int level,
               size_t a_stride, size_t b_stride, size_t d_stride, size_t d_poly, cudaStream_t s)
 {
-    size_t np = (size_t)batch * (level + 1) * (c->n / 2);
-    if (np) HELR_LAUNCH(k_tensor_kernel<<<grid_for(np), 256, 0, s>>>(a, b, d, np, c->n / 2, level + 1, a_stride, b_stride, d_stride, d_poly, c->t.mod));
+    const int hn = c->n / 2;
+    dim3 grid((hn + 255) / 256, level + 1, batch);
+    if (batch) HELR_LAUNCH(k_tensor_kernel<<<grid, 256, 0, s>>>(a, b, d, hn, level + 1, a_stride, b_stride, d_stride, d_poly, c->t.mod));
 }
 void k_cmul_const(he_ctx *c, uint64_t *out, const uint64_t *in, const uint64_t *kp, size_t nlimbs, int period, cudaStream_t s)
 {
@@ -305,31 +292,13 @@ void k_automorph(he_ctx *c, uint64_t *out, const uint64_t *in, size_t nlimbs, ui
 void k_lift(he_ctx *c, const uint64_t *in, uint64_t *out, int batch, int src_prime, size_t in_stride,
             const LimbMap &dst, size_t out_stride, cudaStream_t s)
 {
-    size_t nw = (size_t)batch * dst.period << c->logn;
-    if (nw) HELR_LAUNCH(k_lift_kernel<<<grid_for(nw), 256, 0, s>>>(in, out, nw, c->logn, dst.period, src_prime, in_stride, out_stride, c->t.mod, dst));
+    dim3 grid((c->n + 255) / 256, dst.period, batch);
+    if (batch) HELR_LAUNCH(k_lift_kernel<<<grid, 256, 0, s>>>(in, out, c->n, src_prime, in_stride, out_stride, c->t.mod, dst));
 }
 void k_rescale_combine(he_ctx *c, uint64_t *out, const uint64_t *in, const uint64_t *corr, int batch, int nl,
                        size_t in_stride, size_t corr_stride, size_t out_stride, const uint64_t *inv_pairs, cudaStream_t s)
 {
-    size_t np = (size_t)batch * nl * (c->n / 2);
-    if (np) HELR_LAUNCH(k_combine_kernel<<<grid_for(np), 256, 0, s>>>(out, in, corr, np, c->n / 2, nl, in_stride, corr_stride, out_stride, inv_pairs, c->t.mod));
-}
-void k_modup(he_ctx *c, const uint64_t *dcoef, const uint64_t *dntt, uint64_t *ext, int batch, int level,
-             size_t in_stride, size_t ext_stride, cudaStream_t s)
-{
-    (void)dntt;
-    int nl = level + 1;
-    size_t nw = (size_t)batch * nl * (nl + 1) << c->logn;
-    prof_start(c, PROF_MODUP, s);
-    if (nw) HELR_LAUNCH(k_modup_kernel<<<grid_for(nw), 256, 0, s>>>(dcoef, ext, nw, c->logn, nl, c->nq, in_stride, ext_stride, c->t.mod));
-    prof_stop(c, PROF_MODUP, s, (double)batch * nl * (nl + 1), 1);
-}
-void k_ks_inner(he_ctx *c, const uint64_t *ext, const uint64_t *key, uint64_t *acc, int batch, int level,
-                size_t ext_stride, size_t acc_stride, cudaStream_t s)
-{
-    int nl = level + 1;
-    size_t np = (size_t)batch * (nl + 1) * (c->n / 2);
-    prof_start(c, PROF_KS_INNER, s);
-    if (np) HELR_LAUNCH(k_ks_inner_kernel<<<grid_for(np), 256, 0, s>>>(ext, key, acc, np, c->n / 2, nl, c->nq, ext_stride, acc_stride, c->t.mod));
-    prof_stop(c, PROF_KS_INNER, s, (double)batch, 1);
+    const int hn = c->n / 2;
+    dim3 grid((hn + 255) / 256, nl, batch);
+    if (batch) HELR_LAUNCH(k_combine_kernel<<<grid, 256, 0, s>>>(out, in, corr, hn, in_stride, corr_stride, out_stride, inv_pairs, c->t.mod));
 }

@@ -224,9 +224,10 @@ def small_job_inputs(pair):
     return ctx, he, data, circ
 
 
-def test_iteration_bitwise(small_job_inputs):
-    ctx, he, data, circ = small_job_inputs
-    L = 8
+@pytest.mark.parametrize("L", [8, 7])
+def test_iteration_bitwise(small_job_inputs, L):
+    ctx, he, data, _ = small_job_inputs
+    circ = qgnag.Circuit(he, 16, 256, D, start_level=L)
     Z = [he.encrypt(he.encode(data.blocks[b], L, D), 100 + b) for b in range(data.blocks.shape[0])]
     B = he.encrypt(he.encode(np.tile(data.n * data.bbar_full, circ.m), L, D), 200)
     rng = np.random.default_rng(12)
@@ -244,7 +245,7 @@ def test_iteration_bitwise(small_job_inputs):
     assert np.array_equal(gV.export(), Vn.data)
     # refresh of both
     for x, rx, seed in ((gW, Wn, 301), (gV, Vn, 302)):
-        assert np.array_equal(ctx.refresh(x, D, seed).export(), circ.refresh(rx, seed).data)
+        assert np.array_equal(ctx.refresh(x, circ.L, D, seed).export(), circ.refresh(rx, seed).data)
 
 
 def test_job_step_bitwise_and_weights(small_job_inputs):
@@ -254,14 +255,16 @@ def test_job_step_bitwise_and_weights(small_job_inputs):
     st = job.stats()
     assert (st.n_blocks, st.g, st.m) == (4, 16, 256)
     # encrypted data blocks equal the oracle's encryption of the same packing
+    L = circ.L
+    assert L == 7
     for b in range(4):
-        ref = he.encrypt(he.encode(data.blocks[b], 8, D), qgnag.obj_seed(3, qgnag.SEED_BLOCK, b))
+        ref = he.encrypt(he.encode(data.blocks[b], L, D), qgnag.obj_seed(3, qgnag.SEED_BLOCK, b))
         assert np.array_equal(job.input(0, b).export(), ref.data)
     Bg = job.input(1, 0)
-    Z = [OCt(job.input(0, b).export(), 8, D) for b in range(4)]
-    B = OCt(Bg.export(), 8, D)
+    Z = [OCt(job.input(0, b).export(), L, D) for b in range(4)]
+    B = OCt(Bg.export(), L, D)
     (Ww, _, _), (Vw, _, _) = job.state_words()
-    W, V = OCt(Ww, 8, D), OCt(Vw, 8, D)
+    W, V = OCt(Ww, L, D), OCt(Vw, L, D)
     etas = qgnag.nag_scalars(2)
     for t in range(2):
         job.step(t)

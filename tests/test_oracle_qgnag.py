@@ -149,7 +149,7 @@ def test_encrypted_small_config_matches_fp64_twin(small_run):
     assert err < 1e-3
     # the first iteration's W', V' before refresh as well
     Wn, Vn = trace[0][0], trace[0][1]
-    assert Wn.level == 1 and Vn.level == 1
+    assert Wn.level == 0 and Vn.level == 0
     zw = he.decode(he.decrypt(Wn)).real.reshape(circ.m, circ.g)
     assert np.abs(zw - hist[0][0][None, :]).max() < 1e-3
 
