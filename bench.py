@@ -229,7 +229,7 @@ def ctw_bytes():
 
 
 def info_chunk(job, args):
-    return min(args.chunk if args.chunk else 16, int(job.info.n_blocks))
+    return min(args.chunk if args.chunk else 64, int(job.info.n_blocks))
 
 
 _PINNED = []

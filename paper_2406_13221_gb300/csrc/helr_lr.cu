@@ -270,7 +270,7 @@ extern "C" int he_lr_job_create(he_ctx *c, const double *X, const double *y, siz
         helr_free(c, d);
     }
     // work buffers: chunk of blocks per launch
-    int chunk = batch_blocks > 0 ? batch_blocks : (c->logn >= 16 ? 16 : 32);
+    int chunk = batch_blocks > 0 ? batch_blocks : 64;  // tuned on GB300 at N = 2^16
     chunk = std::min(chunk, mode == HE_LR_FULL_BATCH ? j->nblocks : j->bpb);
     j->chunk = std::max(1, chunk);
     j->chunk_max = j->chunk;
@@ -605,7 +605,7 @@ extern "C" int he_lr_iteration(he_ctx *c, he_ct *const *Z, size_t nb, const he_c
     j.scale0 = W->scale;
     const size_t N = c->n;
     j.ctw = 2 * (size_t)(L + 1) * N;
-    j.chunk = (int)std::min<size_t>(nb, c->logn >= 16 ? 16 : 32);
+    j.chunk = (int)std::min<size_t>(nb, 64);
     int rc = HE_OK;
     uint64_t *zbuf = nullptr;
     std::vector<double> msk(c->nslots, 0.0);

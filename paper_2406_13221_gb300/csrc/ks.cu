@@ -200,5 +200,5 @@ int helr_ks_wave(const he_ctx *c, int nl)
 {
     if (c->ks_wave > 0) return c->ks_wave;
     (void)nl;
-    return 8;  // tuned on GB300 at N = 2^16 (overridable with HELR_KS_WAVE)
+    return 32;  // tuned on GB300 at N = 2^16 (overridable with HELR_KS_WAVE)
 }
