@@ -22,7 +22,7 @@ namespace {
 using namespace nttc;
 
 template <int K1, int K2, int C>
-__global__ void __launch_bounds__(C * Geo<K1>::T)
+__global__ void __launch_bounds__(C * Geo<K1>::T, 4)
     k_ks_modup_cols(const uint64_t *__restrict__ dcoef, uint64_t *__restrict__ mid, const uint64_t *__restrict__ twall,
                     const ModQ *__restrict__ mods, int nl, int pidx)
 {
@@ -137,6 +137,8 @@ struct KsPlan {
     static constexpr size_t SM2 = (size_t)RPC * Geo<K2>::SEG * 8;
     static cudaError_t prepare()
     {
+        cudaFuncSetAttribute(k_ks_modup_cols<K1, K2, C>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_ks_inner_rows<K1, K2, RPC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         cudaError_t e = cudaFuncSetAttribute(k_ks_modup_cols<K1, K2, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM1);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_ks_inner_rows<K1, K2, RPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM2);

@@ -155,6 +155,10 @@ struct NttPlan {
 
     static cudaError_t prepare()
     {
+        cudaFuncSetAttribute(k_ntt_fwd_cols<K1, K2, C>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_ntt_inv_cols<K1, K2, C>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_ntt_fwd_rows<K1, K2, RPC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_ntt_inv_rows<K1, K2, RPC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         cudaError_t e = cudaFuncSetAttribute(k_ntt_fwd_cols<K1, K2, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM1);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_inv_cols<K1, K2, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM1);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_fwd_rows<K1, K2, RPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM2);
