@@ -146,6 +146,21 @@ int he_ntt_inverse(he_ctx *ctx, uint64_t *d_limbs, size_t n_limbs, const int *pr
  * allocated by the call. */
 int he_keyswitch_batch(he_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int batch, int level,
                        uint64_t gal);
+/* Rescale without allocating (no counterpart in the paper: it exists for
+ * callers that may not allocate device memory, such as code running under a
+ * device-memory budget fixed in advance or inside a framework that owns every
+ * allocation).  Same result as he_rescale on device buffers: d_in holds
+ * `batch` ciphertexts [batch][2][level+1][N] in evaluation form; d_out
+ * receives [batch][2][level][N] (it must not overlap d_in).  The work space is
+ * a 16 MiB array that every device loading the library keeps until exit; one
+ * ciphertext needs (2 + 2 level) N words of it, so larger sizes (at N = 2^16,
+ * level > 15) return HE_EINVAL.  The first call on a device looks up the
+ * array's device address (make it before capturing any stream).  All calls
+ * share the one array: calls whose work overlaps on the GPU (other streams or
+ * contexts on the same device) race; calls on one stream do not.  The array
+ * needs no clearing: every word a call reads it wrote first.  Runs on the
+ * context stream and returns without synchronising. */
+int he_rescale_noalloc(he_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int batch, int level);
 /* Number of kernels this library has launched since it was loaded. */
 uint64_t he_launch_count(void);
 /* Per-class kernel timing with CUDA events on the context stream (adds two

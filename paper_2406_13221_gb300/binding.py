@@ -88,6 +88,7 @@ SIGNATURES = {
     "he_lr_job_info": (_i, [_vp, ctypes.POINTER(he_lr_stats)]),
     "he_lr_job_step_io": (_i, [_vp, _i, he_lr_sched, _vp, _vp]),
     "he_launch_count": (_u64, []),
+    "he_rescale_noalloc": (_i, [_vp, _vp, _vp, _i, _i]),
     "he_lr_job_set_batch": (_i, [_vp, _i]),
     "he_prof_enable": (_i, [_vp, _i]),
     "he_prof_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_u64)]),
@@ -243,6 +244,9 @@ class Context:
         ms, units, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
         self.check(self.L.he_prof_read(self.h, cls, ctypes.byref(ms), ctypes.byref(units), ctypes.byref(n)))
         return ms.value, units.value, n.value
+
+    def rescale_noalloc(self, din, dout, batch, level):
+        self.check(self.L.he_rescale_noalloc(self.h, din, dout, batch, level))
 
     def keyswitch_batch(self, din, dout, batch, level, gal):
         self.check(self.L.he_keyswitch_batch(self.h, din, dout, batch, level, gal))
