@@ -109,7 +109,8 @@ def measured_peaks():
 def recorded_traffic(kernel):
     """Bytes per launch recorded by an ncu capture (profiles/traffic.txt) for the
     current source of the kernel; None when the kernel changed since."""
-    src = open(os.path.join(ROOT, "paper_2406_13221_gb300", "csrc", "ntt.cu"), "rb").read()
+    src = b"".join(open(os.path.join(ROOT, "paper_2406_13221_gb300", "csrc", f), "rb").read()
+                   for f in ("ntt_core.cuh", "ks.cu", "ntt.cu"))
     h = hashlib.sha256(src).hexdigest()[:12]
     try:
         for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
@@ -242,31 +243,50 @@ def pinned_u64(n):
     return t.numpy().view(np.uint64)
 
 
-def roofline(prof, steps):
-    """Dominant kernel class by measured time; algorithmic bytes per launch over
-    its average launch-group duration against the measured HBM peak."""
-    peaks = measured_peaks()
+# Integer-instruction cost model (32-bit lowering of the 64-bit modular
+# operations): Harvey butterfly with a Shoup twiddle, Barrett
+# multiply-accumulate, centred lift.
+OPS_BFLY, OPS_MAC, OPS_LIFT = 23, 38, 6
+SMS, LANES, SM_MHZ_MAX = 152, 128, 2070.0
+
+
+def class_work(name, units, units2):
+    """(integer ops, algorithmic DRAM bytes) of a timing class from its work counts."""
     n = 1 << LOGN
+    half_stages = LOGN // 2
+    if name.startswith("ntt"):           # units = limbs, both passes
+        return units * LOGN * (n / 2) * OPS_BFLY, 16.0 * n * units
+    if name == "modup":                  # units = (digit, target) limbs, column pass + lift
+        return units * (half_stages * (n / 2) * OPS_BFLY + n * OPS_LIFT), 8.0 * n * units
+    # ks_inner: units = limbs through the row pass, units2 = limbs of key products
+    return units * half_stages * (n / 2) * OPS_BFLY + units2 * n * OPS_MAC, 8.0 * n * (units + units2)
+
+
+def roofline(prof, steps):
+    """Dominant kernel class by measured time: algorithmic integer operations per
+    launch over its average launch duration against the integer-issue peak
+    (the kernels are ALU-bound; the DRAM view is reported beside it)."""
+    peaks = measured_peaks()
     best = max(prof, key=lambda k: prof[k][0])
-    ms, units, launches = prof[best]
+    ms, units, launches, units2 = prof[best]
     groups = launches / (2 if best.startswith("ntt") else 1)
-    if best.startswith("ntt"):
-        alg_bytes = 16.0 * n * units           # each limb read and written once
-    elif best == "modup":
-        alg_bytes = 8.0 * n * units * (1 + 1.0 / 10)  # write every lifted limb, read each digit once
-    else:
-        alg_bytes = 8.0 * n * units * (2 * 9 * 10 + 2 * 10)  # upper bound at 9 limbs
-    per_launch = alg_bytes / groups if groups else 0
+    ops, alg_bytes = class_work(best, units, units2)
     dur = ms / 1000.0 / groups if groups else 0
-    achieved = per_launch / dur / 1e9 if dur else 0
-    peak = float(peaks.get("hbm_gbs", 6800.0))
-    tr = recorded_traffic(best)
-    return {"kernel": best, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": tr, "alg_bytes_per_launch": per_launch,
-            "avg_launch_ms": round(dur * 1000, 4), "launch_groups": int(groups),
-            "share_of_step": round(ms / sum(v[0] for v in prof.values()), 3) if ms else None,
-            "classes_ms_per_step": {k: round(v[0] / steps, 2) for k, v in prof.items()},
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "fallback" not in peaks else "fallback"}
+    per_launch_ops = ops / groups if groups else 0
+    achieved = per_launch_ops / dur / 1e12 if dur else 0
+    peak = SMS * LANES * SM_MHZ_MAX * 1e6 / 1e12
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_ach = alg_bytes / groups / dur / 1e9 if dur else 0
+    kernel = {"ks_inner": "k_ks_inner_rows", "modup": "k_ks_modup_cols",
+              "ntt_fwd": "k_ntt_fwd_cols+k_ntt_fwd_rows", "ntt_inv": "k_ntt_inv_rows+k_ntt_inv_cols"}[best]
+    return {"kernel": kernel, "bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2), "unit": "Tops/s",
+            "frac": round(achieved / peak, 4), "traffic": recorded_traffic(kernel),
+            "alg_ops_per_launch": per_launch_ops, "avg_launch_ms": round(dur * 1000, 4), "launch_groups": int(groups),
+            "peak_source": "152 SMs x 128 int32 lanes x 2070 MHz (recipe unit counts and max clock)",
+            "hbm_view": {"achieved": round(hbm_ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(hbm_ach / hbm, 4),
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "fallback" not in peaks else "fallback"},
+            "share_of_timed_classes": round(ms / sum(v[0] for v in prof.values()), 3) if ms else None,
+            "classes_ms_per_step": {k: round(v[0] / steps, 2) for k, v in prof.items()}}
 
 
 def twin_error(X, y, job, iters, sched):

@@ -107,6 +107,7 @@ struct ProfClass {
     std::vector<cudaEvent_t> ev;  // start/stop pairs
     size_t used = 0;
     double units = 0;             // work units (limbs for transforms)
+    double units2 = 0;            // second work count (multiply-accumulate limbs of the key inner product)
     unsigned long long launches = 0;
 };
 struct Prof {
@@ -115,7 +116,7 @@ struct Prof {
 };
 struct he_ctx;
 void prof_start(he_ctx *c, int cls, cudaStream_t s);
-void prof_stop(he_ctx *c, int cls, cudaStream_t s, double units, int launches);
+void prof_stop(he_ctx *c, int cls, cudaStream_t s, double units, int launches, double units2 = 0);
 
 // prime index of limb `limb` (an unrolled select: a dynamic index into a kernel
 // parameter array would force the array into local memory)
