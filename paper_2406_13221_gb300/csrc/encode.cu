@@ -361,6 +361,25 @@ int helr_make_ksk(he_ctx *c, uint64_t gal, const uint64_t *sprime, uint64_t *out
     return HE_OK;
 }
 
+// x <- x 2^64 mod q for nlimbs limbs, limb i modulo prime i % period
+__global__ void k_to_mont(uint64_t *x, size_t nwords, int logn, int period, const ModQ *mods)
+{
+    GS_LOOP(i, nwords) {
+        const ModQ m = mods[(i >> logn) % period];
+        uint64_t r64 = reduce64(~0ull, m) + 1;
+        if (r64 == m.q) r64 = 0;
+        x[i] = mulmod(x[i], r64, m);
+    }
+}
+
+int helr_to_montgomery(he_ctx *c, uint64_t *x, size_t nlimbs, int period)
+{
+    size_t nw = nlimbs << c->logn;
+    HELR_LAUNCH(k_to_mont<<<grid_for(nw), 256, 0, c->stream>>>(x, nw, c->logn, period, c->t.mod));
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
+
 int helr_square_dev(he_ctx *c, uint64_t *out, const uint64_t *in, size_t nlimbs)
 {
     size_t nw = nlimbs << c->logn;

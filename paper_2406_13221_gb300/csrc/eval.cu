@@ -122,8 +122,7 @@ int ev_rescale(Eval *ev, const CtB &a, CtB &out)
         HELR_CUDA(c, cudaMemcpy2DAsync(ev->last + p * N, 2 * N * 8, a.d + (size_t)p * nl * N + (size_t)lv * N,
                                        (a.item ? a.item : 2 * nl * N) * 8, N * 8, B, cudaMemcpyDeviceToDevice, s));
     HELR_TRY(helr_ntt_inv(c, ev->last, 2 * (size_t)B, limbmap_single(lv), s));
-    k_lift(c, ev->last, ev->lift, 2 * B, lv, N, limbmap_ct(lv - 1), (size_t)lv * N, s);
-    HELR_TRY(helr_ntt_fwd(c, ev->lift, 2 * (size_t)B * lv, limbmap_ct(lv - 1), s));
+    HELR_TRY(helr_ntt_fwd_lifted(c, ev->last, N, lv, 2 * (size_t)B, ev->lift, limbmap_ct(lv - 1), s));
     KP kp;
     std::vector<uint64_t> h(2);
     for (int j = 0; j < lv; j++) {

@@ -227,6 +227,9 @@ static int ctx_init(he_ctx *c, const he_params *p)
         c->modh[i].s = (uint32_t)(bits - 2);
         c->modh[i].mu = (uint64_t)(((u128)1 << (bits - 2 + 64)) / q);
         c->modh[i].pad = 0;
+        uint64_t inv = q;  // Newton iteration for q^-1 mod 2^64 (q odd: correct to 3 bits, doubling each step)
+        for (int it = 0; it < 6; it++) inv *= 2 - q * inv;
+        c->modh[i].qinv = inv;
         // primitive 2N-th root: first h >= 2 whose (q-1)/2N-th power has order exactly 2N
         for (uint64_t h = 2;; h++) {
             uint64_t psi = h_pow(h, (q - 1) / twon, q);
@@ -401,6 +404,7 @@ int helr_add_key(he_ctx *c, uint64_t gal)
     if (gal == 0) HELR_TRY(helr_square_dev(c, sp, c->d_sk, np));
     else k_automorph(c, sp, c->d_sk, np, gal, c->stream);
     HELR_TRY(helr_make_ksk(c, gal, sp, key));
+    HELR_TRY(helr_to_montgomery(c, key, (size_t)nq * 2 * np, np));
     HELR_CUDA(c, cudaGetLastError());
     helr_free(c, sp);
     c->ksk.push_back({gal, key});
@@ -617,8 +621,7 @@ int helr_keyswitch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, 
     HELR_CUDA(c, cudaMemcpy2DAsync(ws->pl, N * 8, ws->acc + (size_t)nl * N, (size_t)nt * N * 8, N * 8, (size_t)batch * 2,
                                    cudaMemcpyDeviceToDevice, s));
     HELR_TRY(helr_ntt_inv(c, ws->pl, (size_t)batch * 2, limbmap_single(c->nq), s));
-    k_lift(c, ws->pl, ws->lift, batch * 2, c->nq, N, limbmap_ct(level), (size_t)nl * N, s);
-    HELR_TRY(helr_ntt_fwd(c, ws->lift, (size_t)batch * 2 * nl, limbmap_ct(level), s));
+    HELR_TRY(helr_ntt_fwd_lifted(c, ws->pl, N, c->nq, (size_t)batch * 2, ws->lift, limbmap_ct(level), s));
     if (o) {
         k_ks_out(c, *o, ws->acc, ws->lift, batch, nl, s);
     } else {

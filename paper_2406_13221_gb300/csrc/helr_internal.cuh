@@ -22,11 +22,13 @@
 
 // ------------------------------------------------------------------ modular arithmetic
 // Per-prime constants.  Barrett: s = bits(q) - 2, mu = floor(2^(s+64) / q) < 2^63.
+// Montgomery: qinv = q^-1 mod 2^64 (R = 2^64).
 struct ModQ {
     uint64_t q;
     uint64_t mu;
     uint32_t s;
     uint32_t pad;
+    uint64_t qinv;
 };
 
 __host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b)
@@ -53,6 +55,15 @@ __host__ __device__ __forceinline__ uint64_t mulmod(uint64_t a, uint64_t b, cons
     return barrett_reduce(mulhi64(a, b), a * b, m);
 }
 __host__ __device__ __forceinline__ uint64_t reduce64(uint64_t x, const ModQ m) { return barrett_reduce(0, x, m); }
+// Montgomery product a * b * 2^-64 mod q for a, b < q: with a b = hi 2^64 + lo and
+// m = lo q^-1 mod 2^64, a b - m q is divisible by 2^64 and equals (hi - mulhi(m, q)) 2^64.
+// With b stored as b' = b 2^64 mod q it returns a b mod q.
+__host__ __device__ __forceinline__ uint64_t mont_mul(uint64_t a, uint64_t b, const ModQ m)
+{
+    uint64_t lo = a * b, hi = mulhi64(a, b);
+    uint64_t mh = mulhi64(lo * m.qinv, m.q);
+    return hi >= mh ? hi - mh : hi - mh + m.q;
+}
 __host__ __device__ __forceinline__ uint64_t addmod(uint64_t a, uint64_t b, uint64_t q)
 {
     uint64_t s = a + b;
@@ -157,7 +168,7 @@ struct DevTables {
 
 struct KeySwitchKey {
     uint64_t gal;       // 0 = relinearisation
-    uint64_t *d;        // [nq digits][2][nq+1 limbs][N], NTT form
+    uint64_t *d;        // [nq digits][2][nq+1 limbs][N], evaluation form, Montgomery form (k 2^64 mod q)
 };
 
 struct he_ctx {
@@ -240,6 +251,10 @@ int helr_ntt_inv(he_ctx *c, uint64_t *data, size_t nlimbs, const LimbMap &m, cud
 // out-of-place variants (in may equal out)
 int helr_ntt_fwd_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s);
 int helr_ntt_inv_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s);
+// forward transform of centred lifts: source limb b (coefficient form, at src + b * src_stride,
+// modulo prime src_prime) is lifted to every prime of dst and transformed; out is [nsrc][dst.period][N]
+int helr_ntt_fwd_lifted(he_ctx *c, const uint64_t *src, size_t src_stride, int src_prime, size_t nsrc, uint64_t *out,
+                        const LimbMap &dst, cudaStream_t s);
 
 // elementwise / structural kernels (ops.cu)
 void k_add(he_ctx *c, uint64_t *out, const uint64_t *a, const uint64_t *b, size_t nlimbs, const LimbMap &m, int sub, cudaStream_t s);
@@ -314,6 +329,7 @@ int helr_decrypt_dev(he_ctx *c, const uint64_t *d_ct, int level, uint64_t *d_pt)
 int helr_keygen_base(he_ctx *c, uint64_t seed);
 int helr_make_ksk(he_ctx *c, uint64_t gal, const uint64_t *sprime, uint64_t *out);
 int helr_square_dev(he_ctx *c, uint64_t *out, const uint64_t *in, size_t nlimbs);
+int helr_to_montgomery(he_ctx *c, uint64_t *x, size_t nlimbs, int period);
 
 // ------------------------------------------------------------------ batched evaluator (eval.cu)
 // A batch of ciphertexts: item i at d + i * item, polynomials [2][level+1][N];

@@ -114,8 +114,8 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
         load_contig<E>(k1, key + (((size_t)i * 2 + 1) * (nq + 1) + kl) * N + roff + E * l);
 #pragma unroll
         for (int r = 0; r < E; r++) {
-            a0[r] = addmod(a0[r], mulmod(x[r], k0[r], m), q);
-            a1[r] = addmod(a1[r], mulmod(x[r], k1[r], m), q);
+            a0[r] = addmod(a0[r], mont_mul(x[r], k0[r], m), q);  // keys are stored in Montgomery form
+            a1[r] = addmod(a1[r], mont_mul(x[r], k1[r], m), q);
         }
     }
     uint64_t *o0 = acc + (((size_t)b * 2 + 0) * (nl + 1) + t) * N + roff + E * l;
