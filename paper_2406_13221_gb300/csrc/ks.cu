@@ -64,6 +64,16 @@ __device__ __forceinline__ void load_contig(uint64_t (&x)[E], const uint64_t *p)
     }
 }
 
+// 16-byte asynchronous global -> shared copies (cp.async), grouped per digit
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
+{
+    unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 template <int K1, int K2, int RPC>
 __global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
     k_ks_inner_rows(const uint64_t *__restrict__ mid, const uint64_t *__restrict__ dntt, const uint64_t *__restrict__ key,
@@ -71,8 +81,11 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
                     int nq, int pidx, int items)
 {
     using G = Geo<K2>;
-    constexpr int R1 = 1 << K1, R2 = G::R, N = R1 * R2, NG = R1 / RPC, E = G::E;
+    constexpr int R1 = 1 << K1, R2 = G::R, N = R1 * R2, NG = R1 / RPC, E = G::E, NT = RPC * G::T;
+    constexpr int TILE = RPC * R2;  // words of one digit's rows handled by this CTA
     extern __shared__ uint64_t smem[];
+    uint64_t *buf = smem;                    // [2][TILE]: the rows of two digits (double buffer)
+    uint64_t *segs = smem + 2 * TILE;        // exchange segments
     int bid = blockIdx.x;
     const int b = bid % items;  // items sharing one key row are adjacent: the key row is read from L2
     bid /= items;
@@ -84,19 +97,39 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
     const uint64_t *tw = twall + (size_t)pt * N * 2;
     const int l = threadIdx.x % G::T, rl = threadIdx.x / G::T;
     const int row = grp * RPC + rl;
-    const size_t roff = (size_t)row * R2;
-    uint64_t *seg = smem + rl * G::SEG;
+    const size_t roff = (size_t)row * R2, toff = (size_t)grp * RPC * R2;
+    uint64_t *seg = segs + rl * G::SEG;
+    // rows of digit i: the column-pass output for target t, or the input itself when i == t
+    auto src_of = [&](int i) -> const uint64_t * {
+        return i == t ? dntt + ((size_t)b * nl + i) * N + toff : mid + (((size_t)b * nl + i) * (nl + 1) + t) * N + toff;
+    };
+    auto prefetch = [&](int i, uint64_t *dst) {
+        const uint64_t *src = src_of(i);
+#pragma unroll
+        for (int k = 0; k < TILE / 2 / NT; k++) {
+            const int w = 2 * (threadIdx.x + k * NT);
+            cp_async16(dst + w, src + w);
+        }
+    };
     uint64_t a0[E], a1[E];
 #pragma unroll
     for (int r = 0; r < E; r++) a0[r] = a1[r] = 0;
+    prefetch(0, buf);
+    cp_async_commit();
     for (int i = 0; i < nl; i++) {
+        uint64_t *cur = buf + (i & 1) * TILE;
+        if (i + 1 < nl) prefetch(i + 1, buf + ((i + 1) & 1) * TILE);
+        cp_async_commit();
+        cp_async_wait<1>();  // digit i has landed
+        __syncthreads();
         uint64_t x[E];
+        const uint64_t *rows = cur + rl * R2;
         if (i == t) {
-            load_contig<E>(x, dntt + ((size_t)b * nl + i) * N + roff + E * l);
-        } else {
-            const uint64_t *src = mid + (((size_t)b * nl + i) * (nl + 1) + t) * N + roff;
 #pragma unroll
-            for (int r = 0; r < E; r++) x[r] = src[l + G::T * r];
+            for (int r = 0; r < E; r++) x[r] = rows[E * l + r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < E; r++) x[r] = rows[l + G::T * r];
             const int A = R1 + row;
             fwd_strided<K2>(x, tw, A, q, q2);
             to_contig<K2>(x, seg, l);
@@ -107,7 +140,6 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
                 v = v >= q2 ? v - q2 : v;
                 x[r] = v >= q ? v - q : v;
             }
-            __syncthreads();  // seg is rewritten by the next digit
         }
         uint64_t k0[E], k1[E];
         load_contig<E>(k0, key + (((size_t)i * 2 + 0) * (nq + 1) + kl) * N + roff + E * l);
@@ -117,6 +149,7 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
             a0[r] = addmod(a0[r], mont_mul(x[r], k0[r], m), q);  // keys are stored in Montgomery form
             a1[r] = addmod(a1[r], mont_mul(x[r], k1[r], m), q);
         }
+        __syncthreads();  // buffer `cur` and the exchange segments are reused
     }
     uint64_t *o0 = acc + (((size_t)b * 2 + 0) * (nl + 1) + t) * N + roff + E * l;
     uint64_t *o1 = acc + (((size_t)b * 2 + 1) * (nl + 1) + t) * N + roff + E * l;
@@ -134,7 +167,7 @@ struct KsPlan {
     static constexpr int C = (256 / T1) < R2 ? (256 / T1) : R2;
     static constexpr int RPC = (128 / T2) < R1 ? (128 / T2) : R1;
     static constexpr size_t SM1 = (size_t)C * Geo<K1>::SEG * 8;
-    static constexpr size_t SM2 = (size_t)RPC * Geo<K2>::SEG * 8;
+    static constexpr size_t SM2 = (size_t)RPC * Geo<K2>::SEG * 8 + 2 * (size_t)RPC * R2 * 8;
     static cudaError_t prepare()
     {
         cudaFuncSetAttribute(k_ks_modup_cols<K1, K2, C>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
