@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-twin", action="store_true")
+    ap.add_argument("--no-mini", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="HE primitive sweep: batched NTT and key switching vs N, limbs and batch (JSON line per point)")
     return ap.parse_args()
 
 
@@ -200,6 +203,9 @@ def run_ours(args, rank, world):
         e2e_s = allreduce_max(time.time() - h0, world) / (args.steps * world)
         e2e = {"value": round(e2e_s, 5), "unit": "s/iter", "h2d_bytes_per_step": int(sin.nbytes),
                "d2h_bytes_per_step": int(sout.nbytes)}
+    mini = None
+    if not args.no_mini:
+        mini = minibatch_time(ctx, X, y, args)
     roof = roofline(prof, args.steps)
     out = {
         "metric": METRIC, "value": round(sec_iter, 5), "unit": "s/iter", "n_gpus": world, "steps": args.steps,
@@ -214,6 +220,7 @@ def run_ours(args, rank, world):
         "keyswitches_per_iter": ks_per_iter,
         "ntt_limbs_per_s": round((prof["ntt_fwd"][1] + prof["ntt_inv"][1]) / args.steps / (sec_iter * world), 1),
         "plain_one_ct_per_launch_s_per_iter": round(plain, 4) if plain else None,
+        "mini_batch": mini,
         "batched_speedup_vs_plain": round(plain / sec_iter / world, 2) if plain else None,
         "setup_s": round(setup_s, 1),
         "max_abs_err_vs_fp64_twin": err,
@@ -223,6 +230,94 @@ def run_ours(args, rank, world):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(X, y, samples=1)
     return out
+
+
+def minibatch_time(ctx, X, y, args):
+    """Mini-batch QG-NAG (Algorithm 1) on the same data: 1,024-sample batches
+    (8 blocks), the job's own schedule; seconds per iteration over 8 iterations
+    after 3 warm-up iterations, batched and plain (one block per launch)."""
+    import torch
+    from paper_2406_13221_gb300 import binding
+    job = binding.Job(ctx, X, y, binding.MINI_BATCH, 1024, binding.G8, LOG_SCALE, enc_seed=3, key_seed=2)
+    sched = (1.0, 0.1, 413.0, 2.5)
+    out = {}
+    t = 0
+    for mode, bpl in (("batched", 8), ("plain", 1)):
+        job.set_batch(bpl)
+        for _ in range(3):
+            job.step(t, sched)
+            t += 1
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(8):
+            job.step(t, sched)
+            t += 1
+        e1.record()
+        torch.cuda.synchronize()
+        out[mode + "_s_per_iter"] = round(e0.elapsed_time(e1) / 8 / 1000.0, 5)
+    out["keyswitches_per_iter"] = int(job.stats().keyswitches)
+    out["batched_speedup_vs_plain"] = round(out["plain_s_per_iter"] / out["batched_s_per_iter"], 2)
+    job.close()
+    return out
+
+
+def sweep(args):
+    """Batched NTT limbs/s and key switches/s on GB300 (uniform random residues)."""
+    import torch
+    from paper_2406_13221_gb300 import binding, build
+    build.build()
+    for logn in (14, 15, 16):
+        n = 1 << logn
+        for limbs in (8, 16, 24, 32, 40):
+            nq = min(limbs, 38)
+            ctx = binding.Context(logn, nq)
+            for batch in (1, 8, 64, 512):
+                nl = batch * limbs
+                if nl * n * 8 > 8 << 30:
+                    continue
+                buf = torch.randint(0, 1 << 30, (nl * n,), dtype=torch.int64, device="cuda")
+                prime_of = list(range(nq))
+                for _ in range(2):
+                    ctx.ntt_forward(buf.data_ptr(), nl, prime_of)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = max(2, min(50, 4096 // nl))
+                e0.record()
+                for _ in range(reps):
+                    ctx.ntt_forward(buf.data_ptr(), nl, prime_of)
+                    ctx.ntt_inverse(buf.data_ptr(), nl, prime_of)
+                e1.record()
+                torch.cuda.synchronize()
+                sec = e0.elapsed_time(e1) / 1000.0
+                print(json.dumps({"sweep": "ntt", "log_n": logn, "limbs": limbs, "ciphertexts_per_launch": batch,
+                                  "ntt_limbs_per_s": round(2 * reps * nl / sec, 1),
+                                  "hbm_frac_of_alg_bytes": round(2 * reps * nl * 16 * n / sec / 1e9 /
+                                                                 measured_peaks().get("hbm_gbs", 6800.0), 4)}), flush=True)
+                del buf
+            ctx.close()
+    # key switching at the bench chain (N = 2^16, 9 primes + P), relinearisation key
+    ctx = binding.Context(LOGN, NQ)
+    ctx.keygen(2, [])
+    n = 1 << LOGN
+    for level in (7, 4):
+        nl = level + 1
+        for batch in (1, 8, 32, 128):
+            din = torch.randint(0, 1 << 30, (batch * nl * n,), dtype=torch.int64, device="cuda")
+            dout = torch.zeros(batch * 2 * nl * n, dtype=torch.int64, device="cuda")
+            ctx.keyswitch_batch(din.data_ptr(), dout.data_ptr(), batch, level, 0)
+            torch.cuda.synchronize()
+            reps = max(2, 256 // batch)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                ctx.keyswitch_batch(din.data_ptr(), dout.data_ptr(), batch, level, 0)
+            e1.record()
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1000.0
+            print(json.dumps({"sweep": "keyswitch", "log_n": LOGN, "limbs": nl, "batch": batch,
+                              "keyswitch_per_s": round(reps * batch / sec, 1)}), flush=True)
+            del din, dout
 
 
 def ctw_bytes():
@@ -377,6 +472,9 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
+    if args.sweep:
+        sweep(args)
+        return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
