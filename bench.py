@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-twin", action="store_true")
     ap.add_argument("--no-mini", action="store_true")
+    ap.add_argument("--sweep-point", default="", help="log_n,limbs,batch: run only this NTT sweep point")
     ap.add_argument("--sweep", action="store_true",
                     help="HE primitive sweep: batched NTT and key switching vs N, limbs and batch (JSON line per point)")
     return ap.parse_args()
@@ -267,12 +268,19 @@ def sweep(args):
     import torch
     from paper_2406_13221_gb300 import binding, build
     build.build()
+    point = tuple(int(x) for x in args.sweep_point.split(",")) if args.sweep_point else None
     for logn in (14, 15, 16):
         n = 1 << logn
+        if point and logn != point[0]:
+            continue
         for limbs in (8, 16, 24, 32, 40):
+            if point and limbs != point[1]:
+                continue
             nq = min(limbs, 38)
             ctx = binding.Context(logn, nq)
             for batch in (1, 8, 64, 512):
+                if point and batch != point[2]:
+                    continue
                 nl = batch * limbs
                 if nl * n * 8 > 8 << 30:
                     continue
@@ -296,6 +304,8 @@ def sweep(args):
                                                                  measured_peaks().get("hbm_gbs", 6800.0), 4)}), flush=True)
                 del buf
             ctx.close()
+    if point:
+        return
     # key switching at the bench chain (N = 2^16, 9 primes + P), relinearisation key
     ctx = binding.Context(LOGN, NQ)
     ctx.keygen(2, [])
@@ -472,7 +482,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
-    if args.sweep:
+    if args.sweep or args.sweep_point:
         sweep(args)
         return
     if args.impl == "reference":
