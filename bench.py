@@ -111,8 +111,9 @@ def measured_peaks():
 
 
 def recorded_traffic(kernel):
-    """Bytes per launch recorded by an ncu capture (profiles/traffic.txt) for the
-    current source of the kernel; None when the kernel changed since."""
+    """DRAM traffic over algorithmic bytes of one ncu-captured launch of `kernel`
+    (profiles/traffic.txt), valid while the kernel's sources are unchanged (else
+    None); bench.py scales it to its own average launch."""
     src = b"".join(open(os.path.join(ROOT, "paper_2406_13221_gb300", "csrc", f), "rb").read()
                    for f in ("ntt_core.cuh", "ks.cu", "ntt.cu"))
     h = hashlib.sha256(src).hexdigest()[:12]
@@ -355,16 +356,16 @@ OPS_BFLY, OPS_MAC, OPS_LIFT = 23, 38, 6
 SMS, LANES, SM_MHZ_MAX = 152, 128, 2070.0
 
 
-def class_work(name, units, units2):
+def class_work(name, units, units2, dram_limbs):
     """(integer ops, algorithmic DRAM bytes) of a timing class from its work counts."""
     n = 1 << LOGN
     half_stages = LOGN // 2
     if name.startswith("ntt"):           # units = limbs, both passes
         return units * LOGN * (n / 2) * OPS_BFLY, 16.0 * n * units
     if name == "modup":                  # units = (digit, target) limbs, column pass + lift
-        return units * (half_stages * (n / 2) * OPS_BFLY + n * OPS_LIFT), 8.0 * n * units
+        return units * (half_stages * (n / 2) * OPS_BFLY + n * OPS_LIFT), 8.0 * n * dram_limbs
     # ks_inner: units = limbs through the row pass, units2 = limbs of key products
-    return units * half_stages * (n / 2) * OPS_BFLY + units2 * n * OPS_MAC, 8.0 * n * (units + units2)
+    return units * half_stages * (n / 2) * OPS_BFLY + units2 * n * OPS_MAC, 8.0 * n * dram_limbs
 
 
 def roofline(prof, steps):
@@ -373,9 +374,9 @@ def roofline(prof, steps):
     (the kernels are ALU-bound; the DRAM view is reported beside it)."""
     peaks = measured_peaks()
     best = max(prof, key=lambda k: prof[k][0])
-    ms, units, launches, units2 = prof[best]
+    ms, units, launches, units2, dram_limbs = prof[best]
     groups = launches / (2 if best.startswith("ntt") else 1)
-    ops, alg_bytes = class_work(best, units, units2)
+    ops, alg_bytes = class_work(best, units, units2, dram_limbs)
     dur = ms / 1000.0 / groups if groups else 0
     per_launch_ops = ops / groups if groups else 0
     achieved = per_launch_ops / dur / 1e12 if dur else 0
@@ -385,7 +386,9 @@ def roofline(prof, steps):
     kernel = {"ks_inner": "k_ks_inner_rows", "modup": "k_ks_modup_cols",
               "ntt_fwd": "k_ntt_fwd_cols+k_ntt_fwd_rows", "ntt_inv": "k_ntt_inv_rows+k_ntt_inv_cols"}[best]
     return {"kernel": kernel, "bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2), "unit": "Tops/s",
-            "frac": round(achieved / peak, 4), "traffic": recorded_traffic(kernel),
+            "frac": round(achieved / peak, 4),
+            "traffic": (None if recorded_traffic(kernel) is None
+                        else round(recorded_traffic(kernel) * alg_bytes / groups)),
             "alg_ops_per_launch": per_launch_ops, "avg_launch_ms": round(dur * 1000, 4), "launch_groups": int(groups),
             "peak_source": "152 SMs x 128 int32 lanes x 2070 MHz (recipe unit counts and max clock)",
             "hbm_view": {"achieved": round(hbm_ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(hbm_ach / hbm, 4),

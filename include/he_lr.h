@@ -171,10 +171,12 @@ uint64_t he_launch_count(void);
  * key switches for the inner product) and the kernel launches of the class. */
 int he_prof_enable(he_ctx *ctx, int on);
 int he_prof_read(he_ctx *ctx, int cls, double *ms, double *units, uint64_t *launches);
-/* Second work count of a class: for the key-switch inner product (class 3) the
- * limbs of key products (2 keys x digits x targets); 0 for the other classes.
- * Class 3's first count is the limbs that run the row pass of the transform. */
-int he_prof_read2(he_ctx *ctx, int cls, double *units2);
+/* Further work counts of a class: units2 = for the key-switch inner product
+ * (class 3) the limbs of key products (2 keys x digits x targets), 0 for the
+ * other classes (class 3's first count is the limbs that run the row pass of
+ * the transform); dram_limbs (may be NULL) = algorithmic DRAM traffic of the
+ * key-switch classes in limbs (operands shared by a launch counted once). */
+int he_prof_read2(he_ctx *ctx, int cls, double *units2, double *dram_limbs);
 /* Galois element of a left rotation by r. */
 uint64_t he_galois_elt(const he_ctx *ctx, int64_t r);
 

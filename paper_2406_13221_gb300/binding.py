@@ -92,7 +92,7 @@ SIGNATURES = {
     "he_lr_job_set_batch": (_i, [_vp, _i]),
     "he_prof_enable": (_i, [_vp, _i]),
     "he_prof_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_u64)]),
-    "he_prof_read2": (_i, [_vp, _i, ctypes.POINTER(_d)]),
+    "he_prof_read2": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "he_lr_job_free": (_i, [_vp]),
     "he_lr_train": (_i, [_vp, _vp, _vp, _sz, _sz, _i, he_lr_sched, _i, _sz, _i, _u64, _u64, _vp, _sz,
                          ctypes.POINTER(he_lr_stats)]),
@@ -242,11 +242,12 @@ class Context:
         self.check(self.L.he_prof_enable(self.h, int(on)))
 
     def prof_read(self, cls):
-        """(milliseconds, work units, launches, second work count) of a timing class."""
-        ms, units, n, u2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64(), ctypes.c_double()
+        """(milliseconds, work units, launches, second work count, DRAM limbs) of a timing class."""
+        ms, units, n, u2, u3 = (ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64(), ctypes.c_double(),
+                                ctypes.c_double())
         self.check(self.L.he_prof_read(self.h, cls, ctypes.byref(ms), ctypes.byref(units), ctypes.byref(n)))
-        self.check(self.L.he_prof_read2(self.h, cls, ctypes.byref(u2)))
-        return ms.value, units.value, n.value, u2.value
+        self.check(self.L.he_prof_read2(self.h, cls, ctypes.byref(u2), ctypes.byref(u3)))
+        return ms.value, units.value, n.value, u2.value, u3.value
 
     def rescale_noalloc(self, din, dout, batch, level):
         self.check(self.L.he_rescale_noalloc(self.h, din, dout, batch, level))

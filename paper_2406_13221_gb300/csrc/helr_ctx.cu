@@ -24,7 +24,7 @@ void prof_start(he_ctx *c, int cls, cudaStream_t s)
     }
     cudaEventRecord(p.ev[2 * p.used], s);
 }
-void prof_stop(he_ctx *c, int cls, cudaStream_t s, double units, int launches, double units2)
+void prof_stop(he_ctx *c, int cls, cudaStream_t s, double units, int launches, double units2, double units3)
 {
     if (!c->prof.on) return;
     ProfClass &p = c->prof.cls[cls];
@@ -33,6 +33,7 @@ void prof_stop(he_ctx *c, int cls, cudaStream_t s, double units, int launches, d
     p.used++;
     p.units += units;
     p.units2 += units2;
+    p.units3 += units3;
     p.launches += launches;
 }
 
@@ -43,14 +44,15 @@ extern "C" int he_prof_enable(he_ctx *c, int on)
     if (!c) return HE_EINVAL;
     HELR_CUDA(c, cudaStreamSynchronize(c->stream));
     c->prof.on = on;
-    for (auto &p : c->prof.cls) p.used = 0, p.units = 0, p.units2 = 0, p.launches = 0;
+    for (auto &p : c->prof.cls) p.used = 0, p.units = 0, p.units2 = 0, p.units3 = 0, p.launches = 0;
     return HE_OK;
 }
 
-extern "C" int he_prof_read2(he_ctx *c, int cls, double *units2)
+extern "C" int he_prof_read2(he_ctx *c, int cls, double *units2, double *dram_limbs)
 {
     if (!c || cls < 0 || cls >= PROF_NCLASS || !units2) return HE_EINVAL;
     *units2 = c->prof.cls[cls].units2;
+    if (dram_limbs) *dram_limbs = c->prof.cls[cls].units3;
     return HE_OK;
 }
 

@@ -119,6 +119,7 @@ struct ProfClass {
     size_t used = 0;
     double units = 0;             // work units (limbs for transforms)
     double units2 = 0;            // second work count (multiply-accumulate limbs of the key inner product)
+    double units3 = 0;            // algorithmic DRAM limbs (reads + writes, shared operands once per launch)
     unsigned long long launches = 0;
 };
 struct Prof {
@@ -127,7 +128,7 @@ struct Prof {
 };
 struct he_ctx;
 void prof_start(he_ctx *c, int cls, cudaStream_t s);
-void prof_stop(he_ctx *c, int cls, cudaStream_t s, double units, int launches, double units2 = 0);
+void prof_stop(he_ctx *c, int cls, cudaStream_t s, double units, int launches, double units2 = 0, double units3 = 0);
 
 // prime index of limb `limb` (an unrolled select: a dynamic index into a kernel
 // parameter array would force the array into local memory)

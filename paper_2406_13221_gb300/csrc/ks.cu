@@ -202,11 +202,14 @@ int run_fused(he_ctx *c, const uint64_t *dntt, const uint64_t *dcoef, uint64_t *
     }
     prof_start(c, PROF_MODUP, s);
     KsPlan<K1, K2>::modup(c, dcoef, mid, items, nl, s);
-    prof_stop(c, PROF_MODUP, s, (double)items * nl * nl, 1);
+    // column passes of (digit, target != digit); DRAM: digits read once, column-pass limbs written
+    prof_stop(c, PROF_MODUP, s, (double)items * nl * nl, 1, 0, (double)items * nl * (nl + 1));
     prof_start(c, PROF_KS_INNER, s);
     KsPlan<K1, K2>::inner(c, mid, dntt, key, acc, items, nl, s);
     // row passes: nl - 1 digits for each ciphertext target, nl for P; products: 2 keys x nl digits x (nl + 1) targets
-    prof_stop(c, PROF_KS_INNER, s, (double)items * nl * nl, 1, (double)items * 2 * nl * (nl + 1));
+    // DRAM: every digit's rows read once per target, the two key polynomials once per launch, acc written
+    prof_stop(c, PROF_KS_INNER, s, (double)items * nl * nl, 1, (double)items * 2 * nl * (nl + 1),
+              (double)items * nl * (nl + 1) + 2.0 * nl * (nl + 1) + (double)items * 2 * (nl + 1));
     HELR_CUDA(c, cudaGetLastError());
     return HE_OK;
 }
