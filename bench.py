@@ -121,7 +121,7 @@ def recorded_traffic(kernel):
         for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
             p = line.split()
             if len(p) >= 3 and not line.startswith("#") and p[0] == kernel and p[1] == h:
-                return float(p[2])
+                return float(p[2])  # measured / algorithmic DRAM bytes of the captured launch
     except OSError:
         pass
     return None
