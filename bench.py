@@ -244,8 +244,9 @@ def minibatch_time(ctx, X, y, args):
     sched = (1.0, 0.1, 413.0, 2.5)
     out = {}
     t = 0
-    for mode, bpl in (("batched", 8), ("plain", 1)):
+    for mode, bpl, graph in (("batched", 8, False), ("batched_graph", 8, True), ("plain", 1, False)):
         job.set_batch(bpl)
+        job.set_graph(graph)
         for _ in range(3):
             job.step(t, sched)
             t += 1
@@ -260,6 +261,7 @@ def minibatch_time(ctx, X, y, args):
         out[mode + "_s_per_iter"] = round(e0.elapsed_time(e1) / 8 / 1000.0, 5)
     out["keyswitches_per_iter"] = int(job.stats().keyswitches)
     out["batched_speedup_vs_plain"] = round(out["plain_s_per_iter"] / out["batched_s_per_iter"], 2)
+    out["batched_graph_speedup_vs_plain"] = round(out["plain_s_per_iter"] / out["batched_graph_s_per_iter"], 2)
     job.close()
     return out
 

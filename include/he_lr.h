@@ -226,6 +226,11 @@ int he_lr_job_step(he_lr_job *job, int t, he_lr_sched sched);
  * refreshed W and V are written back in the same layout.  Host buffers may be
  * pinned; the copies run on the context stream inside the call. */
 int he_lr_job_step_io(he_lr_job *job, int t, he_lr_sched sched, const uint64_t *state_in, uint64_t *state_out);
+/* Record Steps 1-9 of every later he_lr_job_step as one CUDA graph on a
+ * stream owned by the job (re-recorded each iteration with that iteration's
+ * constants and swapped into the executable graph) and launch it as a unit;
+ * the refresh runs after it.  on = 0 returns to direct launches. */
+int he_lr_job_set_graph(he_lr_job *job, int on);
 /* Data blocks per kernel launch for later steps: 1 = the plain
  * one-ciphertext-per-launch form; at most the value the job was created with. */
 int he_lr_job_set_batch(he_lr_job *job, int blocks_per_launch);

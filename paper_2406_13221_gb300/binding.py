@@ -90,6 +90,7 @@ SIGNATURES = {
     "he_launch_count": (_u64, []),
     "he_rescale_noalloc": (_i, [_vp, _vp, _vp, _i, _i]),
     "he_lr_job_set_batch": (_i, [_vp, _i]),
+    "he_lr_job_set_graph": (_i, [_vp, _i]),
     "he_prof_enable": (_i, [_vp, _i]),
     "he_prof_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_u64)]),
     "he_prof_read2": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
@@ -333,6 +334,9 @@ class Job:
         pin = None if state_in is None else state_in.ctypes.data_as(ctypes.c_void_p)
         pout = None if state_out is None else state_out.ctypes.data_as(ctypes.c_void_p)
         self.ctx.check(self.ctx.L.he_lr_job_step_io(self.h, t, he_lr_sched(*sched), pin, pout))
+
+    def set_graph(self, on=True):
+        self.ctx.check(self.ctx.L.he_lr_job_set_graph(self.h, int(on)))
 
     def set_batch(self, blocks_per_launch):
         self.ctx.check(self.ctx.L.he_lr_job_set_batch(self.h, int(blocks_per_launch)))

@@ -88,6 +88,10 @@ struct he_lr_job {
     he_lr_stats st;
     double upd_total, iter_total;
     int iters_done;
+    // per-iteration CUDA graph (optional)
+    int graph;
+    cudaStream_t gstream;
+    cudaGraphExec_t gexec;
 };
 
 static double f2(const he_lr_sched &s, double t) { return s.max - (s.max - s.min) * pow(t / s.T, s.power); }
@@ -140,6 +144,8 @@ extern "C" int he_lr_job_free(he_lr_job *j)
     helr_free(c, j->buf);
     ev_free(&j->ev);
     cudaStreamSynchronize(c->stream);
+    if (j->gexec) cudaGraphExecDestroy(j->gexec);
+    if (j->gstream) cudaStreamDestroy(j->gstream);
     delete j;
     return HE_OK;
 }
@@ -421,11 +427,9 @@ static int refresh_dev(he_ctx *c, const uint64_t *ct, int level, double scale, i
     return HE_OK;
 }
 
-extern "C" int he_lr_job_step(he_lr_job *j, int t, he_lr_sched sched)
+// Steps 1-9 of iteration t into Wn, Vn (device work only: no allocation, no synchronisation)
+static int job_update(he_lr_job *j, int t, const he_lr_sched &sched, CtB &Wn, CtB &Vn)
 {
-    if (!j || t < 0 || !(sched.T > 0)) return HE_EINVAL;
-    he_ctx *c = j->c;
-    auto t0 = std::chrono::steady_clock::now();
     const double alpha = f2(sched, (double)t), eta = nag_eta(t);
     int b0 = 0, b1 = j->nblocks, k = 0;
     if (j->mode == HE_LR_MINI_BATCH) {
@@ -446,8 +450,68 @@ extern "C" int he_lr_job_step(he_lr_job *j, int t, he_lr_sched sched)
         glevel = g.level;
     }
     CtB acc{j->acc, 1, glevel, gscale, 0};
-    CtB Wn{j->acc + j->ctw, 1, 0, 0, 0}, Vn{j->acc + 2 * j->ctw, 1, 0, 0, 0};
-    HELR_TRY(finish(j, acc, j->B[k], eta, j->inv_n[k], Wn, Vn));
+    Wn = CtB{j->acc + j->ctw, 1, 0, 0, 0};
+    Vn = CtB{j->acc + 2 * j->ctw, 1, 0, 0, 0};
+    return finish(j, acc, j->B[k], eta, j->inv_n[k], Wn, Vn);
+}
+
+// Steps 1-9 recorded into a CUDA graph on the job's stream and launched as one unit
+static int job_update_graph(he_lr_job *j, int t, const he_lr_sched &sched, CtB &Wn, CtB &Vn)
+{
+    he_ctx *c = j->c;
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    cudaStream_t saved = c->stream;
+    const int prof_on = c->prof.on;
+    c->stream = j->gstream;
+    c->prof.on = 0;  // no timing events inside the graph
+    cudaGraph_t g = nullptr;
+    int rc = HE_OK;
+    cudaError_t e = cudaStreamBeginCapture(j->gstream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = job_update(j, t, sched, Wn, Vn);
+        e = cudaStreamEndCapture(j->gstream, &g);
+    }
+    c->stream = saved;
+    c->prof.on = prof_on;
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return helr_fail(c, HE_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    bool updated = false;
+    if (j->gexec) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(j->gexec, g, &info) == cudaSuccess;
+        if (!updated) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(j->gexec);
+            j->gexec = nullptr;
+        }
+    }
+    if (!j->gexec) e = cudaGraphInstantiate(&j->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return helr_fail(c, HE_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    HELR_CUDA(c, cudaGraphLaunch(j->gexec, j->gstream));
+    HELR_CUDA(c, cudaStreamSynchronize(j->gstream));
+    return HE_OK;
+}
+
+extern "C" int he_lr_job_set_graph(he_lr_job *j, int on)
+{
+    if (!j) return HE_EINVAL;
+    if (on && !j->gstream) HELR_CUDA(j->c, cudaStreamCreateWithFlags(&j->gstream, cudaStreamNonBlocking));
+    j->graph = on ? 1 : 0;
+    return HE_OK;
+}
+
+extern "C" int he_lr_job_step(he_lr_job *j, int t, he_lr_sched sched)
+{
+    if (!j || t < 0 || !(sched.T > 0)) return HE_EINVAL;
+    he_ctx *c = j->c;
+    auto t0 = std::chrono::steady_clock::now();
+    CtB Wn{}, Vn{};
+    if (j->graph) HELR_TRY(job_update_graph(j, t, sched, Wn, Vn));
+    else HELR_TRY(job_update(j, t, sched, Wn, Vn));
     HELR_CUDA(c, cudaStreamSynchronize(c->stream));
     auto t1 = std::chrono::steady_clock::now();
     // Step 7: refresh W and V

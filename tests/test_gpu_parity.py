@@ -248,15 +248,17 @@ def test_iteration_bitwise(small_job_inputs, L):
         assert np.array_equal(ctx.refresh(x, circ.L, D, seed).export(), circ.refresh(rx, seed).data)
 
 
-def test_job_step_bitwise_and_weights(small_job_inputs):
+@pytest.mark.parametrize("graph", [False, True])
+def test_job_step_bitwise_and_weights(small_job_inputs, graph):
     ctx, he, data, circ = small_job_inputs
     X, y = synth.small()
     job = binding.Job(ctx, X, y, binding.FULL_BATCH, 1024, binding.G8, 40.0, enc_seed=3, key_seed=2)
+    job.set_graph(graph)
     st = job.stats()
     assert (st.n_blocks, st.g, st.m) == (4, 16, 256)
-    # encrypted data blocks equal the oracle's encryption of the same packing
     L = circ.L
     assert L == 7
+    # encrypted data blocks equal the oracle's encryption of the same packing
     for b in range(4):
         ref = he.encrypt(he.encode(data.blocks[b], L, D), qgnag.obj_seed(3, qgnag.SEED_BLOCK, b))
         assert np.array_equal(job.input(0, b).export(), ref.data)
@@ -278,3 +280,36 @@ def test_job_step_bitwise_and_weights(small_job_inputs):
     wp = plain.train(data, 2)
     for row in (0, 255):
         assert np.abs(job.weights(row) - wp).max() < 1e-3
+
+
+def test_minibatch_job_bitwise(pair):
+    """Algorithm 1 over 3 mini-batches of 1,024 rows (the last one ragged: 952
+    rows), 4 iterations so batch 0 is revisited; the g16 polynomial."""
+    ctx, he = pair
+    X, y = synth.small(seed=11, n=3000, f=15)
+    data = qgnag.TrainData(X, y, g=16, m=256, batch_rows=1024)
+    circ = qgnag.Circuit(he, 16, 256, D, poly=qgnag.G16)
+    job = binding.Job(ctx, X, y, binding.MINI_BATCH, 1024, binding.G16, 40.0, enc_seed=8, key_seed=2, batch_blocks=3)
+    job.set_graph(True)
+    L = circ.L
+    nb = data.blocks.shape[0]
+    assert job.stats().n_blocks == nb == 12
+    Z = [OCt(job.input(0, b).export(), L, D) for b in range(nb)]
+    B = [OCt(job.input(1, k).export(), L, D) for k in range(data.nbatch)]
+    (Ww, _, _), (Vw, _, _) = job.state_words()
+    W, V = OCt(Ww, L, D), OCt(Vw, L, D)
+    sched = (1.0, 0.2, 10.0, 2.5)
+    etas = qgnag.nag_scalars(4)
+    for t in range(4):
+        job.step(t, sched)
+        k = t % data.nbatch
+        blocks = Z[k * 4:(k + 1) * 4]
+        Wn, Vn = circ.iteration(blocks, B[k], W, V, qgnag.schedule(t, *sched), etas[t], 1.0 / float(data.n_k[k]))
+        W = circ.refresh(Wn, qgnag.obj_seed(8, qgnag.SEED_WREF, t))
+        V = circ.refresh(Vn, qgnag.obj_seed(8, qgnag.SEED_VREF, t))
+        (Ww, _, _), (Vw, _, _) = job.state_words()
+        assert np.array_equal(Ww, W.data), t
+        assert np.array_equal(Vw, V.data), t
+    from oracle import plain
+    wp = plain.train(data, 4, mode="mini", sched=sched, poly=qgnag.G16)
+    assert np.abs(job.weights(0) - wp).max() < 1e-3
