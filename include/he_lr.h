@@ -248,6 +248,18 @@ int he_lr_job_block_grad(he_lr_job *job, int block, double alpha, he_ct **out);
 int he_lr_job_info(const he_lr_job *job, he_lr_stats *stats);
 int he_lr_job_free(he_lr_job *job);
 
+/* Several independent full-batch jobs of one context trained in lockstep
+ * (uneven job sizes and feature counts, Sec. 4.2's multi-owner usage run as
+ * separate models): Steps 1-6 of all jobs' data blocks share launches, ordered
+ * by decreasing row width; Steps 7-9 and the refresh run per job.  The jobs
+ * must use one level, scale and sigmoid polynomial; they stay owned by the
+ * caller and must outlive the handle.  blocks_per_launch 0 = 64. */
+typedef struct he_lr_multi he_lr_multi;
+int he_lr_multi_create(he_ctx *ctx, he_lr_job *const *jobs, size_t n_jobs, int blocks_per_launch, he_lr_multi **out);
+/* Iteration t of every job (same schedule); results through he_lr_job_weights. */
+int he_lr_multi_step(he_lr_multi *multi, int t, he_lr_sched sched);
+int he_lr_multi_free(he_lr_multi *multi);
+
 /* Whole training through one call: job_create + iters x job_step + weights
  * of row 0 (w_out holds g values).  stats may be NULL. */
 int he_lr_train(he_ctx *ctx, const double *X, const double *y, size_t n, size_t f, int iters,

@@ -95,6 +95,9 @@ SIGNATURES = {
     "he_prof_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_u64)]),
     "he_prof_read2": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "he_lr_job_free": (_i, [_vp]),
+    "he_lr_multi_create": (_i, [_vp, _vp, _sz, _i, _pp]),
+    "he_lr_multi_step": (_i, [_vp, _i, he_lr_sched]),
+    "he_lr_multi_free": (_i, [_vp]),
     "he_lr_train": (_i, [_vp, _vp, _vp, _sz, _sz, _i, he_lr_sched, _i, _sz, _i, _u64, _u64, _vp, _sz,
                          ctypes.POINTER(he_lr_stats)]),
     "he_lr_iteration": (_i, [_vp, _vp, _sz, _vp, _vp, _vp, _i, _i, _d, _d, _d, _vp, _pp, _pp]),
@@ -380,6 +383,31 @@ class Job:
     def close(self):
         if getattr(self, "h", None):
             self.ctx.L.he_lr_job_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Multi:
+    """he_lr_multi: several full-batch jobs stepped together (jobs stay owned by the caller)."""
+
+    def __init__(self, ctx, jobs, blocks_per_launch=0):
+        self.ctx, self.jobs = ctx, list(jobs)
+        arr = (ctypes.c_void_p * len(jobs))(*[j.h.value for j in jobs])
+        h = ctypes.c_void_p()
+        ctx.check(ctx.L.he_lr_multi_create(ctx.h, arr, len(jobs), blocks_per_launch, ctypes.byref(h)))
+        self.h = h
+
+    def step(self, t, sched=(2.0, 1.0, 81.0, 2.5)):
+        self.ctx.check(self.ctx.L.he_lr_multi_step(self.h, t, he_lr_sched(*sched)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.L.he_lr_multi_free(self.h)
             self.h = None
 
     def __del__(self):

@@ -108,6 +108,34 @@ int ev_mul_relin(Eval *ev, const CtB &a, const CtB &b, CtB &out)
     return HE_OK;
 }
 
+// out = Relin(a (x) b_s) where item i of segment s (items start_s .. start_s + count_s - 1)
+// is multiplied by the single ciphertext bptr[s]; one key switch over the whole batch.
+int ev_mul_relin_seg(Eval *ev, const CtB &a, const uint64_t *const *bptr, const int *start, const int *count, int nseg,
+                     double bscale, CtB &out)
+{
+    he_ctx *c = ev->c;
+    HELR_TRY(check_batch(ev, a));
+    const int B = a.batch, lv = a.level, nl = lv + 1;
+    const size_t N = c->n, lw = (size_t)nl * N;
+    const uint64_t *key = helr_find_key(c, 0);
+    if (!key) return helr_fail(c, HE_EKEY, "no relinearisation key");
+    for (int sg = 0; sg < nseg; sg++)
+        k_tensor(c, a.d + (size_t)start[sg] * a.item, bptr[sg], ev->tens + (size_t)start[sg] * lw, count[sg], lv, a.item, 0, lw,
+                 (size_t)B * lw, c->stream);
+    out.level = lv;
+    out.batch = B;
+    out.scale = a.scale * bscale;
+    KsOut o;
+    o.out = S(out, c);
+    o.rel = ev->tens;
+    o.rel_item = lw;
+    o.rel_poly = (size_t)B * lw;
+    HELR_TRY(helr_keyswitch(c, ev->tens + 2 * (size_t)B * lw, nullptr, B, lv, key, &ev->ks, &o));
+    ev->keyswitches += B;
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
+
 // divide by q_level with rounding: out at level - 1
 int ev_rescale(Eval *ev, const CtB &a, CtB &out)
 {

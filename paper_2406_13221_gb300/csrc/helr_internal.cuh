@@ -357,6 +357,8 @@ int ev_init(he_ctx *c, Eval *ev, int maxb, int maxlevel);
 void ev_free(Eval *ev);
 int ev_mul_relin(Eval *ev, const CtB &a, const CtB &b, CtB &out);
 int ev_rescale(Eval *ev, const CtB &a, CtB &out);
+int ev_mul_relin_seg(Eval *ev, const CtB &a, const uint64_t *const *bptr, const int *start, const int *count, int nseg,
+                     double bscale, CtB &out);
 int ev_rotate(Eval *ev, const CtB &a, int64_t r, CtB &out);
 int ev_rotate_acc(Eval *ev, const CtB &a, int64_t r, CtB &out, int accumulate);
 int ev_add(Eval *ev, const CtB &a, const CtB &b, CtB &out, int sub);

@@ -310,93 +310,163 @@ static int cmul_to(Eval *ev, const CtB &a, double cval, double target, CtB &tmp,
     return HE_OK;
 }
 
-// Steps 1-6 on `cnt` blocks starting at Z; result (level L-5) in g_out
-static int block_grads(he_lr_job *j, const uint64_t *Z, int cnt, const CtB &W, double alpha, CtB &g_out)
+// Work buffers shared by the circuit functions: five ciphertext arrays of `cap`
+// top-level ciphertexts each.
+struct WorkSet {
+    Eval *ev;
+    uint64_t *T[5];
+    size_t ctw;
+    int L;
+    double scale0;
+    const double *poly;
+};
+
+// A run of data blocks that share W, the mask and the row width g.
+struct Seg {
+    int start, count, lg;
+    const uint64_t *W, *mask;
+    double mask_scale;
+};
+
+// ping-pong rotate-and-add over the items with lg > k (a prefix: segments are
+// ordered by decreasing lg); the remaining items are carried over unchanged
+static int rot_step(const WorkSet &ws, CtB &Bt, CtB &R, int64_t r, int rotated, int cnt)
 {
-    Eval *ev = &j->ev;
-    he_ctx *c = j->c;
-    const int L = j->L;
-    const size_t w = j->ctw;
-    CtB Zc{const_cast<uint64_t *>(Z), cnt, L, j->scale0, w};
-    CtB A{j->T0, cnt, 0, 0, w}, Bt{j->T1, cnt, 0, 0, w}, R{j->T2, cnt, 0, 0, w};
-    // 1
-    HELR_TRY(ev_mul_relin(ev, Zc, W, A));
-    HELR_TRY(ev_rescale(ev, A, Bt));
-    // 2: t += Rot(t, 2^k), ping-pong between T1 and T2
-    for (int k = 0; k < j->lg; k++) {
-        HELR_TRY(ev_rotate_acc(ev, Bt, 1 << k, R, 1));
-        std::swap(Bt, R);
+    Eval *ev = ws.ev;
+    CtB pre = Bt, preR = R;
+    pre.batch = rotated;
+    HELR_TRY(ev_rotate_acc(ev, pre, r, preR, 1));
+    if (rotated < cnt) {
+        CtB rest = Bt, restR = R;
+        rest.d = Bt.d + (size_t)rotated * ws.ctw;
+        rest.batch = cnt - rotated;
+        restR.d = R.d + (size_t)rotated * ws.ctw;
+        HELR_TRY(ev_moddrop(ev, rest, rest.level, restR));
     }
-    // 3
-    HELR_TRY(ev_ptmul(ev, Bt, j->mask, j->mask_scale, A));
-    Bt.d = j->T1;
-    R.d = j->T2;
-    HELR_TRY(ev_rescale(ev, A, Bt));
-    // 4
-    for (int k = 0; k < j->lg; k++) {
-        HELR_TRY(ev_rotate_acc(ev, Bt, -(1 << k), R, 1));
-        std::swap(Bt, R);
-    }
-    if (Bt.d != j->T1) {
-        CtB t1{j->T1, cnt, 0, 0, w};
-        HELR_TRY(ev_moddrop(ev, Bt, Bt.level, t1));
-        Bt = t1;
-    }
-    R.d = j->T2;
-    CtB ip = Bt;  // level L-2, in T1
-    // 5
-    const double k0 = alpha * (1.0 - j->poly[0]), k1 = -(alpha * j->poly[1]), k3 = -(alpha * j->poly[2]);
-    CtB sq{j->T3, cnt, 0, 0, w}, c3{j->T4, cnt, 0, 0, w};
-    HELR_TRY(ev_mul_relin(ev, ip, ip, A));
-    HELR_TRY(ev_rescale(ev, A, sq));
-    HELR_TRY(ev_cmul_int(ev, ip, round_half_away(k3 * j->scale0), ip.scale * j->scale0, A));
-    HELR_TRY(ev_rescale(ev, A, c3));
-    CtB cube{j->T0, cnt, 0, 0, w};
-    HELR_TRY(ev_mul_relin(ev, sq, c3, R));
-    HELR_TRY(ev_rescale(ev, R, cube));
-    CtB lin{j->T3, cnt, 0, 0, w}, lind{j->T4, cnt, 0, 0, w};
-    HELR_TRY(cmul_to(ev, ip, k1, cube.scale, R, lin));
-    HELR_TRY(ev_moddrop(ev, lin, cube.level, lind));
-    CtB s{j->T1, cnt, 0, 0, w};
-    HELR_TRY(ev_add(ev, cube, lind, s, 0));
-    HELR_TRY(ev_cadd_int(ev, s, round_half_away(k0 * s.scale)));
-    // 6
-    CtB zd{j->T3, cnt, 0, 0, w};
-    HELR_TRY(ev_moddrop(ev, Zc, s.level, zd));
-    HELR_TRY(ev_mul_relin(ev, s, zd, A));
-    g_out.d = j->T2;
-    g_out.item = w;
-    HELR_TRY(ev_rescale(ev, A, g_out));
-    (void)c;
+    R.level = Bt.level;
+    R.scale = Bt.scale;
+    R.batch = cnt;
+    std::swap(Bt, R);
     return HE_OK;
 }
 
-// Steps 7-9 on the accumulated gradient; W', V' at level L-7 into Wn, Vn
-static int finish(he_lr_job *j, CtB acc, const he_ct *Bct, double eta, double inv_n, CtB &Wn, CtB &Vn)
+// Steps 1-6 on `cnt` blocks at Z (item stride ctw) described by segments;
+// result (level L-5) in g_out (buffer T2)
+static int block_grads_seg(const WorkSet &ws, const uint64_t *Z, int cnt, const Seg *segs, int nseg, double w_scale,
+                           double alpha, CtB &g_out)
 {
-    Eval *ev = &j->ev;
-    const size_t w = j->ctw;
-    CtB R{j->T0, 1, 0, 0, w}, A{j->T1, 1, 0, 0, w}, Bd{j->T2, 1, 0, 0, w};
+    Eval *ev = ws.ev;
+    const int L = ws.L;
+    const size_t w = ws.ctw;
+    CtB Zc{const_cast<uint64_t *>(Z), cnt, L, ws.scale0, w};
+    CtB A{ws.T[0], cnt, 0, 0, w}, Bt{ws.T[1], cnt, 0, 0, w}, R{ws.T[2], cnt, 0, 0, w};
+    std::vector<const uint64_t *> wp(nseg);
+    std::vector<int> st(nseg), ct(nseg);
+    int lgmax = 0;
+    for (int i = 0; i < nseg; i++) {
+        wp[i] = segs[i].W, st[i] = segs[i].start, ct[i] = segs[i].count;
+        lgmax = std::max(lgmax, segs[i].lg);
+    }
+    auto rotated = [&](int k) {
+        int n = 0;
+        for (int i = 0; i < nseg; i++)
+            if (segs[i].lg > k) n = segs[i].start + segs[i].count;
+        return n;
+    };
+    // 1
+    HELR_TRY(ev_mul_relin_seg(ev, Zc, wp.data(), st.data(), ct.data(), nseg, w_scale, A));
+    HELR_TRY(ev_rescale(ev, A, Bt));
+    // 2: t += Rot(t, 2^k), ping-pong between T1 and T2
+    for (int k = 0; k < lgmax; k++) HELR_TRY(rot_step(ws, Bt, R, 1 << k, rotated(k), cnt));
+    // 3: mask of each segment's row width
+    for (int i = 0; i < nseg; i++) {
+        CtB x = Bt, y = A;
+        x.d = Bt.d + (size_t)segs[i].start * w;
+        x.batch = segs[i].count;
+        y.d = A.d + (size_t)segs[i].start * w;
+        HELR_TRY(ev_ptmul(ev, x, segs[i].mask, segs[i].mask_scale, y));
+        A.level = y.level;
+        A.scale = y.scale;
+    }
+    A.batch = cnt;
+    Bt.d = ws.T[1];
+    R.d = ws.T[2];
+    HELR_TRY(ev_rescale(ev, A, Bt));
+    // 4
+    for (int k = 0; k < lgmax; k++) HELR_TRY(rot_step(ws, Bt, R, -(1 << k), rotated(k), cnt));
+    if (Bt.d != ws.T[1]) {
+        CtB t1{ws.T[1], cnt, 0, 0, w};
+        HELR_TRY(ev_moddrop(ev, Bt, Bt.level, t1));
+        Bt = t1;
+    }
+    R.d = ws.T[2];
+    CtB ip = Bt;  // level L-2, in T1
+    // 5
+    const double k0 = alpha * (1.0 - ws.poly[0]), k1 = -(alpha * ws.poly[1]), k3 = -(alpha * ws.poly[2]);
+    CtB sq{ws.T[3], cnt, 0, 0, w}, c3{ws.T[4], cnt, 0, 0, w};
+    HELR_TRY(ev_mul_relin(ev, ip, ip, A));
+    HELR_TRY(ev_rescale(ev, A, sq));
+    HELR_TRY(ev_cmul_int(ev, ip, round_half_away(k3 * ws.scale0), ip.scale * ws.scale0, A));
+    HELR_TRY(ev_rescale(ev, A, c3));
+    CtB cube{ws.T[0], cnt, 0, 0, w};
+    HELR_TRY(ev_mul_relin(ev, sq, c3, R));
+    HELR_TRY(ev_rescale(ev, R, cube));
+    CtB lin{ws.T[3], cnt, 0, 0, w}, lind{ws.T[4], cnt, 0, 0, w};
+    HELR_TRY(cmul_to(ev, ip, k1, cube.scale, R, lin));
+    HELR_TRY(ev_moddrop(ev, lin, cube.level, lind));
+    CtB s{ws.T[1], cnt, 0, 0, w};
+    HELR_TRY(ev_add(ev, cube, lind, s, 0));
+    HELR_TRY(ev_cadd_int(ev, s, round_half_away(k0 * s.scale)));
+    // 6
+    CtB zd{ws.T[3], cnt, 0, 0, w};
+    HELR_TRY(ev_moddrop(ev, Zc, s.level, zd));
+    HELR_TRY(ev_mul_relin(ev, s, zd, A));
+    g_out.d = ws.T[2];
+    g_out.item = w;
+    HELR_TRY(ev_rescale(ev, A, g_out));
+    return HE_OK;
+}
+
+static WorkSet job_ws(he_lr_job *j)
+{
+    return WorkSet{&j->ev, {j->T0, j->T1, j->T2, j->T3, j->T4}, j->ctw, j->L, j->scale0, j->poly};
+}
+
+// Steps 1-6 on `cnt` consecutive blocks of one job
+static int block_grads(he_lr_job *j, const uint64_t *Z, int cnt, const CtB &W, double alpha, CtB &g_out)
+{
+    Seg sg{0, cnt, j->lg, W.d, j->mask, j->mask_scale};
+    return block_grads_seg(job_ws(j), Z, cnt, &sg, 1, W.scale, alpha, g_out);
+}
+
+// Steps 7-9 on the accumulated gradient of one job (row width g = 2^lg... column
+// sums over m = 2^lm rows); W', V' at level L-7 into Wn, Vn
+static int finish_ws(const WorkSet &ws, CtB acc, const he_ct *Bct, const he_ct *W, const he_ct *V, int g, int lm, double eta,
+                     double inv_n, CtB &Wn, CtB &Vn)
+{
+    Eval *ev = ws.ev;
+    const size_t w = ws.ctw;
+    CtB R{ws.T[0], 1, 0, 0, w}, A{ws.T[1], 1, 0, 0, w}, Bd{ws.T[2], 1, 0, 0, w};
     // 7: acc += Rot(acc, g 2^k), ping-pong between acc and R
-    for (int k = 0; k < j->lm; k++) {
-        HELR_TRY(ev_rotate_acc(ev, acc, (int64_t)j->g << k, R, 1));
+    for (int k = 0; k < lm; k++) {
+        HELR_TRY(ev_rotate_acc(ev, acc, (int64_t)g << k, R, 1));
         std::swap(acc, R);
     }
     // 8
     CtB Bv{Bct->d, 1, Bct->level, Bct->scale, 0};
     HELR_TRY(ev_moddrop(ev, Bv, acc.level, Bd));
     HELR_TRY(ev_mul_relin(ev, acc, Bd, A));
-    CtB nG{j->T3, 1, 0, 0, w};
+    CtB nG{ws.T[3], 1, 0, 0, w};
     HELR_TRY(ev_rescale(ev, A, nG));
     // 9
     const int lv = nG.level;
-    const double tgt = j->W->scale;
-    CtB Wv{j->W->d, 1, j->W->level, j->W->scale, 0}, Vv{j->V->d, 1, j->V->level, j->V->scale, 0};
-    CtB G{j->T4, 1, 0, 0, w}, Wd{j->T0, 1, 0, 0, w};
+    const double tgt = W->scale;
+    CtB Wv{W->d, 1, W->level, W->scale, 0}, Vv{V->d, 1, V->level, V->scale, 0};
+    CtB G{ws.T[4], 1, 0, 0, w}, Wd{ws.T[0], 1, 0, 0, w};
     HELR_TRY(cmul_to(ev, nG, inv_n, tgt, A, G));
     HELR_TRY(ev_moddrop(ev, Wv, lv - 1, Wd));
     HELR_TRY(ev_add(ev, Wd, G, Vn, 0));
-    CtB x1{j->T4, 1, 0, 0, w}, x2{j->T0, 1, 0, 0, w};
+    CtB x1{ws.T[4], 1, 0, 0, w}, x2{ws.T[0], 1, 0, 0, w};
     HELR_TRY(ev_moddrop(ev, Wv, lv, Bd));
     HELR_TRY(cmul_to(ev, Bd, 1.0 - eta, tgt, A, x1));
     HELR_TRY(ev_moddrop(ev, Vv, lv, Bd));
@@ -405,6 +475,11 @@ static int finish(he_lr_job *j, CtB acc, const he_ct *Bct, double eta, double in
     HELR_TRY(cmul_to(ev, nG, (1.0 - eta) * inv_n, tgt, A, x2));
     HELR_TRY(ev_add(ev, x1, x2, Wn, 0));
     return HE_OK;
+}
+
+static int finish(he_lr_job *j, CtB acc, const he_ct *Bct, double eta, double inv_n, CtB &Wn, CtB &Vn)
+{
+    return finish_ws(job_ws(j), acc, Bct, j->W, j->V, j->g, j->lm, eta, inv_n, Wn, Vn);
 }
 
 // decrypt, keep the real part of every slot, re-encode at new_level, encrypt
@@ -751,5 +826,121 @@ extern "C" int he_refresh(he_ctx *c, const he_ct *in, int level, double scale, u
         return rc;
     }
     *out = o;
+    return HE_OK;
+}
+
+// ------------------------------------------------------------------ several jobs at once
+// Independent full-batch jobs of one context stepped together: the data blocks
+// of all jobs are ordered by decreasing row width g and Steps 1-6 run over
+// chunks of that order, so every key switch is batched across jobs (segments
+// carry each job's W and mask; rotations a narrower job does not need run on a
+// prefix of the chunk).  Steps 7-9 and the refresh run per job.
+struct he_lr_multi {
+    he_ctx *c;
+    std::vector<he_lr_job *> jobs;
+    std::vector<std::pair<int, int>> order;  // (job, block)
+    int L, chunk;
+    size_t ctw;
+    double scale0;
+    double poly[3];
+    Eval ev;
+    uint64_t *buf;  // 5 x chunk work ciphertexts, chunk staged blocks, njobs accumulators, W' and V'
+    uint64_t *T[5], *Zs, *accs, *wv;
+};
+
+extern "C" int he_lr_multi_free(he_lr_multi *m)
+{
+    if (!m) return HE_EINVAL;
+    cudaStreamSynchronize(m->c->stream);
+    helr_free(m->c, m->buf);
+    ev_free(&m->ev);
+    cudaStreamSynchronize(m->c->stream);
+    delete m;
+    return HE_OK;
+}
+
+extern "C" int he_lr_multi_create(he_ctx *c, he_lr_job *const *jobs, size_t njobs, int blocks_per_launch,
+                                  he_lr_multi **out)
+{
+    if (!c || !jobs || !njobs || !out) return HE_EINVAL;
+    *out = nullptr;
+    for (size_t i = 0; i < njobs; i++) {
+        const he_lr_job *j = jobs[i];
+        if (!j || j->c != c) return helr_fail(c, HE_EINVAL, "job %zu belongs to another context", i);
+        if (j->mode != HE_LR_FULL_BATCH) return helr_fail(c, HE_EINVAL, "job %zu is not a full-batch job", i);
+        if (j->L != jobs[0]->L || j->scale0 != jobs[0]->scale0 || memcmp(j->poly, jobs[0]->poly, sizeof j->poly))
+            return helr_fail(c, HE_EINVAL, "job %zu differs from job 0 in level, scale or polynomial", i);
+    }
+    he_lr_multi *m = new he_lr_multi();
+    m->c = c;
+    m->jobs.assign(jobs, jobs + njobs);
+    m->L = jobs[0]->L;
+    m->ctw = jobs[0]->ctw;
+    m->scale0 = jobs[0]->scale0;
+    memcpy(m->poly, jobs[0]->poly, sizeof m->poly);
+    std::vector<int> idx(njobs);
+    for (size_t i = 0; i < njobs; i++) idx[i] = (int)i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return jobs[a]->lg > jobs[b]->lg; });
+    for (int i : idx)
+        for (int b = 0; b < jobs[i]->nblocks; b++) m->order.push_back({i, b});
+    m->chunk = std::max(1, std::min(blocks_per_launch > 0 ? blocks_per_launch : 64, (int)m->order.size()));
+    int rc = ev_init(c, &m->ev, m->chunk, m->L);
+    const size_t cts = 6 * (size_t)m->chunk + njobs + 2;
+    if (!rc) rc = helr_alloc(c, (void **)&m->buf, sizeof(uint64_t) * m->ctw * cts);
+    if (rc) {
+        he_lr_multi_free(m);
+        return rc;
+    }
+    for (int k = 0; k < 5; k++) m->T[k] = m->buf + (size_t)k * m->chunk * m->ctw;
+    m->Zs = m->buf + (size_t)5 * m->chunk * m->ctw;
+    m->accs = m->Zs + (size_t)m->chunk * m->ctw;
+    m->wv = m->accs + njobs * m->ctw;
+    *out = m;
+    return HE_OK;
+}
+
+extern "C" int he_lr_multi_step(he_lr_multi *m, int t, he_lr_sched sched)
+{
+    if (!m || t < 0 || !(sched.T > 0)) return HE_EINVAL;
+    he_ctx *c = m->c;
+    const double alpha = f2(sched, (double)t), eta = nag_eta(t);
+    const WorkSet ws{&m->ev, {m->T[0], m->T[1], m->T[2], m->T[3], m->T[4]}, m->ctw, m->L, m->scale0, m->poly};
+    std::vector<char> started(m->jobs.size(), 0);
+    double gscale = 0;
+    int glevel = 0;
+    m->ev.keyswitches = 0;
+    for (size_t p = 0; p < m->order.size(); p += m->chunk) {
+        const int cnt = (int)std::min<size_t>(m->chunk, m->order.size() - p);
+        std::vector<Seg> segs;
+        for (int i = 0; i < cnt; i++) {
+            const int jb = m->order[p + i].first, blk = m->order[p + i].second;
+            he_lr_job *j = m->jobs[jb];
+            HELR_CUDA(c, cudaMemcpyAsync(m->Zs + (size_t)i * m->ctw, j->Z + (size_t)blk * m->ctw, m->ctw * 8,
+                                         cudaMemcpyDeviceToDevice, c->stream));
+            if (i == 0 || m->order[p + i - 1].first != jb)
+                segs.push_back(Seg{i, 0, j->lg, j->W->d, j->mask, j->mask_scale});
+            segs.back().count++;
+        }
+        CtB g{};
+        HELR_TRY(block_grads_seg(ws, m->Zs, cnt, segs.data(), (int)segs.size(), m->scale0, alpha, g));
+        for (const Seg &sg : segs) {
+            const int jb = m->order[p + sg.start].first;
+            CtB sub{g.d + (size_t)sg.start * m->ctw, sg.count, g.level, g.scale, m->ctw};
+            HELR_TRY(ev_sum_items(&m->ev, sub, m->accs + (size_t)jb * m->ctw, started[jb]));
+            started[jb] = 1;
+        }
+        gscale = g.scale;
+        glevel = g.level;
+    }
+    for (size_t jb = 0; jb < m->jobs.size(); jb++) {
+        he_lr_job *j = m->jobs[jb];
+        CtB acc{m->accs + jb * m->ctw, 1, glevel, gscale, 0};
+        CtB Wn{m->wv, 1, 0, 0, 0}, Vn{m->wv + m->ctw, 1, 0, 0, 0};
+        HELR_TRY(finish_ws(ws, acc, j->B[0], j->W, j->V, j->g, j->lm, eta, j->inv_n[0], Wn, Vn));
+        HELR_TRY(refresh_dev(c, Wn.d, Wn.level, Wn.scale, j->L, j->scale0, obj_seed(j->enc_seed, 5, t), j->W->d));
+        HELR_TRY(refresh_dev(c, Vn.d, Vn.level, Vn.scale, j->L, j->scale0, obj_seed(j->enc_seed, 6, t), j->V->d));
+        j->W->scale = j->V->scale = j->scale0;
+    }
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
     return HE_OK;
 }

@@ -313,3 +313,32 @@ def test_minibatch_job_bitwise(pair):
     from oracle import plain
     wp = plain.train(data, 4, mode="mini", sched=sched, poly=qgnag.G16)
     assert np.abs(job.weights(0) - wp).max() < 1e-3
+
+
+def test_multi_job_matches_single_jobs(pair):
+    """Three full-batch jobs of different widths (g = 32, 16, 8) stepped together
+    give exactly the words each job gives alone, and track their FP64 twins."""
+    ctx, he = pair
+    shapes = [(700, 5, 21), (1500, 15, 22), (400, 30, 23)]  # (n, f, enc_seed)
+    data = [synth.job(seed=s, n=n, f=f) for n, f, s in shapes]
+    multi_jobs = [binding.Job(ctx, X, y, binding.FULL_BATCH, 1024, binding.G8, 40.0, enc_seed=s, key_seed=2,
+                              batch_blocks=2) for (X, y), (_, _, s) in zip(data, shapes)]
+    alone = [binding.Job(ctx, X, y, binding.FULL_BATCH, 1024, binding.G8, 40.0, enc_seed=s, key_seed=2, batch_blocks=4)
+             for (X, y), (_, _, s) in zip(data, shapes)]
+    assert sorted(j.stats().g for j in multi_jobs) == [8, 16, 32]
+    multi = binding.Multi(ctx, multi_jobs, blocks_per_launch=5)  # chunks straddle jobs
+    for t in range(2):
+        multi.step(t)
+        for j in alone:
+            j.step(t)
+        for jm, ja in zip(multi_jobs, alone):
+            (Wm, _, _), (Vm, _, _) = jm.state_words()
+            (Wa, _, _), (Va, _, _) = ja.state_words()
+            assert np.array_equal(Wm, Wa) and np.array_equal(Vm, Va), t
+    from oracle import plain
+    for (X, y), jm in zip(data, multi_jobs):
+        st = jm.stats()
+        td = qgnag.TrainData(X, y, g=st.g, m=st.m, batch_rows=1024)
+        wp = plain.train(td, 2)
+        assert np.abs(jm.weights(0) - wp).max() < 1e-3
+    multi.close()
