@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-twin", action="store_true")
     ap.add_argument("--no-mini", action="store_true")
+    ap.add_argument("--no-multi", action="store_true")
     ap.add_argument("--sweep-point", default="", help="log_n,limbs,batch: run only this NTT sweep point")
     ap.add_argument("--sweep", action="store_true",
                     help="HE primitive sweep: batched NTT and key switching vs N, limbs and batch (JSON line per point)")
@@ -208,6 +209,11 @@ def run_ours(args, rank, world):
     mini = None
     if not args.no_mini:
         mini = minibatch_time(ctx, X, y, args)
+    multi = None
+    if not args.no_multi and world == 1:
+        del job
+        torch.cuda.empty_cache()
+        multi = multijob_time(ctx)
     roof = roofline(prof, args.steps)
     out = {
         "metric": METRIC, "value": round(sec_iter, 5), "unit": "s/iter", "n_gpus": world, "steps": args.steps,
@@ -223,6 +229,7 @@ def run_ours(args, rank, world):
         "ntt_limbs_per_s": round((prof["ntt_fwd"][1] + prof["ntt_inv"][1]) / args.steps / (sec_iter * world), 1),
         "plain_one_ct_per_launch_s_per_iter": round(plain, 4) if plain else None,
         "mini_batch": mini,
+        "multi_job": multi,
         "batched_speedup_vs_plain": round(plain / sec_iter / world, 2) if plain else None,
         "setup_s": round(setup_s, 1),
         "max_abs_err_vs_fp64_twin": err,
@@ -264,6 +271,50 @@ def minibatch_time(ctx, X, y, args):
     out["batched_graph_speedup_vs_plain"] = round(out["plain_s_per_iter"] / out["batched_graph_s_per_iter"], 2)
     job.close()
     return out
+
+
+def multijob_time(ctx):
+    """16 independent full-batch jobs, n_j log-uniform in [5,000, 100,000],
+    f_j uniform in {32, 64, 128, 200}: seconds per iteration with all jobs
+    stepped together (key switches batched across jobs) against each job alone."""
+    import torch
+    from paper_2406_13221_gb300 import binding, synth
+    shapes = synth.multijob_shapes(seed=5)
+    jobs, alone = [], []
+    for i, (n, f) in enumerate(shapes):
+        X, y = synth.job(seed=100 + i, n=n, f=f)
+        jobs.append(binding.Job(ctx, X, y, binding.FULL_BATCH, 1024, binding.G8, LOG_SCALE, enc_seed=1000 + i,
+                                key_seed=2, batch_blocks=16))
+    multi = binding.Multi(ctx, jobs, blocks_per_launch=64)
+    sched = (2.0, 1.0, 81.0, 2.5)
+    multi.step(0, sched)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for t in (1, 2):
+        multi.step(t, sched)
+    e1.record()
+    torch.cuda.synchronize()
+    agg = e0.elapsed_time(e1) / 2 / 1000.0
+    per = []
+    for i, j in enumerate(jobs):
+        j.step(3, sched)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        j.step(4, sched)
+        a1.record()
+        torch.cuda.synchronize()
+        st = j.stats()
+        per.append({"n": shapes[i][0], "f": shapes[i][1], "g": st.g, "blocks": st.n_blocks,
+                    "s_per_iter_alone": round(a0.elapsed_time(a1) / 1000.0, 4)})
+    multi.close()
+    for j in jobs:
+        j.close()
+    tot = sum(p["s_per_iter_alone"] for p in per)
+    return {"jobs": len(jobs), "blocks": sum(p["blocks"] for p in per), "samples": sum(p["n"] for p in per),
+            "aggregate_s_per_iter": round(agg, 4), "sum_of_jobs_alone_s_per_iter": round(tot, 4),
+            "batched_speedup": round(tot / agg, 3), "per_job": per}
 
 
 def sweep(args):
