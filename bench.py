@@ -142,6 +142,7 @@ def run_ours(args, rank, world):
     job = binding.Job(ctx, X, y, binding.FULL_BATCH, 1024, binding.G8, LOG_SCALE, enc_seed=3, key_seed=2,
                       batch_blocks=args.chunk)
     info = job.stats()
+    chunk_used = info_chunk(job, args)
     setup_s = time.time() - t0
     sched = (2.0, 1.0, 81.0, 2.5)
     t = 0
@@ -186,7 +187,7 @@ def run_ours(args, rank, world):
         t += 1
         torch.cuda.synchronize()
         plain = time.time() - p0
-        job.set_batch(info_chunk(job, args))
+        job.set_batch(chunk_used)
     # ---------------- end to end through the public API with host state
     e2e = None
     if not args.no_e2e:
@@ -211,8 +212,8 @@ def run_ours(args, rank, world):
         mini = minibatch_time(ctx, X, y, args)
     multi = None
     if not args.no_multi and world == 1:
+        job.close()
         del job
-        torch.cuda.empty_cache()
         multi = multijob_time(ctx)
     roof = roofline(prof, args.steps)
     out = {
@@ -221,7 +222,7 @@ def run_ours(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": "full-batch QG-NAG, %d x %d synthetic Financial-shaped data, N=2^16, "
                                "chain 60+8x40 bits + 60-bit P, scale 2^40, 128x256 packing, g8 sigmoid" % (args.rows, N_FEAT),
-                   "blocks": int(info.n_blocks), "blocks_per_launch": info_chunk(job, args),
+                   "blocks": int(info.n_blocks), "blocks_per_launch": chunk_used,
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "no flush: %.1f GiB of encrypted data blocks > 129 MB L2" % (info.n_blocks * ctw_bytes() / 2 ** 30)},
         "keyswitch_per_s": round(ks_per_iter / sec_iter / world, 1) if sec_iter else None,
