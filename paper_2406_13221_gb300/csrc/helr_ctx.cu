@@ -200,6 +200,33 @@ static int upload(he_ctx *c, void **dst, const void *src, size_t bytes)
     return HE_OK;
 }
 
+// The transform runs as a column pass over the first K1 = floor(log N / 2)
+// stages and a row pass over the last K2 = log N - K1 stages; inside the row pass
+// a row of R2 = 2^K2 words is held by T2 = 2^floor(K2/2) threads.  On the
+// row-pass stages after the register exchange (local stage S >= ceil(K2/2),
+// m = 2^S twiddles per row starting at m (R1 + row)), thread l uses twiddles
+// l gpt + g (gpt = m / T2); those blocks are stored transposed, at g T2 + l, so
+// that the threads of a row load adjacent pairs.  All other entries keep the
+// bit-reversed order psi^bitrev(k).
+static void row_pass_layout(uint64_t *pairs, int logn)
+{
+    const int K1 = logn / 2, K2 = logn - K1, R1 = 1 << K1, T2 = 1 << (K2 / 2), LE2 = (K2 + 1) / 2;
+    std::vector<uint64_t> blk;
+    for (int S = LE2; S < K2; S++) {
+        const int m = 1 << S, gpt = m / T2;
+        blk.resize((size_t)m * 2);
+        for (int row = 0; row < R1; row++) {
+            uint64_t *b = pairs + ((size_t)m * (R1 + row)) * 2;
+            std::copy(b, b + (size_t)m * 2, blk.begin());
+            for (int l = 0; l < T2; l++)
+                for (int g = 0; g < gpt; g++) {
+                    b[(size_t)(g * T2 + l) * 2] = blk[(size_t)(l * gpt + g) * 2];
+                    b[(size_t)(g * T2 + l) * 2 + 1] = blk[(size_t)(l * gpt + g) * 2 + 1];
+                }
+        }
+    }
+}
+
 static int ctx_init(he_ctx *c, const he_params *p)
 {
     c->logn = p->log_n;
@@ -264,6 +291,8 @@ static int ctx_init(he_ctx *c, const he_params *p)
             itw[o] = ipw[e];
             itw[o + 1] = h_shoup(ipw[e], q);
         }
+        row_pass_layout(tw.data() + (size_t)i * n * 2, c->logn);
+        row_pass_layout(itw.data() + (size_t)i * n * 2, c->logn);
         uint64_t ni = h_inv((uint64_t)n % q, q);
         ninv[2 * i] = ni;
         ninv[2 * i + 1] = h_shoup(ni, q);
@@ -407,6 +436,7 @@ int helr_add_key(he_ctx *c, uint64_t gal)
     else k_automorph(c, sp, c->d_sk, np, gal, c->stream);
     HELR_TRY(helr_make_ksk(c, gal, sp, key));
     HELR_TRY(helr_to_montgomery(c, key, (size_t)nq * 2 * np, np));
+    HELR_TRY(helr_ks_key_layout(c, key, (size_t)nq * 2 * np));
     HELR_CUDA(c, cudaGetLastError());
     helr_free(c, sp);
     c->ksk.push_back({gal, key});

@@ -169,7 +169,8 @@ struct DevTables {
 
 struct KeySwitchKey {
     uint64_t gal;       // 0 = relinearisation
-    uint64_t *d;        // [nq digits][2][nq+1 limbs][N], evaluation form, Montgomery form (k 2^64 mod q)
+    uint64_t *d;        // [nq digits][2][nq+1 limbs][N], evaluation form, Montgomery form (k 2^64 mod q),
+                        // words reordered inside each transform row as k_ks_inner_rows reads them
 };
 
 struct he_ctx {
@@ -331,6 +332,8 @@ int helr_keygen_base(he_ctx *c, uint64_t seed);
 int helr_make_ksk(he_ctx *c, uint64_t gal, const uint64_t *sprime, uint64_t *out);
 int helr_square_dev(he_ctx *c, uint64_t *out, const uint64_t *in, size_t nlimbs);
 int helr_to_montgomery(he_ctx *c, uint64_t *x, size_t nlimbs, int period);
+int helr_ks_key_layout(he_ctx *c, uint64_t *key, size_t nlimbs);
+cudaError_t helr_fit_carveout(const void *f, int threads, size_t smem);
 
 // ------------------------------------------------------------------ batched evaluator (eval.cu)
 // A batch of ciphertexts: item i at d + i * item, polynomials [2][level+1][N];

@@ -48,20 +48,33 @@ __global__ void __launch_bounds__(C * Geo<K1>::T, 4)
     for (int r = 0; r < G::E; r++) x[r] = lift_centered(src[(size_t)(l + G::T * r) * R2], qi, mt);
     fwd_strided<K1>(x, tw, 1, q, q2);
     to_contig<K1>(x, smem + jj * G::SEG, l);
-    fwd_contig<K1>(x, tw, 1, l, q, q2);
+    fwd_contig<K1, false>(x, tw, 1, l, q, q2);
 #pragma unroll
     for (int r = 0; r < G::E; r++) dst[(size_t)(G::E * l + r) * R2] = x[r];
 }
 
-template <int E>
-__device__ __forceinline__ void load_contig(uint64_t (&x)[E], const uint64_t *p)
+// read-only load that does not allocate in L1
+__device__ __forceinline__ uint64_t ld_stream(const uint64_t *p)
 {
-#pragma unroll
-    for (int r = 0; r < E; r += 2) {
-        ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p + r);
-        x[r] = v.x;
-        x[r + 1] = v.y;
-    }
+    uint64_t v;
+    asm("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+
+// Key rows in the order the row pass consumes them: inside each row of R2 words
+// the word at E l + r (thread l's r-th word on the contiguous assignment) moves
+// to r T + l.  One CTA per row; applied once when a key is generated.
+template <int K2>
+__global__ void __launch_bounds__(1 << K2) k_key_rows(uint64_t *__restrict__ key)
+{
+    using G = Geo<K2>;
+    __shared__ uint64_t row[G::R];
+    uint64_t *p = key + (size_t)blockIdx.x * G::R;
+    const int j = threadIdx.x;
+    row[j] = p[j];
+    __syncthreads();
+    const int r = j / G::T, l = j % G::T;
+    p[j] = row[G::E * l + r];
 }
 
 // 16-byte asynchronous global -> shared copies (cp.async), grouped per digit
@@ -133,7 +146,7 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
             const int A = R1 + row;
             fwd_strided<K2>(x, tw, A, q, q2);
             to_contig<K2>(x, seg, l);
-            fwd_contig<K2>(x, tw, A, l, q, q2);
+            fwd_contig<K2, true>(x, tw, A, l, q, q2);
 #pragma unroll
             for (int r = 0; r < E; r++) {
                 uint64_t v = x[r];
@@ -141,9 +154,17 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
                 x[r] = v >= q ? v - q : v;
             }
         }
+        // key rows are stored with word E l + r at r T + l (see k_key_rows): adjacent
+        // threads read adjacent words; each key word is read once per CTA, so it
+        // bypasses L1 and leaves room there for the twiddles
         uint64_t k0[E], k1[E];
-        load_contig<E>(k0, key + (((size_t)i * 2 + 0) * (nq + 1) + kl) * N + roff + E * l);
-        load_contig<E>(k1, key + (((size_t)i * 2 + 1) * (nq + 1) + kl) * N + roff + E * l);
+        const uint64_t *kp0 = key + (((size_t)i * 2 + 0) * (nq + 1) + kl) * N + roff + l;
+        const uint64_t *kp1 = key + (((size_t)i * 2 + 1) * (nq + 1) + kl) * N + roff + l;
+#pragma unroll
+        for (int r = 0; r < E; r++) {
+            k0[r] = ld_stream(kp0 + r * G::T);
+            k1[r] = ld_stream(kp1 + r * G::T);
+        }
 #pragma unroll
         for (int r = 0; r < E; r++) {
             a0[r] = addmod(a0[r], mont_mul(x[r], k0[r], m), q);  // keys are stored in Montgomery form
@@ -170,11 +191,8 @@ struct KsPlan {
     static constexpr size_t SM2 = (size_t)RPC * Geo<K2>::SEG * 8 + 2 * (size_t)RPC * R2 * 8;
     static cudaError_t prepare()
     {
-        cudaFuncSetAttribute(k_ks_modup_cols<K1, K2, C>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_ks_inner_rows<K1, K2, RPC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaError_t e = cudaFuncSetAttribute(k_ks_modup_cols<K1, K2, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM1);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_ks_inner_rows<K1, K2, RPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM2);
+        cudaError_t e = helr_fit_carveout((const void *)k_ks_modup_cols<K1, K2, C>, C * T1, SM1);
+        if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_inner_rows<K1, K2, RPC>, RPC * T2, SM2);
         return e;
     }
     static void modup(he_ctx *c, const uint64_t *dcoef, uint64_t *mid, int items, int nl, cudaStream_t s)
@@ -232,6 +250,21 @@ int helr_ks_fused(he_ctx *c, const uint64_t *dntt, const uint64_t *dcoef, uint64
     case 16: return run_fused<8, 8>(c, dntt, dcoef, mid, key, acc, items, nl, s);
     default: return helr_fail(c, HE_EINVAL, "log_n %d unsupported", c->logn);
     }
+}
+
+// reorder the rows of nlimbs key limbs ([nlimbs][N], evaluation form) for k_ks_inner_rows
+int helr_ks_key_layout(he_ctx *c, uint64_t *key, size_t nlimbs)
+{
+    const unsigned rows = (unsigned)(nlimbs * (size_t)c->n >> (c->logn - c->logn / 2));
+    switch (c->logn - c->logn / 2) {
+    case 5: HELR_LAUNCH(k_key_rows<5><<<rows, 1 << 5, 0, c->stream>>>(key)); break;
+    case 6: HELR_LAUNCH(k_key_rows<6><<<rows, 1 << 6, 0, c->stream>>>(key)); break;
+    case 7: HELR_LAUNCH(k_key_rows<7><<<rows, 1 << 7, 0, c->stream>>>(key)); break;
+    case 8: HELR_LAUNCH(k_key_rows<8><<<rows, 1 << 8, 0, c->stream>>>(key)); break;
+    default: return helr_fail(c, HE_EINVAL, "log_n %d unsupported", c->logn);
+    }
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
 }
 
 // items per fused wave: the column-pass output of one wave stays in L2

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(C * Geo<K1>::T) k_ntt_fwd_cols(const uint64_t 
     for (int r = 0; r < G::E; r++) x[r] = in[base + (size_t)(l + G::T * r) * R2];
     fwd_strided<K1>(x, tw, 1, q, q2);
     to_contig<K1>(x, smem + jj * G::SEG, l);
-    fwd_contig<K1>(x, tw, 1, l, q, q2);
+    fwd_contig<K1, false>(x, tw, 1, l, q, q2);
 #pragma unroll
     for (int r = 0; r < G::E; r++) out[base + (size_t)(G::E * l + r) * R2] = x[r];
 }
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(C * Geo<K1>::T) k_ntt_lift_cols(const uint64_t
     for (int r = 0; r < G::E; r++) x[r] = lift_centered(sp[(size_t)(l + G::T * r) * R2], qs, mt);
     fwd_strided<K1>(x, tw, 1, q, q2);
     to_contig<K1>(x, smem + jj * G::SEG, l);
-    fwd_contig<K1>(x, tw, 1, l, q, q2);
+    fwd_contig<K1, false>(x, tw, 1, l, q, q2);
 #pragma unroll
     for (int r = 0; r < G::E; r++) op[(size_t)(G::E * l + r) * R2] = x[r];
 }
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T) k_ntt_fwd_rows(uint64_t *__r
     const int A = R1 + row;
     fwd_strided<K2>(x, tw, A, q, q2);
     to_contig<K2>(x, seg, l);
-    fwd_contig<K2>(x, tw, A, l, q, q2);
+    fwd_contig<K2, true>(x, tw, A, l, q, q2);
 #pragma unroll
     for (int r = 0; r < G::E; r++) {
         uint64_t v = x[r];
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T) k_ntt_inv_rows(const uint64_
     for (int r = 0; r < G::E; r++) x[r] = rin[l + G::T * r];
     to_contig<K2>(x, seg, l);
     const int A = R1 + row;
-    inv_contig<K2>(x, tw, A, l, q, q2);
+    inv_contig<K2, true>(x, tw, A, l, q, q2);
     __syncthreads();
     to_strided<K2>(x, seg, l);
     inv_strided<K2>(x, tw, A, q, q2);
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(C * Geo<K1>::T) k_ntt_inv_cols(uint64_t *__res
     // words of this column arrive as j1 = E l + r (contiguous assignment)
 #pragma unroll
     for (int r = 0; r < G::E; r++) x[r] = data[base + (size_t)(G::E * l + r) * R2];
-    inv_contig<K1>(x, tw, 1, l, q, q2);
+    inv_contig<K1, false>(x, tw, 1, l, q, q2);
     to_strided<K1>(x, smem + jj * G::SEG, l);
     inv_strided<K1>(x, tw, 1, q, q2);
     const uint64_t ni = ninv[2 * pr], nip = ninv[2 * pr + 1];
@@ -188,16 +188,11 @@ struct NttPlan {
 
     static cudaError_t prepare()
     {
-        cudaFuncSetAttribute(k_ntt_fwd_cols<K1, K2, C>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_ntt_inv_cols<K1, K2, C>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_ntt_fwd_rows<K1, K2, RPC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_ntt_inv_rows<K1, K2, RPC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_ntt_lift_cols<K1, K2, C>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaError_t e = cudaFuncSetAttribute(k_ntt_fwd_cols<K1, K2, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM1);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_lift_cols<K1, K2, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM1);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_inv_cols<K1, K2, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM1);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_fwd_rows<K1, K2, RPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM2);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt_inv_rows<K1, K2, RPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM2);
+        cudaError_t e = helr_fit_carveout((const void *)k_ntt_fwd_cols<K1, K2, C>, C * T1, SM1);
+        if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ntt_lift_cols<K1, K2, C>, C * T1, SM1);
+        if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ntt_inv_cols<K1, K2, C>, C * T1, SM1);
+        if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ntt_fwd_rows<K1, K2, RPC>, RPC * T2, SM2);
+        if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ntt_inv_rows<K1, K2, RPC>, RPC * T2, SM2);
         return e;
     }
     static void fwd(const uint64_t *in, uint64_t *out, size_t nlimbs, const DevTables &t, const LimbMap &m, cudaStream_t s)
@@ -267,6 +262,26 @@ int dispatch(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const 
 }
 
 }  // namespace
+
+// Allow `smem` bytes of dynamic shared memory and ask for the smallest
+// shared-memory carveout that still holds as many CTAs per SM as registers and
+// threads allow, so that the rest of the SM's on-chip memory serves as L1 (the
+// transforms re-read their twiddles from L1).
+cudaError_t helr_fit_carveout(const void *f, int threads, size_t smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int blocks = 0, dev = 0, maxsm = 0, reserved = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, f, threads, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e != cudaSuccess || maxsm <= 0) return e;
+    const size_t need = (size_t)blocks * (smem + (size_t)reserved);
+    int pct = (int)((need * 100 + (size_t)maxsm - 1) / (size_t)maxsm);
+    pct = pct < 1 ? 1 : pct > 100 ? 100 : pct;
+    return cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+}
 
 int helr_ntt_fwd(he_ctx *c, uint64_t *data, size_t nlimbs, const LimbMap &m, cudaStream_t s)
 {

@@ -66,46 +66,57 @@ __device__ __forceinline__ void fwd_strided(uint64_t (&x)[Geo<K>::E], const uint
     fwd_strided_st<K, 0>(x, tw, A, q, q2);
 }
 
+// Twiddle j of stage block m * A (j < m) for group g of thread l on the
+// contiguous assignment, j = l gpt + g.  Blocks used by the row pass (ROW) are
+// stored with that index transposed, at m A + g T + l, so that the T threads of a
+// row read one contiguous run per load instead of runs gpt pairs apart (the host
+// table builder applies the same permutation to those blocks).
+template <int K, bool ROW>
+__device__ __forceinline__ int tw_contig(int m, int A, int l, int gpt, int g)
+{
+    return ROW ? m * A + g * Geo<K>::T + l : m * A + l * gpt + g;
+}
+
 // forward stages on the contiguous assignment (j = E l + r): local stages s >= LE;
 // half-span h = R / 2^(s+1) <= E/2, gpt = E / 2h groups per thread.
-template <int K, int S>
+template <int K, bool ROW, int S>
 __device__ __forceinline__ void fwd_contig_st(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, int l, uint64_t q, uint64_t q2)
 {
     constexpr int E = Geo<K>::E, R = Geo<K>::R, m = 1 << S, h = R >> (S + 1), gpt = E / (2 * h);
     ulonglong2 w[gpt];
 #pragma unroll
-    for (int g = 0; g < gpt; g++) w[g] = ldtw(tw, m * A + l * gpt + g);
+    for (int g = 0; g < gpt; g++) w[g] = ldtw(tw, tw_contig<K, ROW>(m, A, l, gpt, g));
 #pragma unroll
     for (int bf = 0; bf < E / 2; bf++) {
         const int g = bf / h, k = bf % h;
         ct_bfly(x[g * 2 * h + k], x[g * 2 * h + k + h], w[g].x, w[g].y, q, q2);
     }
-    if constexpr (S + 1 < K) fwd_contig_st<K, S + 1>(x, tw, A, l, q, q2);
+    if constexpr (S + 1 < K) fwd_contig_st<K, ROW, S + 1>(x, tw, A, l, q, q2);
 }
-template <int K>
+template <int K, bool ROW>
 __device__ __forceinline__ void fwd_contig(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, int l, uint64_t q, uint64_t q2)
 {
-    fwd_contig_st<K, Geo<K>::LE>(x, tw, A, l, q, q2);
+    fwd_contig_st<K, ROW, Geo<K>::LE>(x, tw, A, l, q, q2);
 }
 
-template <int K, int S>
+template <int K, bool ROW, int S>
 __device__ __forceinline__ void inv_contig_st(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, int l, uint64_t q, uint64_t q2)
 {
     constexpr int E = Geo<K>::E, R = Geo<K>::R, m = 1 << S, h = R >> (S + 1), gpt = E / (2 * h);
     ulonglong2 w[gpt];
 #pragma unroll
-    for (int g = 0; g < gpt; g++) w[g] = ldtw(tw, m * A + l * gpt + g);
+    for (int g = 0; g < gpt; g++) w[g] = ldtw(tw, tw_contig<K, ROW>(m, A, l, gpt, g));
 #pragma unroll
     for (int bf = 0; bf < E / 2; bf++) {
         const int g = bf / h, k = bf % h;
         gs_bfly(x[g * 2 * h + k], x[g * 2 * h + k + h], w[g].x, w[g].y, q, q2);
     }
-    if constexpr (S - 1 >= Geo<K>::LE) inv_contig_st<K, S - 1>(x, tw, A, l, q, q2);
+    if constexpr (S - 1 >= Geo<K>::LE) inv_contig_st<K, ROW, S - 1>(x, tw, A, l, q, q2);
 }
-template <int K>
+template <int K, bool ROW>
 __device__ __forceinline__ void inv_contig(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, int l, uint64_t q, uint64_t q2)
 {
-    inv_contig_st<K, K - 1>(x, tw, A, l, q, q2);
+    inv_contig_st<K, ROW, K - 1>(x, tw, A, l, q, q2);
 }
 
 template <int K, int S>
