@@ -150,6 +150,23 @@ __device__ __forceinline__ int map_prime(const LimbMap &lm, int i)
     return v;
 }
 
+// A subset of the positions 0..period-1 of a limb map, ascending.  Transforms
+// are launched once per subset of primes that share a butterfly form: primes
+// below HELR_LZ_QMAX take the unreduced forward butterfly, larger ones Harvey's.
+constexpr uint64_t HELR_LZ_QMAX = 1ull << 58;
+struct PosList {
+    int n;
+    unsigned char pos[HELR_MAXQ + 2];
+};
+__device__ __forceinline__ int pos_at(const PosList &pl, int k)
+{
+    int v = pl.pos[0];
+#pragma unroll
+    for (int j = 1; j < HELR_MAXQ + 2; j++)
+        if (j == k) v = pl.pos[j];
+    return v;
+}
+
 // ------------------------------------------------------------------ error state
 struct HeError {
     int code;
@@ -244,6 +261,24 @@ static inline LimbMap limbmap_single(int prime)
     m.period = 1;
     m.p[0] = (unsigned char)prime;
     return m;
+}
+
+// positions of a limb map whose prime takes the unreduced forward butterfly
+// (lazy) or Harvey's (!lazy)
+static inline PosList poslist_of(const he_ctx *c, const LimbMap &m, bool lazy)
+{
+    PosList pl{};
+    for (int j = 0; j < m.period; j++)
+        if ((c->q[m.p[j]] < HELR_LZ_QMAX) == lazy) pl.pos[pl.n++] = (unsigned char)j;
+    return pl;
+}
+// number of limbs l < nlimbs with l mod period in pl
+static inline size_t poslist_count(const PosList &pl, size_t nlimbs, int period)
+{
+    size_t n = nlimbs / (size_t)period * (size_t)pl.n;
+    const int rem = (int)(nlimbs % (size_t)period);
+    for (int j = 0; j < pl.n; j++) n += pl.pos[j] < rem;
+    return n;
 }
 
 // ------------------------------------------------------------------ kernels (launchers)

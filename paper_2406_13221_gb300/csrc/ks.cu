@@ -87,11 +87,13 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-template <int K1, int K2, int RPC>
+// One launch per butterfly form: `tl` lists the targets t (0..nl, nl standing
+// for P) whose primes take the unreduced forward butterfly (LZ) or Harvey's.
+template <int K1, int K2, int RPC, bool LZ>
 __global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
     k_ks_inner_rows(const uint64_t *__restrict__ mid, const uint64_t *__restrict__ dntt, const uint64_t *__restrict__ key,
                     uint64_t *__restrict__ acc, const uint64_t *__restrict__ twall, const ModQ *__restrict__ mods, int nl,
-                    int nq, int pidx, int items)
+                    int nq, int pidx, int items, PosList tl)
 {
     using G = Geo<K2>;
     constexpr int R1 = 1 << K1, R2 = G::R, N = R1 * R2, NG = R1 / RPC, E = G::E, NT = RPC * G::T;
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
     const int b = bid % items;  // items sharing one key row are adjacent: the key row is read from L2
     bid /= items;
     const int grp = bid % NG;
-    const int t = bid / NG;
+    const int t = pos_at(tl, bid / NG);
     const int pt = t < nl ? t : pidx, kl = t < nl ? t : nq;
     const ModQ m = mods[pt];
     const uint64_t q = m.q, q2 = 2 * q;
@@ -144,15 +146,12 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
 #pragma unroll
             for (int r = 0; r < E; r++) x[r] = rows[l + G::T * r];
             const int A = R1 + row;
-            fwd_strided<K2>(x, tw, A, q, q2);
+            fwd_strided<K2, LZ>(x, tw, A, q, q2);
             to_contig<K2>(x, seg, l);
-            fwd_contig<K2, true>(x, tw, A, l, q, q2);
-#pragma unroll
-            for (int r = 0; r < E; r++) {
-                uint64_t v = x[r];
-                v = v >= q2 ? v - q2 : v;
-                x[r] = v >= q ? v - q : v;
-            }
+            fwd_contig<K2, true, LZ>(x, tw, A, l, q, q2);
+            // words stay unreduced (below 4q; with LZ below 20q, the column pass
+            // leaving them below 4q): the Montgomery product below needs only
+            // x k < q 2^64 and returns [0, q)
         }
         // key rows are stored with word E l + r at r T + l (see k_key_rows): adjacent
         // threads read adjacent words; each key word is read once per CTA, so it
@@ -192,20 +191,42 @@ struct KsPlan {
     static cudaError_t prepare()
     {
         cudaError_t e = helr_fit_carveout((const void *)k_ks_modup_cols<K1, K2, C>, C * T1, SM1);
-        if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_inner_rows<K1, K2, RPC>, RPC * T2, SM2);
+        if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_inner_rows<K1, K2, RPC, false>, RPC * T2, SM2);
+        if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_inner_rows<K1, K2, RPC, true>, RPC * T2, SM2);
         return e;
     }
-    static void modup(he_ctx *c, const uint64_t *dcoef, uint64_t *mid, int items, int nl, cudaStream_t s)
+    // targets 0..nl of a key switch at nl limbs (nl = P) whose prime takes (lz) or
+    // does not take the unreduced forward butterfly
+    static PosList targets(const he_ctx *c, int nl, bool lz)
+    {
+        LimbMap m = limbmap_ct(nl - 1);
+        m.period = nl + 1;
+        m.p[nl] = (unsigned char)c->nq;
+        return poslist_of(c, m, lz);
+    }
+    static int modup(he_ctx *c, const uint64_t *dcoef, uint64_t *mid, int items, int nl, cudaStream_t s)
     {
         unsigned grid = (unsigned)((size_t)items * nl * nl * (R2 / C));
         HELR_LAUNCH(k_ks_modup_cols<K1, K2, C><<<grid, C * T1, SM1, s>>>(dcoef, mid, c->t.tw, c->t.mod, nl, c->nq));
+        return 1;
     }
-    static void inner(he_ctx *c, const uint64_t *mid, const uint64_t *dntt, const uint64_t *key, uint64_t *acc, int items,
-                      int nl, cudaStream_t s)
+    static int inner(he_ctx *c, const uint64_t *mid, const uint64_t *dntt, const uint64_t *key, uint64_t *acc, int items,
+                     int nl, cudaStream_t s)
     {
-        unsigned grid = (unsigned)((size_t)items * (nl + 1) * (R1 / RPC));
-        HELR_LAUNCH(k_ks_inner_rows<K1, K2, RPC><<<grid, RPC * T2, SM2, s>>>(mid, dntt, key, acc, c->t.tw, c->t.mod, nl,
-                                                                              c->nq, c->nq, items));
+        int launches = 0;
+        for (int lz = 0; lz < 2; lz++) {
+            const PosList tl = targets(c, nl, lz);
+            if (!tl.n) continue;
+            const unsigned grid = (unsigned)((size_t)items * tl.n * (R1 / RPC));
+            if (lz)
+                HELR_LAUNCH(k_ks_inner_rows<K1, K2, RPC, true><<<grid, RPC * T2, SM2, s>>>(mid, dntt, key, acc, c->t.tw, c->t.mod,
+                                                                                        nl, c->nq, c->nq, items, tl));
+            else
+                HELR_LAUNCH(k_ks_inner_rows<K1, K2, RPC, false><<<grid, RPC * T2, SM2, s>>>(mid, dntt, key, acc, c->t.tw, c->t.mod,
+                                                                                         nl, c->nq, c->nq, items, tl));
+            launches++;
+        }
+        return launches;
     }
 };
 
@@ -219,14 +240,14 @@ int run_fused(he_ctx *c, const uint64_t *dntt, const uint64_t *dcoef, uint64_t *
         prepared = true;
     }
     prof_start(c, PROF_MODUP, s);
-    KsPlan<K1, K2>::modup(c, dcoef, mid, items, nl, s);
+    const int l1 = KsPlan<K1, K2>::modup(c, dcoef, mid, items, nl, s);
     // column passes of (digit, target != digit); DRAM: digits read once, column-pass limbs written
-    prof_stop(c, PROF_MODUP, s, (double)items * nl * nl, 1, 0, (double)items * nl * (nl + 1));
+    prof_stop(c, PROF_MODUP, s, (double)items * nl * nl, l1, 0, (double)items * nl * (nl + 1));
     prof_start(c, PROF_KS_INNER, s);
-    KsPlan<K1, K2>::inner(c, mid, dntt, key, acc, items, nl, s);
+    const int l2 = KsPlan<K1, K2>::inner(c, mid, dntt, key, acc, items, nl, s);
     // row passes: nl - 1 digits for each ciphertext target, nl for P; products: 2 keys x nl digits x (nl + 1) targets
     // DRAM: every digit's rows read once per target, the two key polynomials once per launch, acc written
-    prof_stop(c, PROF_KS_INNER, s, (double)items * nl * nl, 1, (double)items * 2 * nl * (nl + 1),
+    prof_stop(c, PROF_KS_INNER, s, (double)items * nl * nl, l2, (double)items * 2 * nl * (nl + 1),
               (double)items * nl * (nl + 1) + 2.0 * nl * (nl + 1) + (double)items * 2 * (nl + 1));
     HELR_CUDA(c, cudaGetLastError());
     return HE_OK;

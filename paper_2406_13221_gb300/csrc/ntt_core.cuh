@@ -7,9 +7,15 @@
 namespace nttc {
 
 
+// Forward (Cooley-Tukey) butterfly.  Harvey's form keeps words in [0, 4q).  The
+// unreduced form (LZ) drops the conditional subtraction: a butterfly adds less
+// than 2q to each word, so after S stages on inputs below 4q every word is below
+// (4 + 2S) q, which stays under 2^64 for the S <= 16 stages of a transform when
+// q < 2^58 (HELR_LZ_QMAX).  The Shoup product accepts any 64-bit operand.
+template <bool LZ = false>
 __device__ __forceinline__ void ct_bfly(uint64_t &x, uint64_t &y, uint64_t w, uint64_t wp, uint64_t q, uint64_t q2)
 {
-    uint64_t a = x >= q2 ? x - q2 : x;
+    uint64_t a = LZ ? x : (x >= q2 ? x - q2 : x);
     uint64_t t = shoup_lazy(y, w, wp, q);
     x = a + t;
     y = a - t + q2;
@@ -46,7 +52,7 @@ struct Geo {
 //
 // forward stages on the strided assignment (j = l + T r): local stages s < LE;
 // at local stage m = 2^s the E words form m groups of 2 hr (hr = E / 2m).
-template <int K, int S>
+template <int K, bool LZ, int S>
 __device__ __forceinline__ void fwd_strided_st(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, uint64_t q, uint64_t q2)
 {
     constexpr int E = Geo<K>::E, LE = Geo<K>::LE, m = 1 << S, hr = E >> (S + 1);
@@ -56,14 +62,14 @@ __device__ __forceinline__ void fwd_strided_st(uint64_t (&x)[Geo<K>::E], const u
 #pragma unroll
     for (int bf = 0; bf < E / 2; bf++) {
         const int g = bf / hr, k = bf % hr;
-        ct_bfly(x[g * 2 * hr + k], x[g * 2 * hr + k + hr], w[g].x, w[g].y, q, q2);
+        ct_bfly<LZ>(x[g * 2 * hr + k], x[g * 2 * hr + k + hr], w[g].x, w[g].y, q, q2);
     }
-    if constexpr (S + 1 < LE) fwd_strided_st<K, S + 1>(x, tw, A, q, q2);
+    if constexpr (S + 1 < LE) fwd_strided_st<K, LZ, S + 1>(x, tw, A, q, q2);
 }
-template <int K>
+template <int K, bool LZ = false>
 __device__ __forceinline__ void fwd_strided(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, uint64_t q, uint64_t q2)
 {
-    fwd_strided_st<K, 0>(x, tw, A, q, q2);
+    fwd_strided_st<K, LZ, 0>(x, tw, A, q, q2);
 }
 
 // Twiddle j of stage block m * A (j < m) for group g of thread l on the
@@ -79,7 +85,7 @@ __device__ __forceinline__ int tw_contig(int m, int A, int l, int gpt, int g)
 
 // forward stages on the contiguous assignment (j = E l + r): local stages s >= LE;
 // half-span h = R / 2^(s+1) <= E/2, gpt = E / 2h groups per thread.
-template <int K, bool ROW, int S>
+template <int K, bool ROW, bool LZ, int S>
 __device__ __forceinline__ void fwd_contig_st(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, int l, uint64_t q, uint64_t q2)
 {
     constexpr int E = Geo<K>::E, R = Geo<K>::R, m = 1 << S, h = R >> (S + 1), gpt = E / (2 * h);
@@ -89,14 +95,14 @@ __device__ __forceinline__ void fwd_contig_st(uint64_t (&x)[Geo<K>::E], const ui
 #pragma unroll
     for (int bf = 0; bf < E / 2; bf++) {
         const int g = bf / h, k = bf % h;
-        ct_bfly(x[g * 2 * h + k], x[g * 2 * h + k + h], w[g].x, w[g].y, q, q2);
+        ct_bfly<LZ>(x[g * 2 * h + k], x[g * 2 * h + k + h], w[g].x, w[g].y, q, q2);
     }
-    if constexpr (S + 1 < K) fwd_contig_st<K, ROW, S + 1>(x, tw, A, l, q, q2);
+    if constexpr (S + 1 < K) fwd_contig_st<K, ROW, LZ, S + 1>(x, tw, A, l, q, q2);
 }
-template <int K, bool ROW>
+template <int K, bool ROW, bool LZ = false>
 __device__ __forceinline__ void fwd_contig(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, int l, uint64_t q, uint64_t q2)
 {
-    fwd_contig_st<K, ROW, Geo<K>::LE>(x, tw, A, l, q, q2);
+    fwd_contig_st<K, ROW, LZ, Geo<K>::LE>(x, tw, A, l, q, q2);
 }
 
 template <int K, bool ROW, int S>
