@@ -87,10 +87,91 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// ---- tensor memory (TMEM) as accumulator storage between digits
+// Each of the CTA's 4 warps owns a quarter of the 128 TMEM lanes (warp w: lanes
+// 32 w .. 32 w + 31), one lane per thread; the thread's 64-bit accumulators take
+// two 32-bit columns each.  Allocation is per CTA, by warp 0, and is returned
+// before the CTA exits.
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(slot);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(a), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;"); }
+// 16 consecutive 32-bit columns of this thread's lane <-> registers (four
+// 128-bit accumulators).  No memory clobbers: TMEM traffic does not alias global
+// or shared memory, and the key loads must stay free to move ahead of it.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                 "%14, %15, %16};" ::"r"(taddr),
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+                 "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]));
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&w)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+                 "%15}, [%16];"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7]), "=r"(w[8]),
+                   "=r"(w[9]), "=r"(w[10]), "=r"(w[11]), "=r"(w[12]), "=r"(w[13]), "=r"(w[14]), "=r"(w[15])
+                 : "r"(taddr));
+}
+// wait for the loads into a and b; the registers are operands so that no use of
+// them can be scheduled before the wait
+__device__ __forceinline__ void tmem_wait_ld32(uint32_t (&a)[16], uint32_t (&b)[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
+                   "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]),
+                   "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]),
+                   "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]), "+r"(b[14]), "+r"(b[15]));
+}
+
+// 128-bit accumulator held as four 32-bit words (least significant first)
+__device__ __forceinline__ void mac128(uint32_t *acc, uint64_t x, uint64_t k)
+{
+    const uint64_t lo = x * k, hi = __umul64hi(x, k);
+    asm("add.cc.u32 %0, %0, %4;\n\t"
+        "addc.cc.u32 %1, %1, %5;\n\t"
+        "addc.cc.u32 %2, %2, %6;\n\t"
+        "addc.u32 %3, %3, %7;"
+        : "+r"(acc[0]), "+r"(acc[1]), "+r"(acc[2]), "+r"(acc[3])
+        : "r"((uint32_t)lo), "r"((uint32_t)(lo >> 32)), "r"((uint32_t)hi), "r"((uint32_t)(hi >> 32)));
+}
+__device__ __forceinline__ void set128(uint32_t *acc, uint64_t x, uint64_t k)
+{
+    const uint64_t lo = x * k, hi = __umul64hi(x, k);
+    acc[0] = (uint32_t)lo;
+    acc[1] = (uint32_t)(lo >> 32);
+    acc[2] = (uint32_t)hi;
+    acc[3] = (uint32_t)(hi >> 32);
+}
+// Montgomery reduction of T = hi 2^64 + lo: T 2^-64 mod q, for hi < q.
+__device__ __forceinline__ uint64_t redc128(uint64_t hi, uint64_t lo, const ModQ &m)
+{
+    const uint64_t mh = __umul64hi(lo * m.qinv, m.q);
+    return hi >= mh ? hi - mh : hi - mh + m.q;
+}
+
 // One launch per butterfly form: `tl` lists the targets t (0..nl, nl standing
 // for P) whose primes take the unreduced forward butterfly (LZ) or Harvey's.
+//
+// Inner product without per-digit reduction: with keys k' = k 2^64 mod q, the
+// CTA accumulates T = sum_i x_i k'_i exactly in 128 bits (x_i below 20q for LZ,
+// where q < 2^58, and below 4q otherwise, where q < 2^61: T < 9 * 20 q^2 < 2^125
+// or 9 * 4 q^2 < 2^128) and reduces once: T 2^-64 mod q = sum_i x_i k_i mod q
+// (one Montgomery reduction, after reducing the high word below q).  The 128-bit accumulators of both key polynomials live
+// in TMEM between digits (128 columns per thread), so the registers hold only
+// the digit being transformed.
 template <int K1, int K2, int RPC, bool LZ>
-__global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
+__global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
     k_ks_inner_rows(const uint64_t *__restrict__ mid, const uint64_t *__restrict__ dntt, const uint64_t *__restrict__ key,
                     uint64_t *__restrict__ acc, const uint64_t *__restrict__ twall, const ModQ *__restrict__ mods, int nl,
                     int nq, int pidx, int items, PosList tl)
@@ -98,7 +179,11 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
     using G = Geo<K2>;
     constexpr int R1 = 1 << K1, R2 = G::R, N = R1 * R2, NG = R1 / RPC, E = G::E, NT = RPC * G::T;
     constexpr int TILE = RPC * R2;  // words of one digit's rows handled by this CTA
+    constexpr int CH = 4;           // accumulators of one key polynomial per TMEM transfer (16 columns)
+    constexpr uint32_t TCOLS = 8 * E;  // a0[r]: columns 4r..4r+3; a1[r]: 4E + 4r..4E + 4r + 3
+    static_assert(NT == 128 && E % CH == 0 && TCOLS >= 32 && TCOLS <= 128 && (TCOLS & (TCOLS - 1)) == 0, "TMEM layout");
     extern __shared__ uint64_t smem[];
+    __shared__ uint32_t tmem_slot;
     uint64_t *buf = smem;                    // [2][TILE]: the rows of two digits (double buffer)
     uint64_t *segs = smem + 2 * TILE;        // exchange segments
     int bid = blockIdx.x;
@@ -110,7 +195,7 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
     const ModQ m = mods[pt];
     const uint64_t q = m.q, q2 = 2 * q;
     const uint64_t *tw = twall + (size_t)pt * N * 2;
-    const int l = threadIdx.x % G::T, rl = threadIdx.x / G::T;
+    const int l = threadIdx.x % G::T, rl = threadIdx.x / G::T, warp = threadIdx.x / 32;
     const int row = grp * RPC + rl;
     const size_t roff = (size_t)row * R2, toff = (size_t)grp * RPC * R2;
     uint64_t *seg = segs + rl * G::SEG;
@@ -126,11 +211,15 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
             cp_async16(dst + w, src + w);
         }
     };
-    uint64_t a0[E], a1[E];
-#pragma unroll
-    for (int r = 0; r < E; r++) a0[r] = a1[r] = 0;
+    if (warp == 0) tmem_alloc(&tmem_slot, TCOLS);
     prefetch(0, buf);
     cp_async_commit();
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const uint32_t tbase = tmem_slot + ((uint32_t)(32 * warp) << 16);
+    uint64_t *o0 = acc + (((size_t)b * 2 + 0) * (nl + 1) + t) * N + roff + E * l;
+    uint64_t *o1 = acc + (((size_t)b * 2 + 1) * (nl + 1) + t) * N + roff + E * l;
     for (int i = 0; i < nl; i++) {
         uint64_t *cur = buf + (i & 1) * TILE;
         if (i + 1 < nl) prefetch(i + 1, buf + ((i + 1) & 1) * TILE);
@@ -149,34 +238,66 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
             fwd_strided<K2, LZ>(x, tw, A, q, q2);
             to_contig<K2>(x, seg, l);
             fwd_contig<K2, true, LZ>(x, tw, A, l, q, q2);
-            // words stay unreduced (below 4q; with LZ below 20q, the column pass
-            // leaving them below 4q): the Montgomery product below needs only
-            // x k < q 2^64 and returns [0, q)
+            // words stay unreduced: below 4q, or below 20q with LZ (the column
+            // pass leaves them below 4q)
         }
         // key rows are stored with word E l + r at r T + l (see k_key_rows): adjacent
         // threads read adjacent words; each key word is read once per CTA, so it
         // bypasses L1 and leaves room there for the twiddles
-        uint64_t k0[E], k1[E];
         const uint64_t *kp0 = key + (((size_t)i * 2 + 0) * (nq + 1) + kl) * N + roff + l;
         const uint64_t *kp1 = key + (((size_t)i * 2 + 1) * (nq + 1) + kl) * N + roff + l;
+        if (i > 0) tmem_wait_st();  // the previous digit's accumulators are in place
 #pragma unroll
-        for (int r = 0; r < E; r++) {
-            k0[r] = ld_stream(kp0 + r * G::T);
-            k1[r] = ld_stream(kp1 + r * G::T);
-        }
+        for (int c = 0; c < E / CH; c++) {
+            uint32_t s0[4 * CH], s1[4 * CH];
+            const uint32_t c0 = tbase + 4 * CH * c, c1 = tbase + 4 * E + 4 * CH * c;
+            if (i > 0) {
+                tmem_ld16(c0, s0);
+                tmem_ld16(c1, s1);
+                tmem_wait_ld32(s0, s1);
 #pragma unroll
-        for (int r = 0; r < E; r++) {
-            a0[r] = addmod(a0[r], mont_mul(x[r], k0[r], m), q);  // keys are stored in Montgomery form
-            a1[r] = addmod(a1[r], mont_mul(x[r], k1[r], m), q);
+                for (int k = 0; k < CH; k++) {
+                    const int r = c * CH + k;
+                    mac128(s0 + 4 * k, x[r], ld_stream(kp0 + r * G::T));
+                    mac128(s1 + 4 * k, x[r], ld_stream(kp1 + r * G::T));
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < CH; k++) {
+                    const int r = c * CH + k;
+                    set128(s0 + 4 * k, x[r], ld_stream(kp0 + r * G::T));
+                    set128(s1 + 4 * k, x[r], ld_stream(kp1 + r * G::T));
+                }
+            }
+            if (i + 1 < nl) {
+                tmem_st16(c0, s0);
+                tmem_st16(c1, s1);
+            } else {
+                uint64_t r0[CH], r1[CH];
+#pragma unroll
+                for (int k = 0; k < CH; k++) {
+                    uint64_t h0 = ((uint64_t)s0[4 * k + 3] << 32) | s0[4 * k + 2];
+                    uint64_t h1 = ((uint64_t)s1[4 * k + 3] << 32) | s1[4 * k + 2];
+                    // the high word is below q unless q > 2^64 / (20 nl) (LZ) or 2^64 / (4 nl)
+                    h0 = h0 >= q ? reduce64(h0, m) : h0;
+                    h1 = h1 >= q ? reduce64(h1, m) : h1;
+                    r0[k] = redc128(h0, ((uint64_t)s0[4 * k + 1] << 32) | s0[4 * k], m);
+                    r1[k] = redc128(h1, ((uint64_t)s1[4 * k + 1] << 32) | s1[4 * k], m);
+                }
+#pragma unroll
+                for (int k = 0; k < CH; k += 2) {
+                    *reinterpret_cast<ulonglong2 *>(o0 + c * CH + k) = make_ulonglong2(r0[k], r0[k + 1]);
+                    *reinterpret_cast<ulonglong2 *>(o1 + c * CH + k) = make_ulonglong2(r1[k], r1[k + 1]);
+                }
+            }
         }
         __syncthreads();  // buffer `cur` and the exchange segments are reused
     }
-    uint64_t *o0 = acc + (((size_t)b * 2 + 0) * (nl + 1) + t) * N + roff + E * l;
-    uint64_t *o1 = acc + (((size_t)b * 2 + 1) * (nl + 1) + t) * N + roff + E * l;
-#pragma unroll
-    for (int r = 0; r < E; r += 2) {
-        *reinterpret_cast<ulonglong2 *>(o0 + r) = make_ulonglong2(a0[r], a0[r + 1]);
-        *reinterpret_cast<ulonglong2 *>(o1 + r) = make_ulonglong2(a1[r], a1[r + 1]);
+    tmem_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tmem_fence_after();
+        tmem_dealloc(tmem_slot, TCOLS);
     }
 }
 

@@ -17,6 +17,8 @@
 // regroups the words as j = E l + r, and the remaining log2(T) stages run in
 // registers again.  Butterflies are Harvey's lazy forms (values in [0, 4q) in the
 // forward and [0, 2q) in the inverse) with Shoup twiddle products.
+#include <algorithm>
+
 #include "helr_internal.cuh"
 
 #include "ntt_core.cuh"
@@ -266,19 +268,29 @@ int dispatch(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const 
 // Allow `smem` bytes of dynamic shared memory and ask for the smallest
 // shared-memory carveout that still holds as many CTAs per SM as registers and
 // threads allow, so that the rest of the SM's on-chip memory serves as L1 (the
-// transforms re-read their twiddles from L1).
+// transforms re-read their twiddles from L1).  The CTA count is the larger of
+// the runtime's occupancy figure and one computed from the kernel's registers,
+// threads and shared memory (the runtime reports 0 for some kernels).
 cudaError_t helr_fit_carveout(const void *f, int threads, size_t smem)
 {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    int blocks = 0, dev = 0, maxsm = 0, reserved = 0;
+    int blocks = 0, dev = 0, maxsm = 0, reserved = 0, regs_sm = 0, thr_sm = 0;
+    cudaFuncAttributes fa;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, f, threads, smem);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, f);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    if (e != cudaSuccess || maxsm <= 0) return e;
-    const size_t need = (size_t)blocks * (smem + (size_t)reserved);
-    int pct = (int)((need * 100 + (size_t)maxsm - 1) / (size_t)maxsm);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    if (e != cudaSuccess || maxsm <= 0 || threads <= 0) return e;
+    const size_t per_cta = smem + fa.sharedSizeBytes + (size_t)reserved;
+    const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;  // registers are granted per warp in units of 256
+    int own = std::min(regs_sm / std::max(1, warp_regs * ((threads + 31) / 32)), thr_sm / threads);
+    own = std::min(own, (int)((size_t)maxsm / per_cta));
+    blocks = std::max(blocks, own);
+    int pct = (int)(((size_t)blocks * per_cta * 100 + (size_t)maxsm - 1) / (size_t)maxsm);
     pct = pct < 1 ? 1 : pct > 100 ? 100 : pct;
     return cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
 }
