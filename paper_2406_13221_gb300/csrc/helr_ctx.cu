@@ -640,13 +640,13 @@ int helr_keyswitch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, 
         ws = &local;
     }
     cudaStream_t s = c->stream;
-    // 1. coefficient form of every limb
-    HELR_TRY(helr_ntt_inv_oop(c, d_in, ws->dcoef, in_items, limbmap_ct(level), s));
+    // 1. row pass of the inverse transform of every limb (the column pass runs inside ModUp)
+    HELR_TRY(helr_ntt_inv_rows(c, d_in, ws->drow, in_items, limbmap_ct(level), s));
     // 2-3. ModUp fused with the transforms and the inner product, in waves
     const int wave = std::min(ws->wave, batch);
     for (int b0 = 0; b0 < batch; b0 += wave) {
         int cnt = std::min(wave, batch - b0);
-        HELR_TRY(helr_ks_fused(c, d_in + (size_t)b0 * nl * N, ws->dcoef + (size_t)b0 * nl * N, ws->ext, key,
+        HELR_TRY(helr_ks_fused(c, d_in + (size_t)b0 * nl * N, ws->drow + (size_t)b0 * nl * N, ws->ext, key,
                                ws->acc + (size_t)b0 * 2 * nt * N, cnt, nl, s));
     }
     // 4. ModDown: subtract the centred P-part and divide by P
@@ -674,8 +674,8 @@ int helr_ks_scratch_alloc(he_ctx *c, int batch, int level, KsScratch *ws)
     uint64_t *base = nullptr;
     HELR_TRY(helr_alloc(c, (void **)&base, words * 8));
     ws->base = base;
-    ws->dcoef = base;
-    ws->acc = ws->dcoef + (size_t)batch * nl * N;
+    ws->drow = base;
+    ws->acc = ws->drow + (size_t)batch * nl * N;
     ws->pl = ws->acc + (size_t)batch * 2 * nt * N;
     ws->lift = ws->pl + (size_t)batch * 2 * N;
     ws->ext = ws->lift + (size_t)batch * 2 * nl * N;

@@ -290,6 +290,7 @@ int helr_ntt_fwd_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs
 int helr_ntt_inv_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s);
 // forward transform of centred lifts: source limb b (coefficient form, at src + b * src_stride,
 // modulo prime src_prime) is lifted to every prime of dst and transformed; out is [nsrc][dst.period][N]
+int helr_ntt_inv_rows(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s);
 int helr_ntt_fwd_lifted(he_ctx *c, const uint64_t *src, size_t src_stride, int src_prime, size_t nsrc, uint64_t *out,
                         const LimbMap &dst, cudaStream_t s);
 
@@ -325,10 +326,10 @@ void k_automorph_items(he_ctx *c, uint64_t *out, size_t out_item, const uint64_t
                        uint64_t gal, cudaStream_t s);
 
 struct KsScratch {
-    uint64_t *base, *dcoef, *ext, *acc, *pl, *lift;
+    uint64_t *base, *drow, *ext, *acc, *pl, *lift;  // drow: input after the inverse row pass
     int batch, level, wave;
 };
-int helr_ks_fused(he_ctx *c, const uint64_t *dntt, const uint64_t *dcoef, uint64_t *mid, const uint64_t *key, uint64_t *acc,
+int helr_ks_fused(he_ctx *c, const uint64_t *dntt, const uint64_t *drow, uint64_t *mid, const uint64_t *key, uint64_t *acc,
                   int items, int nl, cudaStream_t s);
 int helr_ks_wave(const he_ctx *c, int nl);
 int helr_ks_scratch_alloc(he_ctx *c, int batch, int level, KsScratch *ws);

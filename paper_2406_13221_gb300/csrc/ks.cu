@@ -21,36 +21,59 @@
 namespace {
 using namespace nttc;
 
+// ModUp with the last half of the inverse transform: a CTA takes C adjacent
+// columns of digit i (row pass of the inverse transform already applied), runs
+// the inverse column pass and the factor N^-1, keeps the coefficients in shared
+// memory, then for every target t != i lifts the centred coefficients into q_t
+// and runs the forward column pass.  Each digit column is read once.
 template <int K1, int K2, int C>
-__global__ void __launch_bounds__(C * Geo<K1>::T, 4)
-    k_ks_modup_cols(const uint64_t *__restrict__ dcoef, uint64_t *__restrict__ mid, const uint64_t *__restrict__ twall,
-                    const ModQ *__restrict__ mods, int nl, int pidx)
+__global__ void __launch_bounds__(C * Geo<K1>::T, 3)
+    k_ks_modup_cols(const uint64_t *__restrict__ drow, uint64_t *__restrict__ mid, const uint64_t *__restrict__ twall,
+                    const uint64_t *__restrict__ itwall, const ModQ *__restrict__ mods, const uint64_t *__restrict__ ninv,
+                    int nl, int pidx)
 {
     using G = Geo<K1>;
-    constexpr int R2 = 1 << K2, N = G::R * R2, NG = R2 / C;
+    constexpr int R2 = 1 << K2, N = G::R * R2, NG = R2 / C, E = G::E, T = G::T;
     extern __shared__ uint64_t smem[];
     int bid = blockIdx.x;
-    const int tt = bid % nl;  // targets of one digit column are adjacent: the column is read from L2
-    bid /= nl;
     const int grp = bid % NG;
     bid /= NG;
     const int i = bid % nl, b = bid / nl;
-    const int t = tt < i ? tt : tt + 1;          // target 0..nl, never i
-    const int pt = t < nl ? t : pidx;
-    const ModQ mt = mods[pt];
-    const uint64_t qi = mods[i].q, q = mt.q, q2 = 2 * q;
-    const uint64_t *tw = twall + (size_t)pt * N * 2;
     const int jj = threadIdx.x % C, l = threadIdx.x / C;
-    const uint64_t *src = dcoef + ((size_t)b * nl + i) * N + grp * C + jj;
-    uint64_t *dst = mid + (((size_t)b * nl + i) * (nl + 1) + t) * N + grp * C + jj;
-    uint64_t x[G::E];
+    uint64_t *seg = smem + jj * G::SEG;
+    uint64_t *coef = smem + C * G::SEG;  // [R1][C]: word (j1, jj); each thread reads back only its own words
+    const uint64_t qi = mods[i].q;
+    const size_t col = ((size_t)b * nl + i) * N + grp * C + jj;
+    {
+        const uint64_t *itw = itwall + (size_t)i * N * 2;
+        uint64_t c[E];
+        // words of this column arrive as j1 = E l + r (contiguous assignment)
 #pragma unroll
-    for (int r = 0; r < G::E; r++) x[r] = lift_centered(src[(size_t)(l + G::T * r) * R2], qi, mt);
-    fwd_strided<K1>(x, tw, 1, q, q2);
-    to_contig<K1>(x, smem + jj * G::SEG, l);
-    fwd_contig<K1, false>(x, tw, 1, l, q, q2);
+        for (int r = 0; r < E; r++) c[r] = drow[col + (size_t)(E * l + r) * R2];
+        inv_contig<K1, false>(c, itw, 1, l, qi, 2 * qi);
+        to_strided<K1>(c, seg, l);
+        inv_strided<K1>(c, itw, 1, qi, 2 * qi);
+        const uint64_t ni = ninv[2 * i], nip = ninv[2 * i + 1];
 #pragma unroll
-    for (int r = 0; r < G::E; r++) dst[(size_t)(G::E * l + r) * R2] = x[r];
+        for (int r = 0; r < E; r++) coef[(l + T * r) * C + jj] = shoup(c[r], ni, nip, qi);  // in [0, q_i)
+    }
+    uint64_t *dst = mid + ((size_t)b * nl + i) * (nl + 1) * N + grp * C + jj;
+    for (int tt = 0; tt < nl; tt++) {
+        const int t = tt < i ? tt : tt + 1;  // target 0..nl, never i (that limb is the evaluation-form input)
+        const int pt = t < nl ? t : pidx;
+        const ModQ mt = mods[pt];
+        const uint64_t q = mt.q, q2 = 2 * q;
+        const uint64_t *tw = twall + (size_t)pt * N * 2;
+        uint64_t x[E];
+#pragma unroll
+        for (int r = 0; r < E; r++) x[r] = lift_centered(coef[(l + T * r) * C + jj], qi, mt);
+        fwd_strided<K1>(x, tw, 1, q, q2);
+        __syncthreads();  // the previous exchange has been read
+        to_contig<K1>(x, seg, l);
+        fwd_contig<K1, false>(x, tw, 1, l, q, q2);
+#pragma unroll
+        for (int r = 0; r < E; r++) dst[(size_t)t * N + (size_t)(E * l + r) * R2] = x[r];
+    }
 }
 
 // read-only load that does not allocate in L1
@@ -307,7 +330,7 @@ struct KsPlan {
     static constexpr int R1 = 1 << K1, R2 = 1 << K2;
     static constexpr int C = (256 / T1) < R2 ? (256 / T1) : R2;
     static constexpr int RPC = (128 / T2) < R1 ? (128 / T2) : R1;
-    static constexpr size_t SM1 = (size_t)C * Geo<K1>::SEG * 8;
+    static constexpr size_t SM1 = (size_t)C * Geo<K1>::SEG * 8 + (size_t)C * R1 * 8;
     static constexpr size_t SM2 = (size_t)RPC * Geo<K2>::SEG * 8 + 2 * (size_t)RPC * R2 * 8;
     static cudaError_t prepare()
     {
@@ -325,10 +348,11 @@ struct KsPlan {
         m.p[nl] = (unsigned char)c->nq;
         return poslist_of(c, m, lz);
     }
-    static int modup(he_ctx *c, const uint64_t *dcoef, uint64_t *mid, int items, int nl, cudaStream_t s)
+    static int modup(he_ctx *c, const uint64_t *drow, uint64_t *mid, int items, int nl, cudaStream_t s)
     {
-        unsigned grid = (unsigned)((size_t)items * nl * nl * (R2 / C));
-        HELR_LAUNCH(k_ks_modup_cols<K1, K2, C><<<grid, C * T1, SM1, s>>>(dcoef, mid, c->t.tw, c->t.mod, nl, c->nq));
+        unsigned grid = (unsigned)((size_t)items * nl * (R2 / C));
+        HELR_LAUNCH(k_ks_modup_cols<K1, K2, C><<<grid, C * T1, SM1, s>>>(drow, mid, c->t.tw, c->t.itw, c->t.mod, c->t.ninv,
+                                                                          nl, c->nq));
         return 1;
     }
     static int inner(he_ctx *c, const uint64_t *mid, const uint64_t *dntt, const uint64_t *key, uint64_t *acc, int items,
@@ -352,7 +376,7 @@ struct KsPlan {
 };
 
 template <int K1, int K2>
-int run_fused(he_ctx *c, const uint64_t *dntt, const uint64_t *dcoef, uint64_t *mid, const uint64_t *key, uint64_t *acc,
+int run_fused(he_ctx *c, const uint64_t *dntt, const uint64_t *drow, uint64_t *mid, const uint64_t *key, uint64_t *acc,
               int items, int nl, cudaStream_t s)
 {
     static bool prepared = false;
@@ -361,9 +385,10 @@ int run_fused(he_ctx *c, const uint64_t *dntt, const uint64_t *dcoef, uint64_t *
         prepared = true;
     }
     prof_start(c, PROF_MODUP, s);
-    const int l1 = KsPlan<K1, K2>::modup(c, dcoef, mid, items, nl, s);
-    // column passes of (digit, target != digit); DRAM: digits read once, column-pass limbs written
-    prof_stop(c, PROF_MODUP, s, (double)items * nl * nl, l1, 0, (double)items * nl * (nl + 1));
+    const int l1 = KsPlan<K1, K2>::modup(c, drow, mid, items, nl, s);
+    // forward column passes of (digit, target != digit), inverse column passes of the digits;
+    // DRAM: digits read once, column-pass limbs written
+    prof_stop(c, PROF_MODUP, s, (double)items * nl * nl, l1, (double)items * nl, (double)items * nl * (nl + 1));
     prof_start(c, PROF_KS_INNER, s);
     const int l2 = KsPlan<K1, K2>::inner(c, mid, dntt, key, acc, items, nl, s);
     // row passes: nl - 1 digits for each ciphertext target, nl for P; products: 2 keys x nl digits x (nl + 1) targets
@@ -376,20 +401,21 @@ int run_fused(he_ctx *c, const uint64_t *dntt, const uint64_t *dcoef, uint64_t *
 
 }  // namespace
 
-// ModUp + transforms + inner product for `items` polynomials: dntt / dcoef are
-// [items][nl][N] (evaluation and coefficient form of the same input); mid is
-// scratch of [items][nl][nl+1][N]; acc receives [items][2][nl+1][N].
-int helr_ks_fused(he_ctx *c, const uint64_t *dntt, const uint64_t *dcoef, uint64_t *mid, const uint64_t *key, uint64_t *acc,
+// ModUp + transforms + inner product for `items` polynomials: dntt is the
+// input [items][nl][N] in evaluation form, drow the same after the row pass of
+// the inverse transform; mid is scratch of [items][nl][nl+1][N]; acc receives
+// [items][2][nl+1][N].
+int helr_ks_fused(he_ctx *c, const uint64_t *dntt, const uint64_t *drow, uint64_t *mid, const uint64_t *key, uint64_t *acc,
                   int items, int nl, cudaStream_t s)
 {
     switch (c->logn) {
-    case 10: return run_fused<5, 5>(c, dntt, dcoef, mid, key, acc, items, nl, s);
-    case 11: return run_fused<5, 6>(c, dntt, dcoef, mid, key, acc, items, nl, s);
-    case 12: return run_fused<6, 6>(c, dntt, dcoef, mid, key, acc, items, nl, s);
-    case 13: return run_fused<6, 7>(c, dntt, dcoef, mid, key, acc, items, nl, s);
-    case 14: return run_fused<7, 7>(c, dntt, dcoef, mid, key, acc, items, nl, s);
-    case 15: return run_fused<7, 8>(c, dntt, dcoef, mid, key, acc, items, nl, s);
-    case 16: return run_fused<8, 8>(c, dntt, dcoef, mid, key, acc, items, nl, s);
+    case 10: return run_fused<5, 5>(c, dntt, drow, mid, key, acc, items, nl, s);
+    case 11: return run_fused<5, 6>(c, dntt, drow, mid, key, acc, items, nl, s);
+    case 12: return run_fused<6, 6>(c, dntt, drow, mid, key, acc, items, nl, s);
+    case 13: return run_fused<6, 7>(c, dntt, drow, mid, key, acc, items, nl, s);
+    case 14: return run_fused<7, 7>(c, dntt, drow, mid, key, acc, items, nl, s);
+    case 15: return run_fused<7, 8>(c, dntt, drow, mid, key, acc, items, nl, s);
+    case 16: return run_fused<8, 8>(c, dntt, drow, mid, key, acc, items, nl, s);
     default: return helr_fail(c, HE_EINVAL, "log_n %d unsupported", c->logn);
     }
 }

@@ -210,6 +210,10 @@ struct NttPlan {
                                                                                           src_prime, t.tw, t.mod, dst));
         HELR_LAUNCH(k_ntt_fwd_rows<K1, K2, RPC><<<(unsigned)(nl * (R1 / RPC)), RPC * T2, SM2, s>>>(out, t.tw, t.mod, dst));
     }
+    static void inv_rows(const uint64_t *in, uint64_t *out, size_t nlimbs, const DevTables &t, const LimbMap &m, cudaStream_t s)
+    {
+        HELR_LAUNCH(k_ntt_inv_rows<K1, K2, RPC><<<(unsigned)(nlimbs * (R1 / RPC)), RPC * T2, SM2, s>>>(in, out, t.itw, t.mod, m));
+    }
     static void inv(const uint64_t *in, uint64_t *out, size_t nlimbs, const DevTables &t, const LimbMap &m, cudaStream_t s)
     {
         HELR_LAUNCH(k_ntt_inv_rows<K1, K2, RPC><<<(unsigned)(nlimbs * (R1 / RPC)), RPC * T2, SM2, s>>>(in, out, t.itw, t.mod, m));
@@ -221,6 +225,22 @@ struct Lifted {
     size_t src_stride;
     int src_prime;
 };
+
+template <int K1, int K2>
+int run_inv_rows(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s)
+{
+    static bool prepared = false;
+    if (!prepared) {
+        HELR_CUDA(c, (NttPlan<K1, K2>::prepare()));
+        prepared = true;
+    }
+    if (nlimbs == 0) return HE_OK;
+    prof_start(c, PROF_NTT_INV, s);
+    NttPlan<K1, K2>::inv_rows(in, out, nlimbs, c->t, m, s);
+    prof_stop(c, PROF_NTT_INV, s, 0.5 * (double)nlimbs, 1);  // half of each transform
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
 
 template <int K1, int K2>
 int run(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s, bool inverse,
@@ -310,6 +330,22 @@ int helr_ntt_fwd_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs
 int helr_ntt_inv_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s)
 {
     return dispatch(c, in, out, nlimbs, m, s, true);
+}
+// the row pass of the inverse transform only: the column pass (K1 stages, the
+// factor N^-1) is left to a consumer that reads whole columns
+int helr_ntt_inv_rows(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s)
+{
+    if (nlimbs > (size_t)1 << 24) return helr_fail(c, HE_EINVAL, "too many limbs in one transform batch");
+    switch (c->logn) {
+    case 10: return run_inv_rows<5, 5>(c, in, out, nlimbs, m, s);
+    case 11: return run_inv_rows<5, 6>(c, in, out, nlimbs, m, s);
+    case 12: return run_inv_rows<6, 6>(c, in, out, nlimbs, m, s);
+    case 13: return run_inv_rows<6, 7>(c, in, out, nlimbs, m, s);
+    case 14: return run_inv_rows<7, 7>(c, in, out, nlimbs, m, s);
+    case 15: return run_inv_rows<7, 8>(c, in, out, nlimbs, m, s);
+    case 16: return run_inv_rows<8, 8>(c, in, out, nlimbs, m, s);
+    default: return helr_fail(c, HE_EINVAL, "log_n %d unsupported", c->logn);
+    }
 }
 int helr_ntt_fwd_lifted(he_ctx *c, const uint64_t *src, size_t src_stride, int src_prime, size_t nsrc, uint64_t *out,
                         const LimbMap &dst, cudaStream_t s)
