@@ -653,12 +653,13 @@ int helr_keyswitch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, 
     HELR_CUDA(c, cudaMemcpy2DAsync(ws->pl, N * 8, ws->acc + (size_t)nl * N, (size_t)nt * N * 8, N * 8, (size_t)batch * 2,
                                    cudaMemcpyDeviceToDevice, s));
     HELR_TRY(helr_ntt_inv(c, ws->pl, (size_t)batch * 2, limbmap_single(c->nq), s));
-    HELR_TRY(helr_ntt_fwd_lifted(c, ws->pl, N, c->nq, (size_t)batch * 2, ws->lift, limbmap_ct(level), s));
+    HELR_TRY(helr_ntt_lift_cols(c, ws->pl, N, c->nq, (size_t)batch * 2, ws->lift, limbmap_ct(level), s));
     if (o) {
-        k_ks_out(c, *o, ws->acc, ws->lift, batch, nl, s);
+        HELR_TRY(helr_ks_down(c, *o, ws->acc, ws->lift, batch, nl, s));
     } else {
-        k_rescale_combine(c, d_out, ws->acc, ws->lift, batch * 2, nl, (size_t)nt * N, (size_t)nl * N, (size_t)nl * N,
-                          c->d_pinv, s);
+        KsOut plain;
+        plain.out = Str{d_out, 2 * (size_t)nl * N, (size_t)nl * N};
+        HELR_TRY(helr_ks_down(c, plain, ws->acc, ws->lift, batch, nl, s));
     }
     HELR_CUDA(c, cudaGetLastError());
     if (ws == &local) helr_ks_scratch_free(c, &local);

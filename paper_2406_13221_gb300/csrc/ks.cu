@@ -324,12 +324,76 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
     }
 }
 
+// ModDown output stage fused with the row pass of its forward transform: the
+// CTA finishes the transform of RPC rows of the lifted P-part of limb j (column
+// pass already applied), then forms ks_j = (acc_j - lift_j) P^-1 and the
+// operation around the key switch (KsOut: + rel, + sigma_gal(rot_0), + acc) for
+// those rows, so the lifted limbs are never written in evaluation form.
+// grid: items * 2 polys * nl limbs * (R1 / RPC).
+template <int K1, int K2, int RPC>
+__global__ void __launch_bounds__(RPC * Geo<K2>::T)
+    k_ks_down_rows(KsOut o, const uint64_t *__restrict__ acc, const uint64_t *__restrict__ lift,
+                   const uint64_t *__restrict__ twall, const ModQ *__restrict__ mods, const uint64_t *__restrict__ pinv, int nl)
+{
+    using G = Geo<K2>;
+    constexpr int R1 = 1 << K1, R2 = G::R, N = R1 * R2, NG = R1 / RPC, E = G::E, T = G::T, LOGN = K1 + K2;
+    extern __shared__ uint64_t smem[];
+    int bid = blockIdx.x;
+    const int grp = bid % NG;
+    bid /= NG;
+    const int j = bid % nl;
+    bid /= nl;
+    const int p = bid & 1;
+    const size_t bt = (size_t)(bid >> 1);
+    const int l = threadIdx.x % T, rl = threadIdx.x / T;
+    const int row = grp * RPC + rl;
+    const uint64_t q = mods[j].q, q2 = 2 * q;
+    const uint64_t *tw = twall + (size_t)j * N * 2;
+    const uint64_t *rowp = lift + ((bt * 2 + p) * nl + j) * N + (size_t)row * R2;
+    uint64_t *seg = smem + rl * G::SEG;
+    uint64_t x[E];
+#pragma unroll
+    for (int r = 0; r < E; r++) x[r] = rowp[l + T * r];
+    const int A = R1 + row;
+    fwd_strided<K2>(x, tw, A, q, q2);
+    to_contig<K2>(x, seg, l);
+    fwd_contig<K2, true>(x, tw, A, l, q, q2);
+    __syncthreads();
+    to_strided<K2>(x, seg, l);  // word l + T r of the row: coalesced below
+    const uint64_t pv = pinv[2 * j], pvp = pinv[2 * j + 1];
+    const size_t nt = (size_t)nl + 1;
+#pragma unroll
+    for (int r = 0; r < E; r++) {
+        const int k = row * R2 + l + T * r;
+        const size_t lk = (size_t)j * N + k;
+        uint64_t w = x[r];
+        w = w >= q2 ? w - q2 : w;
+        w = w >= q ? w - q : w;
+        uint64_t v = shoup(submod(acc[(bt * 2 + p) * nt * N + lk], w, q), pv, pvp, q);
+        if (o.rel) v = addmod(v, o.rel[bt * o.rel_item + p * o.rel_poly + lk], q);
+        if (o.rot && p == 0) {
+            // sigma_gal on the evaluation form: position k holds the evaluation at
+            // psi^(2 bitrev(k) + 1); it takes the value at the position of
+            // psi^((2 bitrev(k) + 1) gal)
+            const uint64_t mask2n = (2ull << LOGN) - 1;
+            const uint32_t kk = __brev((uint32_t)k) >> (32 - LOGN);
+            const uint64_t e = ((2ull * kk + 1) * o.gal) & mask2n;
+            const uint32_t ps = __brev((uint32_t)((e - 1) >> 1)) >> (32 - LOGN);
+            v = addmod(v, o.rot[bt * o.rot_item + (size_t)j * N + ps], q);
+        }
+        if (o.acc) v = addmod(v, o.acc[bt * o.acc_item + p * o.acc_poly + lk], q);
+        o.out.p[bt * o.out.item + p * o.out.poly + lk] = v;
+    }
+}
+
 template <int K1, int K2>
 struct KsPlan {
     static constexpr int T1 = Geo<K1>::T, T2 = Geo<K2>::T;
     static constexpr int R1 = 1 << K1, R2 = 1 << K2;
     static constexpr int C = (256 / T1) < R2 ? (256 / T1) : R2;
     static constexpr int RPC = (128 / T2) < R1 ? (128 / T2) : R1;
+    static constexpr int RPCD = (256 / T2) < R1 ? (256 / T2) : R1;
+    static constexpr size_t SMD = (size_t)RPCD * Geo<K2>::SEG * 8;
     static constexpr size_t SM1 = (size_t)C * Geo<K1>::SEG * 8 + (size_t)C * R1 * 8;
     static constexpr size_t SM2 = (size_t)RPC * Geo<K2>::SEG * 8 + 2 * (size_t)RPC * R2 * 8;
     static cudaError_t prepare()
@@ -337,7 +401,13 @@ struct KsPlan {
         cudaError_t e = helr_fit_carveout((const void *)k_ks_modup_cols<K1, K2, C>, C * T1, SM1);
         if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_inner_rows<K1, K2, RPC, false>, RPC * T2, SM2);
         if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_inner_rows<K1, K2, RPC, true>, RPC * T2, SM2);
+        if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_down_rows<K1, K2, RPCD>, RPCD * T2, SMD);
         return e;
+    }
+    static void down(he_ctx *c, const KsOut &o, const uint64_t *acc, const uint64_t *lift, int items, int nl, cudaStream_t s)
+    {
+        const unsigned grid = (unsigned)((size_t)items * 2 * nl * (R1 / RPCD));
+        HELR_LAUNCH(k_ks_down_rows<K1, K2, RPCD><<<grid, RPCD * T2, SMD, s>>>(o, acc, lift, c->t.tw, c->t.mod, c->d_pinv, nl));
     }
     // targets 0..nl of a key switch at nl limbs (nl = P) whose prime takes (lz) or
     // does not take the unreduced forward butterfly
@@ -433,6 +503,38 @@ int helr_ks_key_layout(he_ctx *c, uint64_t *key, size_t nlimbs)
     }
     HELR_CUDA(c, cudaGetLastError());
     return HE_OK;
+}
+
+template <int K1, int K2>
+int run_down(he_ctx *c, const KsOut &o, const uint64_t *acc, const uint64_t *lift, int items, int nl, cudaStream_t s)
+{
+    static bool prepared = false;
+    if (!prepared) {
+        HELR_CUDA(c, (KsPlan<K1, K2>::prepare()));
+        prepared = true;
+    }
+    prof_start(c, PROF_NTT_FWD, s);
+    KsPlan<K1, K2>::down(c, o, acc, lift, items, nl, s);
+    prof_stop(c, PROF_NTT_FWD, s, 0.5 * items * 2 * nl, 1);  // the row half of 2 nl transforms per item
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
+
+// ModDown output: lift is [items][2][nl][N], the centred P-parts after the
+// column pass of their forward transform; acc is [items][2][nl+1][N].
+int helr_ks_down(he_ctx *c, const KsOut &o, const uint64_t *acc, const uint64_t *lift, int items, int nl, cudaStream_t s)
+{
+    if (items <= 0) return HE_OK;
+    switch (c->logn) {
+    case 10: return run_down<5, 5>(c, o, acc, lift, items, nl, s);
+    case 11: return run_down<5, 6>(c, o, acc, lift, items, nl, s);
+    case 12: return run_down<6, 6>(c, o, acc, lift, items, nl, s);
+    case 13: return run_down<6, 7>(c, o, acc, lift, items, nl, s);
+    case 14: return run_down<7, 7>(c, o, acc, lift, items, nl, s);
+    case 15: return run_down<7, 8>(c, o, acc, lift, items, nl, s);
+    case 16: return run_down<8, 8>(c, o, acc, lift, items, nl, s);
+    default: return helr_fail(c, HE_EINVAL, "log_n %d unsupported", c->logn);
+    }
 }
 
 // items per fused wave: the column-pass output of one wave stays in L2

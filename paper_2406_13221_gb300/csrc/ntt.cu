@@ -227,6 +227,26 @@ struct Lifted {
 };
 
 template <int K1, int K2>
+int run_lift_cols(he_ctx *c, const uint64_t *src, size_t src_stride, int src_prime, size_t nsrc, uint64_t *out,
+                  const LimbMap &dst, cudaStream_t s)
+{
+    static bool prepared = false;
+    if (!prepared) {
+        HELR_CUDA(c, (NttPlan<K1, K2>::prepare()));
+        prepared = true;
+    }
+    if (nsrc == 0) return HE_OK;
+    using P = NttPlan<K1, K2>;
+    const size_t nl = nsrc * dst.period;
+    prof_start(c, PROF_NTT_FWD, s);
+    HELR_LAUNCH(k_ntt_lift_cols<K1, K2, P::C><<<(unsigned)(nl * (P::R2 / P::C)), P::C * P::T1, P::SM1, s>>>(
+        src, src_stride, out, dst.period, src_prime, c->t.tw, c->t.mod, dst));
+    prof_stop(c, PROF_NTT_FWD, s, 0.5 * (double)nl, 1);  // the column half of each transform
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
+
+template <int K1, int K2>
 int run_inv_rows(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s)
 {
     static bool prepared = false;
@@ -331,6 +351,23 @@ int helr_ntt_inv_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs
 {
     return dispatch(c, in, out, nlimbs, m, s, true);
 }
+// the column pass of helr_ntt_fwd_lifted only (the row pass is left to a
+// consumer that reads whole rows)
+int helr_ntt_lift_cols(he_ctx *c, const uint64_t *src, size_t src_stride, int src_prime, size_t nsrc, uint64_t *out,
+                       const LimbMap &dst, cudaStream_t s)
+{
+    switch (c->logn) {
+    case 10: return run_lift_cols<5, 5>(c, src, src_stride, src_prime, nsrc, out, dst, s);
+    case 11: return run_lift_cols<5, 6>(c, src, src_stride, src_prime, nsrc, out, dst, s);
+    case 12: return run_lift_cols<6, 6>(c, src, src_stride, src_prime, nsrc, out, dst, s);
+    case 13: return run_lift_cols<6, 7>(c, src, src_stride, src_prime, nsrc, out, dst, s);
+    case 14: return run_lift_cols<7, 7>(c, src, src_stride, src_prime, nsrc, out, dst, s);
+    case 15: return run_lift_cols<7, 8>(c, src, src_stride, src_prime, nsrc, out, dst, s);
+    case 16: return run_lift_cols<8, 8>(c, src, src_stride, src_prime, nsrc, out, dst, s);
+    default: return helr_fail(c, HE_EINVAL, "log_n %d unsupported", c->logn);
+    }
+}
+
 // the row pass of the inverse transform only: the column pass (K1 stages, the
 // factor N^-1) is left to a consumer that reads whole columns
 int helr_ntt_inv_rows(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s)

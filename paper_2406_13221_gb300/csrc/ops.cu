@@ -206,44 +206,9 @@ __global__ void k_automorph_items_kernel(uint64_t *out, size_t out_item, const u
     out[bt * out_item + (limb << logn) + p] = in[bt * in_item + (limb << logn) + ps];
 }
 
-// ModDown output stage fused with relinearisation / rotation / accumulation.
-// grid: (N / 256, nl, items * 2); ks = (accP - lift) * P^-1 per limb j.
-__global__ void k_ks_out_kernel(KsOut o, const uint64_t *acc, const uint64_t *lift, int logn, int nl, const uint64_t *pinv,
-                                const ModQ *mods)
-{
-    const int n = 1 << logn;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const int j = blockIdx.y;
-    const int p = blockIdx.z & 1;
-    const size_t bt = blockIdx.z >> 1;
-    const uint64_t q = mods[j].q;
-    const size_t lk = ((size_t)j << logn) + k;
-    const size_t nt = (size_t)nl + 1;
-    uint64_t a = acc[(bt * 2 + p) * (nt << logn) + lk];
-    uint64_t l = lift[(bt * 2 + p) * ((size_t)nl << logn) + lk];
-    uint64_t v = shoup(submod(a, l, q), pinv[2 * j], pinv[2 * j + 1], q);
-    if (o.rel) v = addmod(v, o.rel[bt * o.rel_item + p * o.rel_poly + lk], q);
-    if (o.rot && p == 0) {
-        const uint64_t mask2n = (2ull << logn) - 1;
-        uint32_t kk = __brev((uint32_t)k) >> (32 - logn);
-        uint64_t e = ((2ull * kk + 1) * o.gal) & mask2n;
-        uint32_t ps = __brev((uint32_t)((e - 1) >> 1)) >> (32 - logn);
-        v = addmod(v, o.rot[bt * o.rot_item + ((size_t)j << logn) + ps], q);
-    }
-    if (o.acc) v = addmod(v, o.acc[bt * o.acc_item + p * o.acc_poly + lk], q);
-    o.out.p[bt * o.out.item + p * o.out.poly + lk] = v;
-}
-
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
-void k_ks_out(he_ctx *c, const KsOut &o, const uint64_t *acc, const uint64_t *lift, int batch, int nl, cudaStream_t s)
-{
-    dim3 grid((c->n + 255) / 256, nl, 2 * batch);
-    if (batch) HELR_LAUNCH(k_ks_out_kernel<<<grid, 256, 0, s>>>(o, acc, lift, c->logn, nl, c->d_pinv, c->t.mod));
-}
-
 void k_ew(he_ctx *c, int op, Str out, Str a, Str b, int batch, int npoly, int nl, const KP *kp, cudaStream_t s)
 {
     static const KP zero = {};
