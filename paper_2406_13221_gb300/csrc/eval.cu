@@ -146,28 +146,17 @@ int ev_rescale(Eval *ev, const CtB &a, CtB &out)
     const int B = a.batch, nl = lv + 1;
     const size_t N = c->n;
     cudaStream_t s = c->stream;
-    for (int p = 0; p < 2; p++)
-        HELR_CUDA(c, cudaMemcpy2DAsync(ev->last + p * N, 2 * N * 8, a.d + (size_t)p * nl * N + (size_t)lv * N,
-                                       (a.item ? a.item : 2 * nl * N) * 8, N * 8, B, cudaMemcpyDeviceToDevice, s));
-    HELR_TRY(helr_ntt_inv(c, ev->last, 2 * (size_t)B, limbmap_single(lv), s));
-    HELR_TRY(helr_ntt_fwd_lifted(c, ev->last, N, lv, 2 * (size_t)B, ev->lift, limbmap_ct(lv - 1), s));
-    KP kp;
-    std::vector<uint64_t> h(2);
-    for (int j = 0; j < lv; j++) {
-        uint64_t x = 0, q = c->q[j], ql = c->q[lv] % q;
-        // q_l^-1 mod q_j by Fermat
-        unsigned __int128 r = 1, b = ql;
-        for (uint64_t e = q - 2; e; e >>= 1, b = b * b % q)
-            if (e & 1) r = r * b % q;
-        x = (uint64_t)r;
-        kp.w[j][0] = x;
-        kp.w[j][1] = (uint64_t)(((unsigned __int128)x << 64) / q);
-    }
+    const size_t item = a.item ? a.item : 2 * (size_t)nl * N;
+    // the dropped limb q_lv of both polynomials: inverse row pass, then the
+    // fused column passes and the output stage (value - centred lift) * q_lv^-1
+    HELR_TRY(helr_ntt_inv_rows(c, a.d + (size_t)lv * N, item, (size_t)nl * N, ev->last, 2 * (size_t)B, limbmap_single(lv), s));
     out.level = lv - 1;
     out.batch = B;
     out.scale = a.scale / (double)c->q[lv];
-    Str in{a.d, a.item, (size_t)nl * N}, corr{ev->lift, 2 * (size_t)lv * N, (size_t)lv * N};
-    k_ew(c, EW_SUBMUL, S(out, c), in, corr, B, 2, lv, &kp, s);
+    KsOut o;
+    o.out = S(out, c);
+    HELR_TRY(helr_ks_down(c, o, a.d, item, (size_t)nl * N, ev->last, lv, ev->lift, B, lv, c->d_qinv + (size_t)lv * c->nq * 2,
+                          s));
     HELR_CUDA(c, cudaGetLastError());
     return HE_OK;
 }

@@ -641,7 +641,7 @@ int helr_keyswitch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, 
     }
     cudaStream_t s = c->stream;
     // 1. row pass of the inverse transform of every limb (the column pass runs inside ModUp)
-    HELR_TRY(helr_ntt_inv_rows(c, d_in, ws->drow, in_items, limbmap_ct(level), s));
+    HELR_TRY(helr_ntt_inv_rows(c, d_in, 2 * N, N, ws->drow, in_items, limbmap_ct(level), s));
     // 2-3. ModUp fused with the transforms and the inner product, in waves
     const int wave = std::min(ws->wave, batch);
     for (int b0 = 0; b0 < batch; b0 += wave) {
@@ -650,17 +650,12 @@ int helr_keyswitch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, 
                                ws->acc + (size_t)b0 * 2 * nt * N, cnt, nl, s));
     }
     // 4. ModDown: subtract the centred P-part and divide by P
-    HELR_CUDA(c, cudaMemcpy2DAsync(ws->pl, N * 8, ws->acc + (size_t)nl * N, (size_t)nt * N * 8, N * 8, (size_t)batch * 2,
-                                   cudaMemcpyDeviceToDevice, s));
-    HELR_TRY(helr_ntt_inv(c, ws->pl, (size_t)batch * 2, limbmap_single(c->nq), s));
-    HELR_TRY(helr_ntt_lift_cols(c, ws->pl, N, c->nq, (size_t)batch * 2, ws->lift, limbmap_ct(level), s));
-    if (o) {
-        HELR_TRY(helr_ks_down(c, *o, ws->acc, ws->lift, batch, nl, s));
-    } else {
-        KsOut plain;
-        plain.out = Str{d_out, 2 * (size_t)nl * N, (size_t)nl * N};
-        HELR_TRY(helr_ks_down(c, plain, ws->acc, ws->lift, batch, nl, s));
-    }
+    HELR_TRY(helr_ntt_inv_rows(c, ws->acc + (size_t)nl * N, 2 * (size_t)nt * N, (size_t)nt * N, ws->pl, (size_t)batch * 2,
+                               limbmap_single(c->nq), s));
+    KsOut plain;
+    plain.out = Str{d_out, 2 * (size_t)nl * N, (size_t)nl * N};
+    HELR_TRY(helr_ks_down(c, o ? *o : plain, ws->acc, 2 * (size_t)nt * N, (size_t)nt * N, ws->pl, c->nq, ws->lift, batch,
+                          nl, c->d_pinv, s));
     HELR_CUDA(c, cudaGetLastError());
     if (ws == &local) helr_ks_scratch_free(c, &local);
     return HE_OK;

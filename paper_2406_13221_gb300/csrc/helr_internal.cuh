@@ -292,7 +292,8 @@ int helr_ntt_inv_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs
 // modulo prime src_prime) is lifted to every prime of dst and transformed; out is [nsrc][dst.period][N]
 int helr_ntt_lift_cols(he_ctx *c, const uint64_t *src, size_t src_stride, int src_prime, size_t nsrc, uint64_t *out,
                        const LimbMap &dst, cudaStream_t s);
-int helr_ntt_inv_rows(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s);
+int helr_ntt_inv_rows(he_ctx *c, const uint64_t *in, size_t in_item, size_t in_poly, uint64_t *out, size_t nlimbs,
+                      const LimbMap &m, cudaStream_t s);
 int helr_ntt_fwd_lifted(he_ctx *c, const uint64_t *src, size_t src_stride, int src_prime, size_t nsrc, uint64_t *out,
                         const LimbMap &dst, cudaStream_t s);
 
@@ -354,7 +355,8 @@ struct KsOut {
 };
 int helr_keyswitch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, int level, const uint64_t *key,
                    KsScratch *ws, const KsOut *o = nullptr);
-int helr_ks_down(he_ctx *c, const KsOut &o, const uint64_t *acc, const uint64_t *lift, int items, int nl, cudaStream_t s);
+int helr_ks_down(he_ctx *c, const KsOut &o, const uint64_t *src, size_t src_item, size_t src_poly, const uint64_t *drow,
+                 int src_prime, uint64_t *lift, int items, int nl, const uint64_t *inv, cudaStream_t s);
 const uint64_t *helr_find_key(const he_ctx *c, uint64_t gal);
 int helr_add_key(he_ctx *c, uint64_t gal);
 int helr_new_ct(he_ctx *c, int level, double scale, he_ct **out);

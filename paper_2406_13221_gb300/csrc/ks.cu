@@ -21,16 +21,23 @@
 namespace {
 using namespace nttc;
 
-// ModUp with the last half of the inverse transform: a CTA takes C adjacent
-// columns of digit i (row pass of the inverse transform already applied), runs
-// the inverse column pass and the factor N^-1, keeps the coefficients in shared
-// memory, then for every target t != i lifts the centred coefficients into q_t
-// and runs the forward column pass.  Each digit column is read once.
-template <int K1, int K2, int C>
+// Second half of an inverse transform followed by a centred lift into several
+// primes and the first half of their forward transforms.  A CTA takes C
+// adjacent columns of one source limb (row pass of the inverse transform
+// already applied), runs the inverse column pass and the factor N^-1, keeps the
+// coefficients in shared memory, then for every target lifts the centred
+// coefficients into q_t and runs the forward column pass.  Each source column
+// is read once.
+//   ModUp (DOWN = false): source (b, i) = digit i of item b, prime q_i, in
+//     drow[b][i]; targets t = 0..nl except i (nl stands for P), out
+//     mid[b][i][t] (t = i is the evaluation-form input itself).
+//   ModDown / rescale (DOWN = true): source k = drow[k], prime src_prime;
+//     targets t = 0..nl-1, out mid[k][t].
+template <int K1, int K2, int C, bool DOWN>
 __global__ void __launch_bounds__(C * Geo<K1>::T, 3)
     k_ks_modup_cols(const uint64_t *__restrict__ drow, uint64_t *__restrict__ mid, const uint64_t *__restrict__ twall,
                     const uint64_t *__restrict__ itwall, const ModQ *__restrict__ mods, const uint64_t *__restrict__ ninv,
-                    int nl, int pidx)
+                    int nl, int pidx, int src_prime)
 {
     using G = Geo<K1>;
     constexpr int R2 = 1 << K2, N = G::R * R2, NG = R2 / C, E = G::E, T = G::T;
@@ -38,14 +45,16 @@ __global__ void __launch_bounds__(C * Geo<K1>::T, 3)
     int bid = blockIdx.x;
     const int grp = bid % NG;
     bid /= NG;
-    const int i = bid % nl, b = bid / nl;
+    const size_t src = (size_t)bid;                       // source limb index in drow
+    const int i = DOWN ? -1 : bid % nl;                    // digit index (ModUp)
+    const int sp = DOWN ? src_prime : i;                   // prime of the source limb
     const int jj = threadIdx.x % C, l = threadIdx.x / C;
     uint64_t *seg = smem + jj * G::SEG;
     uint64_t *coef = smem + C * G::SEG;  // [R1][C]: word (j1, jj); each thread reads back only its own words
-    const uint64_t qi = mods[i].q;
-    const size_t col = ((size_t)b * nl + i) * N + grp * C + jj;
+    const uint64_t qi = mods[sp].q;
+    const size_t col = src * N + grp * C + jj;
     {
-        const uint64_t *itw = itwall + (size_t)i * N * 2;
+        const uint64_t *itw = itwall + (size_t)sp * N * 2;
         uint64_t c[E];
         // words of this column arrive as j1 = E l + r (contiguous assignment)
 #pragma unroll
@@ -53,14 +62,14 @@ __global__ void __launch_bounds__(C * Geo<K1>::T, 3)
         inv_contig<K1, false>(c, itw, 1, l, qi, 2 * qi);
         to_strided<K1>(c, seg, l);
         inv_strided<K1>(c, itw, 1, qi, 2 * qi);
-        const uint64_t ni = ninv[2 * i], nip = ninv[2 * i + 1];
+        const uint64_t ni = ninv[2 * sp], nip = ninv[2 * sp + 1];
 #pragma unroll
-        for (int r = 0; r < E; r++) coef[(l + T * r) * C + jj] = shoup(c[r], ni, nip, qi);  // in [0, q_i)
+        for (int r = 0; r < E; r++) coef[(l + T * r) * C + jj] = shoup(c[r], ni, nip, qi);  // in [0, q_src)
     }
-    uint64_t *dst = mid + ((size_t)b * nl + i) * (nl + 1) * N + grp * C + jj;
+    uint64_t *dst = mid + src * (DOWN ? nl : nl + 1) * N + grp * C + jj;
     for (int tt = 0; tt < nl; tt++) {
-        const int t = tt < i ? tt : tt + 1;  // target 0..nl, never i (that limb is the evaluation-form input)
-        const int pt = t < nl ? t : pidx;
+        const int t = DOWN ? tt : (tt < i ? tt : tt + 1);
+        const int pt = DOWN ? t : (t < nl ? t : pidx);
         const ModQ mt = mods[pt];
         const uint64_t q = mt.q, q2 = 2 * q;
         const uint64_t *tw = twall + (size_t)pt * N * 2;
@@ -324,16 +333,19 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
     }
 }
 
-// ModDown output stage fused with the row pass of its forward transform: the
-// CTA finishes the transform of RPC rows of the lifted P-part of limb j (column
-// pass already applied), then forms ks_j = (acc_j - lift_j) P^-1 and the
+// Output stage of ModDown (and of rescale) fused with the row pass of its
+// forward transform: the CTA finishes the transform of RPC rows of the lifted
+// part of limb j (column pass already applied), then forms
+// (src_j - lift_j) * inv_j (inv: P^-1 or q_l^-1 mod q_j, Shoup pairs) and the
 // operation around the key switch (KsOut: + rel, + sigma_gal(rot_0), + acc) for
 // those rows, so the lifted limbs are never written in evaluation form.
+// src limb j of polynomial p of item b: src + b src_item + p src_poly + j N.
 // grid: items * 2 polys * nl limbs * (R1 / RPC).
 template <int K1, int K2, int RPC>
 __global__ void __launch_bounds__(RPC * Geo<K2>::T)
-    k_ks_down_rows(KsOut o, const uint64_t *__restrict__ acc, const uint64_t *__restrict__ lift,
-                   const uint64_t *__restrict__ twall, const ModQ *__restrict__ mods, const uint64_t *__restrict__ pinv, int nl)
+    k_ks_down_rows(KsOut o, const uint64_t *__restrict__ srcp, size_t src_item, size_t src_poly,
+                   const uint64_t *__restrict__ lift, const uint64_t *__restrict__ twall, const ModQ *__restrict__ mods,
+                   const uint64_t *__restrict__ inv, int nl)
 {
     using G = Geo<K2>;
     constexpr int R1 = 1 << K1, R2 = G::R, N = R1 * R2, NG = R1 / RPC, E = G::E, T = G::T, LOGN = K1 + K2;
@@ -360,8 +372,8 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T)
     fwd_contig<K2, true>(x, tw, A, l, q, q2);
     __syncthreads();
     to_strided<K2>(x, seg, l);  // word l + T r of the row: coalesced below
-    const uint64_t pv = pinv[2 * j], pvp = pinv[2 * j + 1];
-    const size_t nt = (size_t)nl + 1;
+    const uint64_t pv = inv[2 * j], pvp = inv[2 * j + 1];
+    const uint64_t *sv = srcp + bt * src_item + p * src_poly;
 #pragma unroll
     for (int r = 0; r < E; r++) {
         const int k = row * R2 + l + T * r;
@@ -369,7 +381,7 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T)
         uint64_t w = x[r];
         w = w >= q2 ? w - q2 : w;
         w = w >= q ? w - q : w;
-        uint64_t v = shoup(submod(acc[(bt * 2 + p) * nt * N + lk], w, q), pv, pvp, q);
+        uint64_t v = shoup(submod(sv[lk], w, q), pv, pvp, q);
         if (o.rel) v = addmod(v, o.rel[bt * o.rel_item + p * o.rel_poly + lk], q);
         if (o.rot && p == 0) {
             // sigma_gal on the evaluation form: position k holds the evaluation at
@@ -398,16 +410,25 @@ struct KsPlan {
     static constexpr size_t SM2 = (size_t)RPC * Geo<K2>::SEG * 8 + 2 * (size_t)RPC * R2 * 8;
     static cudaError_t prepare()
     {
-        cudaError_t e = helr_fit_carveout((const void *)k_ks_modup_cols<K1, K2, C>, C * T1, SM1);
+        cudaError_t e = helr_fit_carveout((const void *)k_ks_modup_cols<K1, K2, C, false>, C * T1, SM1);
+        if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_modup_cols<K1, K2, C, true>, C * T1, SM1);
         if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_inner_rows<K1, K2, RPC, false>, RPC * T2, SM2);
         if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_inner_rows<K1, K2, RPC, true>, RPC * T2, SM2);
         if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_down_rows<K1, K2, RPCD>, RPCD * T2, SMD);
         return e;
     }
-    static void down(he_ctx *c, const KsOut &o, const uint64_t *acc, const uint64_t *lift, int items, int nl, cudaStream_t s)
+    static void down(he_ctx *c, const KsOut &o, const uint64_t *src, size_t src_item, size_t src_poly, const uint64_t *lift,
+                     int items, int nl, const uint64_t *inv, cudaStream_t s)
     {
         const unsigned grid = (unsigned)((size_t)items * 2 * nl * (R1 / RPCD));
-        HELR_LAUNCH(k_ks_down_rows<K1, K2, RPCD><<<grid, RPCD * T2, SMD, s>>>(o, acc, lift, c->t.tw, c->t.mod, c->d_pinv, nl));
+        HELR_LAUNCH(k_ks_down_rows<K1, K2, RPCD><<<grid, RPCD * T2, SMD, s>>>(o, src, src_item, src_poly, lift, c->t.tw,
+                                                                              c->t.mod, inv, nl));
+    }
+    static void down_cols(he_ctx *c, const uint64_t *drow, size_t nsrc, int src_prime, uint64_t *out, int nl, cudaStream_t s)
+    {
+        const unsigned grid = (unsigned)(nsrc * (R2 / C));
+        HELR_LAUNCH(k_ks_modup_cols<K1, K2, C, true><<<grid, C * T1, SM1, s>>>(drow, out, c->t.tw, c->t.itw, c->t.mod,
+                                                                                c->t.ninv, nl, c->nq, src_prime));
     }
     // targets 0..nl of a key switch at nl limbs (nl = P) whose prime takes (lz) or
     // does not take the unreduced forward butterfly
@@ -421,8 +442,8 @@ struct KsPlan {
     static int modup(he_ctx *c, const uint64_t *drow, uint64_t *mid, int items, int nl, cudaStream_t s)
     {
         unsigned grid = (unsigned)((size_t)items * nl * (R2 / C));
-        HELR_LAUNCH(k_ks_modup_cols<K1, K2, C><<<grid, C * T1, SM1, s>>>(drow, mid, c->t.tw, c->t.itw, c->t.mod, c->t.ninv,
-                                                                          nl, c->nq));
+        HELR_LAUNCH(k_ks_modup_cols<K1, K2, C, false><<<grid, C * T1, SM1, s>>>(drow, mid, c->t.tw, c->t.itw, c->t.mod,
+                                                                                 c->t.ninv, nl, c->nq, 0));
         return 1;
     }
     static int inner(he_ctx *c, const uint64_t *mid, const uint64_t *dntt, const uint64_t *key, uint64_t *acc, int items,
@@ -506,7 +527,8 @@ int helr_ks_key_layout(he_ctx *c, uint64_t *key, size_t nlimbs)
 }
 
 template <int K1, int K2>
-int run_down(he_ctx *c, const KsOut &o, const uint64_t *acc, const uint64_t *lift, int items, int nl, cudaStream_t s)
+int run_down(he_ctx *c, const KsOut *o, const uint64_t *src, size_t src_item, size_t src_poly, const uint64_t *drow,
+             int src_prime, uint64_t *lift, int items, int nl, const uint64_t *inv, cudaStream_t s)
 {
     static bool prepared = false;
     if (!prepared) {
@@ -514,27 +536,44 @@ int run_down(he_ctx *c, const KsOut &o, const uint64_t *acc, const uint64_t *lif
         prepared = true;
     }
     prof_start(c, PROF_NTT_FWD, s);
-    KsPlan<K1, K2>::down(c, o, acc, lift, items, nl, s);
-    prof_stop(c, PROF_NTT_FWD, s, 0.5 * items * 2 * nl, 1);  // the row half of 2 nl transforms per item
+    if (drow) KsPlan<K1, K2>::down_cols(c, drow, (size_t)items * 2, src_prime, lift, nl, s);
+    if (o) KsPlan<K1, K2>::down(c, *o, src, src_item, src_poly, lift, items, nl, inv, s);
+    // 2 nl forward transforms per item (column half, row half), and the inverse column half of 2 source limbs
+    prof_stop(c, PROF_NTT_FWD, s, (drow ? 0.5 * items * 2 * (nl + 1) : 0) + (o ? 0.5 * items * 2 * nl : 0),
+              (drow ? 1 : 0) + (o ? 1 : 0));
     HELR_CUDA(c, cudaGetLastError());
     return HE_OK;
 }
 
-// ModDown output: lift is [items][2][nl][N], the centred P-parts after the
-// column pass of their forward transform; acc is [items][2][nl+1][N].
-int helr_ks_down(he_ctx *c, const KsOut &o, const uint64_t *acc, const uint64_t *lift, int items, int nl, cudaStream_t s)
+static int down_dispatch(he_ctx *c, const KsOut *o, const uint64_t *src, size_t src_item, size_t src_poly,
+                         const uint64_t *drow, int src_prime, uint64_t *lift, int items, int nl, const uint64_t *inv,
+                         cudaStream_t s)
 {
     if (items <= 0) return HE_OK;
     switch (c->logn) {
-    case 10: return run_down<5, 5>(c, o, acc, lift, items, nl, s);
-    case 11: return run_down<5, 6>(c, o, acc, lift, items, nl, s);
-    case 12: return run_down<6, 6>(c, o, acc, lift, items, nl, s);
-    case 13: return run_down<6, 7>(c, o, acc, lift, items, nl, s);
-    case 14: return run_down<7, 7>(c, o, acc, lift, items, nl, s);
-    case 15: return run_down<7, 8>(c, o, acc, lift, items, nl, s);
-    case 16: return run_down<8, 8>(c, o, acc, lift, items, nl, s);
+    case 10: return run_down<5, 5>(c, o, src, src_item, src_poly, drow, src_prime, lift, items, nl, inv, s);
+    case 11: return run_down<5, 6>(c, o, src, src_item, src_poly, drow, src_prime, lift, items, nl, inv, s);
+    case 12: return run_down<6, 6>(c, o, src, src_item, src_poly, drow, src_prime, lift, items, nl, inv, s);
+    case 13: return run_down<6, 7>(c, o, src, src_item, src_poly, drow, src_prime, lift, items, nl, inv, s);
+    case 14: return run_down<7, 7>(c, o, src, src_item, src_poly, drow, src_prime, lift, items, nl, inv, s);
+    case 15: return run_down<7, 8>(c, o, src, src_item, src_poly, drow, src_prime, lift, items, nl, inv, s);
+    case 16: return run_down<8, 8>(c, o, src, src_item, src_poly, drow, src_prime, lift, items, nl, inv, s);
     default: return helr_fail(c, HE_EINVAL, "log_n %d unsupported", c->logn);
     }
+}
+
+// Division by a dropped prime with rounding, for ModDown (by P) and rescale (by
+// q_l), after the inverse row pass of the dropped limbs: drow holds
+// [items][2][N], the dropped limb of every polynomial (prime src_prime) after
+// the row pass of its inverse transform.  The kernels finish its inverse
+// transform, lift it centred into q_0..q_(nl-1), transform it forward
+// (lift: [items][2][nl][N] scratch) and write o.out = (src - lift) * inv plus
+// the KsOut terms, inv holding Shoup pairs of the inverse of the dropped prime
+// modulo each q_j.
+int helr_ks_down(he_ctx *c, const KsOut &o, const uint64_t *src, size_t src_item, size_t src_poly, const uint64_t *drow,
+                 int src_prime, uint64_t *lift, int items, int nl, const uint64_t *inv, cudaStream_t s)
+{
+    return down_dispatch(c, &o, src, src_item, src_poly, drow, src_prime, lift, items, nl, inv, s);
 }
 
 // items per fused wave: the column-pass output of one wave stays in L2
