@@ -227,7 +227,7 @@ def run_ours(args, rank, world):
                    "l2": "no flush: %.1f GiB of encrypted data blocks > 129 MB L2" % (info.n_blocks * ctw_bytes() / 2 ** 30)},
         "keyswitch_per_s": round(ks_per_iter / sec_iter / world, 1) if sec_iter else None,
         "keyswitches_per_iter": ks_per_iter,
-        "ntt_limbs_per_s": round((prof["ntt_fwd"][1] + prof["ntt_inv"][1]) / args.steps / (sec_iter * world), 1),
+        "ntt_limbs_per_s": round(transform_limbs(prof) / args.steps / (sec_iter * world), 1),
         "plain_one_ct_per_launch_s_per_iter": round(plain, 4) if plain else None,
         "mini_batch": mini,
         "multi_job": multi,
@@ -404,46 +404,55 @@ def pinned_u64(n):
 
 
 # Integer-instruction cost model (32-bit lowering of the 64-bit modular
-# operations): Harvey butterfly with a Shoup twiddle, Barrett
-# multiply-accumulate, centred lift.
-OPS_BFLY, OPS_MAC, OPS_LIFT = 23, 38, 6
+# operations): Harvey butterfly with a Shoup twiddle; key
+# product accumulated exactly in 128 bits (64x64 -> 128 product and a 128-bit
+# add, 13) plus its share of the one Montgomery reduction per output word (12
+# over about 6 digits); centred lift; Shoup scaling by N^-1.
+OPS_BFLY, OPS_MAC, OPS_LIFT, OPS_SCALE = 23, 15, 6, 14
 SMS, LANES, SM_MHZ_MAX = 152, 128, 2070.0
+
+
+def transform_limbs(prof):
+    """Limb transforms (forward and inverse, standalone or fused into key
+    switching) counted as whole transforms: the fused kernels report the
+    column or row halves they run."""
+    return (prof["ntt_fwd"][1] + prof["ntt_inv"][1]
+            + 0.5 * (prof["modup"][1] + prof["modup"][3] + prof["ks_inner"][1]))
 
 
 def class_work(name, units, units2, dram_limbs):
     """(integer ops, algorithmic DRAM bytes) of a timing class from its work counts."""
     n = 1 << LOGN
-    half_stages = LOGN // 2
-    if name.startswith("ntt"):           # units = limbs, both passes
-        return units * LOGN * (n / 2) * OPS_BFLY, 16.0 * n * units
-    if name == "modup":                  # units = (digit, target) limbs, column pass + lift
-        return units * (half_stages * (n / 2) * OPS_BFLY + n * OPS_LIFT), 8.0 * n * dram_limbs
-    # ks_inner: units = limbs through the row pass, units2 = limbs of key products
-    return units * half_stages * (n / 2) * OPS_BFLY + units2 * n * OPS_MAC, 8.0 * n * dram_limbs
+    half = (LOGN // 2) * (n / 2) * OPS_BFLY   # one column or row half of a transform
+    if name.startswith("ntt"):           # units = whole-limb transform equivalents
+        return units * 2 * half, 16.0 * n * units
+    if name == "modup":                  # units = forward column halves (+ lift), units2 = inverse column halves
+        return units * (half + n * OPS_LIFT) + units2 * (half + n * OPS_SCALE), 8.0 * n * dram_limbs
+    # ks_inner: units = row halves, units2 = limbs of key products
+    return units * half + units2 * n * OPS_MAC, 8.0 * n * dram_limbs
 
 
 def roofline(prof, steps):
-    """Dominant kernel class by measured time: algorithmic integer operations per
-    launch over its average launch duration against the integer-issue peak
-    (the kernels are ALU-bound; the DRAM view is reported beside it)."""
+    """Dominant kernel class by measured time: its algorithmic integer operations
+    over its measured time against the integer-issue peak (the kernels are
+    ALU-bound; the DRAM view is reported beside it)."""
     peaks = measured_peaks()
     best = max(prof, key=lambda k: prof[k][0])
     ms, units, launches, units2, dram_limbs = prof[best]
-    groups = launches / (2 if best.startswith("ntt") else 1)
     ops, alg_bytes = class_work(best, units, units2, dram_limbs)
-    dur = ms / 1000.0 / groups if groups else 0
-    per_launch_ops = ops / groups if groups else 0
-    achieved = per_launch_ops / dur / 1e12 if dur else 0
+    sec = ms / 1000.0
+    achieved = ops / sec / 1e12 if sec else 0
     peak = SMS * LANES * SM_MHZ_MAX * 1e6 / 1e12
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    hbm_ach = alg_bytes / groups / dur / 1e9 if dur else 0
+    hbm_ach = alg_bytes / sec / 1e9 if sec else 0
     kernel = {"ks_inner": "k_ks_inner_rows", "modup": "k_ks_modup_cols",
-              "ntt_fwd": "k_ntt_fwd_cols+k_ntt_fwd_rows", "ntt_inv": "k_ntt_inv_rows+k_ntt_inv_cols"}[best]
+              "ntt_fwd": "k_ks_modup_cols+k_ks_down_rows+k_ntt_fwd_*", "ntt_inv": "k_ntt_inv_*"}[best]
     return {"kernel": kernel, "bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2), "unit": "Tops/s",
             "frac": round(achieved / peak, 4),
-            "traffic": (None if recorded_traffic(kernel) is None
-                        else round(recorded_traffic(kernel) * alg_bytes / groups)),
-            "alg_ops_per_launch": per_launch_ops, "avg_launch_ms": round(dur * 1000, 4), "launch_groups": int(groups),
+            "traffic": (None if recorded_traffic(kernel) is None or not launches
+                        else round(recorded_traffic(kernel) * alg_bytes / launches)),
+            "alg_ops_per_launch": ops / launches if launches else 0,
+            "avg_launch_ms": round(ms / launches, 4) if launches else None, "launches": int(launches),
             "peak_source": "152 SMs x 128 int32 lanes x 2070 MHz (recipe unit counts and max clock)",
             "hbm_view": {"achieved": round(hbm_ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(hbm_ach / hbm, 4),
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "fallback" not in peaks else "fallback"},

@@ -288,14 +288,9 @@ int helr_ntt_inv(he_ctx *c, uint64_t *data, size_t nlimbs, const LimbMap &m, cud
 // out-of-place variants (in may equal out)
 int helr_ntt_fwd_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s);
 int helr_ntt_inv_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s);
-// forward transform of centred lifts: source limb b (coefficient form, at src + b * src_stride,
-// modulo prime src_prime) is lifted to every prime of dst and transformed; out is [nsrc][dst.period][N]
-int helr_ntt_lift_cols(he_ctx *c, const uint64_t *src, size_t src_stride, int src_prime, size_t nsrc, uint64_t *out,
-                       const LimbMap &dst, cudaStream_t s);
+// row pass of the inverse transform only (see ntt.cu)
 int helr_ntt_inv_rows(he_ctx *c, const uint64_t *in, size_t in_item, size_t in_poly, uint64_t *out, size_t nlimbs,
                       const LimbMap &m, cudaStream_t s);
-int helr_ntt_fwd_lifted(he_ctx *c, const uint64_t *src, size_t src_stride, int src_prime, size_t nsrc, uint64_t *out,
-                        const LimbMap &dst, cudaStream_t s);
 
 // elementwise / structural kernels (ops.cu)
 void k_add(he_ctx *c, uint64_t *out, const uint64_t *a, const uint64_t *b, size_t nlimbs, const LimbMap &m, int sub, cudaStream_t s);
@@ -309,9 +304,6 @@ void k_cadd_const(he_ctx *c, uint64_t *ct0, const uint64_t *kvals_dev, int batch
 void k_automorph(he_ctx *c, uint64_t *out, const uint64_t *in, size_t nlimbs, uint64_t gal, cudaStream_t s);
 void k_lift(he_ctx *c, const uint64_t *in, uint64_t *out, int batch, int src_prime, size_t in_stride,
             const LimbMap &dst, size_t out_stride, cudaStream_t s);
-void k_rescale_combine(he_ctx *c, uint64_t *out, const uint64_t *in, const uint64_t *corr, int batch,
-                       int level, size_t in_stride, size_t corr_stride, size_t out_stride,
-                       const uint64_t *inv_pairs, cudaStream_t s);
 
 // strided elementwise kernel: element (item b, poly p, limb j, k) of X lives at
 // X.p + b * X.item + p * X.poly + j * N + k (limb j reduced modulo q_j)

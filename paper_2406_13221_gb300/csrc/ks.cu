@@ -215,9 +215,9 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
     constexpr uint32_t TCOLS = 8 * E;  // a0[r]: columns 4r..4r+3; a1[r]: 4E + 4r..4E + 4r + 3
     static_assert(NT == 128 && E % CH == 0 && TCOLS >= 32 && TCOLS <= 128 && (TCOLS & (TCOLS - 1)) == 0, "TMEM layout");
     extern __shared__ uint64_t smem[];
-    __shared__ uint32_t tmem_slot;
-    uint64_t *buf = smem;                    // [2][TILE]: the rows of two digits (double buffer)
-    uint64_t *segs = smem + 2 * TILE;        // exchange segments
+    // [2][TILE]: the rows of two digits (double buffer); the rows of the digit
+    // being transformed also serve as its exchange segments once loaded
+    uint64_t *buf = smem;
     int bid = blockIdx.x;
     const int b = bid % items;  // items sharing one key row are adjacent: the key row is read from L2
     bid /= items;
@@ -230,7 +230,6 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
     const int l = threadIdx.x % G::T, rl = threadIdx.x / G::T, warp = threadIdx.x / 32;
     const int row = grp * RPC + rl;
     const size_t roff = (size_t)row * R2, toff = (size_t)grp * RPC * R2;
-    uint64_t *seg = segs + rl * G::SEG;
     // rows of digit i: the column-pass output for target t, or the input itself when i == t
     auto src_of = [&](int i) -> const uint64_t * {
         return i == t ? dntt + ((size_t)b * nl + i) * N + toff : mid + (((size_t)b * nl + i) * (nl + 1) + t) * N + toff;
@@ -243,13 +242,16 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
             cp_async16(dst + w, src + w);
         }
     };
-    if (warp == 0) tmem_alloc(&tmem_slot, TCOLS);
+    // the TMEM address is handed over in the second buffer, before its first use
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(buf + TILE);
+    if (warp == 0) tmem_alloc(tmem_slot, TCOLS);
     prefetch(0, buf);
     cp_async_commit();
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
-    const uint32_t tbase = tmem_slot + ((uint32_t)(32 * warp) << 16);
+    const uint32_t tbase = *tmem_slot + ((uint32_t)(32 * warp) << 16);
+    __syncthreads();  // every thread holds the address before the slot is overwritten
     uint64_t *o0 = acc + (((size_t)b * 2 + 0) * (nl + 1) + t) * N + roff + E * l;
     uint64_t *o1 = acc + (((size_t)b * 2 + 1) * (nl + 1) + t) * N + roff + E * l;
     for (int i = 0; i < nl; i++) {
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
         cp_async_wait<1>();  // digit i has landed
         __syncthreads();
         uint64_t x[E];
-        const uint64_t *rows = cur + rl * R2;
+        uint64_t *rows = cur + rl * R2;
         if (i == t) {
 #pragma unroll
             for (int r = 0; r < E; r++) x[r] = rows[E * l + r];
@@ -268,7 +270,8 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
             for (int r = 0; r < E; r++) x[r] = rows[l + G::T * r];
             const int A = R1 + row;
             fwd_strided<K2, LZ>(x, tw, A, q, q2);
-            to_contig<K2>(x, seg, l);
+            __syncthreads();  // every thread has read its words of the row
+            to_contig_swz<K2>(x, rows, l);
             fwd_contig<K2, true, LZ>(x, tw, A, l, q, q2);
             // words stay unreduced: below 4q, or below 20q with LZ (the column
             // pass leaves them below 4q)
@@ -323,13 +326,13 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
                 }
             }
         }
-        __syncthreads();  // buffer `cur` and the exchange segments are reused
+        __syncthreads();  // buffer `cur` is refilled two digits later
     }
     tmem_fence_before();
     __syncthreads();
     if (warp == 0) {
         tmem_fence_after();
-        tmem_dealloc(tmem_slot, TCOLS);
+        tmem_dealloc(tbase, TCOLS);  // warp 0's lane offset is 0: tbase is the allocation
     }
 }
 
@@ -407,7 +410,7 @@ struct KsPlan {
     static constexpr int RPCD = (256 / T2) < R1 ? (256 / T2) : R1;
     static constexpr size_t SMD = (size_t)RPCD * Geo<K2>::SEG * 8;
     static constexpr size_t SM1 = (size_t)C * Geo<K1>::SEG * 8 + (size_t)C * R1 * 8;
-    static constexpr size_t SM2 = (size_t)RPC * Geo<K2>::SEG * 8 + 2 * (size_t)RPC * R2 * 8;
+    static constexpr size_t SM2 = 2 * (size_t)RPC * R2 * 8;
     static cudaError_t prepare()
     {
         cudaError_t e = helr_fit_carveout((const void *)k_ks_modup_cols<K1, K2, C, false>, C * T1, SM1);

@@ -52,39 +52,6 @@ __global__ void __launch_bounds__(C * Geo<K1>::T) k_ntt_fwd_cols(const uint64_t 
     for (int r = 0; r < G::E; r++) out[base + (size_t)(G::E * l + r) * R2] = x[r];
 }
 
-// pass 1 with a centred lift on load: source limb b (coefficient form, modulo
-// prime src_prime) feeds targets t < nt (primes dst); output [b][t][N] holds
-// the column pass of the lifted limbs.  grid.x = nsrc * nt * (R2 / C).
-template <int K1, int K2, int C>
-__global__ void __launch_bounds__(C * Geo<K1>::T) k_ntt_lift_cols(const uint64_t *__restrict__ src, size_t src_stride,
-                                                                  uint64_t *__restrict__ out, int nt, int src_prime,
-                                                                  const uint64_t *__restrict__ twall, const ModQ *__restrict__ mods,
-                                                                  LimbMap dst)
-{
-    using G = Geo<K1>;
-    constexpr int R2 = 1 << K2, N = G::R * R2, NG = R2 / C;
-    extern __shared__ uint64_t smem[];
-    int bid = blockIdx.x;
-    const int t = bid % nt;
-    bid /= nt;
-    const int grp = bid % NG, b = bid / NG;
-    const int pt = map_prime(dst, t);
-    const ModQ mt = mods[pt];
-    const uint64_t qs = mods[src_prime].q, q = mt.q, q2 = 2 * q;
-    const uint64_t *tw = twall + (size_t)pt * N * 2;
-    const int jj = threadIdx.x % C, l = threadIdx.x / C;
-    const uint64_t *sp = src + (size_t)b * src_stride + grp * C + jj;
-    uint64_t *op = out + ((size_t)b * nt + t) * N + grp * C + jj;
-    uint64_t x[G::E];
-#pragma unroll
-    for (int r = 0; r < G::E; r++) x[r] = lift_centered(sp[(size_t)(l + G::T * r) * R2], qs, mt);
-    fwd_strided<K1>(x, tw, 1, q, q2);
-    to_contig<K1>(x, smem + jj * G::SEG, l);
-    fwd_contig<K1, false>(x, tw, 1, l, q, q2);
-#pragma unroll
-    for (int r = 0; r < G::E; r++) op[(size_t)(G::E * l + r) * R2] = x[r];
-}
-
 // pass 2: rows. grid.x = nlimbs * (R1 / RPC); block = RPC * T2 threads.
 template <int K1, int K2, int RPC>
 __global__ void __launch_bounds__(RPC * Geo<K2>::T) k_ntt_fwd_rows(uint64_t *__restrict__ data, const uint64_t *__restrict__ twall,
@@ -194,7 +161,6 @@ struct NttPlan {
     static cudaError_t prepare()
     {
         cudaError_t e = helr_fit_carveout((const void *)k_ntt_fwd_cols<K1, K2, C>, C * T1, SM1);
-        if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ntt_lift_cols<K1, K2, C>, C * T1, SM1);
         if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ntt_inv_cols<K1, K2, C>, C * T1, SM1);
         if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ntt_fwd_rows<K1, K2, RPC>, RPC * T2, SM2);
         if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ntt_inv_rows<K1, K2, RPC>, RPC * T2, SM2);
@@ -204,14 +170,6 @@ struct NttPlan {
     {
         HELR_LAUNCH(k_ntt_fwd_cols<K1, K2, C><<<(unsigned)(nlimbs * (R2 / C)), C * T1, SM1, s>>>(in, out, t.tw, t.mod, m));
         HELR_LAUNCH(k_ntt_fwd_rows<K1, K2, RPC><<<(unsigned)(nlimbs * (R1 / RPC)), RPC * T2, SM2, s>>>(out, t.tw, t.mod, m));
-    }
-    static void fwd_lifted(const uint64_t *src, size_t src_stride, int src_prime, size_t nsrc, uint64_t *out,
-                           const LimbMap &dst, const DevTables &t, cudaStream_t s)
-    {
-        const size_t nl = nsrc * dst.period;
-        HELR_LAUNCH(k_ntt_lift_cols<K1, K2, C><<<(unsigned)(nl * (R2 / C)), C * T1, SM1, s>>>(src, src_stride, out, dst.period,
-                                                                                          src_prime, t.tw, t.mod, dst));
-        HELR_LAUNCH(k_ntt_fwd_rows<K1, K2, RPC><<<(unsigned)(nl * (R1 / RPC)), RPC * T2, SM2, s>>>(out, t.tw, t.mod, dst));
     }
     static void inv_rows(const uint64_t *in, size_t in_item, size_t in_poly, uint64_t *out, size_t nlimbs, const DevTables &t,
                          const LimbMap &m, cudaStream_t s)
@@ -226,31 +184,6 @@ struct NttPlan {
         HELR_LAUNCH(k_ntt_inv_cols<K1, K2, C><<<(unsigned)(nlimbs * (R2 / C)), C * T1, SM1, s>>>(out, t.itw, t.mod, t.ninv, m));
     }
 };
-
-struct Lifted {
-    size_t src_stride;
-    int src_prime;
-};
-
-template <int K1, int K2>
-int run_lift_cols(he_ctx *c, const uint64_t *src, size_t src_stride, int src_prime, size_t nsrc, uint64_t *out,
-                  const LimbMap &dst, cudaStream_t s)
-{
-    static bool prepared = false;
-    if (!prepared) {
-        HELR_CUDA(c, (NttPlan<K1, K2>::prepare()));
-        prepared = true;
-    }
-    if (nsrc == 0) return HE_OK;
-    using P = NttPlan<K1, K2>;
-    const size_t nl = nsrc * dst.period;
-    prof_start(c, PROF_NTT_FWD, s);
-    HELR_LAUNCH(k_ntt_lift_cols<K1, K2, P::C><<<(unsigned)(nl * (P::R2 / P::C)), P::C * P::T1, P::SM1, s>>>(
-        src, src_stride, out, dst.period, src_prime, c->t.tw, c->t.mod, dst));
-    prof_stop(c, PROF_NTT_FWD, s, 0.5 * (double)nl, 1);  // the column half of each transform
-    HELR_CUDA(c, cudaGetLastError());
-    return HE_OK;
-}
 
 template <int K1, int K2>
 int run_inv_rows(he_ctx *c, const uint64_t *in, size_t in_item, size_t in_poly, uint64_t *out, size_t nlimbs,
@@ -270,8 +203,7 @@ int run_inv_rows(he_ctx *c, const uint64_t *in, size_t in_item, size_t in_poly, 
 }
 
 template <int K1, int K2>
-int run(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s, bool inverse,
-        const Lifted *lf = nullptr)
+int run(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s, bool inverse)
 {
     static bool prepared = false;
     if (!prepared) {
@@ -281,10 +213,7 @@ int run(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbM
     if (nlimbs == 0) return HE_OK;
     const int cls = inverse ? PROF_NTT_INV : PROF_NTT_FWD;
     prof_start(c, cls, s);
-    if (lf) {
-        NttPlan<K1, K2>::fwd_lifted(in, lf->src_stride, lf->src_prime, nlimbs, out, m, c->t, s);
-        nlimbs *= m.period;
-    } else if (inverse) {
+    if (inverse) {
         NttPlan<K1, K2>::inv(in, out, nlimbs, c->t, m, s);
     } else {
         NttPlan<K1, K2>::fwd(in, out, nlimbs, c->t, m, s);
@@ -294,18 +223,17 @@ int run(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbM
     return HE_OK;
 }
 
-int dispatch(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s, bool inv,
-             const Lifted *lf = nullptr)
+int dispatch(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s, bool inv)
 {
     if (nlimbs > (size_t)1 << 24) return helr_fail(c, HE_EINVAL, "too many limbs in one transform batch");
     switch (c->logn) {
-    case 10: return run<5, 5>(c, in, out, nlimbs, m, s, inv, lf);
-    case 11: return run<5, 6>(c, in, out, nlimbs, m, s, inv, lf);
-    case 12: return run<6, 6>(c, in, out, nlimbs, m, s, inv, lf);
-    case 13: return run<6, 7>(c, in, out, nlimbs, m, s, inv, lf);
-    case 14: return run<7, 7>(c, in, out, nlimbs, m, s, inv, lf);
-    case 15: return run<7, 8>(c, in, out, nlimbs, m, s, inv, lf);
-    case 16: return run<8, 8>(c, in, out, nlimbs, m, s, inv, lf);
+    case 10: return run<5, 5>(c, in, out, nlimbs, m, s, inv);
+    case 11: return run<5, 6>(c, in, out, nlimbs, m, s, inv);
+    case 12: return run<6, 6>(c, in, out, nlimbs, m, s, inv);
+    case 13: return run<6, 7>(c, in, out, nlimbs, m, s, inv);
+    case 14: return run<7, 7>(c, in, out, nlimbs, m, s, inv);
+    case 15: return run<7, 8>(c, in, out, nlimbs, m, s, inv);
+    case 16: return run<8, 8>(c, in, out, nlimbs, m, s, inv);
     default: return helr_fail(c, HE_EINVAL, "log_n %d unsupported", c->logn);
     }
 }
@@ -337,7 +265,9 @@ cudaError_t helr_fit_carveout(const void *f, int threads, size_t smem)
     int own = std::min(regs_sm / std::max(1, warp_regs * ((threads + 31) / 32)), thr_sm / threads);
     own = std::min(own, (int)((size_t)maxsm / per_cta));
     blocks = std::max(blocks, own);
-    int pct = (int)(((size_t)blocks * per_cta * 100 + (size_t)maxsm - 1) / (size_t)maxsm);
+    // rounded down: the driver takes the supported configuration at or just
+    // above the requested share, and the configurations are coarser than 1%
+    int pct = (int)((size_t)blocks * per_cta * 100 / (size_t)maxsm);
     pct = pct < 1 ? 1 : pct > 100 ? 100 : pct;
     return cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
 }
@@ -358,23 +288,6 @@ int helr_ntt_inv_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs
 {
     return dispatch(c, in, out, nlimbs, m, s, true);
 }
-// the column pass of helr_ntt_fwd_lifted only (the row pass is left to a
-// consumer that reads whole rows)
-int helr_ntt_lift_cols(he_ctx *c, const uint64_t *src, size_t src_stride, int src_prime, size_t nsrc, uint64_t *out,
-                       const LimbMap &dst, cudaStream_t s)
-{
-    switch (c->logn) {
-    case 10: return run_lift_cols<5, 5>(c, src, src_stride, src_prime, nsrc, out, dst, s);
-    case 11: return run_lift_cols<5, 6>(c, src, src_stride, src_prime, nsrc, out, dst, s);
-    case 12: return run_lift_cols<6, 6>(c, src, src_stride, src_prime, nsrc, out, dst, s);
-    case 13: return run_lift_cols<6, 7>(c, src, src_stride, src_prime, nsrc, out, dst, s);
-    case 14: return run_lift_cols<7, 7>(c, src, src_stride, src_prime, nsrc, out, dst, s);
-    case 15: return run_lift_cols<7, 8>(c, src, src_stride, src_prime, nsrc, out, dst, s);
-    case 16: return run_lift_cols<8, 8>(c, src, src_stride, src_prime, nsrc, out, dst, s);
-    default: return helr_fail(c, HE_EINVAL, "log_n %d unsupported", c->logn);
-    }
-}
-
 // the row pass of the inverse transform only: the column pass (K1 stages, the
 // factor N^-1) is left to a consumer that reads whole columns.  Input limb k is
 // read at in + (k / 2) in_item + (k % 2) in_poly; output limbs are contiguous.
@@ -392,10 +305,4 @@ int helr_ntt_inv_rows(he_ctx *c, const uint64_t *in, size_t in_item, size_t in_p
     case 16: return run_inv_rows<8, 8>(c, in, in_item, in_poly, out, nlimbs, m, s);
     default: return helr_fail(c, HE_EINVAL, "log_n %d unsupported", c->logn);
     }
-}
-int helr_ntt_fwd_lifted(he_ctx *c, const uint64_t *src, size_t src_stride, int src_prime, size_t nsrc, uint64_t *out,
-                        const LimbMap &dst, cudaStream_t s)
-{
-    const Lifted lf{src_stride, src_prime};
-    return dispatch(c, src, out, nsrc, dst, s, false, &lf);
 }

@@ -167,4 +167,22 @@ __device__ __forceinline__ void to_strided(uint64_t (&x)[Geo<K>::E], uint64_t *s
     for (int r = 0; r < E; r++) x[r] = seg[spad<LE>(l + T * r)];
 }
 
+// The same exchange inside an unpadded row segment of R words: word w lives at
+// w ^ ((w >> 4) & 15) (the low four bits XORed with the next four, within its
+// 16-word block).  For the 64-bit words of a row held by 16 threads (one
+// half-warp) both access patterns, l + T r and E l + r, then fall into 16
+// distinct bank pairs.  The caller synchronises before the first write when the
+// segment still holds data other threads are reading.
+__device__ __forceinline__ int swz(int w) { return w ^ ((w >> 4) & 15); }
+template <int K>
+__device__ __forceinline__ void to_contig_swz(uint64_t (&x)[Geo<K>::E], uint64_t *seg, int l)
+{
+    constexpr int E = Geo<K>::E, T = Geo<K>::T;
+#pragma unroll
+    for (int r = 0; r < E; r++) seg[swz(l + T * r)] = x[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < E; r++) x[r] = seg[swz(E * l + r)];
+}
+
 }  // namespace nttc

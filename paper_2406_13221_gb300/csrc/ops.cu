@@ -130,22 +130,6 @@ __global__ void k_lift_kernel(const uint64_t *in, uint64_t *out, int n, int src_
     out[bt * out_stride + (size_t)t * n + k] = lift_centered(in[bt * in_stride + k], mods[src_prime].q, mt);
 }
 
-// out[b][j][k] = (in[b][j][k] - corr[b][j][k]) * inv_j mod q_j, j < nl; grid (N/2 / 256, nl, items)
-__global__ void k_combine_kernel(uint64_t *out, const uint64_t *in, const uint64_t *corr, int half_n, size_t in_stride,
-                                 size_t corr_stride, size_t out_stride, const uint64_t *inv, const ModQ *mods)
-{
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= half_n) return;
-    const int j = blockIdx.y;
-    const size_t bt = blockIdx.z, r = (size_t)j * half_n + w;
-    const uint64_t q = mods[j].q, wv = inv[2 * j], wp = inv[2 * j + 1];
-    ulonglong2 x = reinterpret_cast<const ulonglong2 *>(in + bt * in_stride)[r];
-    ulonglong2 y = reinterpret_cast<const ulonglong2 *>(corr + bt * corr_stride)[r];
-    ulonglong2 z;
-    z.x = shoup(submod(x.x, y.x, q), wv, wp, q);
-    z.y = shoup(submod(x.y, y.y, q), wv, wp, q);
-    reinterpret_cast<ulonglong2 *>(out + bt * out_stride)[r] = z;
-}
 
 // grid: (N/2 / 256, npoly * nl, items)
 __global__ void k_ew_kernel(int op, Str out, Str a, Str b, int half_n, int nl, const KP kp, const ModQ *mods)
@@ -259,11 +243,4 @@ void k_lift(he_ctx *c, const uint64_t *in, uint64_t *out, int batch, int src_pri
 {
     dim3 grid((c->n + 255) / 256, dst.period, batch);
     if (batch) HELR_LAUNCH(k_lift_kernel<<<grid, 256, 0, s>>>(in, out, c->n, src_prime, in_stride, out_stride, c->t.mod, dst));
-}
-void k_rescale_combine(he_ctx *c, uint64_t *out, const uint64_t *in, const uint64_t *corr, int batch, int nl,
-                       size_t in_stride, size_t corr_stride, size_t out_stride, const uint64_t *inv_pairs, cudaStream_t s)
-{
-    const int hn = c->n / 2;
-    dim3 grid((hn + 255) / 256, nl, batch);
-    if (batch) HELR_LAUNCH(k_combine_kernel<<<grid, 256, 0, s>>>(out, in, corr, hn, in_stride, corr_stride, out_stride, inv_pairs, c->t.mod));
 }
