@@ -8,7 +8,9 @@ decrypted weights of an encrypted run must stay within 1e-3 of this run.
 
 With ``sigmoid='exact'`` the logistic function replaces the polynomial; that
 mode exists to pin the algorithm (gradient sign and normalisation, update
-order) against an independent logistic-regression solver.
+order) against an independent logistic-regression solver.  With
+``first_order=True`` the update is the first-order NAG baseline of Sec. 2.3,
+w' = v + gamma (1/n) g, gamma taken from the schedule (constant when max = min).
 """
 import math
 
@@ -34,7 +36,7 @@ def gradient(w, Z, sigmoid="poly", poly=G8):
 
 
 def train(data, iters, mode="full", sched=(2.0, 1.0, 81.0, 2.5), sigmoid="poly",
-          poly=G8, trace=False):
+          poly=G8, trace=False, first_order=False):
     """Returns W (length g) after `iters` iterations; with trace=True also the
     list of (W, V) after each iteration."""
     g = data.g
@@ -52,7 +54,7 @@ def train(data, iters, mode="full", sched=(2.0, 1.0, 81.0, 2.5), sigmoid="poly",
             nbb, inv_n = float(data.n_k[k]) * data.bbar_k[k], 1.0 / float(data.n_k[k])
         grad = np.zeros(g)
         grad[:data.f1] = alpha * gradient(W[:data.f1], Zr, sigmoid, poly)
-        G = nbb * grad * inv_n
+        G = (grad if first_order else nbb * grad) * inv_n
         eta = etas[t]
         Vt = W + G
         W = (1.0 - eta) * Vt + eta * V

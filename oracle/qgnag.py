@@ -27,6 +27,10 @@ Readings where the paper is silent or ambiguous:
   * The sigmoid term is s = F2(t) * (1 - g(ip)) with the polynomial g printed in
     Sec. 4.1, evaluated at depth 2: ip^2 and (k3 ip) in parallel, then their product.
   * t starts at 0; mini-batches are visited in order 0, 1, 2, ... without shuffling.
+  * First-order NAG baseline (Sec. 2.3, the method the paper compares against):
+    the same circuit without the Bbar product (Step 8), so one level less; its
+    learning rate gamma multiplies the sigmoid term where QG-NAG puts F2(t)
+    (a constant schedule max = min = gamma), and V' = W + (1/n) gamma g.
 """
 import math
 
@@ -131,6 +135,7 @@ class TrainData:
 
 # ------------------------------------------------------------------ encrypted iteration
 DEPTH = 7  # levels one iteration consumes
+DEPTH_FIRST_ORDER = 6  # without the Bbar product of Step 8
 
 
 class Circuit:
@@ -138,15 +143,18 @@ class Circuit:
 
     Levels: fresh inputs sit at level L (default: the iteration depth, 7, so the
     iteration ends at level 0; any higher primes of the chain stay unused); the
-    iteration consumes 7 levels and ends at level L - 7."""
+    iteration consumes 7 levels and ends at level L - 7.  With first_order=True
+    the circuit is the first-order NAG baseline: no Bbar product, depth 6."""
 
-    def __init__(self, he: Ckks, g, m, scale, poly=G8, start_level=None):
+    def __init__(self, he: Ckks, g, m, scale, poly=G8, start_level=None, first_order=False):
         self.he, self.g, self.m, self.scale, self.poly = he, g, m, float(scale), poly
+        self.first_order = first_order
+        depth = DEPTH_FIRST_ORDER if first_order else DEPTH
         if g * m != he.nslots:
             raise ValueError("m * g must equal N/2")
-        self.L = min(DEPTH, he.max_level) if start_level is None else start_level
-        if self.L < DEPTH or self.L > he.max_level:
-            raise ValueError("the iteration needs 7 levels")
+        self.L = min(depth, he.max_level) if start_level is None else start_level
+        if self.L < depth or self.L > he.max_level:
+            raise ValueError("the iteration needs %d levels" % depth)
         self.lg, self.lm = int(math.log2(g)), int(math.log2(m))
         mask = np.zeros(he.nslots)
         mask[::g] = 1.0
@@ -201,8 +209,8 @@ class Circuit:
         # Step 7: column sums, every row gets g_c
         for k in range(self.lm):
             acc = he.add(acc, he.rotate(acc, self.g << k))
-        # Step 8: n Bbar_c g_c
-        nG = he.rescale(he.mul(acc, he.moddrop(B, acc.level)))
+        # Step 8: n Bbar_c g_c (the first-order baseline uses g_c itself)
+        nG = acc if B is None else he.rescale(he.mul(acc, he.moddrop(B, acc.level)))
         # Step 9: V' = W + G, W' = (1 - eta) V' + eta V
         lv = nG.level
         tgt = W.scale
@@ -248,7 +256,8 @@ def train(he, circ, data, iters, enc_seed, mode="full", sched=(2.0, 1.0, 81.0, 2
     else:
         bvec = [np.tile(float(data.n_k[k]) * data.bbar_k[k], circ.m) for k in range(data.nbatch)]
         inv_ns = [1.0 / float(data.n_k[k]) for k in range(data.nbatch)]
-    Bct = [he.encrypt(he.encode(v, L, scale), obj_seed(enc_seed, SEED_BBAR, k)) for k, v in enumerate(bvec)]
+    Bct = ([None] * len(bvec) if circ.first_order else
+           [he.encrypt(he.encode(v, L, scale), obj_seed(enc_seed, SEED_BBAR, k)) for k, v in enumerate(bvec)])
     zero = np.zeros(he.nslots)
     W = he.encrypt(he.encode(zero, L, scale), obj_seed(enc_seed, SEED_W0, 0))
     V = he.encrypt(he.encode(zero, L, scale), obj_seed(enc_seed, SEED_V0, 0))

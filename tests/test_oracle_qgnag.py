@@ -164,3 +164,45 @@ def test_encrypted_minibatch_mode_matches_fp64_twin():
     w = qgnag.train(he, circ, data, 3, enc_seed=9, mode="mini", sched=sched)
     wp = plain.train(data, 3, mode="mini", sched=sched, poly=qgnag.G16)
     assert np.abs(w - wp[None, :]).max() < 1e-3
+
+
+def test_first_order_step_closed_form():
+    """Sec. 2.3 first-order NAG from W0 = V0 = 0: V1 = (gamma/n) sum_i (1 - g8(0)) z_i
+    with g8(0) = 1/2, W1 = (1 - eta_0) V1."""
+    X, y = synth.small(seed=5, n=300, f=6)
+    data = qgnag.TrainData(X, y, g=8, m=128, batch_rows=1024)
+    lr = 0.7
+    W1, hist = plain.train(data, 1, sched=(lr, lr, 81.0, 2.5), trace=True, first_order=True)
+    V1 = np.zeros(8)
+    V1[:7] = lr * 0.5 * data.Z.mean(axis=0)
+    eta0 = qgnag.nag_scalars(1)[0]
+    assert np.allclose(hist[0][1], V1, atol=1e-15)
+    assert np.allclose(W1, (1 - eta0) * V1, atol=1e-15)
+
+
+def test_first_order_twin_converges_to_independent_mle():
+    """With the exact sigmoid and a constant rate, first-order NAG reaches the
+    maximiser that scipy's BFGS finds (pins sign and 1/n normalisation)."""
+    X, y = synth.small(seed=4, n=1024, f=7)
+    data = qgnag.TrainData(X, y, g=8, m=128, batch_rows=1024)
+    W = plain.train(data, 400, sigmoid="exact", sched=(2.0, 2.0, 81.0, 2.5), first_order=True)
+    res = minimize(lambda w: -plain.loglik(w, data.Z), np.zeros(8), method="BFGS",
+                   jac=lambda w: -plain.gradient(w, data.Z, "exact") / data.n, tol=1e-12)
+    assert np.abs(W - res.x).max() < 1e-5
+
+
+def test_encrypted_first_order_matches_fp64_twin():
+    """The first-order circuit (no Bbar product, depth 6) against its FP64 twin."""
+    X, y = synth.small(seed=6, n=1024, f=15)
+    he = Ckks(13, 9)
+    data = qgnag.TrainData(X, y, g=16, m=256, batch_rows=1024)
+    circ = qgnag.Circuit(he, 16, 256, 2.0 ** 40, first_order=True)
+    assert circ.L == qgnag.DEPTH_FIRST_ORDER == 6
+    he.keygen(2, circ.rotations())
+    sched = (1.0, 1.0, 81.0, 2.5)
+    w, trace = qgnag.train(he, circ, data, 2, enc_seed=4, sched=sched, return_trace=True)
+    assert trace[0][0].level == 0
+    wp = plain.train(data, 2, sched=sched, first_order=True)
+    assert np.abs(w - wp[None, :]).max() < 1e-3
+    # the first-order and quadratic-gradient updates differ (Bbar is not the identity)
+    assert np.abs(wp - plain.train(data, 2, sched=sched)).max() > 1e-3
