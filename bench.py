@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-twin", action="store_true")
     ap.add_argument("--no-mini", action="store_true")
     ap.add_argument("--no-multi", action="store_true")
+    ap.add_argument("--no-first-order", action="store_true")
     ap.add_argument("--sweep-point", default="", help="log_n,limbs,batch: run only this NTT sweep point")
     ap.add_argument("--sweep", action="store_true",
                     help="HE primitive sweep: batched NTT and key switching vs N, limbs and batch (JSON line per point)")
@@ -210,11 +211,14 @@ def run_ours(args, rank, world):
     mini = None
     if not args.no_mini:
         mini = minibatch_time(ctx, X, y, args)
-    multi = None
-    if not args.no_multi and world == 1:
+    multi = first = None
+    if world == 1 and not (args.no_multi and args.no_first_order):
         job.close()
         del job
-        multi = multijob_time(ctx)
+        if not args.no_first_order:
+            first = first_order_time(ctx, X, y, args)
+        if not args.no_multi:
+            multi = multijob_time(ctx)
     roof = roofline(prof, args.steps)
     out = {
         "metric": METRIC, "value": round(sec_iter, 5), "unit": "s/iter", "n_gpus": world, "steps": args.steps,
@@ -231,6 +235,7 @@ def run_ours(args, rank, world):
         "plain_one_ct_per_launch_s_per_iter": round(plain, 4) if plain else None,
         "mini_batch": mini,
         "multi_job": multi,
+        "first_order_nag": first,
         "batched_speedup_vs_plain": round(plain / sec_iter / world, 2) if plain else None,
         "setup_s": round(setup_s, 1),
         "max_abs_err_vs_fp64_twin": err,
@@ -270,6 +275,30 @@ def minibatch_time(ctx, X, y, args):
     out["keyswitches_per_iter"] = int(job.stats().keyswitches)
     out["batched_speedup_vs_plain"] = round(out["plain_s_per_iter"] / out["batched_s_per_iter"], 2)
     out["batched_graph_speedup_vs_plain"] = round(out["plain_s_per_iter"] / out["batched_graph_s_per_iter"], 2)
+    job.close()
+    return out
+
+
+def first_order_time(ctx, X, y, args):
+    """The first-order NAG baseline (Sec. 2.3: no Bbar product, one level less)
+    on the same full-batch workload at the rate of the paper's first-order
+    Financial run (0.01, constant): seconds per iteration over 2 iterations
+    after one warm-up iteration."""
+    import torch
+    from paper_2406_13221_gb300 import binding
+    job = binding.Job(ctx, X, y, binding.FULL_BATCH | binding.FIRST_ORDER, 1024, binding.G8, LOG_SCALE, enc_seed=3,
+                      key_seed=2, batch_blocks=args.chunk)
+    sched = (0.01, 0.01, 81.0, 2.5)
+    job.step(0, sched)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for t in range(1, 3):
+        job.step(t, sched)
+    e1.record()
+    torch.cuda.synchronize()
+    out = {"s_per_iter": round(e0.elapsed_time(e1) / 2 / 1000.0, 5), "keyswitches_per_iter": int(job.stats().keyswitches),
+           "start_level": 6, "rate": 0.01}
     job.close()
     return out
 

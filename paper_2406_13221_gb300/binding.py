@@ -17,6 +17,7 @@ HE_OK, HE_EINVAL, HE_ENOMEM, HE_ELEVEL, HE_ESCALE, HE_ECUDA, HE_ETIMEOUT, HE_EIN
 CODES = {1: "HE_EINVAL", 2: "HE_ENOMEM", 3: "HE_ELEVEL", 4: "HE_ESCALE", 5: "HE_ECUDA",
          6: "HE_ETIMEOUT", 7: "HE_EINTERNAL", 8: "HE_EKEY"}
 FULL_BATCH, MINI_BATCH = 0, 1
+FIRST_ORDER = 0x100  # OR into the mode: the first-order NAG baseline (no Bbar)
 G8, G16 = 0, 1
 
 
@@ -421,7 +422,8 @@ def lr_iteration(ctx, Z, B, W, V, g, m, alpha, eta, inv_n, poly):
     arr = (ctypes.c_void_p * len(Z))(*[z.h.value for z in Z])
     p = np.asarray(poly, np.float64)
     Wo, Vo = ctypes.c_void_p(), ctypes.c_void_p()
-    ctx.check(ctx.L.he_lr_iteration(ctx.h, arr, len(Z), B.h, W.h, V.h, g, m, float(alpha), float(eta),
+    bh = B.h if B is not None else None  # None: the first-order baseline
+    ctx.check(ctx.L.he_lr_iteration(ctx.h, arr, len(Z), bh, W.h, V.h, g, m, float(alpha), float(eta),
                                     float(inv_n), _ptr(p), ctypes.byref(Wo), ctypes.byref(Vo)))
     return Ct(ctx, Wo), Ct(ctx, Vo)
 

@@ -29,6 +29,7 @@ static const double G8[3] = {0.5, 0.15, -0.0015};
 static const double G16[3] = {0.5, 0.0843, -0.0002};
 static const double BBAR_EPS = 1e-8;
 static const int ITER_DEPTH = 7;  // levels one iteration consumes
+static const int ITER_DEPTH_FO = 6;  // the first-order baseline: no Bbar product
 
 static uint64_t obj_seed(uint64_t base, uint64_t kind, uint64_t index) { return base + (kind << 48) + index; }
 
@@ -66,7 +67,8 @@ extern "C" int he_lr_bbar(const double *X, const double *y, size_t n, size_t f, 
 // ------------------------------------------------------------------ job
 struct he_lr_job {
     he_ctx *c;
-    int mode;
+    int mode;                   // HE_LR_FULL_BATCH or HE_LR_MINI_BATCH
+    bool first_order;           // first-order NAG baseline: no Bbar, depth 6
     double poly[3];
     size_t n, f;
     int g, m, lg, lm, L;
@@ -76,7 +78,7 @@ struct he_lr_job {
     uint64_t enc_seed;
     size_t ctw;                 // words per top-level ciphertext
     uint64_t *Z;                // [nblocks][2][L+1][N]
-    std::vector<he_ct *> B;     // Enc(n Bbar) per mini-batch, or one for the full batch
+    std::vector<he_ct *> B;     // Enc(n Bbar) per mini-batch, or one for the full batch (none first-order)
     std::vector<double> inv_n;
     he_ct *W, *V;
     uint64_t *mask;             // plaintext M at level L-1, scale q_(L-1), evaluation form
@@ -154,15 +156,17 @@ extern "C" int he_lr_job_create(he_ctx *c, const double *X, const double *y, siz
                                 size_t batch_rows, int poly, double log_scale, uint64_t enc_seed, uint64_t key_seed,
                                 int batch_blocks, he_lr_job **out)
 {
+    const bool fo = (mode & HE_LR_FIRST_ORDER) != 0;
+    mode &= ~HE_LR_FIRST_ORDER;
     if (!c || !X || !y || !out || n == 0 || f == 0 || (mode != HE_LR_FULL_BATCH && mode != HE_LR_MINI_BATCH) ||
         (poly != HE_LR_G8 && poly != HE_LR_G16) || !(log_scale > 0 && log_scale < 62))
         return HE_EINVAL;
     *out = nullptr;
     auto t0 = std::chrono::steady_clock::now();
     // fresh ciphertexts sit at the iteration depth: the iteration ends at level 0
-    // and any primes of the chain above level 7 stay unused
-    const int L = ITER_DEPTH;
-    if (c->nq - 1 < L) return helr_fail(c, HE_ELEVEL, "the iteration needs 7 levels (n_q >= 8)");
+    // and any primes of the chain above it stay unused
+    const int L = fo ? ITER_DEPTH_FO : ITER_DEPTH;
+    if (c->nq - 1 < L) return helr_fail(c, HE_ELEVEL, "the iteration needs %d levels (n_q >= %d)", L, L + 1);
     int g = 1;
     while ((size_t)g < f + 1) g <<= 1;
     if (g > c->nslots) return helr_fail(c, HE_EINVAL, "too many features for N/2 slots");
@@ -173,6 +177,7 @@ extern "C" int he_lr_job_create(he_ctx *c, const double *X, const double *y, siz
     he_lr_job *j = new he_lr_job();
     j->c = c;
     j->mode = mode;
+    j->first_order = fo;
     memcpy(j->poly, poly == HE_LR_G8 ? G8 : G16, sizeof j->poly);
     j->n = n;
     j->f = f;
@@ -212,9 +217,10 @@ extern "C" int he_lr_job_create(he_ctx *c, const double *X, const double *y, siz
         row[0] = y[r];
         for (size_t k = 0; k < f; k++) row[k + 1] = y[r] * X[r * f + k];
     }
-    // Bbar per mini-batch (threads over batches), full batch by 1 / sum_k (1 / Bbar_k)
-    std::vector<double> bk((size_t)j->nbatch * g);
-    {
+    // Bbar per mini-batch (threads over batches), full batch by 1 / sum_k (1 / Bbar_k);
+    // the first-order baseline needs only the 1/n scalars
+    std::vector<double> bk(fo ? 0 : (size_t)j->nbatch * g);
+    if (!fo) {
         unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
         std::vector<std::thread> th;
         for (unsigned t = 0; t < nth; t++)
@@ -227,7 +233,13 @@ extern "C" int he_lr_job_create(he_ctx *c, const double *X, const double *y, siz
         for (auto &x : th) x.join();
     }
     std::vector<std::vector<double>> bvec;
-    if (mode == HE_LR_FULL_BATCH) {
+    if (fo) {
+        if (mode == HE_LR_FULL_BATCH)
+            j->inv_n.push_back(1.0 / (double)n);
+        else
+            for (int k = 0; k < j->nbatch; k++)
+                j->inv_n.push_back(1.0 / (double)std::min(batch_rows, n - (size_t)k * batch_rows));
+    } else if (mode == HE_LR_FULL_BATCH) {
         std::vector<double> full(g, 0.0);
         for (size_t a = 0; a <= f; a++) {
             double s = 0.0;
@@ -452,12 +464,16 @@ static int finish_ws(const WorkSet &ws, CtB acc, const he_ct *Bct, const he_ct *
         HELR_TRY(ev_rotate_acc(ev, acc, (int64_t)g << k, R, 1));
         std::swap(acc, R);
     }
-    // 8
-    CtB Bv{Bct->d, 1, Bct->level, Bct->scale, 0};
-    HELR_TRY(ev_moddrop(ev, Bv, acc.level, Bd));
-    HELR_TRY(ev_mul_relin(ev, acc, Bd, A));
+    // 8: n Bbar_c g_c; the first-order baseline (no Bbar) takes g_c itself
     CtB nG{ws.T[3], 1, 0, 0, w};
-    HELR_TRY(ev_rescale(ev, A, nG));
+    if (Bct) {
+        CtB Bv{Bct->d, 1, Bct->level, Bct->scale, 0};
+        HELR_TRY(ev_moddrop(ev, Bv, acc.level, Bd));
+        HELR_TRY(ev_mul_relin(ev, acc, Bd, A));
+        HELR_TRY(ev_rescale(ev, A, nG));
+    } else {
+        HELR_TRY(ev_moddrop(ev, acc, acc.level, nG));  // a copy out of the buffers Step 9 reuses
+    }
     // 9
     const int lv = nG.level;
     const double tgt = W->scale;
@@ -527,7 +543,7 @@ static int job_update(he_lr_job *j, int t, const he_lr_sched &sched, CtB &Wn, Ct
     CtB acc{j->acc, 1, glevel, gscale, 0};
     Wn = CtB{j->acc + j->ctw, 1, 0, 0, 0};
     Vn = CtB{j->acc + 2 * j->ctw, 1, 0, 0, 0};
-    return finish(j, acc, j->B[k], eta, j->inv_n[k], Wn, Vn);
+    return finish(j, acc, j->first_order ? nullptr : j->B[k], eta, j->inv_n[k], Wn, Vn);
 }
 
 // Steps 1-9 recorded into a CUDA graph on the job's stream and launched as one unit
@@ -726,10 +742,11 @@ extern "C" int he_lr_iteration(he_ctx *c, he_ct *const *Z, size_t nb, const he_c
                                int m, double alpha, double eta, double inv_n, const double poly[3], he_ct **W_out,
                                he_ct **V_out)
 {
-    if (!c || !Z || !nb || !B || !W || !V || !poly || !W_out || !V_out || g * m != c->nslots || (g & (g - 1)) || g < 1)
+    if (!c || !Z || !nb || !W || !V || !poly || !W_out || !V_out || g * m != c->nslots || (g & (g - 1)) || g < 1)
         return HE_EINVAL;
     const int L = W->level;
-    if (L < ITER_DEPTH) return helr_fail(c, HE_ELEVEL, "the iteration needs 7 levels");
+    const int depth = B ? ITER_DEPTH : ITER_DEPTH_FO;  // no B: the first-order baseline
+    if (L < depth) return helr_fail(c, HE_ELEVEL, "the iteration needs %d levels", depth);
     for (size_t i = 0; i < nb; i++)
         if (Z[i]->level != L) return helr_fail(c, HE_ELEVEL, "data blocks must share the level of W");
     // a temporary job around the caller's ciphertexts
@@ -786,8 +803,8 @@ extern "C" int he_lr_iteration(he_ctx *c, he_ct *const *Z, size_t nb, const he_c
             glevel = gg.level;
         }
         if (rc) goto out;
-        if ((rc = helr_new_ct(c, L - ITER_DEPTH, 0, &Wo))) goto out;
-        if ((rc = helr_new_ct(c, L - ITER_DEPTH, 0, &Vo))) goto out;
+        if ((rc = helr_new_ct(c, L - depth, 0, &Wo))) goto out;
+        if ((rc = helr_new_ct(c, L - depth, 0, &Vo))) goto out;
         CtB acc{j.acc, 1, glevel, gscale, 0};
         CtB Wn{Wo->d, 1, 0, 0, 0}, Vn{Vo->d, 1, 0, 0, 0};
         if ((rc = finish(&j, acc, B, eta, inv_n, Wn, Vn))) goto out;
@@ -868,8 +885,9 @@ extern "C" int he_lr_multi_create(he_ctx *c, he_lr_job *const *jobs, size_t njob
         const he_lr_job *j = jobs[i];
         if (!j || j->c != c) return helr_fail(c, HE_EINVAL, "job %zu belongs to another context", i);
         if (j->mode != HE_LR_FULL_BATCH) return helr_fail(c, HE_EINVAL, "job %zu is not a full-batch job", i);
-        if (j->L != jobs[0]->L || j->scale0 != jobs[0]->scale0 || memcmp(j->poly, jobs[0]->poly, sizeof j->poly))
-            return helr_fail(c, HE_EINVAL, "job %zu differs from job 0 in level, scale or polynomial", i);
+        if (j->L != jobs[0]->L || j->scale0 != jobs[0]->scale0 || memcmp(j->poly, jobs[0]->poly, sizeof j->poly) ||
+            j->first_order != jobs[0]->first_order)
+            return helr_fail(c, HE_EINVAL, "job %zu differs from job 0 in level, scale, polynomial or method", i);
     }
     he_lr_multi *m = new he_lr_multi();
     m->c = c;
@@ -936,7 +954,7 @@ extern "C" int he_lr_multi_step(he_lr_multi *m, int t, he_lr_sched sched)
         he_lr_job *j = m->jobs[jb];
         CtB acc{m->accs + jb * m->ctw, 1, glevel, gscale, 0};
         CtB Wn{m->wv, 1, 0, 0, 0}, Vn{m->wv + m->ctw, 1, 0, 0, 0};
-        HELR_TRY(finish_ws(ws, acc, j->B[0], j->W, j->V, j->g, j->lm, eta, j->inv_n[0], Wn, Vn));
+        HELR_TRY(finish_ws(ws, acc, j->first_order ? nullptr : j->B[0], j->W, j->V, j->g, j->lm, eta, j->inv_n[0], Wn, Vn));
         HELR_TRY(refresh_dev(c, Wn.d, Wn.level, Wn.scale, j->L, j->scale0, obj_seed(j->enc_seed, 5, t), j->W->d));
         HELR_TRY(refresh_dev(c, Vn.d, Vn.level, Vn.scale, j->L, j->scale0, obj_seed(j->enc_seed, 6, t), j->V->d));
         j->W->scale = j->V->scale = j->scale0;

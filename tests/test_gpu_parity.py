@@ -282,6 +282,46 @@ def test_job_step_bitwise_and_weights(small_job_inputs, graph):
         assert np.abs(job.weights(row) - wp).max() < 1e-3
 
 
+def test_first_order_job_bitwise(pair):
+    """The first-order NAG baseline (no Bbar product, fresh ciphertexts at level
+    6): job state word for word against the oracle's first-order circuit, the
+    cloud-only iteration with no Bbar likewise, weights against the FP64 twin."""
+    ctx, he = pair
+    X, y = synth.small(seed=12, n=1024, f=15)
+    data = qgnag.TrainData(X, y, g=16, m=256, batch_rows=1024)
+    circ = qgnag.Circuit(he, 16, 256, D, first_order=True)  # its rotations are among the fixture's keys
+    job = binding.Job(ctx, X, y, binding.FULL_BATCH | binding.FIRST_ORDER, 1024, binding.G8, 40.0, enc_seed=5,
+                      key_seed=2)
+    L = circ.L
+    assert L == 6
+    with pytest.raises(binding.HeError):
+        job.input(1, 0)  # no Bbar ciphertext in a first-order job
+    Z = [OCt(job.input(0, b).export(), L, D) for b in range(4)]
+    (Ww, lw, _), (Vw, _, _) = job.state_words()
+    assert lw == L
+    W, V = OCt(Ww, L, D), OCt(Vw, L, D)
+    sched = (1.0, 1.0, 81.0, 2.5)
+    etas = qgnag.nag_scalars(2)
+    for t in range(2):
+        if t == 1:  # the cloud-only entry point on the same inputs
+            imp = lambda c: ctx.import_ct(c.data, c.level, c.scale)  # noqa: E731
+            gW, gV = binding.lr_iteration(ctx, [imp(z) for z in Z], None, imp(W), imp(V), 16, 256,
+                                          qgnag.schedule(t, *sched), etas[t], 1.0 / data.n, qgnag.G8)
+        job.step(t, sched)
+        Wn, Vn = circ.iteration(Z, None, W, V, qgnag.schedule(t, *sched), etas[t], 1.0 / data.n)
+        assert Wn.level == 0
+        if t == 1:
+            assert np.array_equal(gW.export(), Wn.data) and np.array_equal(gV.export(), Vn.data)
+        W = circ.refresh(Wn, qgnag.obj_seed(5, qgnag.SEED_WREF, t))
+        V = circ.refresh(Vn, qgnag.obj_seed(5, qgnag.SEED_VREF, t))
+        (Ww, _, _), (Vw, _, _) = job.state_words()
+        assert np.array_equal(Ww, W.data), t
+        assert np.array_equal(Vw, V.data), t
+    from oracle import plain
+    wp = plain.train(data, 2, sched=sched, first_order=True)
+    assert np.abs(job.weights(0) - wp).max() < 1e-3
+
+
 def test_minibatch_job_bitwise(pair):
     """Algorithm 1 over 3 mini-batches of 1,024 rows (the last one ragged: 952
     rows), 4 iterations so batch 0 is revisited; the g16 polynomial."""
