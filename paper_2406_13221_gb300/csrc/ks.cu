@@ -85,6 +85,13 @@ __global__ void __launch_bounds__(C * Geo<K1>::T, 3)
     }
 }
 
+// bulk prefetch of `bytes` (a multiple of 16) from a 16-byte aligned global
+// address into L2 (no data returned to the thread)
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // read-only load that does not allocate in L1
 __device__ __forceinline__ uint64_t ld_stream(const uint64_t *p)
 {
@@ -365,6 +372,16 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T)
     const uint64_t q = mods[j].q, q2 = 2 * q;
     const uint64_t *tw = twall + (size_t)j * N * 2;
     const uint64_t *rowp = lift + ((bt * 2 + p) * nl + j) * N + (size_t)row * R2;
+    const uint64_t *sv = srcp + bt * src_item + p * src_poly;
+    if (threadIdx.x == 0) {
+        // the output stage's operand rows of this CTA (contiguous RPC rows of
+        // limb j) start their way into L2 while the transform runs
+        const size_t tile = (size_t)j * N + (size_t)grp * RPC * R2;
+        constexpr unsigned bytes = RPC * R2 * 8;
+        prefetch_l2(sv + tile, bytes);
+        if (o.rel) prefetch_l2(o.rel + bt * o.rel_item + p * o.rel_poly + tile, bytes);
+        if (o.acc) prefetch_l2(o.acc + bt * o.acc_item + p * o.acc_poly + tile, bytes);
+    }
     uint64_t *seg = smem + rl * G::SEG;
     uint64_t x[E];
 #pragma unroll
@@ -376,7 +393,6 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T)
     __syncthreads();
     to_strided<K2>(x, seg, l);  // word l + T r of the row: coalesced below
     const uint64_t pv = inv[2 * j], pvp = inv[2 * j + 1];
-    const uint64_t *sv = srcp + bt * src_item + p * src_poly;
 #pragma unroll
     for (int r = 0; r < E; r++) {
         const int k = row * R2 + l + T * r;
