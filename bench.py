@@ -170,9 +170,9 @@ def run_ours(args, rank, world):
     prof = {name: ctx.prof_read(i) for i, name in enumerate(["ntt_fwd", "ntt_inv", "modup", "ks_inner"])}
     ctx.prof_enable(False)
     st = job.stats()
-    ms_max = allreduce_max(ms, world)
-    sec_iter = ms_max / 1000.0 / (args.steps * world)
     ks_per_iter = int(st.keyswitches)
+    ms_max, sec_iter, rates = replica_rates(ms, args.steps, world,
+                                            {"ks": ks_per_iter, "limbs": transform_limbs(prof) / args.steps})
     err = None
     if not args.no_twin:
         err = twin_error(X, y, job, t, sched)
@@ -229,9 +229,9 @@ def run_ours(args, rank, world):
                    "blocks": int(info.n_blocks), "blocks_per_launch": chunk_used,
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "no flush: %.1f GiB of encrypted data blocks > 129 MB L2" % (info.n_blocks * ctw_bytes() / 2 ** 30)},
-        "keyswitch_per_s": round(ks_per_iter / sec_iter / world, 1) if sec_iter else None,
+        "keyswitch_per_s": round(rates["ks"], 1) if sec_iter else None,
         "keyswitches_per_iter": ks_per_iter,
-        "ntt_limbs_per_s": round(transform_limbs(prof) / args.steps / (sec_iter * world), 1),
+        "ntt_limbs_per_s": round(rates["limbs"], 1) if sec_iter else None,
         "plain_one_ct_per_launch_s_per_iter": round(plain, 4) if plain else None,
         "mini_batch": mini,
         "multi_job": multi,
@@ -505,13 +505,25 @@ def barrier(world):
 
 
 def allreduce_max(v, world):
+    """Maximum of v over the ranks (NCCL on the GPU run, gloo on the CPU tests)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([float(v)], device="cuda")
+    t = torch.tensor([float(v)], device="cuda" if dist.get_backend() == "nccl" else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_rates(ms_local, steps, world, per_iter):
+    """Whole-job figures of `world` independent replicas that each ran `steps`
+    iterations: the slowest rank's time bounds the job, so seconds per
+    iteration = max-over-ranks ms / (steps * world); every per-iteration count
+    in `per_iter` becomes a whole-job rate (count / seconds per iteration)."""
+    ms_max = allreduce_max(ms_local, world)
+    sec_iter = ms_max / 1000.0 / (steps * world)
+    rates = {k: (v / sec_iter if sec_iter else None) for k, v in per_iter.items()}
+    return ms_max, sec_iter, rates
 
 
 # ------------------------------------------------------------------ CPU oracle
