@@ -551,7 +551,7 @@ def cpu_baseline(X, y, samples=1, steps=1, warmup=0):
         t0 = time.time()
         acc = None
         for z in Z:
-            g = circ.block_grad(z, W, 2.0)
+            g = circ.block_grad(z, W)
             acc = g if acc is None else he.add(acc, g)
         t1 = time.time()
         Wn, Vn = circ.finish(acc, B, W, V, 0.99, 1.0 / data.n)

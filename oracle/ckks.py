@@ -222,6 +222,17 @@ class Ckks:
         self.L.orc_cadd_int(self.ctx, ct.level, _p(ct.data), round_half_away(c * ct.scale), _p(out))
         return Ct(out, ct.level, ct.scale)
 
+    def ptadd(self, ct, pt):
+        """c0 + m for a plaintext m at the ciphertext's level and scale."""
+        if pt.level != ct.level:
+            raise ValueError("level mismatch")
+        self._check_scales(ct, pt)
+        out = ct.data.copy()
+        c0 = np.zeros_like(ct.data[0])
+        self.L.orc_add(self.ctx, ct.level, 1, _p(np.ascontiguousarray(ct.data[0])), _p(pt.data), _p(c0), 0)
+        out[0] = c0
+        return Ct(out, ct.level, ct.scale)
+
     def ptmul(self, ct, pt):
         if pt.level != ct.level:
             raise ValueError("level mismatch")

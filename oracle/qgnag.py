@@ -24,13 +24,21 @@ Readings where the paper is silent or ambiguous:
     rate as 2 - (t/81)^2.5, i.e. 1 + gamma with gamma running from 1 down to 0);
     Bbar and g are unnormalised sums, so n * Bbar is encrypted and 1/n is applied
     as a public scalar at the end.
-  * The sigmoid term is s = F2(t) * (1 - g(ip)) with the polynomial g printed in
-    Sec. 4.1, evaluated at depth 2: ip^2 and (k3 ip) in parallel, then their product.
+  * The circuit of Han et al. that Sec. 2.2 builds on is not given.  Reading:
+    row sums by rotate-and-add put ip_r in column 0 (the other columns hold
+    partial sums); the column-0 mask M is folded into the plaintext products of
+    the sigmoid polynomial, s = (1 - c0) M - c1 (M t) - c3 t^2 (M t), evaluated
+    at depth 2 (t^2 and (-c3 M) t in parallel, then their product), which is
+    zero outside column 0; s is then replicated across the row by rotate-and-
+    add.  This is the same function as masking ip first, with one level less,
+    and the replication runs at a lower level.
+  * The multiplier on G, F2(t), is applied with the public scalars of the
+    update (Algorithm 1: V_temp = W + (1 + gamma) G), together with 1/n.
   * t starts at 0; mini-batches are visited in order 0, 1, 2, ... without shuffling.
   * First-order NAG baseline (Sec. 2.3, the method the paper compares against):
     the same circuit without the Bbar product (Step 8), so one level less; its
-    learning rate gamma multiplies the sigmoid term where QG-NAG puts F2(t)
-    (a constant schedule max = min = gamma), and V' = W + (1/n) gamma g.
+    learning rate gamma takes the place of F2(t) (a constant schedule max = min
+    = gamma), and V' = W + (1/n) gamma g.
 """
 import math
 
@@ -134,17 +142,17 @@ class TrainData:
 
 
 # ------------------------------------------------------------------ encrypted iteration
-DEPTH = 7  # levels one iteration consumes
-DEPTH_FIRST_ORDER = 6  # without the Bbar product of Step 8
+DEPTH = 6  # levels one iteration consumes
+DEPTH_FIRST_ORDER = 5  # without the Bbar product of Step 8
 
 
 class Circuit:
     """The encrypted QG-NAG iteration on one parameter set.
 
-    Levels: fresh inputs sit at level L (default: the iteration depth, 7, so the
+    Levels: fresh inputs sit at level L (default: the iteration depth, 6, so the
     iteration ends at level 0; any higher primes of the chain stay unused); the
-    iteration consumes 7 levels and ends at level L - 7.  With first_order=True
-    the circuit is the first-order NAG baseline: no Bbar product, depth 6."""
+    iteration consumes 6 levels and ends at level L - 6.  With first_order=True
+    the circuit is the first-order NAG baseline: no Bbar product, depth 5."""
 
     def __init__(self, he: Ckks, g, m, scale, poly=G8, start_level=None, first_order=False):
         self.he, self.g, self.m, self.scale, self.poly = he, g, m, float(scale), poly
@@ -156,10 +164,20 @@ class Circuit:
         if self.L < depth or self.L > he.max_level:
             raise ValueError("the iteration needs %d levels" % depth)
         self.lg, self.lm = int(math.log2(g)), int(math.log2(m))
+        c0, c1, c3 = poly
         mask = np.zeros(he.nslots)
         mask[::g] = 1.0
-        lv = self.L - 1
-        self.mask = he.encode(mask, lv, float(he.q[lv]))
+        # the scale chain of Steps 1-5 (fresh Z and W at `scale`), for the
+        # masked polynomial plaintexts
+        q = [float(x) for x in he.q]
+        L = self.L
+        t_scale = scale * scale / q[L]                       # Step 1
+        sq_scale = t_scale * t_scale / q[L - 1]              # t^2
+        c3_scale = t_scale * scale / q[L - 1]                # (-c3 M) t, plaintext at `scale`
+        self.s_scale = sq_scale * c3_scale / q[L - 2]        # the cube and s
+        self.p3 = he.encode(-c3 * mask, L - 1, scale)
+        self.p1 = he.encode(-c1 * mask, L - 1, self.s_scale * q[L - 1] / t_scale)  # rescales to s_scale
+        self.p0 = he.encode((1.0 - c0) * mask, L - 3, self.s_scale)
 
     def rotations(self):
         rs = [1 << k for k in range(self.lg)]
@@ -176,35 +194,29 @@ class Circuit:
         out.scale = target
         return out
 
-    def block_grad(self, Z, W, alpha):
-        """Steps 1-6 for one data block: slotwise s_r * z_rc, s = alpha (1 - g(z_r . w))."""
-        he, L = self.he, self.L
-        c0, c1, c3 = self.poly
+    def block_grad(self, Z, W):
+        """Steps 1-6 for one data block: slotwise s_r * z_rc, s = 1 - g(z_r . w)."""
+        he = self.he
         # Step 1: z_rc * w_c
         t = he.rescale(he.mul(Z, W))
         # Step 2: row sums into column 0
         for k in range(self.lg):
             t = he.add(t, he.rotate(t, 1 << k))
-        # Step 3: keep column 0
-        t = he.rescale(he.ptmul(t, self.mask))
-        # Step 4: replicate ip_r across the row
-        for k in range(self.lg):
-            t = he.add(t, he.rotate(t, -(1 << k)))
-        ip = t
-        # Step 5: s = alpha (1 - c0) - alpha c1 ip - alpha c3 ip^3
-        k0 = alpha * (1.0 - c0)
-        k1 = -(alpha * c1)
-        k3 = -(alpha * c3)
-        sq = he.rescale(he.mul(ip, ip))
-        c3t = he.rescale(he.cmul(ip, k3, self.scale))
+        # Steps 3 and 5: s = (1 - c0) M - c1 (M t) - c3 t^2 (M t), zero outside column 0
+        sq = he.rescale(he.mul(t, t))
+        c3t = he.rescale(he.ptmul(t, self.p3))
         cube = he.rescale(he.mul(sq, c3t))
-        lin = he.moddrop(self.cmul_to(ip, k1, cube.scale), cube.level)
-        s = he.cadd(he.add(cube, lin), k0)
+        lin = he.rescale(he.ptmul(t, self.p1))
+        lin.scale = cube.scale  # p1's scale was chosen for this
+        s = he.ptadd(he.add(cube, he.moddrop(lin, cube.level)), self.p0)
+        # Step 4: replicate s_r across the row
+        for k in range(self.lg):
+            s = he.add(s, he.rotate(s, -(1 << k)))
         # Step 6: s_r * z_rc
         return he.rescale(he.mul(s, he.moddrop(Z, s.level)))
 
-    def finish(self, acc, B, W, V, eta, inv_n):
-        """Steps 7-9 on the accumulated gradient ciphertext."""
+    def finish(self, acc, B, W, V, alpha, eta, inv_n):
+        """Steps 7-9 on the accumulated gradient ciphertext; alpha = F2(t)."""
         he = self.he
         # Step 7: column sums, every row gets g_c
         for k in range(self.lm):
@@ -214,19 +226,19 @@ class Circuit:
         # Step 9: V' = W + G, W' = (1 - eta) V' + eta V
         lv = nG.level
         tgt = W.scale
-        G = self.cmul_to(nG, inv_n, tgt)
+        G = self.cmul_to(nG, alpha * inv_n, tgt)
         Vn = he.add(he.moddrop(W, lv - 1), G)
         Wn = he.add(he.add(self.cmul_to(he.moddrop(W, lv), 1.0 - eta, tgt),
                            self.cmul_to(he.moddrop(V, lv), eta, tgt)),
-                    self.cmul_to(nG, (1.0 - eta) * inv_n, tgt))
+                    self.cmul_to(nG, (1.0 - eta) * alpha * inv_n, tgt))
         return Wn, Vn
 
     def iteration(self, Zs, B, W, V, alpha, eta, inv_n):
         acc = None
         for Z in Zs:
-            gct = self.block_grad(Z, W, alpha)
+            gct = self.block_grad(Z, W)
             acc = gct if acc is None else he_add(self.he, acc, gct)
-        return self.finish(acc, B, W, V, eta, inv_n)
+        return self.finish(acc, B, W, V, alpha, eta, inv_n)
 
     def refresh(self, ct, seed):
         """Step 7 stand-in: decrypt, keep the real part of the slots, re-encode at

@@ -197,7 +197,7 @@ def test_encrypted_first_order_matches_fp64_twin():
     he = Ckks(13, 9)
     data = qgnag.TrainData(X, y, g=16, m=256, batch_rows=1024)
     circ = qgnag.Circuit(he, 16, 256, 2.0 ** 40, first_order=True)
-    assert circ.L == qgnag.DEPTH_FIRST_ORDER == 6
+    assert circ.L == qgnag.DEPTH_FIRST_ORDER == 5
     he.keygen(2, circ.rotations())
     sched = (1.0, 1.0, 81.0, 2.5)
     w, trace = qgnag.train(he, circ, data, 2, enc_seed=4, sched=sched, return_trace=True)

@@ -166,3 +166,19 @@ def test_rescale_rounds_to_nearest(he):
                 for v in vals[:64]]
         assert [int(x) for x in out.data[0, j, :64]] == want
     assert not out.data[1].any()
+
+
+def test_ptadd_adds_the_message():
+    """c0 + m decrypts to the sum of the messages (same level and scale)."""
+    he = Ckks(10, 3)
+    he.keygen(3, [])
+    rng = np.random.default_rng(21)
+    a, b = rng.uniform(-1, 1, he.nslots), rng.uniform(-1, 1, he.nslots)
+    ct = he.encrypt(he.encode(a, 2, 2.0 ** 30), 5)
+    out = he.ptadd(ct, he.encode(b, 2, 2.0 ** 30))
+    # the encryption noise cancels in the difference: what is left is b up to encoding rounding
+    diff = he.decode(he.decrypt(out)).real - he.decode(he.decrypt(ct)).real
+    assert np.abs(diff - b).max() < 1e-7
+    assert np.abs(he.decode(he.decrypt(out)).real - (a + b)).max() < 1e-4
+    with pytest.raises(ValueError):
+        he.ptadd(ct, he.encode(b, 1, 2.0 ** 30))
