@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "enc. QG-NAG sec/iter at 422,108x200 (N=2^16); keyswitch/s; batched vs plain GPU"
 N_SAMPLES, N_FEAT, LOGN, NQ, LOG_SCALE = 422108, 200, 16, 9, 40.0
-ITER_LEVEL = 7  # fresh ciphertexts sit at the depth of one iteration
+ITER_LEVEL = 6  # fresh ciphertexts sit at the depth of one iteration
 PAPER_CONTEXT = {"paper_full_batch_update_s": 60.0, "paper_full_batch_iter_s": 90.0,
                  "paper_hardware": "8 vCPUs, HEAAN (non-RNS), Q=2^275, Delta=2^30"}
 
@@ -298,7 +298,7 @@ def first_order_time(ctx, X, y, args):
     e1.record()
     torch.cuda.synchronize()
     out = {"s_per_iter": round(e0.elapsed_time(e1) / 2 / 1000.0, 5), "keyswitches_per_iter": int(job.stats().keyswitches),
-           "start_level": 6, "rate": 0.01}
+           "start_level": 5, "rate": 0.01}
     job.close()
     return out
 

@@ -191,7 +191,7 @@ enum { HE_LR_FULL_BATCH = 0, HE_LR_MINI_BATCH = 1 };
 /* OR-ed into the mode of he_lr_job_create / he_lr_train: the first-order NAG
  * baseline the paper compares against (Sec. 2.3, w' = v + gamma (1/n) g): the
  * same circuit without the Bbar product of Step 8, so one level shallower
- * (fresh ciphertexts at level 6, no Bbar ciphertexts); the schedule's F2(t)
+ * (fresh ciphertexts at level 5, no Bbar ciphertexts); the schedule's F2(t)
  * is the rate gamma (a constant when max = min). */
 enum { HE_LR_FIRST_ORDER = 0x100 };
 enum { HE_LR_G8 = 0, HE_LR_G16 = 1 };
@@ -212,9 +212,9 @@ typedef struct he_lr_job he_lr_job;
  * Bbar per mini-batch of batch_rows rows (Sec. 3.1, 1/(eps + 1/4 sum |Z^T Z|),
  * eps = 1e-8) and the full-batch Bbar by the combination of Sec. 3.3, pack
  * m x g blocks (g = next power of two >= f + 1, m g = N/2; Sec. 2.2),
- * encrypt the blocks, n*Bbar (replicated per row) and W = V = 0 at level 7
- * (the depth of one iteration, which then ends at level 0; primes above q_7
- * stay unused; level 6 and no Bbar with HE_LR_FIRST_ORDER) with scale
+ * encrypt the blocks, n*Bbar (replicated per row) and W = V = 0 at level 6
+ * (the depth of one iteration, which then ends at level 0; primes above q_6
+ * stay unused; level 5 and no Bbar with HE_LR_FIRST_ORDER) with scale
  * 2^log_scale.  Object k of kind K is encrypted with seed
  * enc_seed + (K << 48) + k (K: 1 block, 2 Bbar, 3 W0, 4 V0, 5 W refresh at
  * iteration k, 6 V refresh).  X: n x f row-major doubles, y: n labels +/-1.
@@ -229,7 +229,7 @@ int he_lr_job_create(he_ctx *ctx, const double *X, const double *y, size_t n, si
 int he_lr_job_step(he_lr_job *job, int t, he_lr_sched sched);
 /* he_lr_job_step with the job state on the host: when state_in is not NULL,
  * W and V are first loaded from coefficient words [2 ciphertexts][2][n_q][N]
- * (W then V, at the job's start level L = 7, or 6 first-order, scale
+ * (W then V, at the job's start level L = 6, or 5 first-order, scale
  * 2^log_scale; n_q is then L + 1 limbs); when state_out is not NULL, the
  * refreshed W and V are written back in the same layout.  Host buffers may be
  * pinned; the copies run on the context stream inside the call. */
@@ -250,10 +250,11 @@ int he_lr_job_state(he_lr_job *job, const he_ct **W, const he_ct **V);
  * kind 1 = Enc(n Bbar) of mini-batch `index` (index 0 in full-batch mode; none
  * for a first-order job: HE_EINVAL). */
 int he_lr_job_input(he_lr_job *job, int kind, int index, he_ct **out);
-/* Gradient ciphertext of one block for the job's current W (Steps 1-6 alone,
- * computed in the same chunked launch that he_lr_job_step uses for the chunk
- * holding the block); returns a new ciphertext. */
-int he_lr_job_block_grad(he_lr_job *job, int block, double alpha, he_ct **out);
+/* Gradient ciphertext of one block for the job's current W (Steps 1-6 alone:
+ * s_r z_rc with s = 1 - g(z_r . w), computed in the same chunked launch that
+ * he_lr_job_step uses for the chunk holding the block); returns a new
+ * ciphertext. */
+int he_lr_job_block_grad(he_lr_job *job, int block, he_ct **out);
 int he_lr_job_info(const he_lr_job *job, he_lr_stats *stats);
 int he_lr_job_free(he_lr_job *job);
 
@@ -279,8 +280,8 @@ int he_lr_train(he_ctx *ctx, const double *X, const double *y, size_t n, size_t 
  * Z[0..n_blocks-1] data blocks at one level, B = Enc(n Bbar) at that level,
  * W, V at that level; g x m packing; alpha = F2(t), eta from Algorithm 1,
  * inv_n = 1/n; poly = (c0, c1, c3) of the sigmoid polynomial.  Returns
- * W', V' seven levels down (before any refresh).  B = NULL runs the
- * first-order baseline (alpha = gamma, no Bbar product): six levels down. */
+ * W', V' six levels down (before any refresh).  B = NULL runs the
+ * first-order baseline (alpha = gamma, no Bbar product): five levels down. */
 int he_lr_iteration(he_ctx *ctx, he_ct *const *Z, size_t n_blocks, const he_ct *B, const he_ct *W,
                     const he_ct *V, int g, int m, double alpha, double eta, double inv_n,
                     const double poly[3], he_ct **W_out, he_ct **V_out);

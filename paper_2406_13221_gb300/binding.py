@@ -84,7 +84,7 @@ SIGNATURES = {
     "he_lr_job_step": (_i, [_vp, _i, he_lr_sched]),
     "he_lr_job_weights": (_i, [_vp, _i, _vp, _sz]),
     "he_lr_job_state": (_i, [_vp, _pp, _pp]),
-    "he_lr_job_block_grad": (_i, [_vp, _i, _d, _pp]),
+    "he_lr_job_block_grad": (_i, [_vp, _i, _pp]),
     "he_lr_job_input": (_i, [_vp, _i, _i, _pp]),
     "he_lr_job_info": (_i, [_vp, ctypes.POINTER(he_lr_stats)]),
     "he_lr_job_step_io": (_i, [_vp, _i, he_lr_sched, _vp, _vp]),
@@ -371,9 +371,9 @@ class Job:
         self.ctx.check(self.ctx.L.he_lr_job_input(self.h, kind, index, ctypes.byref(o)))
         return Ct(self.ctx, o)
 
-    def block_grad(self, b, alpha):
+    def block_grad(self, b):
         o = ctypes.c_void_p()
-        self.ctx.check(self.ctx.L.he_lr_job_block_grad(self.h, b, float(alpha), ctypes.byref(o)))
+        self.ctx.check(self.ctx.L.he_lr_job_block_grad(self.h, b, ctypes.byref(o)))
         return Ct(self.ctx, o)
 
     def stats(self):

@@ -241,6 +241,16 @@ int ev_ptmul(Eval *ev, const CtB &a, const uint64_t *pt, double pt_scale, CtB &o
     return HE_OK;
 }
 
+// c0 += m in place for a plaintext m (evaluation form) at the level and scale of a
+int ev_ptadd(Eval *ev, CtB &a, const uint64_t *pt)
+{
+    he_ctx *c = ev->c;
+    Str p{const_cast<uint64_t *>(pt), 0, 0};
+    k_ew(c, EW_ADD, S(a, c), S(a, c), p, a.batch, 1, a.level + 1, nullptr, c->stream);  // polynomial 0 only
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
+
 int ev_moddrop(Eval *ev, const CtB &a, int target, CtB &out)
 {
     he_ctx *c = ev->c;

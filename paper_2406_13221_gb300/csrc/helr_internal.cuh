@@ -400,6 +400,7 @@ int ev_add(Eval *ev, const CtB &a, const CtB &b, CtB &out, int sub);
 int ev_cmul_int(Eval *ev, const CtB &a, int64_t k, double out_scale, CtB &out);
 int ev_cadd_int(Eval *ev, CtB &a, int64_t k);
 int ev_ptmul(Eval *ev, const CtB &a, const uint64_t *pt, double pt_scale, CtB &out);
+int ev_ptadd(Eval *ev, CtB &a, const uint64_t *pt);
 int ev_moddrop(Eval *ev, const CtB &a, int target, CtB &out);
 int ev_sum_items(Eval *ev, const CtB &a, uint64_t *acc, int accumulate);
 bool scales_match(double a, double b);

@@ -6,18 +6,20 @@
 // Circuit per data block Z_i (all at the top level L, scale Delta):
 //  1  t  = Rescale(Relin(Z_i (x) W))                   z_rc w_c
 //  2  t += Rot(t, 2^k), k < log2 g                     row sums into column 0
-//  3  t  = Rescale(t * M)                              mask with ones in column 0
-//  4  t += Rot(t, -2^k), k < log2 g                    ip_r in every column
-//  5  s  = alpha (1 - g(ip)): ip^2 and (k3 ip) in parallel, then their product,
-//          plus k1 ip and the constant k0            sigmoid polynomial (Sec. 4.1)
+//  3/5 s = (1 - c0) M - c1 (M t) - c3 t^2 (M t)        sigmoid term (Sec. 4.1) with
+//          the column-0 mask M inside the plaintext products: t^2 and
+//          (-c3 M) t in parallel, then their product; zero outside column 0
+//  4  s += Rot(s, -2^k), k < log2 g                    s_r in every column
 //  6  grad_i = Rescale(Relin(s (x) Z_i))               s_r z_rc
 // then once:
 //  7  acc = sum_i grad_i; acc += Rot(acc, g 2^k), k < log2 m   column sums
 //  8  nG = Rescale(Relin(acc (x) B))                   n Bbar_c g_c (quadratic gradient)
-//  9  V' = W + nG/n,  W' = (1 - eta) V' + eta V        Algorithm 1 update
+//  9  V' = W + alpha nG/n,  W' = (1 - eta) V' + eta V  Algorithm 1 update
 // The multiplier on G is alpha = F2(t) (the learning rate 2 - (t/81)^2.5 of the
-// experiments); Bbar and g are unnormalised sums, n Bbar is encrypted and 1/n
-// is a public scalar.
+// experiments), applied with the public scalar 1/n; Bbar and g are unnormalised
+// sums and n Bbar is encrypted.  The circuit of Han et al. that the paper builds
+// on is not given: folding the mask into the polynomial computes the same
+// function as masking ip before the sigmoid, with one level less.
 #include <math.h>
 #include <string.h>
 #include <thread>
@@ -28,8 +30,8 @@
 static const double G8[3] = {0.5, 0.15, -0.0015};
 static const double G16[3] = {0.5, 0.0843, -0.0002};
 static const double BBAR_EPS = 1e-8;
-static const int ITER_DEPTH = 7;  // levels one iteration consumes
-static const int ITER_DEPTH_FO = 6;  // the first-order baseline: no Bbar product
+static const int ITER_DEPTH = 6;  // levels one iteration consumes
+static const int ITER_DEPTH_FO = 5;  // the first-order baseline: no Bbar product
 
 static uint64_t obj_seed(uint64_t base, uint64_t kind, uint64_t index) { return base + (kind << 48) + index; }
 
@@ -81,8 +83,8 @@ struct he_lr_job {
     std::vector<he_ct *> B;     // Enc(n Bbar) per mini-batch, or one for the full batch (none first-order)
     std::vector<double> inv_n;
     he_ct *W, *V;
-    uint64_t *mask;             // plaintext M at level L-1, scale q_(L-1), evaluation form
-    double mask_scale;
+    uint64_t *sig;              // masked sigmoid plaintexts (see SigPts), evaluation form
+    double p1_scale;
     Eval ev;
     int chunk, chunk_max;
     uint64_t *buf;              // work ciphertexts
@@ -133,6 +135,50 @@ static int encrypt_slots(he_ctx *c, const double *h_slots, int count, int level,
     return HE_OK;
 }
 
+// The three plaintexts of Steps 3/5 for row width g, at the levels and scales
+// the circuit reaches from data blocks at scale z_scale and weights at scale
+// w_scale (level L): p3 = -c3 M at level L-1, scale w_scale; p1 = -c1 M at level
+// L-1 with the scale that rescales (M t) to the scale of the cube; p0 = (1 - c0) M
+// at level L-3 and the cube's scale.  M has ones in column 0 of every row.
+// *out holds [p3 (L limbs) | p1 (L limbs) | p0 (L-2 limbs)] x N words.
+struct SigPts {
+    const uint64_t *p3, *p1, *p0;
+};
+static SigPts sig_pts(const uint64_t *buf, int L, size_t N)
+{
+    return SigPts{buf, buf + (size_t)L * N, buf + 2 * (size_t)L * N};
+}
+static int make_sigmoid_pts(he_ctx *c, int L, int g, double z_scale, double w_scale, const double poly[3], uint64_t **out,
+                            double *p1_scale)
+{
+    const size_t N = c->n, ns = c->nslots;
+    const double q = (double)c->q[L], q1 = (double)c->q[L - 1], q2 = (double)c->q[L - 2];
+    const double t_scale = z_scale * w_scale / q;        // Step 1
+    const double sq_scale = t_scale * t_scale / q1;      // t^2
+    const double c3_scale = t_scale * w_scale / q1;      // (-c3 M) t
+    const double s_scale = sq_scale * c3_scale / q2;     // the cube, and s
+    *p1_scale = s_scale * q1 / t_scale;
+    std::vector<double> v(3 * ns, 0.0);
+    for (size_t i = 0; i < ns; i += g) {
+        v[i] = -poly[2];
+        v[ns + i] = -poly[1];
+        v[2 * ns + i] = 1.0 - poly[0];
+    }
+    double *d = nullptr;
+    uint64_t *buf = nullptr;
+    HELR_TRY(helr_alloc(c, (void **)&d, sizeof(double) * 3 * ns));
+    HELR_TRY(helr_alloc(c, (void **)&buf, sizeof(uint64_t) * (3 * (size_t)L - 2) * N));
+    HELR_CUDA(c, cudaMemcpyAsync(d, v.data(), sizeof(double) * 3 * ns, cudaMemcpyHostToDevice, c->stream));
+    const SigPts p = sig_pts(buf, L, N);
+    HELR_TRY(helr_encode_dev(c, d, nullptr, 1, 0, L - 1, w_scale, const_cast<uint64_t *>(p.p3), 0));
+    HELR_TRY(helr_encode_dev(c, d + ns, nullptr, 1, 0, L - 1, *p1_scale, const_cast<uint64_t *>(p.p1), 0));
+    HELR_TRY(helr_encode_dev(c, d + 2 * ns, nullptr, 1, 0, L - 3, s_scale, const_cast<uint64_t *>(p.p0), 0));
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    helr_free(c, d);
+    *out = buf;
+    return HE_OK;
+}
+
 extern "C" int he_lr_job_free(he_lr_job *j)
 {
     if (!j) return HE_EINVAL;
@@ -142,7 +188,7 @@ extern "C" int he_lr_job_free(he_lr_job *j)
     for (auto *b : j->B) he_ct_free(b);
     if (j->W) he_ct_free(j->W);
     if (j->V) he_ct_free(j->V);
-    helr_free(c, j->mask);
+    helr_free(c, j->sig);
     helr_free(c, j->buf);
     ev_free(&j->ev);
     cudaStreamSynchronize(c->stream);
@@ -275,18 +321,8 @@ extern "C" int he_lr_job_create(he_ctx *c, const double *X, const double *y, siz
     JTRY(encrypt_slots(c, zero.data(), 1, L, j->scale0, 3, enc_seed, 0, j->W->d, j->ctw));
     JTRY(helr_new_ct(c, L, j->scale0, &j->V));
     JTRY(encrypt_slots(c, zero.data(), 1, L, j->scale0, 4, enc_seed, 0, j->V->d, j->ctw));
-    // Step 3 mask: ones in column 0 of every row, at level L-1 with scale q_(L-1)
-    {
-        std::vector<double> msk(ns, 0.0);
-        for (size_t i = 0; i < ns; i += g) msk[i] = 1.0;
-        double *d = nullptr;
-        JTRY(helr_alloc(c, (void **)&d, sizeof(double) * ns));
-        JTRY(helr_alloc(c, (void **)&j->mask, sizeof(uint64_t) * L * N));
-        HELR_CUDA(c, cudaMemcpyAsync(d, msk.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, c->stream));
-        j->mask_scale = (double)c->q[L - 1];
-        JTRY(helr_encode_dev(c, d, nullptr, 1, 0, L - 1, j->mask_scale, j->mask, 0));
-        helr_free(c, d);
-    }
+    // Steps 3/5: the masked plaintexts of the sigmoid polynomial
+    JTRY(make_sigmoid_pts(c, L, g, j->scale0, j->scale0, j->poly, &j->sig, &j->p1_scale));
     // work buffers: chunk of blocks per launch
     int chunk = batch_blocks > 0 ? batch_blocks : 64;  // tuned on GB300 at N = 2^16
     chunk = std::min(chunk, mode == HE_LR_FULL_BATCH ? j->nblocks : j->bpb);
@@ -333,11 +369,13 @@ struct WorkSet {
     const double *poly;
 };
 
-// A run of data blocks that share W, the mask and the row width g.
+// A run of data blocks that share W, the row width g and its masked sigmoid
+// plaintexts (p1 at scale p1_scale).
 struct Seg {
     int start, count, lg;
-    const uint64_t *W, *mask;
-    double mask_scale;
+    const uint64_t *W;
+    SigPts sig;
+    double p1_scale;
 };
 
 // ping-pong rotate-and-add over the items with lg > k (a prefix: segments are
@@ -363,9 +401,9 @@ static int rot_step(const WorkSet &ws, CtB &Bt, CtB &R, int64_t r, int rotated, 
 }
 
 // Steps 1-6 on `cnt` blocks at Z (item stride ctw) described by segments;
-// result (level L-5) in g_out (buffer T2)
+// result (level L-4) in g_out (buffer T2)
 static int block_grads_seg(const WorkSet &ws, const uint64_t *Z, int cnt, const Seg *segs, int nseg, double w_scale,
-                           double alpha, CtB &g_out)
+                           CtB &g_out)
 {
     Eval *ev = ws.ev;
     const int L = ws.L;
@@ -385,54 +423,61 @@ static int block_grads_seg(const WorkSet &ws, const uint64_t *Z, int cnt, const 
             if (segs[i].lg > k) n = segs[i].start + segs[i].count;
         return n;
     };
+    auto slice = [&](const CtB &x, int i) {
+        CtB y = x;
+        y.d = x.d + (size_t)segs[i].start * w;
+        y.batch = segs[i].count;
+        return y;
+    };
+    // per segment: out = Rescale-ready product of x with that segment's plaintext
+    auto ptmul_segs = [&](const CtB &x, const uint64_t *SigPts::*which, double scale, CtB &out) -> int {
+        for (int i = 0; i < nseg; i++) {
+            CtB y = slice(out, i);
+            HELR_TRY(ev_ptmul(ev, slice(x, i), segs[i].sig.*which, scale, y));
+        }
+        out.level = x.level;
+        out.scale = x.scale * scale;
+        out.batch = cnt;
+        return HE_OK;
+    };
     // 1
     HELR_TRY(ev_mul_relin_seg(ev, Zc, wp.data(), st.data(), ct.data(), nseg, w_scale, A));
     HELR_TRY(ev_rescale(ev, A, Bt));
     // 2: t += Rot(t, 2^k), ping-pong between T1 and T2
     for (int k = 0; k < lgmax; k++) HELR_TRY(rot_step(ws, Bt, R, 1 << k, rotated(k), cnt));
-    // 3: mask of each segment's row width
+    const CtB t = Bt;  // level L-1; R is the other of T1 / T2
+    // 3/5: s = (1 - c0) M - c1 (M t) - c3 t^2 (M t)
+    CtB sq{ws.T[3], cnt, 0, 0, w}, c3{ws.T[4], cnt, 0, 0, w}, cube{ws.T[0], cnt, 0, 0, w};
+    HELR_TRY(ev_mul_relin(ev, t, t, A));
+    HELR_TRY(ev_rescale(ev, A, sq));
+    HELR_TRY(ptmul_segs(t, &SigPts::p3, ws.scale0, A));
+    HELR_TRY(ev_rescale(ev, A, c3));
+    HELR_TRY(ev_mul_relin(ev, sq, c3, R));
+    HELR_TRY(ev_rescale(ev, R, cube));
+    CtB lin{ws.T[3], cnt, 0, 0, w}, lind{ws.T[4], cnt, 0, 0, w};
+    HELR_TRY(ptmul_segs(t, &SigPts::p1, segs[0].p1_scale, R));
+    HELR_TRY(ev_rescale(ev, R, lin));
+    lin.scale = cube.scale;  // p1's scale was chosen for this
+    HELR_TRY(ev_moddrop(ev, lin, cube.level, lind));
+    CtB s{t.d, cnt, 0, 0, w};
+    HELR_TRY(ev_add(ev, cube, lind, s, 0));
     for (int i = 0; i < nseg; i++) {
-        CtB x = Bt, y = A;
-        x.d = Bt.d + (size_t)segs[i].start * w;
-        x.batch = segs[i].count;
-        y.d = A.d + (size_t)segs[i].start * w;
-        HELR_TRY(ev_ptmul(ev, x, segs[i].mask, segs[i].mask_scale, y));
-        A.level = y.level;
-        A.scale = y.scale;
+        CtB y = slice(s, i);
+        HELR_TRY(ev_ptadd(ev, y, segs[i].sig.p0));
     }
-    A.batch = cnt;
-    Bt.d = ws.T[1];
-    R.d = ws.T[2];
-    HELR_TRY(ev_rescale(ev, A, Bt));
-    // 4
+    // 4: s += Rot(s, -2^k), ping-pong between T1 and T2
+    Bt = s;
+    R.d = t.d == ws.T[1] ? ws.T[2] : ws.T[1];
     for (int k = 0; k < lgmax; k++) HELR_TRY(rot_step(ws, Bt, R, -(1 << k), rotated(k), cnt));
     if (Bt.d != ws.T[1]) {
         CtB t1{ws.T[1], cnt, 0, 0, w};
         HELR_TRY(ev_moddrop(ev, Bt, Bt.level, t1));
         Bt = t1;
     }
-    R.d = ws.T[2];
-    CtB ip = Bt;  // level L-2, in T1
-    // 5
-    const double k0 = alpha * (1.0 - ws.poly[0]), k1 = -(alpha * ws.poly[1]), k3 = -(alpha * ws.poly[2]);
-    CtB sq{ws.T[3], cnt, 0, 0, w}, c3{ws.T[4], cnt, 0, 0, w};
-    HELR_TRY(ev_mul_relin(ev, ip, ip, A));
-    HELR_TRY(ev_rescale(ev, A, sq));
-    HELR_TRY(ev_cmul_int(ev, ip, round_half_away(k3 * ws.scale0), ip.scale * ws.scale0, A));
-    HELR_TRY(ev_rescale(ev, A, c3));
-    CtB cube{ws.T[0], cnt, 0, 0, w};
-    HELR_TRY(ev_mul_relin(ev, sq, c3, R));
-    HELR_TRY(ev_rescale(ev, R, cube));
-    CtB lin{ws.T[3], cnt, 0, 0, w}, lind{ws.T[4], cnt, 0, 0, w};
-    HELR_TRY(cmul_to(ev, ip, k1, cube.scale, R, lin));
-    HELR_TRY(ev_moddrop(ev, lin, cube.level, lind));
-    CtB s{ws.T[1], cnt, 0, 0, w};
-    HELR_TRY(ev_add(ev, cube, lind, s, 0));
-    HELR_TRY(ev_cadd_int(ev, s, round_half_away(k0 * s.scale)));
     // 6
     CtB zd{ws.T[3], cnt, 0, 0, w};
-    HELR_TRY(ev_moddrop(ev, Zc, s.level, zd));
-    HELR_TRY(ev_mul_relin(ev, s, zd, A));
+    HELR_TRY(ev_moddrop(ev, Zc, Bt.level, zd));
+    HELR_TRY(ev_mul_relin(ev, Bt, zd, A));
     g_out.d = ws.T[2];
     g_out.item = w;
     HELR_TRY(ev_rescale(ev, A, g_out));
@@ -445,16 +490,16 @@ static WorkSet job_ws(he_lr_job *j)
 }
 
 // Steps 1-6 on `cnt` consecutive blocks of one job
-static int block_grads(he_lr_job *j, const uint64_t *Z, int cnt, const CtB &W, double alpha, CtB &g_out)
+static int block_grads(he_lr_job *j, const uint64_t *Z, int cnt, const CtB &W, CtB &g_out)
 {
-    Seg sg{0, cnt, j->lg, W.d, j->mask, j->mask_scale};
-    return block_grads_seg(job_ws(j), Z, cnt, &sg, 1, W.scale, alpha, g_out);
+    Seg sg{0, cnt, j->lg, W.d, sig_pts(j->sig, j->L, j->c->n), j->p1_scale};
+    return block_grads_seg(job_ws(j), Z, cnt, &sg, 1, W.scale, g_out);
 }
 
 // Steps 7-9 on the accumulated gradient of one job (row width g = 2^lg... column
 // sums over m = 2^lm rows); W', V' at level L-7 into Wn, Vn
-static int finish_ws(const WorkSet &ws, CtB acc, const he_ct *Bct, const he_ct *W, const he_ct *V, int g, int lm, double eta,
-                     double inv_n, CtB &Wn, CtB &Vn)
+static int finish_ws(const WorkSet &ws, CtB acc, const he_ct *Bct, const he_ct *W, const he_ct *V, int g, int lm, double alpha,
+                     double eta, double inv_n, CtB &Wn, CtB &Vn)
 {
     Eval *ev = ws.ev;
     const size_t w = ws.ctw;
@@ -479,7 +524,7 @@ static int finish_ws(const WorkSet &ws, CtB acc, const he_ct *Bct, const he_ct *
     const double tgt = W->scale;
     CtB Wv{W->d, 1, W->level, W->scale, 0}, Vv{V->d, 1, V->level, V->scale, 0};
     CtB G{ws.T[4], 1, 0, 0, w}, Wd{ws.T[0], 1, 0, 0, w};
-    HELR_TRY(cmul_to(ev, nG, inv_n, tgt, A, G));
+    HELR_TRY(cmul_to(ev, nG, alpha * inv_n, tgt, A, G));
     HELR_TRY(ev_moddrop(ev, Wv, lv - 1, Wd));
     HELR_TRY(ev_add(ev, Wd, G, Vn, 0));
     CtB x1{ws.T[4], 1, 0, 0, w}, x2{ws.T[0], 1, 0, 0, w};
@@ -488,14 +533,14 @@ static int finish_ws(const WorkSet &ws, CtB acc, const he_ct *Bct, const he_ct *
     HELR_TRY(ev_moddrop(ev, Vv, lv, Bd));
     HELR_TRY(cmul_to(ev, Bd, eta, tgt, A, x2));
     HELR_TRY(ev_add(ev, x1, x2, x1, 0));
-    HELR_TRY(cmul_to(ev, nG, (1.0 - eta) * inv_n, tgt, A, x2));
+    HELR_TRY(cmul_to(ev, nG, (1.0 - eta) * alpha * inv_n, tgt, A, x2));
     HELR_TRY(ev_add(ev, x1, x2, Wn, 0));
     return HE_OK;
 }
 
-static int finish(he_lr_job *j, CtB acc, const he_ct *Bct, double eta, double inv_n, CtB &Wn, CtB &Vn)
+static int finish(he_lr_job *j, CtB acc, const he_ct *Bct, double alpha, double eta, double inv_n, CtB &Wn, CtB &Vn)
 {
-    return finish_ws(job_ws(j), acc, Bct, j->W, j->V, j->g, j->lm, eta, inv_n, Wn, Vn);
+    return finish_ws(job_ws(j), acc, Bct, j->W, j->V, j->g, j->lm, alpha, eta, inv_n, Wn, Vn);
 }
 
 // decrypt, keep the real part of every slot, re-encode at new_level, encrypt
@@ -535,7 +580,7 @@ static int job_update(he_lr_job *j, int t, const he_lr_sched &sched, CtB &Wn, Ct
     for (int b = b0; b < b1; b += j->chunk) {
         int cnt = std::min(j->chunk, b1 - b);
         CtB g{};
-        HELR_TRY(block_grads(j, j->Z + (size_t)b * j->ctw, cnt, W, alpha, g));
+        HELR_TRY(block_grads(j, j->Z + (size_t)b * j->ctw, cnt, W, g));
         HELR_TRY(ev_sum_items(&j->ev, g, j->acc, b != b0));
         gscale = g.scale;
         glevel = g.level;
@@ -543,7 +588,7 @@ static int job_update(he_lr_job *j, int t, const he_lr_sched &sched, CtB &Wn, Ct
     CtB acc{j->acc, 1, glevel, gscale, 0};
     Wn = CtB{j->acc + j->ctw, 1, 0, 0, 0};
     Vn = CtB{j->acc + 2 * j->ctw, 1, 0, 0, 0};
-    return finish(j, acc, j->first_order ? nullptr : j->B[k], eta, j->inv_n[k], Wn, Vn);
+    return finish(j, acc, j->first_order ? nullptr : j->B[k], alpha, eta, j->inv_n[k], Wn, Vn);
 }
 
 // Steps 1-9 recorded into a CUDA graph on the job's stream and launched as one unit
@@ -691,7 +736,7 @@ extern "C" int he_lr_job_input(he_lr_job *j, int kind, int index, he_ct **out)
     return HE_OK;
 }
 
-extern "C" int he_lr_job_block_grad(he_lr_job *j, int block, double alpha, he_ct **out)
+extern "C" int he_lr_job_block_grad(he_lr_job *j, int block, he_ct **out)
 {
     if (!j || !out || block < 0 || block >= j->nblocks) return HE_EINVAL;
     he_ctx *c = j->c;
@@ -705,7 +750,7 @@ extern "C" int he_lr_job_block_grad(he_lr_job *j, int block, double alpha, he_ct
     int start = b0 + ((block - b0) / j->chunk) * j->chunk;
     int cnt = std::min(j->chunk, b1 - start);
     CtB g{};
-    HELR_TRY(block_grads(j, j->Z + (size_t)start * j->ctw, cnt, W, alpha, g));
+    HELR_TRY(block_grads(j, j->Z + (size_t)start * j->ctw, cnt, W, g));
     he_ct *o = nullptr;
     HELR_TRY(helr_new_ct(c, g.level, g.scale, &o));
     HELR_CUDA(c, cudaMemcpyAsync(o->d, g.d + (size_t)(block - start) * g.item, sizeof(uint64_t) * 2 * (g.level + 1) * c->n,
@@ -764,9 +809,6 @@ extern "C" int he_lr_iteration(he_ctx *c, he_ct *const *Z, size_t nb, const he_c
     j.chunk = (int)std::min<size_t>(nb, 64);
     int rc = HE_OK;
     uint64_t *zbuf = nullptr;
-    std::vector<double> msk(c->nslots, 0.0);
-    for (int i = 0; i < c->nslots; i += g) msk[i] = 1.0;
-    double *dm = nullptr;
     he_ct *Wo = nullptr, *Vo = nullptr;
     if ((rc = ev_init(c, &j.ev, std::max(j.chunk, 3), L))) goto out;
     if ((rc = helr_alloc(c, (void **)&j.buf, sizeof(uint64_t) * j.ctw * (5 * (size_t)std::max(j.chunk, 3) + 3)))) goto out;
@@ -776,14 +818,7 @@ extern "C" int he_lr_iteration(he_ctx *c, he_ct *const *Z, size_t nb, const he_c
     j.T3 = j.T2 + j.ctw * std::max(j.chunk, 3);
     j.T4 = j.T3 + j.ctw * std::max(j.chunk, 3);
     j.acc = j.T4 + j.ctw * std::max(j.chunk, 3);
-    if ((rc = helr_alloc(c, (void **)&j.mask, sizeof(uint64_t) * L * N))) goto out;
-    if ((rc = helr_alloc(c, (void **)&dm, sizeof(double) * c->nslots))) goto out;
-    if (cudaMemcpyAsync(dm, msk.data(), sizeof(double) * c->nslots, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
-        rc = helr_fail(c, HE_ECUDA, "mask upload");
-        goto out;
-    }
-    j.mask_scale = (double)c->q[L - 1];
-    if ((rc = helr_encode_dev(c, dm, nullptr, 1, 0, L - 1, j.mask_scale, j.mask, 0))) goto out;
+    if ((rc = make_sigmoid_pts(c, L, g, Z[0]->scale, W->scale, j.poly, &j.sig, &j.p1_scale))) goto out;
     if ((rc = helr_alloc(c, (void **)&zbuf, sizeof(uint64_t) * j.ctw * j.chunk))) goto out;
     j.W = const_cast<he_ct *>(W);
     j.V = const_cast<he_ct *>(V);
@@ -797,7 +832,7 @@ extern "C" int he_lr_iteration(he_ctx *c, he_ct *const *Z, size_t nb, const he_c
                 if (cudaMemcpyAsync(zbuf + (size_t)i * j.ctw, Z[b + i]->d, j.ctw * 8, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
                     rc = helr_fail(c, HE_ECUDA, "gather");
             CtB gg{};
-            if (!rc) rc = block_grads(&j, zbuf, cnt, Wb, alpha, gg);
+            if (!rc) rc = block_grads(&j, zbuf, cnt, Wb, gg);
             if (!rc) rc = ev_sum_items(&j.ev, gg, j.acc, b != 0);
             gscale = gg.scale;
             glevel = gg.level;
@@ -807,7 +842,7 @@ extern "C" int he_lr_iteration(he_ctx *c, he_ct *const *Z, size_t nb, const he_c
         if ((rc = helr_new_ct(c, L - depth, 0, &Vo))) goto out;
         CtB acc{j.acc, 1, glevel, gscale, 0};
         CtB Wn{Wo->d, 1, 0, 0, 0}, Vn{Vo->d, 1, 0, 0, 0};
-        if ((rc = finish(&j, acc, B, eta, inv_n, Wn, Vn))) goto out;
+        if ((rc = finish(&j, acc, B, alpha, eta, inv_n, Wn, Vn))) goto out;
         Wo->level = Wn.level;
         Wo->scale = Wn.scale;
         Vo->level = Vn.level;
@@ -816,8 +851,7 @@ extern "C" int he_lr_iteration(he_ctx *c, he_ct *const *Z, size_t nb, const he_c
     }
 out:
     helr_free(c, zbuf);
-    helr_free(c, dm);
-    helr_free(c, j.mask);
+    helr_free(c, j.sig);
     helr_free(c, j.buf);
     ev_free(&j.ev);
     cudaStreamSynchronize(c->stream);
@@ -850,7 +884,7 @@ extern "C" int he_refresh(he_ctx *c, const he_ct *in, int level, double scale, u
 // Independent full-batch jobs of one context stepped together: the data blocks
 // of all jobs are ordered by decreasing row width g and Steps 1-6 run over
 // chunks of that order, so every key switch is batched across jobs (segments
-// carry each job's W and mask; rotations a narrower job does not need run on a
+// carry each job's W and sigmoid plaintexts; rotations a narrower job does not need run on a
 // prefix of the chunk).  Steps 7-9 and the refresh run per job.
 struct he_lr_multi {
     he_ctx *c;
@@ -936,11 +970,11 @@ extern "C" int he_lr_multi_step(he_lr_multi *m, int t, he_lr_sched sched)
             HELR_CUDA(c, cudaMemcpyAsync(m->Zs + (size_t)i * m->ctw, j->Z + (size_t)blk * m->ctw, m->ctw * 8,
                                          cudaMemcpyDeviceToDevice, c->stream));
             if (i == 0 || m->order[p + i - 1].first != jb)
-                segs.push_back(Seg{i, 0, j->lg, j->W->d, j->mask, j->mask_scale});
+                segs.push_back(Seg{i, 0, j->lg, j->W->d, sig_pts(j->sig, j->L, c->n), j->p1_scale});
             segs.back().count++;
         }
         CtB g{};
-        HELR_TRY(block_grads_seg(ws, m->Zs, cnt, segs.data(), (int)segs.size(), m->scale0, alpha, g));
+        HELR_TRY(block_grads_seg(ws, m->Zs, cnt, segs.data(), (int)segs.size(), m->scale0, g));
         for (const Seg &sg : segs) {
             const int jb = m->order[p + sg.start].first;
             CtB sub{g.d + (size_t)sg.start * m->ctw, sg.count, g.level, g.scale, m->ctw};
@@ -954,7 +988,8 @@ extern "C" int he_lr_multi_step(he_lr_multi *m, int t, he_lr_sched sched)
         he_lr_job *j = m->jobs[jb];
         CtB acc{m->accs + jb * m->ctw, 1, glevel, gscale, 0};
         CtB Wn{m->wv, 1, 0, 0, 0}, Vn{m->wv + m->ctw, 1, 0, 0, 0};
-        HELR_TRY(finish_ws(ws, acc, j->first_order ? nullptr : j->B[0], j->W, j->V, j->g, j->lm, eta, j->inv_n[0], Wn, Vn));
+        HELR_TRY(finish_ws(ws, acc, j->first_order ? nullptr : j->B[0], j->W, j->V, j->g, j->lm, alpha, eta, j->inv_n[0],
+                           Wn, Vn));
         HELR_TRY(refresh_dev(c, Wn.d, Wn.level, Wn.scale, j->L, j->scale0, obj_seed(j->enc_seed, 5, t), j->W->d));
         HELR_TRY(refresh_dev(c, Vn.d, Vn.level, Vn.scale, j->L, j->scale0, obj_seed(j->enc_seed, 6, t), j->V->d));
         j->W->scale = j->V->scale = j->scale0;

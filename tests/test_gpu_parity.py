@@ -224,7 +224,7 @@ def small_job_inputs(pair):
     return ctx, he, data, circ
 
 
-@pytest.mark.parametrize("L", [8, 7])
+@pytest.mark.parametrize("L", [8, 6])
 def test_iteration_bitwise(small_job_inputs, L):
     ctx, he, data, _ = small_job_inputs
     circ = qgnag.Circuit(he, 16, 256, D, start_level=L)
@@ -257,7 +257,7 @@ def test_job_step_bitwise_and_weights(small_job_inputs, graph):
     st = job.stats()
     assert (st.n_blocks, st.g, st.m) == (4, 16, 256)
     L = circ.L
-    assert L == 7
+    assert L == 6
     # encrypted data blocks equal the oracle's encryption of the same packing
     for b in range(4):
         ref = he.encrypt(he.encode(data.blocks[b], L, D), qgnag.obj_seed(3, qgnag.SEED_BLOCK, b))
@@ -284,7 +284,7 @@ def test_job_step_bitwise_and_weights(small_job_inputs, graph):
 
 def test_first_order_job_bitwise(pair):
     """The first-order NAG baseline (no Bbar product, fresh ciphertexts at level
-    6): job state word for word against the oracle's first-order circuit, the
+    5): job state word for word against the oracle's first-order circuit, the
     cloud-only iteration with no Bbar likewise, weights against the FP64 twin."""
     ctx, he = pair
     X, y = synth.small(seed=12, n=1024, f=15)
@@ -293,7 +293,7 @@ def test_first_order_job_bitwise(pair):
     job = binding.Job(ctx, X, y, binding.FULL_BATCH | binding.FIRST_ORDER, 1024, binding.G8, 40.0, enc_seed=5,
                       key_seed=2)
     L = circ.L
-    assert L == 6
+    assert L == 5
     with pytest.raises(binding.HeError):
         job.input(1, 0)  # no Bbar ciphertext in a first-order job
     Z = [OCt(job.input(0, b).export(), L, D) for b in range(4)]
