@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-mini", action="store_true")
     ap.add_argument("--no-multi", action="store_true")
     ap.add_argument("--no-first-order", action="store_true")
+    ap.add_argument("--no-bbar", action="store_true")
     ap.add_argument("--sweep-point", default="", help="log_n,limbs,batch: run only this NTT sweep point")
     ap.add_argument("--sweep", action="store_true",
                     help="HE primitive sweep: batched NTT and key switching vs N, limbs and batch (JSON line per point)")
@@ -211,6 +212,9 @@ def run_ours(args, rank, world):
     mini = None
     if not args.no_mini:
         mini = minibatch_time(ctx, X, y, args)
+    bbar = None
+    if world == 1 and not args.no_bbar:
+        bbar = bbar_time(ctx, X, y)
     multi = first = None
     if world == 1 and not (args.no_multi and args.no_first_order):
         job.close()
@@ -236,6 +240,7 @@ def run_ours(args, rank, world):
         "mini_batch": mini,
         "multi_job": multi,
         "first_order_nag": first,
+        "client_bbar": bbar,
         "batched_speedup_vs_plain": round(plain / sec_iter / world, 2) if plain else None,
         "setup_s": round(setup_s, 1),
         "max_abs_err_vs_fp64_twin": err,
@@ -277,6 +282,24 @@ def minibatch_time(ctx, X, y, args):
     out["batched_graph_speedup_vs_plain"] = round(out["plain_s_per_iter"] / out["batched_graph_s_per_iter"], 2)
     job.close()
     return out
+
+
+def bbar_time(ctx, X, y):
+    """Client precompute of Bbar_k for every 1,024-row mini-batch (Sec. 3.1):
+    on the device (host arrays in, host array out, transfers included) against
+    the host routine on one thread (8 batches, extrapolated)."""
+    from paper_2406_13221_gb300 import binding
+    nb = -(-X.shape[0] // 1024)
+    binding.lr_bbar_batches(ctx, X[:4096], y[:4096], 1024, 256)  # first-call set-up
+    t0 = time.time()
+    binding.lr_bbar_batches(ctx, X, y, 1024, 256)
+    gpu = time.time() - t0
+    t0 = time.time()
+    for k in range(8):
+        binding.lr_bbar(X, y, 1024 * k, 1024, 256)
+    host = (time.time() - t0) * nb / 8
+    return {"batches": nb, "device_s": round(gpu, 4), "host_one_thread_s": round(host, 3),
+            "host_sample": "8 of %d batches, extrapolated" % nb}
 
 
 def first_order_time(ctx, X, y, args):
@@ -554,7 +577,7 @@ def cpu_baseline(X, y, samples=1, steps=1, warmup=0):
             g = circ.block_grad(z, W)
             acc = g if acc is None else he.add(acc, g)
         t1 = time.time()
-        Wn, Vn = circ.finish(acc, B, W, V, 0.99, 1.0 / data.n)
+        Wn, Vn = circ.finish(acc, B, W, V, 2.0, 0.99, 1.0 / data.n)
         circ.refresh(Wn, 7)
         circ.refresh(Vn, 8)
         t2 = time.time()

@@ -294,6 +294,14 @@ int he_refresh(he_ctx *ctx, const he_ct *in, int level, double scale, uint64_t s
  * rows [row0, row0 + rows) of Z = y * [1 | X]. */
 int he_lr_bbar(const double *X, const double *y, size_t n, size_t f, size_t row0, size_t rows,
                size_t g, double *out);
+/* The same precompute for every mini-batch of batch_rows rows at once, on the
+ * device (Sec. 3.1 Bbar_k, Algorithm 1; used by he_lr_job_create for f + 1 <=
+ * 256): out[k][0..g) for k < ceil(n / batch_rows), host memory, padded columns
+ * 0.  The Gram sums run in row order and the absolute row sums in column order
+ * without fused multiply-adds, so the values equal he_lr_bbar's bit for bit.
+ * Requires f + 1 <= 256 and g >= f + 1 (else HE_EINVAL). */
+int he_lr_bbar_batches(he_ctx *ctx, const double *X, const double *y, size_t n, size_t f, size_t batch_rows,
+                       size_t g, double *out);
 
 #ifdef __cplusplus
 }

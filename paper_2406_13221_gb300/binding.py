@@ -104,6 +104,7 @@ SIGNATURES = {
     "he_lr_iteration": (_i, [_vp, _vp, _sz, _vp, _vp, _vp, _i, _i, _d, _d, _d, _vp, _pp, _pp]),
     "he_refresh": (_i, [_vp, _vp, _i, _d, _u64, _pp]),
     "he_lr_bbar": (_i, [_vp, _vp, _sz, _sz, _sz, _sz, _sz, _vp]),
+    "he_lr_bbar_batches": (_i, [_vp, _vp, _vp, _sz, _sz, _sz, _sz, _vp]),
 }
 
 _lib = None
@@ -450,6 +451,16 @@ def zeta_table(log_n):
     if rc:
         raise HeError(rc, "he_zeta_table")
     return re, im
+
+
+def lr_bbar_batches(ctx, X, y, batch_rows, g):
+    """Bbar_k of every mini-batch, computed on the device: array [nbatch, g]."""
+    X = np.ascontiguousarray(X, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    nb = -(-X.shape[0] // batch_rows)
+    out = np.zeros((nb, g))
+    ctx.check(ctx.L.he_lr_bbar_batches(ctx.h, _ptr(X), _ptr(y), X.shape[0], X.shape[1], batch_rows, g, _ptr(out)))
+    return out
 
 
 def lr_bbar(X, y, row0, rows, g):

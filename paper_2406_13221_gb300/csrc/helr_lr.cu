@@ -66,6 +66,85 @@ extern "C" int he_lr_bbar(const double *X, const double *y, size_t n, size_t f, 
     return HE_OK;
 }
 
+// Bbar_k of every mini-batch k on the GPU (the same client precompute).  One
+// CTA per (batch, 16 rows a of H = Z_k^T Z_k), one thread per column b: each
+// Gram entry is accumulated over the rows in row order and each absolute row
+// sum over the columns in column order, with separate multiplies and adds (no
+// contraction), so the result equals bbar_rows bit for bit.
+static const int BB_TA = 16, BB_RC = 32;
+__global__ void __launch_bounds__(256) k_bbar(const double *__restrict__ X, const double *__restrict__ y, size_t n, int f,
+                                              size_t batch_rows, int g, double *__restrict__ out)
+{
+    extern __shared__ double bsm[];
+    const int f1 = f + 1, k = blockIdx.y, a0 = blockIdx.x * BB_TA, b = threadIdx.x;
+    double *zs = bsm;                  // [BB_RC][f1]: rows of Z_k
+    double *Hs = bsm + BB_RC * f1;     // [BB_TA][f1]: rows a0.. of H
+    const size_t r0 = (size_t)k * batch_rows, r1 = min(n, r0 + batch_rows);
+    double acc[BB_TA];
+#pragma unroll
+    for (int a = 0; a < BB_TA; a++) acc[a] = 0.0;
+    for (size_t rc = r0; rc < r1; rc += BB_RC) {
+        const int cnt = (int)min((size_t)BB_RC, r1 - rc);
+        for (int idx = threadIdx.x; idx < cnt * f1; idx += blockDim.x) {
+            const int rr = idx / f1, c = idx % f1;
+            const double yr = y[rc + rr];
+            zs[idx] = c == 0 ? yr : __dmul_rn(yr, X[(rc + rr) * f + c - 1]);
+        }
+        __syncthreads();
+        if (b < f1)
+            for (int rr = 0; rr < cnt; rr++) {
+                const double zb = zs[rr * f1 + b];
+#pragma unroll
+                for (int a = 0; a < BB_TA; a++)
+                    if (a0 + a < f1) acc[a] = __dadd_rn(acc[a], __dmul_rn(zs[rr * f1 + a0 + a], zb));
+            }
+        __syncthreads();
+    }
+    if (b < f1)
+#pragma unroll
+        for (int a = 0; a < BB_TA; a++) Hs[a * f1 + b] = acc[a];
+    __syncthreads();
+    const int a = a0 + (int)threadIdx.x;
+    if (threadIdx.x < BB_TA && a < f1) {
+        double s = 0.0;
+        for (int bb = 0; bb < f1; bb++) s = __dadd_rn(s, fabs(Hs[threadIdx.x * f1 + bb]));
+        out[(size_t)k * g + a] = 1.0 / __dadd_rn(BBAR_EPS, __dmul_rn(0.25, s));
+    }
+}
+
+// Bbar_k for the mini-batches of batch_rows rows of Z = y [1 | X] (n x f host
+// arrays) into out[nbatch][g] (host), computed on the device
+static int bbar_batches_dev(he_ctx *c, const double *X, const double *y, size_t n, size_t f, size_t batch_rows, size_t g,
+                            double *out)
+{
+    const size_t nbatch = (n + batch_rows - 1) / batch_rows, f1 = f + 1;
+    const size_t smem = (size_t)(BB_RC + BB_TA) * f1 * sizeof(double);
+    double *dX = nullptr, *dy = nullptr, *dout = nullptr;
+    HELR_TRY(helr_alloc(c, (void **)&dX, sizeof(double) * n * f));
+    HELR_TRY(helr_alloc(c, (void **)&dy, sizeof(double) * n));
+    HELR_TRY(helr_alloc(c, (void **)&dout, sizeof(double) * nbatch * g));
+    HELR_CUDA(c, cudaMemcpyAsync(dX, X, sizeof(double) * n * f, cudaMemcpyHostToDevice, c->stream));
+    HELR_CUDA(c, cudaMemcpyAsync(dy, y, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    HELR_CUDA(c, cudaMemsetAsync(dout, 0, sizeof(double) * nbatch * g, c->stream));  // padded columns
+    HELR_CUDA(c, cudaFuncSetAttribute(k_bbar, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const dim3 grid((unsigned)((f1 + BB_TA - 1) / BB_TA), (unsigned)nbatch);
+    HELR_LAUNCH(k_bbar<<<grid, 256, smem, c->stream>>>(dX, dy, n, (int)f, batch_rows, (int)g, dout));
+    HELR_CUDA(c, cudaGetLastError());
+    HELR_CUDA(c, cudaMemcpyAsync(out, dout, sizeof(double) * nbatch * g, cudaMemcpyDeviceToHost, c->stream));
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    helr_free(c, dX);
+    helr_free(c, dy);
+    helr_free(c, dout);
+    return HE_OK;
+}
+
+extern "C" int he_lr_bbar_batches(he_ctx *c, const double *X, const double *y, size_t n, size_t f, size_t batch_rows,
+                                  size_t g, double *out)
+{
+    if (!c || !X || !y || !out || n == 0 || f == 0 || batch_rows == 0 || g < f + 1 || f + 1 > 256) return HE_EINVAL;
+    return bbar_batches_dev(c, X, y, n, f, batch_rows, g, out);
+}
+
 // ------------------------------------------------------------------ job
 struct he_lr_job {
     he_ctx *c;
@@ -265,8 +344,12 @@ extern "C" int he_lr_job_create(he_ctx *c, const double *X, const double *y, siz
     }
     // Bbar per mini-batch (threads over batches), full batch by 1 / sum_k (1 / Bbar_k);
     // the first-order baseline needs only the 1/n scalars
+    // (on the device for up to 256 columns; wider data on the host threads,
+    // with the same arithmetic)
     std::vector<double> bk(fo ? 0 : (size_t)j->nbatch * g);
-    if (!fo) {
+    if (!fo && f + 1 <= 256) {
+        JTRY(bbar_batches_dev(c, X, y, n, f, batch_rows, g, bk.data()));
+    } else if (!fo) {
         unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
         std::vector<std::thread> th;
         for (unsigned t = 0; t < nth; t++)

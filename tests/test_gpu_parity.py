@@ -322,6 +322,27 @@ def test_first_order_job_bitwise(pair):
     assert np.abs(job.weights(0) - wp).max() < 1e-3
 
 
+@pytest.mark.parametrize("f", [37, 200])
+def test_bbar_batches_on_device_equal_host(pair, f):
+    """Bbar_k of every mini-batch (Sec. 3.1) computed on the device equals the
+    host routine bit for bit (same summation orders) and the oracle's numpy
+    computation within rounding; the last batch is ragged."""
+    ctx, _ = pair
+    X, y = synth.job(seed=f, n=5000, f=f, n_gauss=f // 2)
+    g = qgnag.pad_cols(f + 1)
+    dev = binding.lr_bbar_batches(ctx, X, y, 1024, g)
+    assert dev.shape == (5, g)
+    Z = qgnag.make_z(X, y)
+    for k in range(5):
+        rows = min(1024, 5000 - 1024 * k)
+        assert np.array_equal(dev[k], binding.lr_bbar(X, y, 1024 * k, rows, g)), k
+        ref = qgnag.bbar_rows(Z[1024 * k:1024 * k + rows], g)
+        assert np.allclose(dev[k], ref, rtol=1e-12, atol=0), k
+    assert not dev[:, f + 1:].any()
+    with pytest.raises(binding.HeError):
+        binding.lr_bbar_batches(ctx, np.zeros((10, 300)), np.ones(10), 1024, 512)  # more than 256 columns
+
+
 def test_minibatch_job_bitwise(pair):
     """Algorithm 1 over 3 mini-batches of 1,024 rows (the last one ragged: 952
     rows), 4 iterations so batch 0 is revisited; the g16 polynomial."""
