@@ -442,7 +442,7 @@ def ctw_bytes():
 
 
 def info_chunk(job, args):
-    return min(args.chunk if args.chunk else 64, int(job.info.n_blocks))
+    return min(args.chunk if args.chunk else 256, int(job.info.n_blocks))
 
 
 _PINNED = []

@@ -263,7 +263,7 @@ int he_lr_job_free(he_lr_job *job);
  * separate models): Steps 1-6 of all jobs' data blocks share launches, ordered
  * by decreasing row width; Steps 7-9 and the refresh run per job.  The jobs
  * must use one level, scale and sigmoid polynomial; they stay owned by the
- * caller and must outlive the handle.  blocks_per_launch 0 = 64. */
+ * caller and must outlive the handle.  blocks_per_launch 0 = 256. */
 typedef struct he_lr_multi he_lr_multi;
 int he_lr_multi_create(he_ctx *ctx, he_lr_job *const *jobs, size_t n_jobs, int blocks_per_launch, he_lr_multi **out);
 /* Iteration t of every job (same schedule); results through he_lr_job_weights. */

@@ -407,7 +407,7 @@ extern "C" int he_lr_job_create(he_ctx *c, const double *X, const double *y, siz
     // Steps 3/5: the masked plaintexts of the sigmoid polynomial
     JTRY(make_sigmoid_pts(c, L, g, j->scale0, j->scale0, j->poly, &j->sig, &j->p1_scale));
     // work buffers: chunk of blocks per launch
-    int chunk = batch_blocks > 0 ? batch_blocks : 64;  // tuned on GB300 at N = 2^16
+    int chunk = batch_blocks > 0 ? batch_blocks : 256;  // tuned on GB300 at N = 2^16
     chunk = std::min(chunk, mode == HE_LR_FULL_BATCH ? j->nblocks : j->bpb);
     j->chunk = std::max(1, chunk);
     j->chunk_max = j->chunk;
@@ -1018,7 +1018,7 @@ extern "C" int he_lr_multi_create(he_ctx *c, he_lr_job *const *jobs, size_t njob
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return jobs[a]->lg > jobs[b]->lg; });
     for (int i : idx)
         for (int b = 0; b < jobs[i]->nblocks; b++) m->order.push_back({i, b});
-    m->chunk = std::max(1, std::min(blocks_per_launch > 0 ? blocks_per_launch : 64, (int)m->order.size()));
+    m->chunk = std::max(1, std::min(blocks_per_launch > 0 ? blocks_per_launch : 256, (int)m->order.size()));
     int rc = ev_init(c, &m->ev, m->chunk, m->L);
     const size_t cts = 6 * (size_t)m->chunk + njobs + 2;
     if (!rc) rc = helr_alloc(c, (void **)&m->buf, sizeof(uint64_t) * m->ctw * cts);
