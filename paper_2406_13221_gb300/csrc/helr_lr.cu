@@ -120,22 +120,26 @@ static int bbar_batches_dev(he_ctx *c, const double *X, const double *y, size_t 
     const size_t nbatch = (n + batch_rows - 1) / batch_rows, f1 = f + 1;
     const size_t smem = (size_t)(BB_RC + BB_TA) * f1 * sizeof(double);
     double *dX = nullptr, *dy = nullptr, *dout = nullptr;
-    HELR_TRY(helr_alloc(c, (void **)&dX, sizeof(double) * n * f));
-    HELR_TRY(helr_alloc(c, (void **)&dy, sizeof(double) * n));
-    HELR_TRY(helr_alloc(c, (void **)&dout, sizeof(double) * nbatch * g));
-    HELR_CUDA(c, cudaMemcpyAsync(dX, X, sizeof(double) * n * f, cudaMemcpyHostToDevice, c->stream));
-    HELR_CUDA(c, cudaMemcpyAsync(dy, y, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
-    HELR_CUDA(c, cudaMemsetAsync(dout, 0, sizeof(double) * nbatch * g, c->stream));  // padded columns
-    HELR_CUDA(c, cudaFuncSetAttribute(k_bbar, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const dim3 grid((unsigned)((f1 + BB_TA - 1) / BB_TA), (unsigned)nbatch);
-    HELR_LAUNCH(k_bbar<<<grid, 256, smem, c->stream>>>(dX, dy, n, (int)f, batch_rows, (int)g, dout));
-    HELR_CUDA(c, cudaGetLastError());
-    HELR_CUDA(c, cudaMemcpyAsync(out, dout, sizeof(double) * nbatch * g, cudaMemcpyDeviceToHost, c->stream));
-    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    auto run = [&]() -> int {
+        HELR_TRY(helr_alloc(c, (void **)&dX, sizeof(double) * n * f));
+        HELR_TRY(helr_alloc(c, (void **)&dy, sizeof(double) * n));
+        HELR_TRY(helr_alloc(c, (void **)&dout, sizeof(double) * nbatch * g));
+        HELR_CUDA(c, cudaMemcpyAsync(dX, X, sizeof(double) * n * f, cudaMemcpyHostToDevice, c->stream));
+        HELR_CUDA(c, cudaMemcpyAsync(dy, y, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+        HELR_CUDA(c, cudaMemsetAsync(dout, 0, sizeof(double) * nbatch * g, c->stream));  // padded columns
+        HELR_CUDA(c, cudaFuncSetAttribute(k_bbar, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const dim3 grid((unsigned)((f1 + BB_TA - 1) / BB_TA), (unsigned)nbatch);
+        HELR_LAUNCH(k_bbar<<<grid, 256, smem, c->stream>>>(dX, dy, n, (int)f, batch_rows, (int)g, dout));
+        HELR_CUDA(c, cudaGetLastError());
+        HELR_CUDA(c, cudaMemcpyAsync(out, dout, sizeof(double) * nbatch * g, cudaMemcpyDeviceToHost, c->stream));
+        HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+        return HE_OK;
+    };
+    const int rc = run();
     helr_free(c, dX);
     helr_free(c, dy);
     helr_free(c, dout);
-    return HE_OK;
+    return rc;
 }
 
 extern "C" int he_lr_bbar_batches(he_ctx *c, const double *X, const double *y, size_t n, size_t f, size_t batch_rows,
@@ -245,15 +249,23 @@ static int make_sigmoid_pts(he_ctx *c, int L, int g, double z_scale, double w_sc
     }
     double *d = nullptr;
     uint64_t *buf = nullptr;
-    HELR_TRY(helr_alloc(c, (void **)&d, sizeof(double) * 3 * ns));
-    HELR_TRY(helr_alloc(c, (void **)&buf, sizeof(uint64_t) * (3 * (size_t)L - 2) * N));
-    HELR_CUDA(c, cudaMemcpyAsync(d, v.data(), sizeof(double) * 3 * ns, cudaMemcpyHostToDevice, c->stream));
-    const SigPts p = sig_pts(buf, L, N);
-    HELR_TRY(helr_encode_dev(c, d, nullptr, 1, 0, L - 1, w_scale, const_cast<uint64_t *>(p.p3), 0));
-    HELR_TRY(helr_encode_dev(c, d + ns, nullptr, 1, 0, L - 1, *p1_scale, const_cast<uint64_t *>(p.p1), 0));
-    HELR_TRY(helr_encode_dev(c, d + 2 * ns, nullptr, 1, 0, L - 3, s_scale, const_cast<uint64_t *>(p.p0), 0));
-    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    auto run = [&]() -> int {
+        HELR_TRY(helr_alloc(c, (void **)&d, sizeof(double) * 3 * ns));
+        HELR_TRY(helr_alloc(c, (void **)&buf, sizeof(uint64_t) * (3 * (size_t)L - 2) * N));
+        HELR_CUDA(c, cudaMemcpyAsync(d, v.data(), sizeof(double) * 3 * ns, cudaMemcpyHostToDevice, c->stream));
+        const SigPts p = sig_pts(buf, L, N);
+        HELR_TRY(helr_encode_dev(c, d, nullptr, 1, 0, L - 1, w_scale, const_cast<uint64_t *>(p.p3), 0));
+        HELR_TRY(helr_encode_dev(c, d + ns, nullptr, 1, 0, L - 1, *p1_scale, const_cast<uint64_t *>(p.p1), 0));
+        HELR_TRY(helr_encode_dev(c, d + 2 * ns, nullptr, 1, 0, L - 3, s_scale, const_cast<uint64_t *>(p.p0), 0));
+        HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+        return HE_OK;
+    };
+    const int rc = run();
     helr_free(c, d);
+    if (rc) {
+        helr_free(c, buf);
+        return rc;
+    }
     *out = buf;
     return HE_OK;
 }
