@@ -403,3 +403,53 @@ def test_multi_job_matches_single_jobs(pair):
         wp = plain.train(td, 2)
         assert np.abs(jm.weights(0) - wp).max() < 1e-3
     multi.close()
+
+
+@pytest.fixture(scope="module")
+def full_pair():
+    """N = 2^16 with the full chain (60 + 8 x 40 bits + 60-bit P): the parameters
+    of the 422,108 x 200 workload, 128 x 256 packing."""
+    ctx = binding.Context(16, 9)
+    he = Ckks(16, 9)
+    return ctx, he
+
+
+def test_full_shape_iteration_bitwise(full_pair):
+    """One full-batch iteration at N = 2^16 on two 128 x 256 blocks of
+    Financial-shaped data (201 columns padded to 256): the job's W' and V' after
+    the refresh equal the oracle's word for word."""
+    ctx, he = full_pair
+    X, y = synth.financial(seed=3, n=256)
+    data = qgnag.TrainData(X, y, g=256, m=128, batch_rows=1024)
+    circ = qgnag.Circuit(he, 256, 128, D)
+    he.keygen(2, circ.rotations())
+    job = binding.Job(ctx, X, y, binding.FULL_BATCH, 1024, binding.G8, 40.0, enc_seed=7, key_seed=2)
+    L = circ.L
+    Z = [OCt(job.input(0, b).export(), L, D) for b in range(2)]
+    B = OCt(job.input(1, 0).export(), L, D)
+    (Ww, _, _), (Vw, _, _) = job.state_words()
+    W, V = OCt(Ww, L, D), OCt(Vw, L, D)
+    job.step(0)
+    Wn, Vn = circ.iteration(Z, B, W, V, qgnag.schedule(0), qgnag.nag_scalars(1)[0], 1.0 / data.n)
+    W = circ.refresh(Wn, qgnag.obj_seed(7, qgnag.SEED_WREF, 0))
+    V = circ.refresh(Vn, qgnag.obj_seed(7, qgnag.SEED_VREF, 0))
+    (Ww, _, _), (Vw, _, _) = job.state_words()
+    assert np.array_equal(Ww, W.data)
+    assert np.array_equal(Vw, V.data)
+
+
+def test_full_shape_launch_configuration_against_twin(full_pair):
+    """The launch configuration of the bench at N = 2^16 (256 blocks per launch,
+    key switches in waves of 128 items) on 300 blocks, the last one ragged:
+    decrypted weights within 1e-3 of the FP64 twin after 3 iterations."""
+    ctx, _ = full_pair
+    X, y = synth.financial(seed=4, n=300 * 128 - 37)
+    data = qgnag.TrainData(X, y, g=256, m=128, batch_rows=1024)
+    job = binding.Job(ctx, X, y, binding.FULL_BATCH, 1024, binding.G8, 40.0, enc_seed=9, key_seed=2)
+    assert job.stats().n_blocks == 300
+    for t in range(3):
+        job.step(t)
+    from oracle import plain
+    wp = plain.train(data, 3)
+    for row in (0, 64, 127):
+        assert np.abs(job.weights(row) - wp).max() < 1e-3
