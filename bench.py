@@ -419,7 +419,7 @@ def sweep(args):
     n = 1 << LOGN
     for level in (7, 4):
         nl = level + 1
-        for batch in (1, 8, 32, 128):
+        for batch in (1, 8, 32, 128, 256):
             din = torch.randint(0, 1 << 30, (batch * nl * n,), dtype=torch.int64, device="cuda")
             dout = torch.zeros(batch * 2 * nl * n, dtype=torch.int64, device="cuda")
             ctx.keyswitch_batch(din.data_ptr(), dout.data_ptr(), batch, level, 0)
