@@ -478,7 +478,8 @@ def class_work(name, units, units2, dram_limbs):
     half = (LOGN // 2) * (n / 2) * OPS_BFLY   # one column or row half of a transform
     if name.startswith("ntt"):           # units = whole-limb transform equivalents
         return units * 2 * half, 16.0 * n * units
-    if name == "modup":                  # units = forward column halves (+ lift), units2 = inverse column halves
+    if name == "modup":                  # k_ks_modup_cols (ModUp, ModDown and rescale): units = forward column
+        #                                      halves (+ lift), units2 = inverse column halves
         return units * (half + n * OPS_LIFT) + units2 * (half + n * OPS_SCALE), 8.0 * n * dram_limbs
     # ks_inner: units = row halves, units2 = limbs of key products
     return units * half + units2 * n * OPS_MAC, 8.0 * n * dram_limbs
@@ -498,7 +499,7 @@ def roofline(prof, steps):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     hbm_ach = alg_bytes / sec / 1e9 if sec else 0
     kernel = {"ks_inner": "k_ks_inner_rows", "modup": "k_ks_modup_cols",
-              "ntt_fwd": "k_ks_modup_cols+k_ks_down_rows+k_ntt_fwd_*", "ntt_inv": "k_ntt_inv_*"}[best]
+              "ntt_fwd": "k_ks_down_rows+k_ntt_fwd_*", "ntt_inv": "k_ntt_inv_*"}[best]
     return {"kernel": kernel, "bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2), "unit": "Tops/s",
             "frac": round(achieved / peak, 4),
             "traffic": (None if recorded_traffic(kernel) is None or not launches

@@ -554,12 +554,19 @@ int run_down(he_ctx *c, const KsOut *o, const uint64_t *src, size_t src_item, si
         HELR_CUDA(c, (KsPlan<K1, K2>::prepare()));
         prepared = true;
     }
-    prof_start(c, PROF_NTT_FWD, s);
-    if (drow) KsPlan<K1, K2>::down_cols(c, drow, (size_t)items * 2, src_prime, lift, nl, s);
-    if (o) KsPlan<K1, K2>::down(c, *o, src, src_item, src_poly, lift, items, nl, inv, s);
-    // 2 nl forward transforms per item (column half, row half), and the inverse column half of 2 source limbs
-    prof_stop(c, PROF_NTT_FWD, s, (drow ? 0.5 * items * 2 * (nl + 1) : 0) + (o ? 0.5 * items * 2 * nl : 0),
-              (drow ? 1 : 0) + (o ? 1 : 0));
+    if (drow) {
+        // the column kernel is the one ModUp runs, timed with it: 2 nl forward
+        // column halves and 2 inverse column halves per item; DRAM: 2 source
+        // limbs read, 2 nl written
+        prof_start(c, PROF_MODUP, s);
+        KsPlan<K1, K2>::down_cols(c, drow, (size_t)items * 2, src_prime, lift, nl, s);
+        prof_stop(c, PROF_MODUP, s, (double)items * 2 * nl, 1, (double)items * 2, (double)items * 2 * (nl + 1));
+    }
+    if (o) {
+        prof_start(c, PROF_NTT_FWD, s);
+        KsPlan<K1, K2>::down(c, *o, src, src_item, src_poly, lift, items, nl, inv, s);
+        prof_stop(c, PROF_NTT_FWD, s, 0.5 * items * 2 * nl, 1);  // row halves of 2 nl transforms per item
+    }
     HELR_CUDA(c, cudaGetLastError());
     return HE_OK;
 }
