@@ -21,6 +21,17 @@
 namespace {
 using namespace nttc;
 
+// a centred residue s (signed, |s| <= q_src / 2) reduced into [0, q_t); the
+// Barrett step only when |s| can reach q_t
+__device__ __forceinline__ uint64_t lift_signed(uint64_t s, uint64_t q, const ModQ &mt, bool reduce)
+{
+    const bool neg = (int64_t)s < 0;
+    if (!reduce) return neg ? s + q : s;
+    uint64_t m = neg ? 0 - s : s;
+    m = m < q ? m : reduce64(m, mt);
+    return neg && m ? q - m : m;
+}
+
 // Second half of an inverse transform followed by a centred lift into several
 // primes and the first half of their forward transforms.  A CTA takes C
 // adjacent columns of one source limb (row pass of the inverse transform
@@ -64,7 +75,11 @@ __global__ void __launch_bounds__(C * Geo<K1>::T, 3)
         inv_strided<K1>(c, itw, 1, qi, 2 * qi);
         const uint64_t ni = ninv[2 * sp], nip = ninv[2 * sp + 1];
 #pragma unroll
-        for (int r = 0; r < E; r++) coef[(l + T * r) * C + jj] = shoup(c[r], ni, nip, qi);  // in [0, q_src)
+        for (int r = 0; r < E; r++) {
+            // the centred representative, stored as a signed 64-bit word
+            const uint64_t v = shoup(c[r], ni, nip, qi);  // in [0, q_src)
+            coef[(l + T * r) * C + jj] = v > (qi >> 1) ? v - qi : v;
+        }
     }
     uint64_t *dst = mid + src * (DOWN ? nl : nl + 1) * N + grp * C + jj;
     for (int tt = 0; tt < nl; tt++) {
@@ -73,9 +88,10 @@ __global__ void __launch_bounds__(C * Geo<K1>::T, 3)
         const ModQ mt = mods[pt];
         const uint64_t q = mt.q, q2 = 2 * q;
         const uint64_t *tw = twall + (size_t)pt * N * 2;
+        const bool reduce = (qi >> 1) >= q;  // centred words may reach q_t (a 60-bit source into a 40-bit target)
         uint64_t x[E];
 #pragma unroll
-        for (int r = 0; r < E; r++) x[r] = lift_centered(coef[(l + T * r) * C + jj], qi, mt);
+        for (int r = 0; r < E; r++) x[r] = lift_signed(coef[(l + T * r) * C + jj], q, mt, reduce);
         fwd_strided<K1>(x, tw, 1, q, q2);
         __syncthreads();  // the previous exchange has been read
         to_contig<K1>(x, seg, l);
