@@ -385,7 +385,8 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T)
     const size_t bt = (size_t)(bid >> 1);
     const int l = threadIdx.x % T, rl = threadIdx.x / T;
     const int row = grp * RPC + rl;
-    const uint64_t q = mods[j].q, q2 = 2 * q;
+    const ModQ mq = mods[j];
+    const uint64_t q = mq.q, q2 = 2 * q;
     const uint64_t *tw = twall + (size_t)j * N * 2;
     const uint64_t *rowp = lift + ((bt * 2 + p) * nl + j) * N + (size_t)row * R2;
     const uint64_t *sv = srcp + bt * src_item + p * src_poly;
@@ -408,16 +409,16 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T)
     fwd_contig<K2, true>(x, tw, A, l, q, q2);
     __syncthreads();
     to_strided<K2>(x, seg, l);  // word l + T r of the row: coalesced below
-    const uint64_t pv = inv[2 * j], pvp = inv[2 * j + 1];
+    const uint64_t pv = inv[2 * j], pvp = inv[2 * j + 1], q4 = 4 * q;
+    // lazy arithmetic, one reduction at the end: src + 4q - w < 5q (w < 4q from
+    // Harvey's butterflies), the Shoup product < 2q, each added term < q: the
+    // sum stays below 5q < 2^64 for primes below 2^61
 #pragma unroll
     for (int r = 0; r < E; r++) {
         const int k = row * R2 + l + T * r;
         const size_t lk = (size_t)j * N + k;
-        uint64_t w = x[r];
-        w = w >= q2 ? w - q2 : w;
-        w = w >= q ? w - q : w;
-        uint64_t v = shoup(submod(sv[lk], w, q), pv, pvp, q);
-        if (o.rel) v = addmod(v, o.rel[bt * o.rel_item + p * o.rel_poly + lk], q);
+        uint64_t v = shoup_lazy(sv[lk] + (q4 - x[r]), pv, pvp, q);
+        if (o.rel) v += o.rel[bt * o.rel_item + p * o.rel_poly + lk];
         if (o.rot && p == 0) {
             // sigma_gal on the evaluation form: position k holds the evaluation at
             // psi^(2 bitrev(k) + 1); it takes the value at the position of
@@ -426,10 +427,10 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T)
             const uint32_t kk = __brev((uint32_t)k) >> (32 - LOGN);
             const uint64_t e = ((2ull * kk + 1) * o.gal) & mask2n;
             const uint32_t ps = __brev((uint32_t)((e - 1) >> 1)) >> (32 - LOGN);
-            v = addmod(v, o.rot[bt * o.rot_item + (size_t)j * N + ps], q);
+            v += o.rot[bt * o.rot_item + (size_t)j * N + ps];
         }
-        if (o.acc) v = addmod(v, o.acc[bt * o.acc_item + p * o.acc_poly + lk], q);
-        o.out.p[bt * o.out.item + p * o.out.poly + lk] = v;
+        if (o.acc) v += o.acc[bt * o.acc_item + p * o.acc_poly + lk];
+        o.out.p[bt * o.out.item + p * o.out.poly + lk] = reduce64(v, mq);
     }
 }
 
