@@ -304,9 +304,20 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
         // bypasses L1 and leaves room there for the twiddles
         const uint64_t *kp0 = key + (((size_t)i * 2 + 0) * (nq + 1) + kl) * N + roff + l;
         const uint64_t *kp1 = key + (((size_t)i * 2 + 1) * (nq + 1) + kl) * N + roff + l;
+        // key words of chunk c in flight while chunk c - 1 is accumulated
+        uint64_t ka[2][CH], kb[2][CH];
+        auto load_keys = [&](int c, uint64_t (&k0v)[CH], uint64_t (&k1v)[CH]) {
+#pragma unroll
+            for (int k = 0; k < CH; k++) {
+                k0v[k] = ld_stream(kp0 + (c * CH + k) * G::T);
+                k1v[k] = ld_stream(kp1 + (c * CH + k) * G::T);
+            }
+        };
+        load_keys(0, ka[0], kb[0]);
         if (i > 0) tmem_wait_st();  // the previous digit's accumulators are in place
 #pragma unroll
         for (int c = 0; c < E / CH; c++) {
+            if (c + 1 < E / CH) load_keys(c + 1, ka[(c + 1) & 1], kb[(c + 1) & 1]);
             uint32_t s0[4 * CH], s1[4 * CH];
             const uint32_t c0 = tbase + 4 * CH * c, c1 = tbase + 4 * E + 4 * CH * c;
             if (i > 0) {
@@ -315,16 +326,14 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
                 tmem_wait_ld32(s0, s1);
 #pragma unroll
                 for (int k = 0; k < CH; k++) {
-                    const int r = c * CH + k;
-                    mac128(s0 + 4 * k, x[r], ld_stream(kp0 + r * G::T));
-                    mac128(s1 + 4 * k, x[r], ld_stream(kp1 + r * G::T));
+                    mac128(s0 + 4 * k, x[c * CH + k], ka[c & 1][k]);
+                    mac128(s1 + 4 * k, x[c * CH + k], kb[c & 1][k]);
                 }
             } else {
 #pragma unroll
                 for (int k = 0; k < CH; k++) {
-                    const int r = c * CH + k;
-                    set128(s0 + 4 * k, x[r], ld_stream(kp0 + r * G::T));
-                    set128(s1 + 4 * k, x[r], ld_stream(kp1 + r * G::T));
+                    set128(s0 + 4 * k, x[c * CH + k], ka[c & 1][k]);
+                    set128(s1 + 4 * k, x[c * CH + k], kb[c & 1][k]);
                 }
             }
             if (i + 1 < nl) {
