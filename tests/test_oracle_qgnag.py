@@ -206,3 +206,38 @@ def test_encrypted_first_order_matches_fp64_twin():
     assert np.abs(w - wp[None, :]).max() < 1e-3
     # the first-order and quadratic-gradient updates differ (Bbar is not the identity)
     assert np.abs(wp - plain.train(data, 2, sched=sched)).max() > 1e-3
+
+
+def test_masked_polynomial_is_zero_outside_column_zero():
+    """Reading of the Sec. 2.2 circuit: with the mask inside the plaintext
+    products, s = (1 - c0) M - c1 (M t) - c3 t^2 (M t) decrypts to 1 - g8(ip_r)
+    in column 0 of row r and to 0 elsewhere (although t holds partial sums
+    there); after the replication every column of row r holds 1 - g8(ip_r)."""
+    X, y = synth.small(seed=8, n=256, f=15)
+    he = Ckks(13, 9)
+    data = qgnag.TrainData(X, y, g=16, m=256, batch_rows=1024)
+    circ = qgnag.Circuit(he, 16, 256, 2.0 ** 40)
+    he.keygen(3, circ.rotations())
+    L, D = circ.L, 2.0 ** 40
+    rng = np.random.default_rng(8)
+    w = rng.uniform(-1, 1, 16)
+    Z = he.encrypt(he.encode(data.blocks[0], L, D), 1)
+    W = he.encrypt(he.encode(np.tile(w, 256), L, D), 2)
+    t = he.rescale(he.mul(Z, W))
+    for k in range(circ.lg):
+        t = he.add(t, he.rotate(t, 1 << k))
+    sq = he.rescale(he.mul(t, t))
+    cube = he.rescale(he.mul(sq, he.rescale(he.ptmul(t, circ.p3))))
+    lin = he.rescale(he.ptmul(t, circ.p1))
+    lin.scale = cube.scale
+    s = he.ptadd(he.add(cube, he.moddrop(lin, cube.level)), circ.p0)
+    got = he.decode(he.decrypt(s)).real.reshape(256, 16)
+    ip = data.blocks[0].reshape(256, 16) @ w
+    c0, c1, c3 = qgnag.G8
+    want = 1.0 - (c0 + c1 * ip + c3 * ip ** 3)
+    assert np.abs(got[:, 0] - want).max() < 1e-6
+    assert np.abs(got[:, 1:]).max() < 1e-6
+    for k in range(circ.lg):
+        s = he.add(s, he.rotate(s, -(1 << k)))
+    rep = he.decode(he.decrypt(s)).real.reshape(256, 16)
+    assert np.abs(rep - want[:, None]).max() < 1e-6
