@@ -113,13 +113,22 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "fallback": True}
 
 
+def kernel_sources_hash():
+    """sha256 (12 hex digits) of the transform and key-switch sources with
+    comments and whitespace removed: it changes with the code, not the prose."""
+    import re
+    src = "".join(open(os.path.join(ROOT, "paper_2406_13221_gb300", "csrc", f)).read()
+                  for f in ("ntt_core.cuh", "ks.cu", "ntt.cu"))
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return hashlib.sha256("".join(src.split()).encode()).hexdigest()[:12]
+
+
 def recorded_traffic(kernel):
     """DRAM traffic over algorithmic bytes of one ncu-captured launch of `kernel`
     (profiles/traffic.txt), valid while the kernel's sources are unchanged (else
     None); bench.py scales it to its own average launch."""
-    src = b"".join(open(os.path.join(ROOT, "paper_2406_13221_gb300", "csrc", f), "rb").read()
-                   for f in ("ntt_core.cuh", "ks.cu", "ntt.cu"))
-    h = hashlib.sha256(src).hexdigest()[:12]
+    h = kernel_sources_hash()
     try:
         for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
             p = line.split()

@@ -1,5 +1,6 @@
 // ks.cu -- fused hybrid key switching (the relinearisation inside every Mul and
-// the key switch inside every rotation, Sec. 2.1).
+// the key switch inside every rotation, Sec. 2.1), and the division by a
+// dropped prime shared by ModDown and rescale.
 //
 // Key switching of d (level l, L = l + 1 limbs) with one special prime P and
 // one digit per ciphertext prime:
@@ -7,14 +8,22 @@
 //            every target modulus t in {q_0..q_l, P};
 //   inner    acc_t = sum_i NTT_t(digit i) * key_(i,t)   (two key polynomials);
 //   ModDown  out_j = (acc_j - centred(acc_P) mod q_j) * P^-1.
-// The forward transforms of ModUp are fused with their neighbours:
-//   k_ks_modup_cols  lifts digit i into target t while loading and runs the
-//                    column pass of the transform (t = i is skipped: that limb
-//                    is the evaluation-form input itself);
+// The transforms are split into a column pass and a row pass (see ntt.cu) and
+// fused with their neighbours:
+//   k_ntt_inv_rows   (ntt.cu) row pass of the inverse transform of the input;
+//   k_ks_modup_cols  finishes the inverse transform of digit i (column pass,
+//                    N^-1), then lifts it into every target t != i and runs
+//                    the forward column pass (t = i is the evaluation-form
+//                    input itself);
 //   k_ks_inner_rows  finishes the row pass of every digit for one target and
-//                    multiplies-accumulates with the key rows in registers, so
-//                    the transformed digits are never written out.
-// Items run in waves small enough for the column-pass output to stay in L2.
+//                    multiplies-accumulates with the key rows (128-bit sums in
+//                    tensor memory), so the transformed digits are never stored;
+//   k_ntt_inv_rows   row pass of the inverse transform of the P part;
+//   k_ks_modup_cols  (ModDown mode) its column pass, the lift into q_0..q_l and
+//                    their forward column passes;
+//   k_ks_down_rows   the forward row passes fused with the output stage.
+// Key switches run in waves of items; each key row is read from DRAM once per
+// wave and served from L2 to the wave's items.
 #include <stdlib.h>
 #include "ntt_core.cuh"
 
