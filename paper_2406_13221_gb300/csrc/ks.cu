@@ -234,6 +234,11 @@ __device__ __forceinline__ uint64_t redc128(uint64_t hi, uint64_t lo, const ModQ
 // (one Montgomery reduction, after reducing the high word below q).  The 128-bit accumulators of both key polynomials live
 // in TMEM between digits (128 columns per thread), so the registers hold only
 // the digit being transformed.
+//
+// The row twiddles depend on the target and the row, not on the digit: the CTA
+// copies those of its rows into shared memory once and serves every digit from
+// there.  One digit buffer (the next digit's rows are requested as soon as the
+// exchange has read the current ones) keeps the CTA at 48 KB, 4 CTAs per SM.
 template <int K1, int K2, int RPC, bool LZ>
 __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
     k_ks_inner_rows(const uint64_t *__restrict__ mid, const uint64_t *__restrict__ dntt, const uint64_t *__restrict__ key,
@@ -247,9 +252,11 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
     constexpr uint32_t TCOLS = 8 * E;  // a0[r]: columns 4r..4r+3; a1[r]: 4E + 4r..4E + 4r + 3
     static_assert(NT == 128 && E % CH == 0 && TCOLS >= 32 && TCOLS <= 128 && (TCOLS & (TCOLS - 1)) == 0, "TMEM layout");
     extern __shared__ uint64_t smem[];
-    // [2][TILE]: the rows of two digits (double buffer); the rows of the digit
-    // being transformed also serve as its exchange segments once loaded
+    // [TILE]: the rows of one digit, which also serve as its exchange segments
     uint64_t *buf = smem;
+    // [RPC][R2] twiddle pairs of the CTA's rows: stage block m at pairs m - 1 .. 2m - 2
+    // of its row (the last pair unused), then the TMEM address slot
+    uint64_t *tws = smem + TILE;
     int bid = blockIdx.x;
     const int b = bid % items;  // items sharing one key row are adjacent: the key row is read from L2
     bid /= items;
@@ -274,43 +281,52 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
             cp_async16(dst + w, src + w);
         }
     };
-    // the TMEM address is handed over in the second buffer, before its first use
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(buf + TILE);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tws + 2 * RPC * R2);
     if (warp == 0) tmem_alloc(tmem_slot, TCOLS);
     prefetch(0, buf);
+    // pair j of stage block m of row r sits at m (R1 + r) + j in the table
+    for (int k = threadIdx.x; k < RPC * R2; k += NT) {
+        const int pr = k % R2, rr = k / R2;
+        if (pr == R2 - 1) continue;
+        const int mm = 1 << (31 - __clz(pr + 1));
+        cp_async16(tws + 2 * k, tw + 2 * (mm * (R1 + grp * RPC + rr) + (pr + 1 - mm)));
+    }
     cp_async_commit();
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
     const uint32_t tbase = *tmem_slot + ((uint32_t)(32 * warp) << 16);
-    __syncthreads();  // every thread holds the address before the slot is overwritten
+    // the transform indexes stage block m at m A + j: with A = 1 that is pair
+    // m - 1 + j from the start of the row's copy
+    const uint64_t *twr = tws + 2 * (rl * R2 - 1);
     uint64_t *o0 = acc + (((size_t)b * 2 + 0) * (nl + 1) + t) * N + roff + E * l;
     uint64_t *o1 = acc + (((size_t)b * 2 + 1) * (nl + 1) + t) * N + roff + E * l;
     for (int i = 0; i < nl; i++) {
-        uint64_t *cur = buf + (i & 1) * TILE;
-        if (i + 1 < nl) prefetch(i + 1, buf + ((i + 1) & 1) * TILE);
-        cp_async_commit();
-        cp_async_wait<1>();  // digit i has landed
+        cp_async_wait<0>();  // digit i (and, for i = 0, the twiddles) have landed
         __syncthreads();
         uint64_t x[E];
-        uint64_t *rows = cur + rl * R2;
+        uint64_t *rows = buf + rl * R2;
         if (i == t) {
 #pragma unroll
             for (int r = 0; r < E; r++) x[r] = rows[E * l + r];
         } else {
 #pragma unroll
             for (int r = 0; r < E; r++) x[r] = rows[l + G::T * r];
-            const int A = R1 + row;
-            fwd_strided<K2, LZ>(x, tw, A, q, q2);
+            fwd_strided<K2, LZ, true>(x, twr, 1, q, q2);
             __syncthreads();  // every thread has read its words of the row
             to_contig_swz<K2>(x, rows, l);
-            fwd_contig<K2, true, LZ>(x, tw, A, l, q, q2);
+        }
+        __syncthreads();  // the buffer is read: it takes the next digit
+        if (i + 1 < nl) prefetch(i + 1, buf);
+        cp_async_commit();
+        if (i != t) {
+            fwd_contig<K2, true, LZ, true>(x, twr, 1, l, q, q2);
             // words stay unreduced: below 4q, or below 20q with LZ (the column
             // pass leaves them below 4q)
         }
         // key rows are stored with word E l + r at r T + l (see k_key_rows): adjacent
         // threads read adjacent words; each key word is read once per CTA, so it
-        // bypasses L1 and leaves room there for the twiddles
+        // bypasses L1
         const uint64_t *kp0 = key + (((size_t)i * 2 + 0) * (nq + 1) + kl) * N + roff + l;
         const uint64_t *kp1 = key + (((size_t)i * 2 + 1) * (nq + 1) + kl) * N + roff + l;
         // key words of chunk c in flight while chunk c - 1 is accumulated
@@ -367,7 +383,6 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
                 }
             }
         }
-        __syncthreads();  // buffer `cur` is refilled two digits later
     }
     tmem_fence_before();
     __syncthreads();
@@ -461,7 +476,8 @@ struct KsPlan {
     static constexpr int RPCD = (256 / T2) < R1 ? (256 / T2) : R1;
     static constexpr size_t SMD = (size_t)RPCD * Geo<K2>::SEG * 8;
     static constexpr size_t SM1 = (size_t)C * Geo<K1>::SEG * 8 + (size_t)C * R1 * 8;
-    static constexpr size_t SM2 = 2 * (size_t)RPC * R2 * 8;
+    // one digit's rows, the row twiddle pairs, the TMEM address slot
+    static constexpr size_t SM2 = (size_t)RPC * R2 * 8 + (size_t)RPC * R2 * 16 + 16;
     static cudaError_t prepare()
     {
         cudaError_t e = helr_fit_carveout((const void *)k_ks_modup_cols<K1, K2, C, false>, C * T1, SM1);

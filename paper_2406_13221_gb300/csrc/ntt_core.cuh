@@ -30,9 +30,15 @@ __device__ __forceinline__ void gs_bfly(uint64_t &x, uint64_t &y, uint64_t w, ui
     x = a;
 }
 
+// twiddle pair idx (w, Shoup companion) from the global table, or from a copy
+// in shared memory (SH)
+template <bool SH = false>
 __device__ __forceinline__ ulonglong2 ldtw(const uint64_t *tw, int idx)
 {
-    return __ldg(reinterpret_cast<const ulonglong2 *>(tw) + idx);
+    if constexpr (SH)
+        return reinterpret_cast<const ulonglong2 *>(tw)[idx];
+    else
+        return __ldg(reinterpret_cast<const ulonglong2 *>(tw) + idx);
 }
 
 // padded shared-memory position of word j inside one column/row segment
@@ -52,24 +58,24 @@ struct Geo {
 //
 // forward stages on the strided assignment (j = l + T r): local stages s < LE;
 // at local stage m = 2^s the E words form m groups of 2 hr (hr = E / 2m).
-template <int K, bool LZ, int S>
+template <int K, bool LZ, bool SH, int S>
 __device__ __forceinline__ void fwd_strided_st(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, uint64_t q, uint64_t q2)
 {
     constexpr int E = Geo<K>::E, LE = Geo<K>::LE, m = 1 << S, hr = E >> (S + 1);
     ulonglong2 w[m];
 #pragma unroll
-    for (int g = 0; g < m; g++) w[g] = ldtw(tw, m * A + g);
+    for (int g = 0; g < m; g++) w[g] = ldtw<SH>(tw, m * A + g);
 #pragma unroll
     for (int bf = 0; bf < E / 2; bf++) {
         const int g = bf / hr, k = bf % hr;
         ct_bfly<LZ>(x[g * 2 * hr + k], x[g * 2 * hr + k + hr], w[g].x, w[g].y, q, q2);
     }
-    if constexpr (S + 1 < LE) fwd_strided_st<K, LZ, S + 1>(x, tw, A, q, q2);
+    if constexpr (S + 1 < LE) fwd_strided_st<K, LZ, SH, S + 1>(x, tw, A, q, q2);
 }
-template <int K, bool LZ = false>
+template <int K, bool LZ = false, bool SH = false>
 __device__ __forceinline__ void fwd_strided(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, uint64_t q, uint64_t q2)
 {
-    fwd_strided_st<K, LZ, 0>(x, tw, A, q, q2);
+    fwd_strided_st<K, LZ, SH, 0>(x, tw, A, q, q2);
 }
 
 // Twiddle j of stage block m * A (j < m) for group g of thread l on the
@@ -85,24 +91,24 @@ __device__ __forceinline__ int tw_contig(int m, int A, int l, int gpt, int g)
 
 // forward stages on the contiguous assignment (j = E l + r): local stages s >= LE;
 // half-span h = R / 2^(s+1) <= E/2, gpt = E / 2h groups per thread.
-template <int K, bool ROW, bool LZ, int S>
+template <int K, bool ROW, bool LZ, bool SH, int S>
 __device__ __forceinline__ void fwd_contig_st(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, int l, uint64_t q, uint64_t q2)
 {
     constexpr int E = Geo<K>::E, R = Geo<K>::R, m = 1 << S, h = R >> (S + 1), gpt = E / (2 * h);
     ulonglong2 w[gpt];
 #pragma unroll
-    for (int g = 0; g < gpt; g++) w[g] = ldtw(tw, tw_contig<K, ROW>(m, A, l, gpt, g));
+    for (int g = 0; g < gpt; g++) w[g] = ldtw<SH>(tw, tw_contig<K, ROW>(m, A, l, gpt, g));
 #pragma unroll
     for (int bf = 0; bf < E / 2; bf++) {
         const int g = bf / h, k = bf % h;
         ct_bfly<LZ>(x[g * 2 * h + k], x[g * 2 * h + k + h], w[g].x, w[g].y, q, q2);
     }
-    if constexpr (S + 1 < K) fwd_contig_st<K, ROW, LZ, S + 1>(x, tw, A, l, q, q2);
+    if constexpr (S + 1 < K) fwd_contig_st<K, ROW, LZ, SH, S + 1>(x, tw, A, l, q, q2);
 }
-template <int K, bool ROW, bool LZ = false>
+template <int K, bool ROW, bool LZ = false, bool SH = false>
 __device__ __forceinline__ void fwd_contig(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, int l, uint64_t q, uint64_t q2)
 {
-    fwd_contig_st<K, ROW, LZ, Geo<K>::LE>(x, tw, A, l, q, q2);
+    fwd_contig_st<K, ROW, LZ, SH, Geo<K>::LE>(x, tw, A, l, q, q2);
 }
 
 template <int K, bool ROW, int S>
