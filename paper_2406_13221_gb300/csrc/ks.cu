@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(C * Geo<K1>::T, 3)
         uint64_t x[E];
 #pragma unroll
         for (int r = 0; r < E; r++) x[r] = lift_signed(coef[(l + T * r) * C + jj], q, mt, reduce);
-        fwd_strided<K1>(x, tw, 1, q, q2);
+        fwd_strided<K1, false, false, true>(x, tw, 1, q, q2);  // lifted words are below q
         __syncthreads();  // the previous exchange has been read
         to_contig<K1>(x, seg, l);
         fwd_contig<K1, false>(x, tw, 1, l, q, q2);

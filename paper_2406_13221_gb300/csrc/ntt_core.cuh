@@ -58,7 +58,8 @@ struct Geo {
 //
 // forward stages on the strided assignment (j = l + T r): local stages s < LE;
 // at local stage m = 2^s the E words form m groups of 2 hr (hr = E / 2m).
-template <int K, bool LZ, bool SH, int S>
+// LT2: the words enter below 2q, so the first stage needs no correction
+template <int K, bool LZ, bool SH, bool LT2, int S>
 __device__ __forceinline__ void fwd_strided_st(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, uint64_t q, uint64_t q2)
 {
     constexpr int E = Geo<K>::E, LE = Geo<K>::LE, m = 1 << S, hr = E >> (S + 1);
@@ -68,14 +69,14 @@ __device__ __forceinline__ void fwd_strided_st(uint64_t (&x)[Geo<K>::E], const u
 #pragma unroll
     for (int bf = 0; bf < E / 2; bf++) {
         const int g = bf / hr, k = bf % hr;
-        ct_bfly<LZ>(x[g * 2 * hr + k], x[g * 2 * hr + k + hr], w[g].x, w[g].y, q, q2);
+        ct_bfly<LZ || (LT2 && S == 0)>(x[g * 2 * hr + k], x[g * 2 * hr + k + hr], w[g].x, w[g].y, q, q2);
     }
-    if constexpr (S + 1 < LE) fwd_strided_st<K, LZ, SH, S + 1>(x, tw, A, q, q2);
+    if constexpr (S + 1 < LE) fwd_strided_st<K, LZ, SH, LT2, S + 1>(x, tw, A, q, q2);
 }
-template <int K, bool LZ = false, bool SH = false>
+template <int K, bool LZ = false, bool SH = false, bool LT2 = false>
 __device__ __forceinline__ void fwd_strided(uint64_t (&x)[Geo<K>::E], const uint64_t *tw, int A, uint64_t q, uint64_t q2)
 {
-    fwd_strided_st<K, LZ, SH, 0>(x, tw, A, q, q2);
+    fwd_strided_st<K, LZ, SH, LT2, 0>(x, tw, A, q, q2);
 }
 
 // Twiddle j of stage block m * A (j < m) for group g of thread l on the
