@@ -23,7 +23,8 @@
  *   - Levels: a ciphertext at level l has limbs q_0..q_l; fresh encryptions
  *     sit at level n_q - 1.
  *   - Words exchanged with the host (he_ct_export / he_ct_import) are in
- *     coefficient form, layout [2][level+1][N], limb j reduced modulo q_j.
+ *     coefficient form, layout [2][level+1][N], limb j reduced modulo q_j
+ *     (he_ct_import returns HE_EINVAL on a word >= q_j).
  *   - The library fails loudly: there is no CPU fallback for any call that
  *     computes on ciphertexts; without a usable CUDA device they return
  *     HE_ECUDA.

@@ -617,6 +617,9 @@ extern "C" int he_ct_import(he_ctx *c, const uint64_t *words, size_t nw, int lev
     if (!c || !words || !out || level < 0 || level >= c->nq) return HE_EINVAL;
     const size_t need = 2 * (size_t)(level + 1) * c->n;
     if (nw < need) return helr_fail(c, HE_EINVAL, "import buffer too small");
+    for (size_t k = 0; k < need; k++)
+        if (words[k] >= c->q[(k / c->n) % (size_t)(level + 1)])
+            return helr_fail(c, HE_EINVAL, "import word not reduced modulo its prime");
     he_ct *ct = nullptr;
     HELR_TRY(helr_new_ct(c, level, scale, &ct));
     HELR_CUDA(c, cudaMemcpyAsync(ct->d, words, need * 8, cudaMemcpyHostToDevice, c->stream));

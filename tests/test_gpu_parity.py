@@ -212,6 +212,15 @@ def test_errors_are_reported(pair):
     with pytest.raises(binding.HeError) as e:
         ctx.add(a, low)
     assert e.value.code == binding.HE_ELEVEL
+    # imported words must be reduced modulo their limb's prime
+    lv, sc = a.info()
+    words = a.export()
+    bad = words.copy()
+    bad[1, lv, 7] = ctx.primes[lv]
+    with pytest.raises(binding.HeError) as e:
+        ctx.import_ct(bad, lv, sc)
+    assert e.value.code == binding.HE_EINVAL
+    assert np.array_equal(ctx.import_ct(words, lv, sc).export(), words)
 
 
 # ------------------------------------------------------------------ the iteration
