@@ -150,6 +150,13 @@ def run_ours(args, rank, world):
     t0 = time.time()
     X, y = synth.financial(seed=1, n=args.rows)
     ctx = binding.Context(LOGN, NQ)
+    # key-switch wave per level from the library's autotuner (the relinearisation
+    # key it times with comes from the same seed the job uses for its keys)
+    ta = time.time()
+    ctx.keygen(2)
+    tuned_levels = ctx.autotune(None, 256)
+    autotune = {"ks_wave_by_level": [ctx.ks_wave(lv) for lv in range(NQ)], "levels_measured": tuned_levels,
+                "s": round(time.time() - ta, 2)}
     job = binding.Job(ctx, X, y, binding.FULL_BATCH, 1024, binding.G8, LOG_SCALE, enc_seed=3, key_seed=2,
                       batch_blocks=args.chunk)
     info = job.stats()
@@ -252,6 +259,7 @@ def run_ours(args, rank, world):
         "client_bbar": bbar,
         "batched_speedup_vs_plain": round(plain / sec_iter / world, 2) if plain else None,
         "setup_s": round(setup_s, 1),
+        "autotune": autotune,
         "max_abs_err_vs_fp64_twin": err,
         "clocks": clocks, "gpu_launches": int(launches), "roofline": roof, "e2e": e2e,
         "context": PAPER_CONTEXT,

@@ -147,6 +147,24 @@ int he_ntt_inverse(he_ctx *ctx, uint64_t *d_limbs, size_t n_limbs, const int *pr
  * allocated by the call. */
 int he_keyswitch_batch(he_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int batch, int level,
                        uint64_t gal);
+/* Autotuning of the key-switch wave: the number of items whose ModUp and
+ * inner product share one DRAM read of each key row (the run-time tile of the
+ * fused key switch of Sec. 2.1; scratch [wave][level+1][level+2][N] words).
+ * For every level it times `items` batched relinearisations (16 or more;
+ * 0 = 256) with waves of 16, 32, 64, 128 and 256 items (those <= items) on the
+ * context stream and keeps the smallest wave within 1% of the fastest; later
+ * key switches of this context use it.
+ * table_path (may be NULL): a text table keyed by device, SM count, log N,
+ * n_q and the primes; levels it already holds are loaded instead of measured,
+ * and the file is rewritten when anything was measured.  *measured (may be
+ * NULL) receives the number of levels measured.  Needs he_keygen first
+ * (HE_EKEY); device memory for the largest wave is allocated and freed by the
+ * call (a wave that does not fit is skipped); HE_EINVAL when the table cannot
+ * be written.  The environment variable HELR_KS_WAVE, when set, overrides
+ * every table. */
+int he_autotune(he_ctx *ctx, const char *table_path, int items, int *measured);
+/* The wave key switches at `level` use (> 0), or -HE_EINVAL. */
+int he_ks_wave(const he_ctx *ctx, int level);
 /* Rescale without allocating (no counterpart in the paper: it exists for
  * callers that may not allocate device memory, such as code running under a
  * device-memory budget fixed in advance or inside a framework that owns every

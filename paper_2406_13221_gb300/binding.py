@@ -79,6 +79,8 @@ SIGNATURES = {
     "he_ntt_forward": (_i, [_vp, _vp, _sz, _vp, _i]),
     "he_ntt_inverse": (_i, [_vp, _vp, _sz, _vp, _i]),
     "he_keyswitch_batch": (_i, [_vp, _vp, _vp, _i, _i, _u64]),
+    "he_autotune": (_i, [_vp, ctypes.c_char_p, _i, ctypes.POINTER(_i)]),
+    "he_ks_wave": (_i, [_vp, _i]),
     "he_galois_elt": (_u64, [_vp, _i64]),
     "he_lr_job_create": (_i, [_vp, _vp, _vp, _sz, _sz, _i, _sz, _i, _d, _u64, _u64, _i, _pp]),
     "he_lr_job_step": (_i, [_vp, _i, he_lr_sched]),
@@ -257,6 +259,18 @@ class Context:
 
     def rescale_noalloc(self, din, dout, batch, level):
         self.check(self.L.he_rescale_noalloc(self.h, din, dout, batch, level))
+
+    def autotune(self, path=None, items=0):
+        """Choose the key-switch wave per level (he_autotune); returns the number of levels measured."""
+        n = ctypes.c_int()
+        self.check(self.L.he_autotune(self.h, None if path is None else os.fsencode(path), int(items), ctypes.byref(n)))
+        return n.value
+
+    def ks_wave(self, level):
+        w = self.L.he_ks_wave(self.h, int(level))
+        if w <= 0:
+            self.check(-w)
+        return w
 
     def keyswitch_batch(self, din, dout, batch, level, gal):
         self.check(self.L.he_keyswitch_batch(self.h, din, dout, batch, level, gal))

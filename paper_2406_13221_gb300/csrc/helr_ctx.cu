@@ -646,7 +646,10 @@ int helr_keyswitch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, 
     // 1. row pass of the inverse transform of every limb (the column pass runs inside ModUp)
     HELR_TRY(helr_ntt_inv_rows(c, d_in, 2 * N, N, ws->drow, in_items, limbmap_ct(level), s));
     // 2-3. ModUp fused with the transforms and the inner product, in waves
-    const int wave = std::min(ws->wave, batch);
+    // (the wave of this limb count, within the scratch's capacity)
+    const size_t per_item = (size_t)nl * nt * N;
+    const int wave = (int)std::max<size_t>(
+        1, std::min({(size_t)(ws->wave > 0 ? ws->wave : helr_ks_wave(c, nl)), (size_t)batch, ws->ext_cap / per_item}));
     for (int b0 = 0; b0 < batch; b0 += wave) {
         int cnt = std::min(wave, batch - b0);
         HELR_TRY(helr_ks_fused(c, d_in + (size_t)b0 * nl * N, ws->drow + (size_t)b0 * nl * N, ws->ext, key,
@@ -668,8 +671,11 @@ int helr_ks_scratch_alloc(he_ctx *c, int batch, int level, KsScratch *ws)
 {
     const int nl = level + 1, nt = nl + 1;
     const size_t N = c->n;
-    const int wave = std::min(helr_ks_wave(c, nl), batch);
-    size_t words = (size_t)batch * (nl * N + 2 * nt * N + 2 * N + 2 * (size_t)nl * N) + (size_t)wave * nl * nt * N;
+    // ext holds one wave at any limb count up to nl, each with its own wave size
+    size_t ext = 0;
+    for (int k = 1; k <= nl; k++)
+        ext = std::max(ext, (size_t)std::min(helr_ks_wave(c, k), batch) * k * (k + 1) * N);
+    size_t words = (size_t)batch * (nl * N + 2 * nt * N + 2 * N + 2 * (size_t)nl * N) + ext;
     uint64_t *base = nullptr;
     HELR_TRY(helr_alloc(c, (void **)&base, words * 8));
     ws->base = base;
@@ -680,7 +686,8 @@ int helr_ks_scratch_alloc(he_ctx *c, int batch, int level, KsScratch *ws)
     ws->ext = ws->lift + (size_t)batch * 2 * nl * N;
     ws->batch = batch;
     ws->level = level;
-    ws->wave = wave;
+    ws->wave = 0;
+    ws->ext_cap = ext;
     return HE_OK;
 }
 void helr_ks_scratch_free(he_ctx *c, KsScratch *ws)

@@ -214,7 +214,8 @@ struct he_ctx {
     std::vector<KeySwitchKey> ksk;
     HeError err;
     Prof prof;
-    int ks_wave = 0;               // items per fused key-switch wave (0 = sized for L2)
+    int ks_wave = 0;               // items per fused key-switch wave forced by HELR_KS_WAVE (0 = none)
+    int ks_wave_tab[HELR_MAXQ + 1] = {};  // wave per limb count chosen by he_autotune (0 = default)
 };
 
 struct he_ct {
@@ -322,10 +323,14 @@ void k_automorph_items(he_ctx *c, uint64_t *out, size_t out_item, const uint64_t
 
 struct KsScratch {
     uint64_t *base, *drow, *ext, *acc, *pl, *lift;  // drow: input after the inverse row pass
-    int batch, level, wave;
+    int batch, level;
+    int wave;        // items per wave forced for every call (0: helr_ks_wave of the call's limb count)
+    size_t ext_cap;  // words of ext: a wave of w items at nl limbs needs w nl (nl + 1) N
 };
 int helr_ks_fused(he_ctx *c, const uint64_t *dntt, const uint64_t *drow, uint64_t *mid, const uint64_t *key, uint64_t *acc,
                   int items, int nl, cudaStream_t s);
+// items per fused key-switch wave at nl limbs: HELR_KS_WAVE, else the
+// he_autotune table, else 128 (autotune.cu)
 int helr_ks_wave(const he_ctx *c, int nl);
 int helr_ks_scratch_alloc(he_ctx *c, int batch, int level, KsScratch *ws);
 void helr_ks_scratch_free(he_ctx *c, KsScratch *ws);

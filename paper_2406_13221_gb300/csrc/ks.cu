@@ -653,12 +653,3 @@ int helr_ks_down(he_ctx *c, const KsOut &o, const uint64_t *src, size_t src_item
     return down_dispatch(c, &o, src, src_item, src_poly, drow, src_prime, lift, items, nl, inv, s);
 }
 
-// items per fused wave: each key row is read from DRAM once per wave and then
-// served from L2 to the wave's items, so larger waves amortise it better, up to
-// the scratch of [wave][nl][nl+1][N] words (3.7 GB at 128 items, 7 limbs)
-int helr_ks_wave(const he_ctx *c, int nl)
-{
-    if (c->ks_wave > 0) return c->ks_wave;
-    (void)nl;
-    return 128;  // tuned on GB300 at N = 2^16 (overridable with HELR_KS_WAVE)
-}

@@ -195,6 +195,41 @@ def test_batched_keyswitch_bitwise(pair):
         assert np.array_equal(got[b], he.keyswitch(level, gal, polys[b]))
 
 
+def test_autotune_table_and_parity(pair, tmp_path):
+    """he_autotune measures every level once and writes its table; a second
+    context with the same parameters loads the table without measuring; key
+    switches of more than one wave with the chosen waves equal the oracle's."""
+    _, he = pair
+    path = tmp_path / "ks_wave.txt"
+    ctx = binding.Context(13, 9)
+    ctx.keygen(2, [3])
+    assert ctx.autotune(str(path), items=40) == 9
+    lines = path.read_text().splitlines()
+    assert lines[0] == "he_lr ks-wave table v1" and lines[1].startswith("key ")
+    waves = {int(f[1]): int(f[3]) for f in (ln.split() for ln in lines[2:])}
+    assert sorted(waves) == list(range(1, 10))
+    assert set(waves.values()) <= {16, 32}  # the candidates up to 40 items
+    assert [ctx.ks_wave(lv) for lv in range(9)] == [waves[nl] for nl in range(1, 10)]
+    ctx2 = binding.Context(13, 9)
+    ctx2.keygen(2, [3])
+    assert ctx2.autotune(str(path), items=40) == 0
+    assert [ctx2.ks_wave(lv) for lv in range(9)] == [waves[nl] for nl in range(1, 10)]
+    level, batch = 5, 40
+    rng = np.random.default_rng(14)
+    n = ctx2.n
+    polys = np.stack([np.stack([rng.integers(0, he.q[j], n, dtype=np.uint64) for j in range(level + 1)])
+                      for _ in range(batch)])
+    gal = he.galois_elt(3)
+    dev = to_dev(polys)
+    ctx2.ntt_forward(dev.data_ptr(), batch * (level + 1), list(range(level + 1)))
+    out = torch.zeros(batch * 2 * (level + 1) * n, dtype=torch.int64, device="cuda")
+    ctx2.keyswitch_batch(dev.data_ptr(), out.data_ptr(), batch, level, gal)
+    ctx2.ntt_inverse(out.data_ptr(), batch * 2 * (level + 1), list(range(level + 1)))
+    got = from_dev(out).reshape(batch, 2, level + 1, n)
+    for b in (0, 17, batch - 1):  # first wave, a later wave, the ragged last one
+        assert np.array_equal(got[b], he.keyswitch(level, gal, polys[b]))
+
+
 def test_errors_are_reported(pair):
     ctx, he = pair
     a, _ = enc_pair(ctx, he, rand_slots(ctx.nslots, 11), 25)
