@@ -231,6 +231,10 @@ def run_ours(args, rank, world):
     bbar = None
     if world == 1 and not args.no_bbar:
         bbar = bbar_time(ctx, X, y)
+    # the oracle on a sample of the job's own ciphertexts, before the job is released
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(X, y, samples=1, job=job, ctx=ctx)
     multi = first = None
     if world == 1 and not (args.no_multi and args.no_first_order):
         job.close()
@@ -264,8 +268,8 @@ def run_ours(args, rank, world):
         "clocks": clocks, "gpu_launches": int(launches), "roofline": roof, "e2e": e2e,
         "context": PAPER_CONTEXT,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(X, y, samples=1)
+    if cb is not None:
+        out["cpu_baseline"] = cb
     return out
 
 
@@ -568,12 +572,16 @@ def replica_rates(ms_local, steps, world, per_iter):
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_baseline(X, y, samples=1, steps=1, warmup=0):
+def cpu_baseline(X, y, samples=1, steps=1, warmup=0, job=None, ctx=None):
     """The CPU oracle on a bounded sample of the same workload: Steps 1-6 on
     `samples` data blocks plus Steps 7-9 and the refresh once, at N = 2^16;
-    sec/iter extrapolated linearly to all blocks (key generation untimed)."""
+    sec/iter extrapolated linearly to all blocks (key generation untimed).
+    With the GPU job at hand the oracle takes the job's own ciphertexts (its
+    first blocks, Enc(n Bbar), its current W and V), and the GPU's iteration on
+    the same inputs (he_lr_iteration) is compared with the oracle's W', V' word
+    for word; the small configuration then runs in full on both sides."""
     from oracle import qgnag
-    from oracle.ckks import Ckks
+    from oracle.ckks import Ckks, Ct as OCt
     cores = os.cpu_count()
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
     data = qgnag.TrainData(X, y, g=256, m=128, batch_rows=1024)
@@ -583,11 +591,18 @@ def cpu_baseline(X, y, samples=1, steps=1, warmup=0):
     he.keygen(2, circ.rotations())
     keygen_s = time.time() - k0
     L, D = circ.L, 2.0 ** LOG_SCALE
-    Z = [he.encrypt(he.encode(data.blocks[b], L, D), qgnag.obj_seed(3, 1, b)) for b in range(samples)]
-    B = he.encrypt(he.encode(np.tile(data.n * data.bbar_full, 128), L, D), qgnag.obj_seed(3, 2, 0))
-    W = he.encrypt(he.encode(np.zeros(he.nslots), L, D), 5)
-    V = he.encrypt(he.encode(np.zeros(he.nslots), L, D), 6)
-    vals = []
+    if job is not None:
+        Z = [OCt(job.input(0, b).export(), L, D) for b in range(samples)]
+        B = OCt(job.input(1, 0).export(), L, D)
+        (Ww, lw, sw), (Vw, lv, sv) = job.state_words()
+        W, V = OCt(Ww, lw, sw), OCt(Vw, lv, sv)
+    else:
+        Z = [he.encrypt(he.encode(data.blocks[b], L, D), qgnag.obj_seed(3, 1, b)) for b in range(samples)]
+        B = he.encrypt(he.encode(np.tile(data.n * data.bbar_full, 128), L, D), qgnag.obj_seed(3, 2, 0))
+        W = he.encrypt(he.encode(np.zeros(he.nslots), L, D), 5)
+        V = he.encrypt(he.encode(np.zeros(he.nslots), L, D), 6)
+    alpha, eta = 2.0, 0.99
+    vals, first = [], None
     for i in range(warmup + steps):
         t0 = time.time()
         acc = None
@@ -595,16 +610,75 @@ def cpu_baseline(X, y, samples=1, steps=1, warmup=0):
             g = circ.block_grad(z, W)
             acc = g if acc is None else he.add(acc, g)
         t1 = time.time()
-        Wn, Vn = circ.finish(acc, B, W, V, 2.0, 0.99, 1.0 / data.n)
+        Wn, Vn = circ.finish(acc, B, W, V, alpha, eta, 1.0 / data.n)
         circ.refresh(Wn, 7)
         circ.refresh(Vn, 8)
         t2 = time.time()
+        first = first or (Wn, Vn)
         est = (t1 - t0) / samples * data.blocks.shape[0] + (t2 - t1)
         if i >= warmup:
             vals.append(est)
-    return {"value": round(float(np.mean(vals)), 1), "unit": "s/iter", "cores": cores, "kind": "oracle",
-            "sample": "Steps 1-6 on %d of %d blocks + Steps 7-9 and refresh once, N=2^16, extrapolated "
-                      "linearly to all blocks; keygen (%.0f s) untimed" % (samples, data.blocks.shape[0], keygen_s)}
+    out = {"value": round(float(np.mean(vals)), 1), "unit": "s/iter", "cores": cores, "kind": "oracle",
+           "sample": "Steps 1-6 on %d of %d blocks + Steps 7-9 and refresh once, N=2^16, extrapolated "
+                     "linearly to all blocks; keygen (%.0f s) untimed" % (samples, data.blocks.shape[0], keygen_s)}
+    if job is not None:
+        from paper_2406_13221_gb300 import binding
+        imp = lambda c: ctx.import_ct(c.data, c.level, c.scale)  # noqa: E731
+        gW, gV = binding.lr_iteration(ctx, [imp(z) for z in Z], imp(B), imp(W), imp(V), 256, 128, alpha, eta,
+                                      1.0 / data.n, qgnag.G8)
+        out["bitwise_equal_gpu"] = bool(np.array_equal(gW.export(), first[0].data) and
+                                        np.array_equal(gV.export(), first[1].data))
+        out["check"] = ("the sample's W', V' (Steps 1-9 on the job's own block, Enc(n Bbar), W and V) "
+                        "against he_lr_iteration on the same ciphertexts, word for word")
+        out["small_config"] = small_config_run()
+    return out
+
+
+def small_config_run(iters=2):
+    """The small configuration in full (1,024 x 15 + bias, N=2^13, 4 blocks of
+    256 x 16, 2 full-batch iterations): the GPU job and the oracle from the
+    job's own encrypted inputs, state compared word for word after every
+    iteration; seconds per iteration of each (refresh included)."""
+    import torch
+    from oracle import qgnag
+    from oracle.ckks import Ckks, Ct as OCt
+    from paper_2406_13221_gb300 import binding, synth
+    Xs, ys = synth.small()
+    ctx = binding.Context(13, NQ)
+    job = binding.Job(ctx, Xs, ys, binding.FULL_BATCH, 1024, binding.G8, LOG_SCALE, enc_seed=3, key_seed=2)
+    he = Ckks(13, NQ)
+    data = qgnag.TrainData(Xs, ys, g=16, m=256, batch_rows=1024)
+    circ = qgnag.Circuit(he, 16, 256, 2.0 ** LOG_SCALE)
+    he.keygen(2, circ.rotations())
+    L, D = circ.L, 2.0 ** LOG_SCALE
+    nb = data.blocks.shape[0]
+    Z = [OCt(job.input(0, b).export(), L, D) for b in range(nb)]
+    B = OCt(job.input(1, 0).export(), L, D)
+    (Ww, _, _), (Vw, _, _) = job.state_words()
+    W, V = OCt(Ww, L, D), OCt(Vw, L, D)
+    etas = qgnag.nag_scalars(iters)
+    gpu, orc, equal = [], [], True
+    for t in range(iters):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        job.step(t)
+        e1.record()
+        torch.cuda.synchronize()
+        gpu.append(e0.elapsed_time(e1) / 1e3)
+        t0 = time.time()
+        Wn, Vn = circ.iteration(Z, B, W, V, qgnag.schedule(t), etas[t], 1.0 / data.n)
+        W = circ.refresh(Wn, qgnag.obj_seed(3, qgnag.SEED_WREF, t))
+        V = circ.refresh(Vn, qgnag.obj_seed(3, qgnag.SEED_VREF, t))
+        orc.append(time.time() - t0)
+        (Ww, _, _), (Vw, _, _) = job.state_words()
+        equal = equal and np.array_equal(Ww, W.data) and np.array_equal(Vw, V.data)
+    job.close()
+    ctx.close()
+    return {"workload": "1,024 x 15 (+bias) synthetic, N=2^13, %d blocks of 256 x 16, %d full-batch iterations"
+                        % (nb, iters),
+            "gpu_s_per_iter": round(float(np.mean(gpu)), 5), "oracle_s_per_iter": round(float(np.mean(orc)), 3),
+            "bitwise_equal": bool(equal)}
 
 
 def run_reference(args, rank, world):
