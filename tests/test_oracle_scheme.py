@@ -127,6 +127,19 @@ def test_rotation_matches_plaintext_roll(he, r):
     assert np.abs(got - np.roll(z, -r)).max() < 1e-7
 
 
+def test_keys_depend_on_the_galois_element_not_the_request(he):
+    """A key is a function of (seed, galois element): a context asked for only
+    the rotation by 2 switches keys to exactly the words of one asked for a
+    longer list, so contexts built for different circuits share keys."""
+    other = Ckks(11, 9)
+    other.keygen(7, [2])
+    c = enc(he, rand_slots(he, 21), 23)
+    d = c.data[1]
+    for gal in (0, he.galois_elt(2)):
+        assert np.array_equal(other.keyswitch(c.level, gal, d), he.keyswitch(c.level, gal, d))
+    assert np.array_equal(other.rotate(c, 2).data, he.rotate(c, 2).data)
+
+
 def test_rotation_at_lower_level(he):
     z = rand_slots(he, 9)
     c = he.moddrop(enc(he, z, 19), 3)
