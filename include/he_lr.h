@@ -72,7 +72,11 @@ typedef struct {
  * encoder tables on the device.  cuda_stream: a cudaStream_t (NULL = legacy
  * default stream); every kernel of this context runs on it. */
 int he_ctx_create(const he_params *p, void *cuda_stream, he_ctx **out);
+/* Waits for the context stream, then frees the tables and keys.  Ciphertexts,
+ * plaintexts and jobs of the context must be freed first. */
 int he_ctx_destroy(he_ctx *ctx);
+/* Message of the last failing call on ctx (owned by ctx, valid until its next
+ * call); "null context" for NULL. */
 const char *he_last_error(const he_ctx *ctx);
 /* Prime chain q_0..q_{n_q-1}, P (n >= n_q + 1 entries). */
 int he_ctx_primes(const he_ctx *ctx, uint64_t *out, size_t n);
@@ -103,12 +107,21 @@ int he_encrypt(he_ctx *ctx, const he_pt *pt, uint64_t seed, he_ct **out);
 /* Dec_sk (Sec. 2.1): c0 + c1 s. */
 int he_decrypt(he_ctx *ctx, const he_ct *ct, he_pt **out);
 
+/* Ciphertext words to the host in coefficient form, [2][level+1][N]
+ * (n_words >= 2 (level + 1) N, else HE_EINVAL); level and scale may be NULL.
+ * Synchronises the context stream. */
 int he_ct_export(const he_ct *ct, uint64_t *words, size_t n_words, int *level, double *scale);
+/* A new ciphertext from host words in the layout of he_ct_export (copied;
+ * the caller keeps `words`).  0 <= level < n_q; a word >= q_j in limb j is
+ * HE_EINVAL.  Synchronises the context stream. */
 int he_ct_import(he_ctx *ctx, const uint64_t *words, size_t n_words, int level, double scale,
                  he_ct **out);
 /* Plaintext words in coefficient form, [level+1][N]. */
 int he_pt_export(const he_pt *pt, uint64_t *words, size_t n_words, int *level, double *scale);
+/* Level and scale of a ciphertext (either pointer may be NULL). */
 int he_ct_level(const he_ct *ct, int *level, double *scale);
+/* Free a ciphertext or plaintext (stream-ordered on its context's stream);
+ * NULL is HE_EINVAL. */
 int he_ct_free(he_ct *ct);
 int he_pt_free(he_pt *pt);
 
@@ -117,7 +130,12 @@ int he_pt_free(he_pt *pt);
  * product followed by relinearisation; its scale is the product of scales
  * and it does not rescale.  Rescale divides by q_level with rounding.
  * cMul multiplies by round_half_away(c * const_scale); cAdd adds
- * round_half_away(c * scale) to every slot.  Rotate by r slots to the left. */
+ * round_half_away(c * scale) to every slot.  Rotate by r slots to the left
+ * (HE_EKEY without its key).  ModDrop keeps the limbs q_0..q_level without
+ * scaling (level <= the input's, else HE_ELEVEL).  PtMul multiplies by an
+ * encoded plaintext of the same level (else HE_ELEVEL); the scales multiply.
+ * Level and scale errors are HE_ELEVEL and HE_ESCALE; the output is owned by
+ * the caller (he_ct_free). */
 int he_add(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
 int he_sub(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
 int he_mul(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
