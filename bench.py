@@ -184,7 +184,9 @@ def run_ours(args, rank, world):
     clocks = clocks_stop(clk)
     launches = binding.launch_count() - l0
     ms = e0.elapsed_time(e1)
-    prof = {name: ctx.prof_read(i) for i, name in enumerate(["ntt_fwd", "ntt_inv", "modup", "ks_inner"])}
+    prof = {name: ctx.prof_read(i) for i, name in enumerate(CLASSES)}
+    ks_prof = ctx.prof_read(4)
+    ks_by_limbs = ctx.prof_keyswitches()
     ctx.prof_enable(False)
     st = job.stats()
     ks_per_iter = int(st.keyswitches)
@@ -243,7 +245,11 @@ def run_ours(args, rank, world):
             first = first_order_time(ctx, X, y, args)
         if not args.no_multi:
             multi = multijob_time(ctx)
-    roof = roofline(prof, args.steps)
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = clocks.get("sm_max_mhz") or float(measured_peaks().get("sm_max_mhz", 2070.0))
+    roof = roofline(prof, ks_prof, ks_by_limbs, args.steps, ms_max / 1000.0 / args.steps, props.multi_processor_count,
+                    sm_mhz)
+    ntt = standalone_ntt(ctx)
     out = {
         "metric": METRIC, "value": round(sec_iter, 5), "unit": "s/iter", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": False,
@@ -256,6 +262,9 @@ def run_ours(args, rank, world):
         "keyswitch_per_s": round(rates["ks"], 1) if sec_iter else None,
         "keyswitches_per_iter": ks_per_iter,
         "ntt_limbs_per_s": round(rates["limbs"], 1) if sec_iter else None,
+        "keyswitch_hbm_frac": roof["keyswitch_hbm_frac_of_iteration"],
+        "ntt_standalone": ntt,
+        "ntt_hbm_frac": ntt["hbm_frac"],
         "plain_one_ct_per_launch_s_per_iter": round(plain, 4) if plain else None,
         "mini_batch": mini,
         "multi_job": multi,
@@ -476,13 +485,12 @@ def pinned_u64(n):
     return t.numpy().view(np.uint64)
 
 
-# Integer-instruction cost model (32-bit lowering of the 64-bit modular
-# operations): Harvey butterfly with a Shoup twiddle; key
-# product accumulated exactly in 128 bits (64x64 -> 128 product and a 128-bit
-# add, 13) plus its share of the one Montgomery reduction per output word (12
-# over about 6 digits); centred lift; Shoup scaling by N^-1.
-OPS_BFLY, OPS_MAC, OPS_LIFT, OPS_SCALE = 23, 15, 6, 14
-SMS, LANES, SM_MHZ_MAX = 152, 128, 2070.0
+# The integer multiply pipe (fmaheavy: every IMAD and 32x32 -> 64 product)
+# issues 16 lanes per clock in each of the 4 sub-partitions of an SM.
+FMAHEAVY_LANES_PER_SM = 64
+CLASSES = ["ntt_fwd", "ntt_inv", "modup", "ks_inner"]  # timing classes 0-3; class 4 = whole key switches
+KERNEL_OF_CLASS = {"ks_inner": "k_ks_inner_rows", "modup": "k_ks_modup_cols",
+                   "ntt_fwd": "k_ks_down_rows+k_ntt_fwd_*", "ntt_inv": "k_ntt_inv_*"}
 
 
 def transform_limbs(prof):
@@ -493,45 +501,123 @@ def transform_limbs(prof):
             + 0.5 * (prof["modup"][1] + prof["modup"][3] + prof["ks_inner"][1]))
 
 
-def class_work(name, units, units2, dram_limbs):
-    """(integer ops, algorithmic DRAM bytes) of a timing class from its work counts."""
+def class_butterflies(name, units, units2):
+    """Butterflies a timing class executed, from its work counts: a column or
+    row half of a transform is (log N / 2) stages of N/2 butterflies."""
     n = 1 << LOGN
-    half = (LOGN // 2) * (n / 2) * OPS_BFLY   # one column or row half of a transform
-    if name.startswith("ntt"):           # units = whole-limb transform equivalents
-        return units * 2 * half, 16.0 * n * units
-    if name == "modup":                  # k_ks_modup_cols (ModUp, ModDown and rescale): units = forward column
-        #                                      halves (+ lift), units2 = inverse column halves
-        return units * (half + n * OPS_LIFT) + units2 * (half + n * OPS_SCALE), 8.0 * n * dram_limbs
-    # ks_inner: units = row halves, units2 = limbs of key products
-    return units * half + units2 * n * OPS_MAC, 8.0 * n * dram_limbs
+    half = (LOGN // 2) * (n / 2)
+    if name.startswith("ntt"):  # whole-limb transform equivalents
+        return units * 2 * half
+    if name == "modup":         # forward column halves + inverse column halves
+        return (units + units2) * half
+    return units * half         # ks_inner: row halves
 
 
-def roofline(prof, steps):
-    """Dominant kernel class by measured time: its algorithmic integer operations
-    over its measured time against the integer-issue peak (the kernels are
-    ALU-bound; the DRAM view is reported beside it)."""
+def recorded_keyswitch_traffic(by_limbs):
+    """Measured DRAM bytes per key switch (ncu, profiles/traffic.txt lines
+    `keyswitch <code-sha> nl=<L> <bytes per key switch>`) weighted by the key
+    switches of each limb count; None unless every limb count issued has a
+    record for the current kernel sources."""
+    h = kernel_sources_hash()
+    rec = {}
+    try:
+        for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
+            p = line.split()
+            if len(p) >= 4 and not line.startswith("#") and p[0] == "keyswitch" and p[1] == h and p[2].startswith("nl="):
+                rec[int(p[2][3:])] = float(p[3])
+    except OSError:
+        return None
+    tot = sum(by_limbs.values())
+    if not tot or any(nl not in rec for nl in by_limbs):
+        return None
+    return sum(rec[nl] * k for nl, k in by_limbs.items()) / tot
+
+
+def recorded_fmaheavy(kernel):
+    """Integer-multiply-pipe (fmaheavy) warp instructions per butterfly of
+    `kernel` from an ncu capture (profiles/traffic.txt lines `fmaheavy
+    <kernel> <code-sha> <instr per butterfly>`), valid for the current kernel
+    sources only."""
+    h = kernel_sources_hash()
+    try:
+        for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
+            p = line.split()
+            if len(p) >= 4 and not line.startswith("#") and p[0] == "fmaheavy" and p[1] == kernel and p[2] == h:
+                return float(p[3])
+    except OSError:
+        pass
+    return None
+
+
+def roofline(prof, ks, ks_by_limbs, steps, sec_iter, sms, sm_mhz):
+    """The key switch as the unit of work (the fused kernels of one key switch
+    run as one pipeline): algorithmic bytes of every key switch the timed steps
+    issued (3L limbs per item, 2L(L+1) key limbs per wave) over the time spent
+    inside key switches, against the measured HBM copy bandwidth.  Beside it:
+    the same bytes over the whole iteration, and the dominant kernel class on
+    the integer multiply pipe (its butterflies per second times the measured
+    instructions per butterfly, against SMs x 64 lanes x clock)."""
     peaks = measured_peaks()
-    best = max(prof, key=lambda k: prof[k][0])
-    ms, units, launches, units2, dram_limbs = prof[best]
-    ops, alg_bytes = class_work(best, units, units2, dram_limbs)
-    sec = ms / 1000.0
-    achieved = ops / sec / 1e12 if sec else 0
-    peak = SMS * LANES * SM_MHZ_MAX * 1e6 / 1e12
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    hbm_ach = alg_bytes / sec / 1e9 if sec else 0
-    kernel = {"ks_inner": "k_ks_inner_rows", "modup": "k_ks_modup_cols",
-              "ntt_fwd": "k_ks_down_rows+k_ntt_fwd_*", "ntt_inv": "k_ntt_inv_*"}[best]
-    return {"kernel": kernel, "bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2), "unit": "Tops/s",
-            "frac": round(achieved / peak, 4),
-            "traffic": (None if recorded_traffic(kernel) is None or not launches
-                        else round(recorded_traffic(kernel) * alg_bytes / launches)),
-            "alg_ops_per_launch": ops / launches if launches else 0,
-            "avg_launch_ms": round(ms / launches, 4) if launches else None, "launches": int(launches),
-            "peak_source": "152 SMs x 128 int32 lanes x 2070 MHz (recipe unit counts and max clock)",
-            "hbm_view": {"achieved": round(hbm_ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(hbm_ach / hbm, 4),
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "fallback" not in peaks else "fallback"},
-            "share_of_timed_classes": round(ms / sum(v[0] for v in prof.values()), 3) if ms else None,
-            "classes_ms_per_step": {k: round(v[0] / steps, 2) for k, v in prof.items()}}
+    n = 1 << LOGN
+    ks_ms, ks_n, _, ks_limbs, ks_alg_limbs = ks
+    alg = ks_alg_limbs * 8.0 * n
+    sec = ks_ms / 1000.0
+    achieved = alg / sec / 1e9 if sec else 0.0
+    traffic = recorded_keyswitch_traffic(ks_by_limbs)
+    best = max(CLASSES, key=lambda k: prof[k][0])
+    ms, units, launches, units2, _ = prof[best]
+    bf = class_butterflies(best, units, units2)
+    ipb = recorded_fmaheavy(KERNEL_OF_CLASS[best])
+    pipe_peak = sms * FMAHEAVY_LANES_PER_SM * sm_mhz * 1e6 / 32.0  # warp instructions per second
+    issue = None
+    if ipb is not None and ms:
+        ach = bf * ipb / (ms / 1000.0)
+        issue = {"kernel": KERNEL_OF_CLASS[best], "pipe": "fmaheavy (integer multiply)",
+                 "instr_per_butterfly": ipb, "achieved": round(ach / 1e12, 4), "peak": round(pipe_peak / 1e12, 4),
+                 "unit": "T warp-instr/s", "frac": round(ach / pipe_peak, 4), "sms": sms, "sm_mhz": sm_mhz}
+    ts = sum(prof[k][0] for k in CLASSES)
+    return {"kernel": "key switch (k_ntt_inv_rows + k_ks_modup_cols + k_ks_inner_rows + k_ks_down_rows)",
+            "unit_of_work": "one key switch", "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+            "unit": "GB/s", "frac": round(achieved / hbm, 4),
+            "traffic": round(traffic) if traffic is not None else None,
+            "alg_bytes_per_unit": round(alg / ks_n) if ks_n else None, "units": int(ks_n),
+            "avg_unit_us": round(1000.0 * ks_ms / ks_n, 3) if ks_n else None,
+            "keyswitches_by_limbs": {str(k): int(v / steps) for k, v in sorted(ks_by_limbs.items())},
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "fallback" not in peaks else "fallback 6.8 TB/s",
+            "share_of_step": round(sec / (sec_iter * steps), 3) if sec_iter else None,
+            "keyswitch_hbm_frac_of_iteration": round(alg / steps / sec_iter / 1e9 / hbm, 4) if sec_iter else None,
+            "dominant_class": best, "dominant_share": round(ms / ts, 3) if ts else None,
+            "issue_view": issue,
+            "classes_ms_per_step": {k: round(prof[k][0] / steps, 2) for k in CLASSES}}
+
+
+def standalone_ntt(ctx, limbs=256, reps=10):
+    """Batched forward + inverse transforms of `limbs` limbs at N = 2^16 (256
+    MiB, beyond L2) outside key switching: limbs per second and the HBM
+    fraction at 16N algorithmic bytes per limb transform (read + write once)."""
+    import torch
+    n = 1 << LOGN
+    buf = torch.randint(0, 1 << 30, (limbs * n,), dtype=torch.int64, device="cuda")
+    prime_of = list(range(NQ))
+    for _ in range(2):
+        ctx.ntt_forward(buf.data_ptr(), limbs, prime_of)
+        ctx.ntt_inverse(buf.data_ptr(), limbs, prime_of)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        ctx.ntt_forward(buf.data_ptr(), limbs, prime_of)
+        ctx.ntt_inverse(buf.data_ptr(), limbs, prime_of)
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1000.0
+    rate = 2 * reps * limbs / sec
+    hbm = float(measured_peaks().get("hbm_gbs", 6800.0))
+    del buf
+    return {"limbs_per_launch": limbs, "log_n": LOGN, "ntt_limbs_per_s": round(rate, 1),
+            "achieved_gbs": round(rate * 16 * n / 1e9, 1), "peak_gbs": hbm,
+            "hbm_frac": round(rate * 16 * n / 1e9 / hbm, 4)}
 
 
 def twin_error(X, y, job, iters, sched):

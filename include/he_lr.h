@@ -202,7 +202,9 @@ int he_rescale_noalloc(he_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int b
 uint64_t he_launch_count(void);
 /* Per-class kernel timing with CUDA events on the context stream (adds two
  * event records per timed launch group).  Classes: 0 forward NTT, 1 inverse
- * NTT, 2 ModUp lift, 3 key-switch inner product.  Enabling resets the sums;
+ * NTT, 2 ModUp lift, 3 key-switch inner product, 4 whole key switches (spans
+ * the launches of classes 0-3 that belong to a key switch; units = key
+ * switches).  Enabling resets the sums;
  * he_prof_read synchronises the stream and returns the summed milliseconds,
  * the work units (limbs for transforms, digit x modulus limbs for ModUp,
  * key switches for the inner product) and the kernel launches of the class. */
@@ -214,6 +216,13 @@ int he_prof_read(he_ctx *ctx, int cls, double *ms, double *units, uint64_t *laun
  * the transform); dram_limbs (may be NULL) = algorithmic DRAM traffic of the
  * key-switch classes in limbs (operands shared by a launch counted once). */
 int he_prof_read2(he_ctx *ctx, int cls, double *units2, double *dram_limbs);
+/* Class 4's counts: units2 = summed input limbs of the key switches,
+ * dram_limbs = their algorithmic DRAM traffic in limbs of N words (a key
+ * switch at L limbs reads its input once and writes two polynomials: 3L; the
+ * 2L(L+1) key limbs it uses are read once per wave of items).
+ * he_prof_keyswitches writes the key switches issued since profiling was
+ * enabled per input limb count: by_limbs[L] for L < n. */
+int he_prof_keyswitches(he_ctx *ctx, double *by_limbs, size_t n);
 /* Galois element of a left rotation by r. */
 uint64_t he_galois_elt(const he_ctx *ctx, int64_t r);
 

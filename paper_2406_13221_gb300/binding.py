@@ -97,6 +97,7 @@ SIGNATURES = {
     "he_prof_enable": (_i, [_vp, _i]),
     "he_prof_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_u64)]),
     "he_prof_read2": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
+    "he_prof_keyswitches": (_i, [_vp, _vp, _sz]),
     "he_lr_job_free": (_i, [_vp]),
     "he_lr_multi_create": (_i, [_vp, _vp, _sz, _i, _pp]),
     "he_lr_multi_step": (_i, [_vp, _i, he_lr_sched]),
@@ -256,6 +257,12 @@ class Context:
         self.check(self.L.he_prof_read(self.h, cls, ctypes.byref(ms), ctypes.byref(units), ctypes.byref(n)))
         self.check(self.L.he_prof_read2(self.h, cls, ctypes.byref(u2), ctypes.byref(u3)))
         return ms.value, units.value, n.value, u2.value, u3.value
+
+    def prof_keyswitches(self):
+        """Key switches issued since profiling was enabled, per input limb count."""
+        out = np.zeros(64)
+        self.check(self.L.he_prof_keyswitches(self.h, _ptr(out), len(out)))
+        return {nl: int(v) for nl, v in enumerate(out) if v}
 
     def rescale_noalloc(self, din, dout, batch, level):
         self.check(self.L.he_rescale_noalloc(self.h, din, dout, batch, level))
@@ -441,6 +448,22 @@ def lr_iteration(ctx, Z, B, W, V, g, m, alpha, eta, inv_n, poly):
     ctx.check(ctx.L.he_lr_iteration(ctx.h, arr, len(Z), bh, W.h, V.h, g, m, float(alpha), float(eta),
                                     float(inv_n), _ptr(p), ctypes.byref(Wo), ctypes.byref(Vo)))
     return Ct(ctx, Wo), Ct(ctx, Vo)
+
+
+def lr_train(ctx, X, y, iters, sched=(2.0, 1.0, 81.0, 2.5), mode=FULL_BATCH, batch_rows=1024, poly=G8,
+             enc_seed=3, key_seed=2, g=None):
+    """he_lr_train: the whole training in one call; returns (decrypted weights
+    of row 0 [g values], he_lr_stats)."""
+    X = np.ascontiguousarray(X, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    n, f = X.shape
+    if g is None:
+        g = 1 << int(np.ceil(np.log2(f + 1)))
+    w = np.zeros(g)
+    st = he_lr_stats()
+    ctx.check(ctx.L.he_lr_train(ctx.h, _ptr(X), _ptr(y), n, f, int(iters), he_lr_sched(*sched), mode, batch_rows,
+                                poly, enc_seed, key_seed, _ptr(w), g, ctypes.byref(st)))
+    return w, st
 
 
 def launch_count():

@@ -45,6 +45,14 @@ extern "C" int he_prof_enable(he_ctx *c, int on)
     HELR_CUDA(c, cudaStreamSynchronize(c->stream));
     c->prof.on = on;
     for (auto &p : c->prof.cls) p.used = 0, p.units = 0, p.units2 = 0, p.units3 = 0, p.launches = 0;
+    for (double &k : c->prof.ks_by_limbs) k = 0;
+    return HE_OK;
+}
+
+extern "C" int he_prof_keyswitches(he_ctx *c, double *by_limbs, size_t n)
+{
+    if (!c || !by_limbs) return HE_EINVAL;
+    for (size_t i = 0; i < n; i++) by_limbs[i] = i < HELR_MAXQ + 2 ? c->prof.ks_by_limbs[i] : 0;
     return HE_OK;
 }
 
@@ -248,6 +256,15 @@ static int ctx_init(he_ctx *c, const he_params *p)
     v = h_next_prime(p->p_bits, twon, used);
     if (!v) return helr_fail(c, HE_EINVAL, "no special prime");
     used.push_back(v);
+    // the key inner product accumulates up to n_q products below 20 q^2 (primes
+    // under 2^58, unreduced butterflies) or 4 q^2 exactly in 128 bits
+    for (int i = 0; i < c->nprime; i++) {
+        const u128 q2 = (u128)used[i] * used[i];
+        const unsigned f = (unsigned)c->nq * (used[i] < HELR_LZ_QMAX ? 20u : 4u);
+        if (q2 > ~(u128)0 / f)
+            return helr_fail(c, HE_EINVAL, "prime %d (%llu): %u 128-bit key products could overflow", i,
+                             (unsigned long long)used[i], f);
+    }
     for (int i = 0; i < c->nprime; i++) {
         uint64_t q = used[i];
         c->q[i] = q;
@@ -643,6 +660,7 @@ int helr_keyswitch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, 
         ws = &local;
     }
     cudaStream_t s = c->stream;
+    prof_start(c, PROF_KS, s);
     // 1. row pass of the inverse transform of every limb (the column pass runs inside ModUp)
     HELR_TRY(helr_ntt_inv_rows(c, d_in, 2 * N, N, ws->drow, in_items, limbmap_ct(level), s));
     // 2-3. ModUp fused with the transforms and the inner product, in waves
@@ -663,6 +681,10 @@ int helr_keyswitch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, 
     HELR_TRY(helr_ks_down(c, o ? *o : plain, ws->acc, 2 * (size_t)nt * N, (size_t)nt * N, ws->pl, c->nq, ws->lift, batch,
                           nl, c->d_pinv, s));
     HELR_CUDA(c, cudaGetLastError());
+    const double waves = (double)((batch + wave - 1) / wave);
+    prof_stop(c, PROF_KS, s, (double)batch, 0, (double)batch * nl,
+              3.0 * nl * batch + waves * 2.0 * nl * (nl + 1));
+    if (c->prof.on) c->prof.ks_by_limbs[nl] += batch;
     if (ws == &local) helr_ks_scratch_free(c, &local);
     return HE_OK;
 }

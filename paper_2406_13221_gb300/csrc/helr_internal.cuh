@@ -113,7 +113,11 @@ extern std::atomic<unsigned long long> g_helr_launches;
     } while (0)
 
 // Optional per-class kernel timing with CUDA events on the context stream.
-enum { PROF_NTT_FWD = 0, PROF_NTT_INV = 1, PROF_MODUP = 2, PROF_KS_INNER = 3, PROF_NCLASS = 4 };
+// PROF_KS spans whole key switches (it overlaps the kernel classes): units =
+// key switches, units2 = their summed limb counts, units3 = algorithmic DRAM
+// limbs of a key switch at L limbs (input limb read, two output limbs written:
+// 3L per item; the 2L(L+1) key limbs once per wave).
+enum { PROF_NTT_FWD = 0, PROF_NTT_INV = 1, PROF_MODUP = 2, PROF_KS_INNER = 3, PROF_KS = 4, PROF_NCLASS = 5 };
 struct ProfClass {
     std::vector<cudaEvent_t> ev;  // start/stop pairs
     size_t used = 0;
@@ -125,6 +129,7 @@ struct ProfClass {
 struct Prof {
     int on = 0;
     ProfClass cls[PROF_NCLASS];
+    double ks_by_limbs[HELR_MAXQ + 2] = {};  // key switches issued per input limb count
 };
 struct he_ctx;
 void prof_start(he_ctx *c, int cls, cudaStream_t s);

@@ -228,9 +228,11 @@ __device__ __forceinline__ uint64_t redc128(uint64_t hi, uint64_t lo, const ModQ
 // for P) whose primes take the unreduced forward butterfly (LZ) or Harvey's.
 //
 // Inner product without per-digit reduction: with keys k' = k 2^64 mod q, the
-// CTA accumulates T = sum_i x_i k'_i exactly in 128 bits (x_i below 20q for LZ,
-// where q < 2^58, and below 4q otherwise, where q < 2^61: T < 9 * 20 q^2 < 2^125
-// or 9 * 4 q^2 < 2^128) and reduces once: T 2^-64 mod q = sum_i x_i k_i mod q
+// CTA accumulates T = sum_i x_i k'_i over the nl digits exactly in 128 bits
+// (x_i below 20q for LZ, where q < 2^58, and below 4q otherwise: T < nl 20 q^2
+// or nl 4 q^2, which he_ctx_create keeps below 2^128 for every prime of the
+// chain and nl <= n_q; with primes of at most 60 bits that holds up to 39
+// digits) and reduces once: T 2^-64 mod q = sum_i x_i k_i mod q
 // (one Montgomery reduction, after reducing the high word below q).  The 128-bit accumulators of both key polynomials live
 // in TMEM between digits (128 columns per thread), so the registers hold only
 // the digit being transformed.

@@ -52,38 +52,64 @@ def test_recorded_traffic_lookup(tmp_path, monkeypatch):
     assert bench.recorded_traffic("k_unknown") is None
 
 
-def test_class_work_counts():
+def test_class_butterflies():
     n = 1 << bench.LOGN
-    half = (bench.LOGN // 2) * (n / 2) * bench.OPS_BFLY
-    ops, byt = bench.class_work("ntt_fwd", 3, 0, 0)
-    assert ops == pytest.approx(3 * 2 * half) and byt == pytest.approx(3 * 16.0 * n)
-    ops, byt = bench.class_work("modup", 5, 2, 11)
-    assert ops == pytest.approx(5 * (half + n * bench.OPS_LIFT) + 2 * (half + n * bench.OPS_SCALE))
-    assert byt == pytest.approx(11 * 8.0 * n)
-    ops, byt = bench.class_work("ks_inner", 4, 7, 9)
-    assert ops == pytest.approx(4 * half + 7 * n * bench.OPS_MAC) and byt == pytest.approx(9 * 8.0 * n)
+    half = (bench.LOGN // 2) * (n / 2)
+    assert bench.class_butterflies("ntt_fwd", 3, 0) == pytest.approx(3 * 2 * half)
+    assert bench.class_butterflies("modup", 5, 2) == pytest.approx(7 * half)
+    assert bench.class_butterflies("ks_inner", 4, 99) == pytest.approx(4 * half)
 
 
-def test_roofline_picks_the_slowest_class(monkeypatch):
+def _traffic_file(tmp_path, body):
+    (tmp_path / "profiles").mkdir(exist_ok=True)
+    (tmp_path / "profiles" / "traffic.txt").write_text(body)
+
+
+def test_keyswitch_traffic_and_pipe_records(tmp_path, monkeypatch):
+    _copy_sources(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h = bench.kernel_sources_hash()
+    _traffic_file(tmp_path, "# comment keyswitch %s nl=7 1.0\n"
+                            "keyswitch %s nl=7 700.0\n"
+                            "keyswitch %s nl=4 400.0\n"
+                            "keyswitch 000000000000 nl=5 9.0\n"
+                            "fmaheavy k_ks_modup_cols %s 15.9\n"
+                            "fmaheavy k_ks_inner_rows 000000000000 3.0\n" % (h, h, h, h))
+    # weighted by the key switches of each limb count
+    assert bench.recorded_keyswitch_traffic({7: 1, 4: 3}) == pytest.approx((700 + 3 * 400) / 4)
+    assert bench.recorded_keyswitch_traffic({7: 1, 5: 1}) is None  # no record for 5 limbs at this hash
+    assert bench.recorded_keyswitch_traffic({}) is None
+    assert bench.recorded_fmaheavy("k_ks_modup_cols") == pytest.approx(15.9)
+    assert bench.recorded_fmaheavy("k_ks_inner_rows") is None
+
+
+def test_roofline_of_the_key_switch(monkeypatch):
     monkeypatch.setattr(bench, "measured_peaks", lambda: {"hbm_gbs": 7000.0})
-    monkeypatch.setattr(bench, "recorded_traffic", lambda k: 0.5 if k == "k_ks_modup_cols" else None)
+    monkeypatch.setattr(bench, "recorded_keyswitch_traffic", lambda by: 2.0e6)
+    monkeypatch.setattr(bench, "recorded_fmaheavy", lambda k: 16.0 if k == "k_ks_modup_cols" else None)
+    n = 1 << bench.LOGN
     # (ms, units, launches, units2, dram_limbs) per class over 2 steps
     prof = {"ntt_fwd": (100.0, 10, 4, 0, 0), "ntt_inv": (50.0, 5, 2, 0, 0),
             "modup": (400.0, 100, 8, 20, 300), "ks_inner": (300.0, 90, 8, 500, 200)}
-    r = bench.roofline(prof, 2)
-    assert r["kernel"] == "k_ks_modup_cols" and r["bound"] == "alu" and r["launches"] == 8
-    ops, byt = bench.class_work("modup", 100, 20, 300)
-    peak = bench.SMS * bench.LANES * bench.SM_MHZ_MAX * 1e6 / 1e12
-    assert r["peak"] == pytest.approx(round(peak, 2))
-    assert r["achieved"] == pytest.approx(round(ops / 0.4 / 1e12, 2))
-    assert r["frac"] == pytest.approx(ops / 0.4 / 1e12 / peak, abs=1e-4)
-    assert r["traffic"] == round(0.5 * byt / 8)  # the record's ratio scaled to one average launch
-    assert r["hbm_view"]["achieved"] == pytest.approx(round(byt / 0.4 / 1e9, 1))
-    assert r["share_of_timed_classes"] == pytest.approx(round(400 / 850, 3))
+    ks = (800.0, 40, 0, 200, 1000)  # 40 key switches, 1000 algorithmic limbs, 0.8 s
+    r = bench.roofline(prof, ks, {5: 40}, 2, 0.5, 152, 2070.0)
+    alg = 1000 * 8.0 * n
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 7000.0
+    assert r["achieved"] == pytest.approx(round(alg / 0.8 / 1e9, 1))
+    assert r["frac"] == pytest.approx(alg / 0.8 / 1e9 / 7000.0, abs=1e-4)
+    assert r["alg_bytes_per_unit"] == round(alg / 40) and r["traffic"] == 2000000
+    assert r["keyswitch_hbm_frac_of_iteration"] == pytest.approx(alg / 2 / 0.5 / 1e9 / 7000.0, abs=1e-4)
+    assert r["share_of_step"] == pytest.approx(0.8)
+    assert r["keyswitches_by_limbs"] == {"5": 20}
+    assert r["dominant_class"] == "modup" and r["dominant_share"] == pytest.approx(round(400 / 850, 3))
+    iv = r["issue_view"]
+    bf = bench.class_butterflies("modup", 100, 20)
+    peak = 152 * 64 * 2070e6 / 32
+    assert iv["frac"] == pytest.approx(bf * 16.0 / 0.4 / peak, abs=1e-4) and iv["sms"] == 152
     assert r["classes_ms_per_step"] == {"ntt_fwd": 50.0, "ntt_inv": 25.0, "modup": 200.0, "ks_inner": 150.0}
-    # without a record for the dominant kernel the traffic is null
+    # without an instruction record for the dominant kernel there is no issue view
     prof["ks_inner"] = (500.0, 90, 8, 500, 200)
-    assert bench.roofline(prof, 2)["traffic"] is None
+    assert bench.roofline(prof, ks, {5: 40}, 2, 0.5, 152, 2070.0)["issue_view"] is None
 
 
 def test_transform_limbs_counts_halves():

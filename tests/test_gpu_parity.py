@@ -63,15 +63,17 @@ def test_ntt_matches_oracle(logn, nlimbs):
     assert np.array_equal(from_dev(dev).reshape(nlimbs, n), data)
 
 
+PAIR_ROTATIONS = [1, 2, 4, 8, -1, -2, -4, -8, 3, 100, -77] + [16 << k for k in range(8)]
+
+
 @pytest.fixture(scope="module")
 def pair():
     """GPU context and oracle with identical parameters and keys (N = 2^13)."""
     logn, nq = 13, 9
     ctx = binding.Context(logn, nq)
     he = Ckks(logn, nq)
-    rots = [1, 2, 4, 8, -1, -2, -4, -8, 3, 100, -77] + [16 << k for k in range(8)]
-    ctx.keygen(2, rots)
-    he.keygen(2, rots)
+    ctx.keygen(2, PAIR_ROTATIONS)
+    he.keygen(2, PAIR_ROTATIONS)
     return ctx, he
 
 
@@ -366,6 +368,24 @@ def test_first_order_job_bitwise(pair):
     assert np.abs(job.weights(0) - wp).max() < 1e-3
 
 
+def test_lr_train_whole_job(pair):
+    """he_lr_train (job creation, two full-batch iterations and the decryption
+    in one call) returns the weights the oracle's whole training run decrypts,
+    bit for bit, and they lie within 1e-3 of the FP64 twin."""
+    ctx, he = pair
+    X, y = synth.small(seed=13, n=1024, f=15)
+    w, st = binding.lr_train(ctx, X, y, 2, enc_seed=17, key_seed=2)
+    assert (st.n_blocks, st.g, st.m) == (4, 16, 256)
+    assert st.keyswitches > 0
+    data = qgnag.TrainData(X, y, g=16, m=256, batch_rows=1024)
+    circ = qgnag.Circuit(he, 16, 256, D)
+    he.keygen(2, sorted(set(PAIR_ROTATIONS) | set(circ.rotations())))
+    ref = qgnag.train(he, circ, data, 2, enc_seed=17)
+    assert np.array_equal(w.view(np.uint64), ref[0].view(np.uint64))
+    from oracle import plain
+    assert np.abs(w - plain.train(data, 2)).max() < 1e-3
+
+
 @pytest.mark.parametrize("f", [37, 200])
 def test_bbar_batches_on_device_equal_host(pair, f):
     """Bbar_k of every mini-batch (Sec. 3.1) computed on the device equals the
@@ -422,7 +442,9 @@ def test_minibatch_job_bitwise(pair):
 
 def test_multi_job_matches_single_jobs(pair):
     """Three full-batch jobs of different widths (g = 32, 16, 8) stepped together
-    give exactly the words each job gives alone, and track their FP64 twins."""
+    give, word for word, the state the oracle's circuit gives for each job on
+    the job's own encrypted inputs, the words each job gives alone, and track
+    their FP64 twins."""
     ctx, he = pair
     shapes = [(700, 5, 21), (1500, 15, 22), (400, 30, 23)]  # (n, f, enc_seed)
     data = [synth.job(seed=s, n=n, f=f) for n, f, s in shapes]
@@ -431,19 +453,41 @@ def test_multi_job_matches_single_jobs(pair):
     alone = [binding.Job(ctx, X, y, binding.FULL_BATCH, 1024, binding.G8, 40.0, enc_seed=s, key_seed=2, batch_blocks=4)
              for (X, y), (_, _, s) in zip(data, shapes)]
     assert sorted(j.stats().g for j in multi_jobs) == [8, 16, 32]
+    # the oracle side of every job: its circuit, its encrypted inputs, its start state
+    circs, inputs, states = [], [], []
+    rots = set(PAIR_ROTATIONS)
+    for (X, y), jm in zip(data, multi_jobs):
+        st = jm.stats()
+        td = qgnag.TrainData(X, y, g=st.g, m=st.m, batch_rows=1024)
+        circ = qgnag.Circuit(he, st.g, st.m, D)
+        rots |= set(circ.rotations())
+        L = circ.L
+        Z = [OCt(jm.input(0, b).export(), L, D) for b in range(st.n_blocks)]
+        B = OCt(jm.input(1, 0).export(), L, D)
+        (Ww, _, _), (Vw, _, _) = jm.state_words()
+        circs.append((circ, td))
+        inputs.append((Z, B))
+        states.append((OCt(Ww, L, D), OCt(Vw, L, D)))
+    he.keygen(2, sorted(rots))  # keys depend on the seed and the Galois element only
     multi = binding.Multi(ctx, multi_jobs, blocks_per_launch=5)  # chunks straddle jobs
+    etas = qgnag.nag_scalars(2)
     for t in range(2):
         multi.step(t)
         for j in alone:
             j.step(t)
-        for jm, ja in zip(multi_jobs, alone):
+        for i, (jm, ja) in enumerate(zip(multi_jobs, alone)):
             (Wm, _, _), (Vm, _, _) = jm.state_words()
             (Wa, _, _), (Va, _, _) = ja.state_words()
             assert np.array_equal(Wm, Wa) and np.array_equal(Vm, Va), t
+            (circ, td), (Z, B), (W, V) = circs[i], inputs[i], states[i]
+            Wn, Vn = circ.iteration(Z, B, W, V, qgnag.schedule(t), etas[t], 1.0 / td.n)
+            seed = shapes[i][2]
+            W = circ.refresh(Wn, qgnag.obj_seed(seed, qgnag.SEED_WREF, t))
+            V = circ.refresh(Vn, qgnag.obj_seed(seed, qgnag.SEED_VREF, t))
+            states[i] = (W, V)
+            assert np.array_equal(Wm, W.data) and np.array_equal(Vm, V.data), (t, i)
     from oracle import plain
-    for (X, y), jm in zip(data, multi_jobs):
-        st = jm.stats()
-        td = qgnag.TrainData(X, y, g=st.g, m=st.m, batch_rows=1024)
+    for (circ, td), jm in zip(circs, multi_jobs):
         wp = plain.train(td, 2)
         assert np.abs(jm.weights(0) - wp).max() < 1e-3
     multi.close()

@@ -1,8 +1,9 @@
 """he_rescale_noalloc: a rescale for callers that may not allocate device memory
 (code running under a device-memory budget fixed in advance, or inside a host
 framework that owns every allocation).  It must return exactly what he_rescale
-returns, on consecutive calls that share its fixed work space, and refuse sizes
-the work space cannot hold.
+returns, and what the oracle's rescale (rounded division by the dropped prime)
+returns, on consecutive calls that share its fixed work space, and refuse
+sizes the work space cannot hold.
 
 This file is collected last so that a failure here never hides another test.
 """
@@ -15,6 +16,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
+from oracle.ckks import Ckks, Ct as OCt  # noqa: E402
 from paper_2406_13221_gb300 import binding, build  # noqa: E402
 
 build.build()
@@ -37,6 +39,11 @@ def reference(ctx, words, level):
     return np.stack(out)
 
 
+def oracle_rescale(he, words, level):
+    """The oracle's rescale of each ciphertext (coefficient words)."""
+    return np.stack([he.rescale(OCt(w, level, 2.0 ** 40)).data for w in words])
+
+
 def no_alloc(ctx, words, level):
     batch, n = words.shape[0], ctx.n
     dev_in = torch.from_numpy(np.ascontiguousarray(words).view(np.int64)).cuda()
@@ -50,16 +57,21 @@ def no_alloc(ctx, words, level):
 
 def test_no_alloc_rescale_matches_he_rescale_on_two_calls():
     ctx = binding.Context(13, 9)
+    he = Ckks(13, 9)
     for call, (level, batch) in enumerate(((8, 3), (4, 5))):
         words = random_ct_words(ctx.primes, level, batch, ctx.n, seed=40 + call)
-        assert np.array_equal(no_alloc(ctx, words, level), reference(ctx, words, level)), call
+        got = no_alloc(ctx, words, level)
+        assert np.array_equal(got, reference(ctx, words, level)), call
+        assert np.array_equal(got, oracle_rescale(he, words, level)), call
 
 
 def test_no_alloc_rescale_splits_large_batches_and_refuses_oversized_work():
     ctx = binding.Context(16, 17)
     level, batch = 7, 3  # 16 limbs of 2^16 words per ciphertext: two per pass of the work space
     words = random_ct_words(ctx.primes, level, batch, ctx.n, seed=50)
-    assert np.array_equal(no_alloc(ctx, words, level), reference(ctx, words, level))
+    got = no_alloc(ctx, words, level)
+    assert np.array_equal(got, reference(ctx, words, level))
+    assert np.array_equal(got, oracle_rescale(Ckks(16, 17), words, level))
     with pytest.raises(binding.HeError) as e:
         ctx.rescale_noalloc(1, 1, 1, 16)  # (2 + 2*16) * 2^16 words exceed the work space
     assert e.value.code == binding.HE_EINVAL
