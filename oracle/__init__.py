@@ -83,6 +83,7 @@ def _declare(L):
         "orc_rotate_gal": (i32, [vp, i32, u64, vp, vp]),
         "orc_galois_elt": (u64, [vp, i64]),
         "orc_rotate": (i32, [vp, i32, i64, vp, vp]),
+        "orc_rotsum_gal": (i32, [vp, i32, vp, i32, vp, vp]),
         "orc_rescale": (None, [vp, i32, i32, vp, vp]),
         "orc_moddrop": (None, [vp, i32, i32, i32, vp, vp]),
         "orc_cmul_int": (None, [vp, i32, i32, vp, i64, vp]),

@@ -193,6 +193,15 @@ class Ckks:
             raise KeyError("no rotation key for %d" % r)
         return Ct(out, ct.level, ct.scale)
 
+    def rotsum(self, ct, rots):
+        """ct + sum_j Rot(ct, r_j) with one shared ModUp and one ModDown
+        (hoisted rotations; a single rotation equals add(ct, rotate(ct, r)))."""
+        gals = np.array([self.galois_elt(r) for r in rots], np.uint64)
+        out = np.zeros_like(ct.data)
+        if self.L.orc_rotsum_gal(self.ctx, ct.level, _p(gals), len(gals), _p(ct.data), _p(out)):
+            raise KeyError("no rotation key for one of %s" % (list(rots),))
+        return Ct(out, ct.level, ct.scale)
+
     def rescale(self, ct):
         lv = ct.level
         if lv < 1:

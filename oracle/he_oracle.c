@@ -715,16 +715,15 @@ void orc_tensor(const orc_ctx *c, int level, const uint64_t *a, const uint64_t *
     }
 }
 
-/* Hybrid key switching of one polynomial d at `level` under the key tagged gal:
- *  ModUp: digit i = centred limb i of d, reduced into every modulus q_0..q_level, P;
- *  inner product with the key digits; ModDown: subtract the centred P-residue and
- *  multiply by P^-1 mod q_j.  out: [2][level+1][N]. */
-int orc_keyswitch(const orc_ctx *c, int level, uint64_t gal, const uint64_t *d, uint64_t *out)
+/* Hybrid key switching (Sec. 2.1, relinearisation and rotation keys) in two
+ * halves.  ks_inner_add: ModUp and inner product of one polynomial d at
+ * `level` with `key`: digit i = centred limb i of d, reduced into every
+ * modulus t in {q_0..q_level, P}; acc_t += sum_i digit_i * key_(i,t) for both
+ * key polynomials (acc: [2][level+2][N], t = level+1 standing for P).
+ * ks_moddown: out_j = (acc_j - centred(acc_P) mod q_j) * P^-1 mod q_j. */
+static void ks_inner_add(const orc_ctx *c, int level, const uint64_t *key, const uint64_t *d, uint64_t *acc)
 {
-    const uint64_t *key = find_ksk(c, gal);
-    if (!key) return -1;
     int n = c->n, nl = level + 1, nql = c->nq + 1, nt = level + 2;
-    uint64_t *acc = (uint64_t *)calloc((size_t)2 * nt * n, sizeof(uint64_t));
     #pragma omp parallel for schedule(dynamic)
     for (int t = 0; t < nt; t++) {
         const prime_tab *tb = limb_tab(c, level, t);
@@ -744,6 +743,10 @@ int orc_keyswitch(const orc_ctx *c, int level, uint64_t gal, const uint64_t *d, 
         }
         free(x); free(y);
     }
+}
+static void ks_moddown(const orc_ctx *c, int level, const uint64_t *acc, uint64_t *out)
+{
+    int n = c->n, nl = level + 1, nt = level + 2;
     uint64_t P = c->q[c->nq];
     for (int p = 0; p < 2; p++) {
         const uint64_t *ap = acc + ((size_t)p * nt + level + 1) * n;
@@ -754,6 +757,16 @@ int orc_keyswitch(const orc_ctx *c, int level, uint64_t gal, const uint64_t *d, 
             for (int k = 0; k < n; k++) oj[k] = mulmod(submod(aj[k], smod(center(ap[k], P), q), q), pinv, q);
         }
     }
+}
+
+/* key switching of one polynomial d at `level` under the key tagged gal; out: [2][level+1][N] */
+int orc_keyswitch(const orc_ctx *c, int level, uint64_t gal, const uint64_t *d, uint64_t *out)
+{
+    const uint64_t *key = find_ksk(c, gal);
+    if (!key) return -1;
+    uint64_t *acc = (uint64_t *)calloc((size_t)2 * (level + 2) * c->n, sizeof(uint64_t));
+    ks_inner_add(c, level, key, d, acc);
+    ks_moddown(c, level, acc, out);
     free(acc);
     return 0;
 }
@@ -805,6 +818,46 @@ uint64_t orc_galois_elt(const orc_ctx *c, int64_t r)
 int orc_rotate(const orc_ctx *c, int level, int64_t r, const uint64_t *ct, uint64_t *out)
 {
     return orc_rotate_gal(c, level, orc_galois_elt(c, r), ct, out);
+}
+
+/* Sum of a ciphertext and several of its rotations with one shared ModUp and
+ * one ModDown (hoisted rotations): out = ct + sum_j Rot_{g_j}(ct).  Rotation j
+ * key-switches sigma_{g_j}(c1) with the key for s(X^{g_j}); since the centred
+ * digit decomposition commutes with the automorphism (a signed permutation of
+ * coefficients), every rotation reuses the digits of c1, and the inner
+ * products of all rotations are added over {q_0..q_level, P} before a single
+ * division by P.  c0 contributes c0 + sum_j sigma_{g_j}(c0).  With one
+ * rotation the result equals ct + Rot(ct) word for word. */
+int orc_rotsum_gal(const orc_ctx *c, int level, const uint64_t *gals, int ngal, const uint64_t *ct, uint64_t *out)
+{
+    int n = c->n, nl = level + 1;
+    for (int j = 0; j < ngal; j++)
+        if (!find_ksk(c, gals[j])) return -1;
+    uint64_t *acc = (uint64_t *)calloc((size_t)2 * (level + 2) * n, sizeof(uint64_t));
+    uint64_t *r = (uint64_t *)malloc(sizeof(uint64_t) * nl * n);
+    uint64_t *ks = (uint64_t *)malloc(sizeof(uint64_t) * 2 * nl * n);
+    memcpy(out, ct, sizeof(uint64_t) * 2 * nl * n);
+    for (int j = 0; j < ngal; j++) {
+        for (int i = 0; i < nl; i++) {
+            uint64_t q = c->q[i];
+            /* sigma_j(c0) into out_0, sigma_j(c1) into r */
+            automorph(n, q, gals[j], ct + (size_t)i * n, r + (size_t)i * n);
+            uint64_t *o = out + (size_t)i * n;
+            for (int k = 0; k < n; k++) o[k] = addmod(o[k], r[(size_t)i * n + k], q);
+            automorph(n, q, gals[j], ct + ((size_t)nl + i) * n, r + (size_t)i * n);
+        }
+        ks_inner_add(c, level, find_ksk(c, gals[j]), r, acc);
+    }
+    ks_moddown(c, level, acc, ks);
+    for (int p = 0; p < 2; p++)
+        for (int i = 0; i < nl; i++) {
+            uint64_t q = c->q[i];
+            uint64_t *o = out + ((size_t)p * nl + i) * n;
+            const uint64_t *b = ks + ((size_t)p * nl + i) * n;
+            for (int k = 0; k < n; k++) o[k] = addmod(o[k], b[k], q);
+        }
+    free(acc); free(r); free(ks);
+    return 0;
 }
 
 /* rescale: drop q_level with rounding, c_j <- (c_j - [c_level]_centred) * q_level^-1 mod q_j.

@@ -146,6 +146,20 @@ DEPTH = 6  # levels one iteration consumes
 DEPTH_FIRST_ORDER = 5  # without the Bbar product of Step 8
 
 
+def rot_groups(nbits, step, rho):
+    """Rotation amounts of a rotate-and-sum over 2^nbits positions spaced `step`
+    slots apart, taken 2^rho positions at a time: group e (e = 0, rho, 2 rho,
+    ...) of width w = min(rho, nbits - e) adds the rotations by m 2^e step for
+    0 < m < 2^w.  After the groups up to e, slot c holds the sum of the
+    2^(e + w) slots c, c + step, c + 2 step, ... (rho = 1: the log-step sum of
+    Sec. 2.2, one rotation per step)."""
+    out = []
+    for e in range(0, nbits, rho):
+        w = min(rho, nbits - e)
+        out.append([step * (m << e) for m in range(1, 1 << w)])
+    return out
+
+
 class Circuit:
     """The encrypted QG-NAG iteration on one parameter set.
 
@@ -154,9 +168,10 @@ class Circuit:
     iteration consumes 6 levels and ends at level L - 6.  With first_order=True
     the circuit is the first-order NAG baseline: no Bbar product, depth 5."""
 
-    def __init__(self, he: Ckks, g, m, scale, poly=G8, start_level=None, first_order=False):
+    def __init__(self, he: Ckks, g, m, scale, poly=G8, start_level=None, first_order=False, rot_radix_log=2):
         self.he, self.g, self.m, self.scale, self.poly = he, g, m, float(scale), poly
         self.first_order = first_order
+        self.rho = rot_radix_log
         depth = DEPTH_FIRST_ORDER if first_order else DEPTH
         if g * m != he.nslots:
             raise ValueError("m * g must equal N/2")
@@ -179,10 +194,18 @@ class Circuit:
         self.p1 = he.encode(-c1 * mask, L - 1, self.s_scale * q[L - 1] / t_scale)  # rescales to s_scale
         self.p0 = he.encode((1.0 - c0) * mask, L - 3, self.s_scale)
 
+    def groups(self, nbits, step):
+        return rot_groups(nbits, step, self.rho)
+
+    def rotsum(self, ct, nbits, step):
+        for rots in self.groups(nbits, step):
+            ct = self.he.rotsum(ct, rots)
+        return ct
+
     def rotations(self):
-        rs = [1 << k for k in range(self.lg)]
-        rs += [-(1 << k) for k in range(self.lg)]
-        rs += [self.g << k for k in range(self.lm)]
+        rs = []
+        for grp in self.groups(self.lg, 1) + self.groups(self.lg, -1) + self.groups(self.lm, self.g):
+            rs += grp
         return rs
 
     def cmul_to(self, ct, c, target):
@@ -200,8 +223,7 @@ class Circuit:
         # Step 1: z_rc * w_c
         t = he.rescale(he.mul(Z, W))
         # Step 2: row sums into column 0
-        for k in range(self.lg):
-            t = he.add(t, he.rotate(t, 1 << k))
+        t = self.rotsum(t, self.lg, 1)
         # Steps 3 and 5: s = (1 - c0) M - c1 (M t) - c3 t^2 (M t), zero outside column 0
         sq = he.rescale(he.mul(t, t))
         c3t = he.rescale(he.ptmul(t, self.p3))
@@ -210,8 +232,7 @@ class Circuit:
         lin.scale = cube.scale  # p1's scale was chosen for this
         s = he.ptadd(he.add(cube, he.moddrop(lin, cube.level)), self.p0)
         # Step 4: replicate s_r across the row
-        for k in range(self.lg):
-            s = he.add(s, he.rotate(s, -(1 << k)))
+        s = self.rotsum(s, self.lg, -1)
         # Step 6: s_r * z_rc
         return he.rescale(he.mul(s, he.moddrop(Z, s.level)))
 
@@ -219,8 +240,7 @@ class Circuit:
         """Steps 7-9 on the accumulated gradient ciphertext; alpha = F2(t)."""
         he = self.he
         # Step 7: column sums, every row gets g_c
-        for k in range(self.lm):
-            acc = he.add(acc, he.rotate(acc, self.g << k))
+        acc = self.rotsum(acc, self.lm, self.g)
         # Step 8: n Bbar_c g_c (the first-order baseline uses g_c itself)
         nG = acc if B is None else he.rescale(he.mul(acc, he.moddrop(B, acc.level)))
         # Step 9: V' = W + G, W' = (1 - eta) V' + eta V

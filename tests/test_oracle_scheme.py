@@ -195,3 +195,33 @@ def test_ptadd_adds_the_message():
     assert np.abs(he.decode(he.decrypt(out)).real - (a + b)).max() < 1e-4
     with pytest.raises(ValueError):
         he.ptadd(ct, he.encode(b, 1, 2.0 ** 30))
+
+
+def test_hoisted_rotation_sum_single_rotation_is_add_of_rotate(he):
+    """One rotation through the hoisted path is exactly ct + Rot(ct): the
+    shared ModUp and ModDown reduce to the key switch of one rotation."""
+    ct = enc(he, rand_slots(he, 41), 43)
+    for r in (1, -2, 300):
+        assert np.array_equal(he.rotsum(ct, [r]).data, he.add(ct, he.rotate(ct, r)).data), r
+    low = he.moddrop(ct, 3)
+    assert np.array_equal(he.rotsum(low, [4]).data, he.add(low, he.rotate(low, 4)).data)
+
+
+def test_hoisted_rotation_sum_decrypts_to_the_slot_sum(he):
+    """ct + sum_j Rot(ct, r_j) with the inner products summed before one
+    ModDown decrypts to z + sum_j rot(z, r_j) within the key-switching noise,
+    and differs in its words from the sequential sum (one rounding, not
+    several)."""
+    z = rand_slots(he, 42)
+    ct = enc(he, z, 44)
+    rots = [1, 2, -1, 64]
+    got = he.rotsum(ct, rots)
+    want = z + sum(np.roll(z, -r) for r in rots)
+    assert np.abs(dec(he, got) - want).max() < 1e-6
+    seq = ct
+    for r in rots:
+        seq = he.add(seq, he.rotate(ct, r))
+    assert not np.array_equal(got.data, seq.data)
+    assert np.abs(dec(he, got) - dec(he, seq)).max() < 1e-6
+    with pytest.raises(KeyError):
+        he.rotsum(ct, [1, 5])  # no key for 5
