@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-multi", action="store_true")
     ap.add_argument("--no-first-order", action="store_true")
     ap.add_argument("--no-bbar", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="default key-switch waves (profiling runs)")
     ap.add_argument("--sweep-point", default="", help="log_n,limbs,batch: run only this NTT sweep point")
     ap.add_argument("--sweep", action="store_true",
                     help="HE primitive sweep: batched NTT and key switching vs N, limbs and batch (JSON line per point)")
@@ -154,7 +155,7 @@ def run_ours(args, rank, world):
     # key it times with comes from the same seed the job uses for its keys)
     ta = time.time()
     ctx.keygen(2)
-    tuned_levels = ctx.autotune(None, 256)
+    tuned_levels = 0 if args.no_autotune else ctx.autotune(None, 256)
     autotune = {"ks_wave_by_level": [ctx.ks_wave(lv) for lv in range(NQ)], "levels_measured": tuned_levels,
                 "s": round(time.time() - ta, 2)}
     job = binding.Job(ctx, X, y, binding.FULL_BATCH, 1024, binding.G8, LOG_SCALE, enc_seed=3, key_seed=2,

@@ -142,6 +142,14 @@ int he_mul(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
 int he_rescale(he_ctx *ctx, const he_ct *a, he_ct **out);
 int he_moddrop(he_ctx *ctx, const he_ct *a, int level, he_ct **out);
 int he_rotate(he_ctx *ctx, const he_ct *a, int64_t r, he_ct **out);
+/* a + sum_j Rot(a, rots[j]) for 1 <= n_rot <= 7 rotations whose key switches
+ * share one ModUp and one ModDown (hoisted rotations; Sec. 2.1 rotation, used
+ * by the rotate-and-sum of Sec. 2.2): the digits of a's second polynomial are
+ * lifted and transformed once, the inner products of every rotation are
+ * summed over {q_0..q_l, P} and divided by P once.  With one rotation the
+ * result equals he_add(a, he_rotate(a, r)) word for word.  HE_EKEY when a
+ * rotation key is missing, HE_EINVAL for n_rot outside 1..7. */
+int he_rotsum(he_ctx *ctx, const he_ct *a, const int64_t *rots, size_t n_rot, he_ct **out);
 int he_cmul(he_ctx *ctx, const he_ct *a, double c, double const_scale, he_ct **out);
 int he_cadd(he_ctx *ctx, const he_ct *a, double c, he_ct **out);
 int he_ptmul(he_ctx *ctx, const he_ct *a, const he_pt *pt, he_ct **out);
@@ -223,6 +231,15 @@ int he_prof_read2(he_ctx *ctx, int cls, double *units2, double *dram_limbs);
  * he_prof_keyswitches writes the key switches issued since profiling was
  * enabled per input limb count: by_limbs[L] for L < n. */
 int he_prof_keyswitches(he_ctx *ctx, double *by_limbs, size_t n);
+/* The rotate-and-sum steps of the training circuit (the row sums and their
+ * replication, Sec. 2.2 SumColVec, and the column sums of the full-batch
+ * gradient, Sec. 3.3) over 2^k positions run as hoisted groups of 2^r
+ * positions: each group sums the rotations by m 2^e (0 < m < 2^r) of one
+ * ciphertext with one ModUp and one ModDown (Sec. 2.1 key switching shared by
+ * the rotations), so r = 1 is the plain log-step sum.  Sets r for later jobs
+ * and iterations of ctx (default 2; 1..3, else HE_EINVAL).  A job must run
+ * with the r it was created with (its rotation keys depend on it). */
+int he_set_rotation_radix(he_ctx *ctx, int log2_radix);
 /* Galois element of a left rotation by r. */
 uint64_t he_galois_elt(const he_ctx *ctx, int64_t r);
 

@@ -98,6 +98,8 @@ SIGNATURES = {
     "he_prof_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_u64)]),
     "he_prof_read2": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "he_prof_keyswitches": (_i, [_vp, _vp, _sz]),
+    "he_set_rotation_radix": (_i, [_vp, _i]),
+    "he_rotsum": (_i, [_vp, _vp, _vp, _sz, _pp]),
     "he_lr_job_free": (_i, [_vp]),
     "he_lr_multi_create": (_i, [_vp, _vp, _sz, _i, _pp]),
     "he_lr_multi_step": (_i, [_vp, _i, he_lr_sched]),
@@ -226,6 +228,12 @@ class Context:
     def rotate(self, a, r):
         return self._op("he_rotate", a.h, int(r))
 
+    def rotsum(self, a, rots):
+        r = np.asarray(rots, np.int64)
+        o = ctypes.c_void_p()
+        self.check(self.L.he_rotsum(self.h, a.h, _ptr(r), len(r), ctypes.byref(o)))
+        return Ct(self, o)
+
     def cmul(self, a, c, const_scale):
         return self._op("he_cmul", a.h, float(c), float(const_scale))
 
@@ -257,6 +265,10 @@ class Context:
         self.check(self.L.he_prof_read(self.h, cls, ctypes.byref(ms), ctypes.byref(units), ctypes.byref(n)))
         self.check(self.L.he_prof_read2(self.h, cls, ctypes.byref(u2), ctypes.byref(u3)))
         return ms.value, units.value, n.value, u2.value, u3.value
+
+    def set_rotation_radix(self, log2_radix):
+        """Rotate-and-sum steps as hoisted groups of 2^log2_radix positions."""
+        self.check(self.L.he_set_rotation_radix(self.h, int(log2_radix)))
 
     def prof_keyswitches(self):
         """Key switches issued since profiling was enabled, per input limb count."""

@@ -180,7 +180,8 @@ int ev_rotate_acc(Eval *ev, const CtB &a, int64_t r, CtB &out, int accumulate)
     o.out = S(out, c);
     o.rot = a.d;
     o.rot_item = a.item;
-    o.gal = gal;
+    o.gals[0] = gal;
+    o.ngal = 1;
     if (accumulate) {
         o.acc = a.d;
         o.acc_item = a.item;
@@ -192,6 +193,27 @@ int ev_rotate_acc(Eval *ev, const CtB &a, int64_t r, CtB &out, int accumulate)
     return HE_OK;
 }
 int ev_rotate(Eval *ev, const CtB &a, int64_t r, CtB &out) { return ev_rotate_acc(ev, a, r, out, 0); }
+// out = a + sum_j Rot(a, rots[j]) with one ModUp and one ModDown per item
+// (hoisted rotations); out must not alias a
+int ev_rotsum(Eval *ev, const CtB &a, const int64_t *rots, int nrot, CtB &out)
+{
+    he_ctx *c = ev->c;
+    HELR_TRY(check_batch(ev, a));
+    if (nrot < 1 || nrot > HELR_MAX_HOIST) return helr_fail(c, HE_EINVAL, "%d rotations in one hoisted sum", nrot);
+    HoistKeys hk{};
+    hk.n = nrot;
+    for (int j = 0; j < nrot; j++) {
+        hk.gal[j] = he_galois_elt(c, rots[j]);
+        hk.key[j] = helr_find_key(c, hk.gal[j]);
+        if (!hk.key[j]) return helr_fail(c, HE_EKEY, "no rotation key for %lld", (long long)rots[j]);
+    }
+    out.level = a.level;
+    out.batch = a.batch;
+    out.scale = a.scale;
+    HELR_TRY(helr_rotsum(c, a.d, a.item, a.batch, a.level, hk, &ev->ks, S(out, c)));
+    ev->keyswitches += (uint64_t)a.batch * nrot;
+    return HE_OK;
+}
 
 int ev_add(Eval *ev, const CtB &a, const CtB &b, CtB &out, int sub)
 {
@@ -368,6 +390,23 @@ extern "C" int he_rotate(he_ctx *c, const he_ct *a, int64_t r, he_ct **out)
     if (!rc) {
         CtB ob{o->d, 1, a->level, a->scale, 0};
         rc = ev_rotate(&ev, view(a), r, ob);
+    }
+    ev_free(&ev);
+    if (rc) { if (o) he_ct_free(o); return rc; }
+    *out = o;
+    return HE_OK;
+}
+
+extern "C" int he_rotsum(he_ctx *c, const he_ct *a, const int64_t *rots, size_t n_rot, he_ct **out)
+{
+    if (!c || !a || !out || !rots || n_rot < 1 || n_rot > HELR_MAX_HOIST) return HE_EINVAL;
+    Eval ev{};
+    HELR_TRY(one_eval(c, a->level, &ev));
+    he_ct *o = nullptr;
+    int rc = helr_new_ct(c, a->level, a->scale, &o);
+    if (!rc) {
+        CtB ob{o->d, 1, a->level, a->scale, 0};
+        rc = ev_rotsum(&ev, view(a), rots, (int)n_rot, ob);
     }
     ev_free(&ev);
     if (rc) { if (o) he_ct_free(o); return rc; }

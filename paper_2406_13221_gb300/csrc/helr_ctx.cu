@@ -49,6 +49,15 @@ extern "C" int he_prof_enable(he_ctx *c, int on)
     return HE_OK;
 }
 
+extern "C" int he_set_rotation_radix(he_ctx *c, int log2_radix)
+{
+    if (!c) return HE_EINVAL;
+    if (log2_radix < 1 || (1 << log2_radix) - 1 > HELR_MAX_HOIST)
+        return helr_fail(c, HE_EINVAL, "rotation radix 2^%d unsupported (1..3)", log2_radix);
+    c->rot_radix_log = log2_radix;
+    return HE_OK;
+}
+
 extern "C" int he_prof_keyswitches(he_ctx *c, double *by_limbs, size_t n)
 {
     if (!c || !by_limbs) return HE_EINVAL;
@@ -686,6 +695,60 @@ int helr_keyswitch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, 
               3.0 * nl * batch + waves * 2.0 * nl * (nl + 1));
     if (c->prof.on) c->prof.ks_by_limbs[nl] += batch;
     if (ws == &local) helr_ks_scratch_free(c, &local);
+    return HE_OK;
+}
+
+// Hoisted rotation sum: out = a + sum_j Rot_{gal_j}(a) for every item of the
+// batch.  The second polynomials are decomposed once (inverse row pass, ModUp
+// with the column passes, the row passes of the lifted digits), the inner
+// products of all rotations are summed over {q_0..q_l, P} (the automorphisms
+// act on the transformed digits), and one ModDown forms
+//   out_0 = a_0 + sum_j sigma_j(a_0) + KS_0,  out_1 = a_1 + KS_1
+// in its output stage.  out must not alias a.
+int helr_rotsum(he_ctx *c, const uint64_t *a, size_t a_item, int batch, int level, const HoistKeys &hk, KsScratch *ws,
+                Str out)
+{
+    const int nl = level + 1, nt = nl + 1;
+    const size_t N = c->n, lw = (size_t)nl * N;
+    if (hk.n < 1 || hk.n > HELR_MAX_HOIST) return helr_fail(c, HE_EINVAL, "%d rotations in one hoisted sum", hk.n);
+    // the summed 128-bit products must not overflow: hk.n * nl terms below q^2
+    for (int t = 0; t <= nl; t++) {
+        const uint64_t q = t < nl ? c->q[t] : c->q[c->nq];
+        if ((u128)q * q > ~(u128)0 / ((unsigned)hk.n * (unsigned)nl))
+            return helr_fail(c, HE_EINVAL, "%d rotations x %d digits overflow the 128-bit sums", hk.n, nl);
+    }
+    cudaStream_t s = c->stream;
+    prof_start(c, PROF_KS, s);
+    // 1. row pass of the inverse transform of every second-polynomial limb
+    HELR_TRY(helr_ntt_inv_rows(c, a + lw, a_item, N, ws->drow, (size_t)batch * nl, limbmap_ct(level), s, nl));
+    // 2. ModUp, the digits' transforms and the summed inner products, in waves
+    const size_t per_item = (size_t)nl * nt * N;
+    const int wave = (int)std::max<size_t>(
+        1, std::min({(size_t)(ws->wave > 0 ? ws->wave : helr_ks_wave(c, nl)), (size_t)batch, ws->ext_cap / per_item}));
+    for (int b0 = 0; b0 < batch; b0 += wave) {
+        const int cnt = std::min(wave, batch - b0);
+        HELR_TRY(helr_ks_hoisted(c, a + (size_t)b0 * a_item + lw, a_item, ws->drow + (size_t)b0 * nl * N, ws->ext, hk,
+                                 ws->acc + (size_t)b0 * 2 * nt * N, cnt, nl, s));
+    }
+    // 3. one ModDown, with the c0 terms of every rotation and a itself
+    HELR_TRY(helr_ntt_inv_rows(c, ws->acc + (size_t)nl * N, 2 * (size_t)nt * N, (size_t)nt * N, ws->pl, (size_t)batch * 2,
+                               limbmap_single(c->nq), s));
+    KsOut o;
+    o.out = out;
+    o.rot = a;
+    o.rot_item = a_item;
+    for (int j = 0; j < hk.n; j++) o.gals[j] = hk.gal[j];
+    o.ngal = hk.n;
+    o.acc = a;
+    o.acc_item = a_item;
+    o.acc_poly = lw;
+    HELR_TRY(helr_ks_down(c, o, ws->acc, 2 * (size_t)nt * N, (size_t)nt * N, ws->pl, c->nq, ws->lift, batch, nl, c->d_pinv, s));
+    HELR_CUDA(c, cudaGetLastError());
+    const double waves = (double)((batch + wave - 1) / wave);
+    // algorithmic DRAM: input read once, output written once, the keys of every rotation once per wave
+    prof_stop(c, PROF_KS, s, (double)batch * hk.n, 0, (double)batch * hk.n * nl,
+              3.0 * nl * batch + waves * hk.n * 2.0 * nl * (nl + 1));
+    if (c->prof.on) c->prof.ks_by_limbs[nl] += (double)batch * hk.n;
     return HE_OK;
 }
 

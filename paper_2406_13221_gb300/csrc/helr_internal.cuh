@@ -221,6 +221,7 @@ struct he_ctx {
     Prof prof;
     int ks_wave = 0;               // items per fused key-switch wave forced by HELR_KS_WAVE (0 = none)
     int ks_wave_tab[HELR_MAXQ + 1] = {};  // wave per limb count chosen by he_autotune (0 = default)
+    int rot_radix_log = 2;         // rotate-and-sum steps as hoisted groups of 2^rot_radix_log positions
 };
 
 struct he_ct {
@@ -295,8 +296,9 @@ int helr_ntt_inv(he_ctx *c, uint64_t *data, size_t nlimbs, const LimbMap &m, cud
 int helr_ntt_fwd_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s);
 int helr_ntt_inv_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs, const LimbMap &m, cudaStream_t s);
 // row pass of the inverse transform only (see ntt.cu)
+// (input limb k is read at in + (k / per_item) in_item + (k % per_item) in_poly)
 int helr_ntt_inv_rows(he_ctx *c, const uint64_t *in, size_t in_item, size_t in_poly, uint64_t *out, size_t nlimbs,
-                      const LimbMap &m, cudaStream_t s);
+                      const LimbMap &m, cudaStream_t s, int per_item = 2);
 
 // elementwise / structural kernels (ops.cu)
 void k_add(he_ctx *c, uint64_t *out, const uint64_t *a, const uint64_t *b, size_t nlimbs, const LimbMap &m, int sub, cudaStream_t s);
@@ -345,18 +347,39 @@ void helr_ks_scratch_free(he_ctx *c, KsScratch *ws);
 // rel: polynomials (d0, d1) of a tensor; rot: c0 of the rotated ciphertext;
 // acc: a ciphertext added to the result (rotate-and-add). Views are strided
 // [item][poly][limb][N]; out must not alias rot or acc.
+// Rotations whose key switches share one ModUp and one ModDown (hoisted
+// rotation sums) take at most this many Galois elements per call.
+#define HELR_MAX_HOIST 7
 struct KsOut {
     Str out;
     const uint64_t *rel = nullptr;
     size_t rel_item = 0, rel_poly = 0;
-    const uint64_t *rot = nullptr;
+    const uint64_t *rot = nullptr;  // out_0 += sum_j sigma_gals[j](rot_0)
     size_t rot_item = 0;
-    uint64_t gal = 0;
+    uint64_t gals[HELR_MAX_HOIST] = {};
+    int ngal = 0;
     const uint64_t *acc = nullptr;
     size_t acc_item = 0, acc_poly = 0;
 };
+// keys and Galois elements of the rotations of one hoisted rotation sum
+struct HoistKeys {
+    const uint64_t *key[HELR_MAX_HOIST];
+    uint64_t gal[HELR_MAX_HOIST];
+    int n;
+};
 int helr_keyswitch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, int level, const uint64_t *key,
                    KsScratch *ws, const KsOut *o = nullptr);
+// Hoisted rotation sum over a batch: out = a + sum_j Rot_{gal_j}(a) for every
+// item of a ([items][2][nl][N] at stride a_item), one ModUp and one ModDown per
+// item (helr_ctx.cu); hk lists the keys and Galois elements.
+int helr_rotsum(he_ctx *c, const uint64_t *a, size_t a_item, int batch, int level, const HoistKeys &hk, KsScratch *ws,
+                Str out);
+// ModUp of the input's digits, their full forward transforms and the summed
+// inner products of every rotation of hk (ks.cu): dntt = second polynomials in
+// evaluation form (item stride din_item), drow = the same after the inverse row
+// pass ([items][nl][N]), mid = scratch [items][nl][nl+1][N], acc = [items][2][nl+1][N].
+int helr_ks_hoisted(he_ctx *c, const uint64_t *dntt, size_t din_item, const uint64_t *drow, uint64_t *mid,
+                    const HoistKeys &hk, uint64_t *acc, int items, int nl, cudaStream_t s);
 int helr_ks_down(he_ctx *c, const KsOut &o, const uint64_t *src, size_t src_item, size_t src_poly, const uint64_t *drow,
                  int src_prime, uint64_t *lift, int items, int nl, const uint64_t *inv, cudaStream_t s);
 const uint64_t *helr_find_key(const he_ctx *c, uint64_t gal);
@@ -406,6 +429,12 @@ int ev_mul_relin_seg(Eval *ev, const CtB &a, const uint64_t *const *bptr, const 
                      double bscale, CtB &out);
 int ev_rotate(Eval *ev, const CtB &a, int64_t r, CtB &out);
 int ev_rotate_acc(Eval *ev, const CtB &a, int64_t r, CtB &out, int accumulate);
+int ev_rotsum(Eval *ev, const CtB &a, const int64_t *rots, int nrot, CtB &out);
+// Rotate-and-sum over 2^nbits positions spaced `step` slots apart as hoisted
+// groups of 2^rho positions: group e (e = 0, rho, 2 rho, ...) of width
+// w = min(rho, nbits - e) sums the rotations by m 2^e step, 0 < m < 2^w.
+// Appends the rotation amounts of group e to out; returns w.
+int rot_group_amounts(int e, int nbits, int rho, int64_t step, int64_t *out);
 int ev_add(Eval *ev, const CtB &a, const CtB &b, CtB &out, int sub);
 int ev_cmul_int(Eval *ev, const CtB &a, int64_t k, double out_scale, CtB &out);
 int ev_cadd_int(Eval *ev, CtB &a, int64_t k);

@@ -341,10 +341,18 @@ extern "C" int he_lr_job_create(he_ctx *c, const double *X, const double *y, siz
         }                             \
     } while (0)
 
-    // keys for the rotations of Steps 2, 4 and 7
+    // keys for the rotations of Steps 2, 4 and 7 (hoisted groups)
     std::vector<int64_t> rots;
-    for (int k = 0; k < j->lg; k++) rots.push_back(1 << k), rots.push_back(-(1 << k));
-    for (int k = 0; k < j->lm; k++) rots.push_back((int64_t)g << k);
+    int64_t amt[HELR_MAX_HOIST];
+    const int rho = c->rot_radix_log;
+    for (int e = 0; e < j->lg; e += rho) {
+        const int n = (1 << rot_group_amounts(e, j->lg, rho, 1, amt)) - 1;
+        for (int k = 0; k < n; k++) rots.push_back(amt[k]), rots.push_back(-amt[k]);
+    }
+    for (int e = 0; e < j->lm; e += rho) {
+        const int n = (1 << rot_group_amounts(e, j->lm, rho, g, amt)) - 1;
+        rots.insert(rots.end(), amt, amt + n);
+    }
     JTRY(he_keygen(c, key_seed, rots.data(), rots.size()));
 
     // Step 1: Z = y [1 | X], blocks of m rows x g columns, row-major in the slots
@@ -473,20 +481,40 @@ struct Seg {
     double p1_scale;
 };
 
-// ping-pong rotate-and-add over the items with lg > k (a prefix: segments are
-// ordered by decreasing lg); the remaining items are carried over unchanged
-static int rot_step(const WorkSet &ws, CtB &Bt, CtB &R, int64_t r, int rotated, int cnt)
+int rot_group_amounts(int e, int nbits, int rho, int64_t step, int64_t *out)
+{
+    const int w = std::min(rho, nbits - e);
+    for (int m = 1; m < (1 << w); m++) out[m - 1] = step * ((int64_t)m << e);
+    return w;
+}
+
+// Group e of a rotate-and-sum (Sec. 2.2 SumColVec and its replication), as one
+// hoisted rotation sum per run of items that share the group's width: an item
+// of row width 2^lg takes width min(rho, lg - e) (segments are ordered by
+// decreasing lg, so equal widths are contiguous); items with lg <= e are
+// carried over unchanged.  Ping-pong: the result ends in Bt, R takes the input.
+static int rot_group(const WorkSet &ws, CtB &Bt, CtB &R, int e, int64_t step, const Seg *segs, int nseg, int cnt)
 {
     Eval *ev = ws.ev;
-    CtB pre = Bt, preR = R;
-    pre.batch = rotated;
-    HELR_TRY(ev_rotate_acc(ev, pre, r, preR, 1));
-    if (rotated < cnt) {
-        CtB rest = Bt, restR = R;
-        rest.d = Bt.d + (size_t)rotated * ws.ctw;
-        rest.batch = cnt - rotated;
-        restR.d = R.d + (size_t)rotated * ws.ctw;
-        HELR_TRY(ev_moddrop(ev, rest, rest.level, restR));
+    const int rho = ev->c->rot_radix_log;
+    auto width = [&](int i) { return std::max(0, std::min(rho, segs[i].lg - e)); };
+    for (int i = 0; i < nseg;) {
+        const int w = width(i);
+        int k = i + 1;
+        while (k < nseg && width(k) == w) k++;
+        const int start = segs[i].start, end = segs[k - 1].start + segs[k - 1].count;
+        CtB a = Bt, o = R;
+        a.d = Bt.d + (size_t)start * ws.ctw;
+        a.batch = end - start;
+        o.d = R.d + (size_t)start * ws.ctw;
+        if (w > 0) {
+            int64_t rots[HELR_MAX_HOIST];
+            const int n = (1 << rot_group_amounts(e, segs[i].lg, rho, step, rots)) - 1;
+            HELR_TRY(ev_rotsum(ev, a, rots, n, o));
+        } else {
+            HELR_TRY(ev_moddrop(ev, a, a.level, o));
+        }
+        i = k;
     }
     R.level = Bt.level;
     R.scale = Bt.scale;
@@ -512,12 +540,6 @@ static int block_grads_seg(const WorkSet &ws, const uint64_t *Z, int cnt, const 
         wp[i] = segs[i].W, st[i] = segs[i].start, ct[i] = segs[i].count;
         lgmax = std::max(lgmax, segs[i].lg);
     }
-    auto rotated = [&](int k) {
-        int n = 0;
-        for (int i = 0; i < nseg; i++)
-            if (segs[i].lg > k) n = segs[i].start + segs[i].count;
-        return n;
-    };
     auto slice = [&](const CtB &x, int i) {
         CtB y = x;
         y.d = x.d + (size_t)segs[i].start * w;
@@ -538,8 +560,9 @@ static int block_grads_seg(const WorkSet &ws, const uint64_t *Z, int cnt, const 
     // 1
     HELR_TRY(ev_mul_relin_seg(ev, Zc, wp.data(), st.data(), ct.data(), nseg, w_scale, A));
     HELR_TRY(ev_rescale(ev, A, Bt));
-    // 2: t += Rot(t, 2^k), ping-pong between T1 and T2
-    for (int k = 0; k < lgmax; k++) HELR_TRY(rot_step(ws, Bt, R, 1 << k, rotated(k), cnt));
+    // 2: row sums, t += sum_m Rot(t, m 2^e) per hoisted group, ping-pong between T1 and T2
+    const int rho = ev->c->rot_radix_log;
+    for (int e = 0; e < lgmax; e += rho) HELR_TRY(rot_group(ws, Bt, R, e, 1, segs, nseg, cnt));
     const CtB t = Bt;  // level L-1; R is the other of T1 / T2
     // 3/5: s = (1 - c0) M - c1 (M t) - c3 t^2 (M t)
     CtB sq{ws.T[3], cnt, 0, 0, w}, c3{ws.T[4], cnt, 0, 0, w}, cube{ws.T[0], cnt, 0, 0, w};
@@ -560,10 +583,10 @@ static int block_grads_seg(const WorkSet &ws, const uint64_t *Z, int cnt, const 
         CtB y = slice(s, i);
         HELR_TRY(ev_ptadd(ev, y, segs[i].sig.p0));
     }
-    // 4: s += Rot(s, -2^k), ping-pong between T1 and T2
+    // 4: s += sum_m Rot(s, -m 2^e) per hoisted group, ping-pong between T1 and T2
     Bt = s;
     R.d = t.d == ws.T[1] ? ws.T[2] : ws.T[1];
-    for (int k = 0; k < lgmax; k++) HELR_TRY(rot_step(ws, Bt, R, -(1 << k), rotated(k), cnt));
+    for (int e = 0; e < lgmax; e += rho) HELR_TRY(rot_group(ws, Bt, R, e, -1, segs, nseg, cnt));
     if (Bt.d != ws.T[1]) {
         CtB t1{ws.T[1], cnt, 0, 0, w};
         HELR_TRY(ev_moddrop(ev, Bt, Bt.level, t1));
@@ -599,9 +622,12 @@ static int finish_ws(const WorkSet &ws, CtB acc, const he_ct *Bct, const he_ct *
     Eval *ev = ws.ev;
     const size_t w = ws.ctw;
     CtB R{ws.T[0], 1, 0, 0, w}, A{ws.T[1], 1, 0, 0, w}, Bd{ws.T[2], 1, 0, 0, w};
-    // 7: acc += Rot(acc, g 2^k), ping-pong between acc and R
-    for (int k = 0; k < lm; k++) {
-        HELR_TRY(ev_rotate_acc(ev, acc, (int64_t)g << k, R, 1));
+    // 7: column sums, acc += sum_m Rot(acc, g m 2^e) per hoisted group, ping-pong between acc and R
+    const int rho = ev->c->rot_radix_log;
+    for (int e = 0; e < lm; e += rho) {
+        int64_t rots[HELR_MAX_HOIST];
+        const int n = (1 << rot_group_amounts(e, lm, rho, g, rots)) - 1;
+        HELR_TRY(ev_rotsum(ev, acc, rots, n, R));
         std::swap(acc, R);
     }
     // 8: n Bbar_c g_c; the first-order baseline (no Bbar) takes g_c itself

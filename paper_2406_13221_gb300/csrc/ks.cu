@@ -110,6 +110,18 @@ __global__ void __launch_bounds__(C * Geo<K1>::T, 3)
     }
 }
 
+// sigma_gal on the evaluation form: position k holds the evaluation at
+// psi^(2 bitrev(k) + 1), so sigma_gal(x) takes at k the value x holds at the
+// position of psi^((2 bitrev(k) + 1) gal).  The product is needed modulo 2N
+// only, so 32-bit arithmetic suffices.
+template <int LOGN>
+__device__ __forceinline__ uint32_t auto_pos(uint32_t k, uint64_t gal)
+{
+    const uint32_t kk = __brev(k) >> (32 - LOGN);
+    const uint32_t e = ((2u * kk + 1u) * (uint32_t)gal) & ((2u << LOGN) - 1u);
+    return __brev((e - 1u) >> 1) >> (32 - LOGN);
+}
+
 // bulk prefetch of `bytes` (a multiple of 16) from a 16-byte aligned global
 // address into L2 (no data returned to the thread)
 __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
@@ -446,8 +458,9 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T)
     to_strided<K2>(x, seg, l);  // word l + T r of the row: coalesced below
     const uint64_t pv = inv[2 * j], pvp = inv[2 * j + 1], q4 = 4 * q;
     // lazy arithmetic, one reduction at the end: src + 4q - w < 5q (w < 4q from
-    // Harvey's butterflies), the Shoup product < 2q, each added term < q: the
-    // sum stays below 5q < 2^64 for primes below 2^61
+    // Harvey's butterflies), the Shoup product < 2q, each added term < q (rel,
+    // acc and up to HELR_MAX_HOIST rotation terms): the sum stays below
+    // (4 + 7) q < 2^64 for primes below 2^60
 #pragma unroll
     for (int r = 0; r < E; r++) {
         const int k = row * R2 + l + T * r;
@@ -455,17 +468,149 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T)
         uint64_t v = shoup_lazy(sv[lk] + (q4 - x[r]), pv, pvp, q);
         if (o.rel) v += o.rel[bt * o.rel_item + p * o.rel_poly + lk];
         if (o.rot && p == 0) {
-            // sigma_gal on the evaluation form: position k holds the evaluation at
-            // psi^(2 bitrev(k) + 1); it takes the value at the position of
-            // psi^((2 bitrev(k) + 1) gal)
-            const uint64_t mask2n = (2ull << LOGN) - 1;
-            const uint32_t kk = __brev((uint32_t)k) >> (32 - LOGN);
-            const uint64_t e = ((2ull * kk + 1) * o.gal) & mask2n;
-            const uint32_t ps = __brev((uint32_t)((e - 1) >> 1)) >> (32 - LOGN);
-            v += o.rot[bt * o.rot_item + (size_t)j * N + ps];
+#pragma unroll
+            for (int g = 0; g < HELR_MAX_HOIST; g++)
+                if (g < o.ngal) v += o.rot[bt * o.rot_item + (size_t)j * N + auto_pos<LOGN>((uint32_t)k, o.gals[g])];
         }
         if (o.acc) v += o.acc[bt * o.acc_item + p * o.acc_poly + lk];
         o.out.p[bt * o.out.item + p * o.out.poly + lk] = reduce64(v, mq);
+    }
+}
+
+// Hoisted rotations, step 1: the forward row pass of every lifted digit
+// (column pass already applied by k_ks_modup_cols in ModUp mode), in place in
+// mid[b][i][t] for the targets t != i (t = nl standing for P), words reduced to
+// [0, q_t).  grid: items * nl digits * nl targets * (R1 / RPC).
+template <int K1, int K2, int RPC>
+__global__ void __launch_bounds__(RPC * Geo<K2>::T)
+    k_ks_digit_rows(uint64_t *__restrict__ mid, const uint64_t *__restrict__ twall, const ModQ *__restrict__ mods, int nl,
+                    int pidx)
+{
+    using G = Geo<K2>;
+    constexpr int R1 = 1 << K1, R2 = G::R, N = R1 * R2, NG = R1 / RPC, E = G::E, T = G::T;
+    extern __shared__ uint64_t smem[];
+    int bid = blockIdx.x;
+    const int grp = bid % NG;
+    bid /= NG;
+    const int tt = bid % nl;
+    bid /= nl;
+    const int i = bid % nl;
+    const size_t b = (size_t)(bid / nl);
+    const int t = tt < i ? tt : tt + 1;
+    const int pt = t < nl ? t : pidx;
+    const uint64_t q = mods[pt].q, q2 = 2 * q;
+    const uint64_t *tw = twall + (size_t)pt * N * 2;
+    const int l = threadIdx.x % T, rl = threadIdx.x / T;
+    const int row = grp * RPC + rl;
+    uint64_t *rowp = mid + ((b * nl + i) * (nl + 1) + t) * N + (size_t)row * R2;
+    uint64_t *seg = smem + rl * G::SEG;
+    uint64_t x[E];
+#pragma unroll
+    for (int r = 0; r < E; r++) x[r] = rowp[l + T * r];
+    const int A = R1 + row;
+    fwd_strided<K2>(x, tw, A, q, q2);
+    to_contig<K2>(x, seg, l);
+    fwd_contig<K2, true>(x, tw, A, l, q, q2);
+#pragma unroll
+    for (int r = 0; r < E; r++) {
+        uint64_t v = x[r];
+        v = v >= q2 ? v - q2 : v;
+        x[r] = v >= q ? v - q : v;
+    }
+    __syncthreads();
+    to_strided<K2>(x, seg, l);
+#pragma unroll
+    for (int r = 0; r < E; r++) rowp[l + T * r] = x[r];
+}
+
+// Hoisted rotations, step 2: the inner products of every rotation j of hk,
+// summed over j before the one ModDown:
+//   acc_t = sum_j sum_i sigma_j(D_(i,t)) * key_j(i,t)     (both key polynomials)
+// with D_(i,t) digit i of the second polynomial lifted into target t and
+// transformed (mid, or the input itself in evaluation form when t == i).  The
+// automorphism acts on the evaluation form as a permutation that maps every
+// row of R2 words onto one source row (the top bits of a position decide the
+// top bits of its image), so each output row gathers from one row of each
+// digit, which L1 keeps while the row's threads read it.  Keys are in
+// Montgomery form and in the row order of k_key_rows (word E l + r of a row
+// at r T + l): thread u takes key positions u, u + TPR, ..., coalesced, and
+// the columns they stand for.  Sums are exact in 128 bits (words below q,
+// at most HELR_MAX_HOIST * nl terms below q^2: < 2^128 for the chains the
+// context admits) and reduced once.
+// grid: items (fastest: the items of a wave share each key row through L2) *
+// (nl + 1) targets * (R1 / RPC).
+template <int K1, int K2>
+struct HoistGeo {
+    static constexpr int R1 = 1 << K1, R2 = 1 << K2;
+    static constexpr int TPR = R2 < 64 ? R2 : 64;                   // threads per row
+    static constexpr int PPT = R2 / TPR;                            // positions per thread
+    static constexpr int RPC = (256 / TPR) < R1 ? (256 / TPR) : R1; // rows per CTA
+    static constexpr int THREADS = RPC * TPR;
+};
+template <int K1, int K2>
+__global__ void __launch_bounds__(HoistGeo<K1, K2>::THREADS)
+    k_ks_hoist_ip(const uint64_t *__restrict__ mid, const uint64_t *__restrict__ dntt, size_t din_item, HoistKeys hk,
+                  uint64_t *__restrict__ acc, const ModQ *__restrict__ mods, int nl, int nq, int pidx, int items)
+{
+    using G = Geo<K2>;
+    using H = HoistGeo<K1, K2>;
+    constexpr int R1 = 1 << K1, R2 = 1 << K2, N = R1 * R2, LOGN = K1 + K2;
+    constexpr int TPR = H::TPR, PPT = H::PPT, RPC = H::RPC, NG = R1 / RPC;
+    int bid = blockIdx.x;
+    const int b = bid % items;
+    bid /= items;
+    const int grp = bid % NG;
+    const int t = bid / NG;  // target 0..nl (nl = P)
+    const int pt = t < nl ? t : pidx, kl = t < nl ? t : nq;
+    const ModQ m = mods[pt];
+    const int u = threadIdx.x % TPR, rl = threadIdx.x / TPR;
+    const int row = grp * RPC + rl;
+    const size_t roff = (size_t)row * R2;
+    int col[PPT];
+#pragma unroll
+    for (int mm = 0; mm < PPT; mm++) {
+        const int p = u + TPR * mm;
+        col[mm] = G::E * (p % G::T) + p / G::T;
+    }
+    uint32_t a0[PPT][4], a1[PPT][4];
+#pragma unroll
+    for (int mm = 0; mm < PPT; mm++)
+#pragma unroll
+        for (int w = 0; w < 4; w++) a0[mm][w] = a1[mm][w] = 0;
+    for (int j = 0; j < hk.n; j++) {
+        // an unrolled select: a dynamic index into the parameter arrays would
+        // move them into local memory
+        const uint64_t *key = hk.key[0];
+        uint64_t gal = hk.gal[0];
+#pragma unroll
+        for (int g = 1; g < HELR_MAX_HOIST; g++)
+            if (g == j) key = hk.key[g], gal = hk.gal[g];
+        uint32_t ps[PPT];
+#pragma unroll
+        for (int mm = 0; mm < PPT; mm++) ps[mm] = auto_pos<LOGN>((uint32_t)(roff + col[mm]), gal);
+        for (int i = 0; i < nl; i++) {
+            const uint64_t *src = i == t ? dntt + (size_t)b * din_item + (size_t)i * N
+                                         : mid + (((size_t)b * nl + i) * (nl + 1) + t) * N;
+            const uint64_t *k0 = key + (((size_t)i * 2 + 0) * (nq + 1) + kl) * N + roff + u;
+            const uint64_t *k1 = key + (((size_t)i * 2 + 1) * (nq + 1) + kl) * N + roff + u;
+#pragma unroll
+            for (int mm = 0; mm < PPT; mm++) {
+                const uint64_t x = __ldg(src + ps[mm]);
+                mac128(a0[mm], x, ld_stream(k0 + TPR * mm));
+                mac128(a1[mm], x, ld_stream(k1 + TPR * mm));
+            }
+        }
+    }
+    uint64_t *o0 = acc + (((size_t)b * 2 + 0) * (nl + 1) + t) * N + roff;
+    uint64_t *o1 = acc + (((size_t)b * 2 + 1) * (nl + 1) + t) * N + roff;
+#pragma unroll
+    for (int mm = 0; mm < PPT; mm++) {
+        uint64_t h0 = ((uint64_t)a0[mm][3] << 32) | a0[mm][2];
+        uint64_t h1 = ((uint64_t)a1[mm][3] << 32) | a1[mm][2];
+        h0 = h0 >= m.q ? reduce64(h0, m) : h0;
+        h1 = h1 >= m.q ? reduce64(h1, m) : h1;
+        o0[col[mm]] = redc128(h0, ((uint64_t)a0[mm][1] << 32) | a0[mm][0], m);
+        o1[col[mm]] = redc128(h1, ((uint64_t)a1[mm][1] << 32) | a1[mm][0], m);
     }
 }
 
@@ -487,7 +632,20 @@ struct KsPlan {
         if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_inner_rows<K1, K2, RPC, false>, RPC * T2, SM2);
         if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_inner_rows<K1, K2, RPC, true>, RPC * T2, SM2);
         if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_down_rows<K1, K2, RPCD>, RPCD * T2, SMD);
+        if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_digit_rows<K1, K2, RPCD>, RPCD * T2, SMD);
+        if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_hoist_ip<K1, K2>, HoistGeo<K1, K2>::THREADS, 0);
         return e;
+    }
+    // hoisted rotations: row passes of the lifted digits, then the summed inner products
+    static void hoisted(he_ctx *c, const uint64_t *dntt, size_t din_item, uint64_t *mid, const HoistKeys &hk, uint64_t *acc,
+                        int items, int nl, cudaStream_t s)
+    {
+        const unsigned g1 = (unsigned)((size_t)items * nl * nl * (R1 / RPCD));
+        HELR_LAUNCH(k_ks_digit_rows<K1, K2, RPCD><<<g1, RPCD * T2, SMD, s>>>(mid, c->t.tw, c->t.mod, nl, c->nq));
+        using H = HoistGeo<K1, K2>;
+        const unsigned g2 = (unsigned)((size_t)items * (nl + 1) * (R1 / H::RPC));
+        HELR_LAUNCH(k_ks_hoist_ip<K1, K2><<<g2, H::THREADS, 0, s>>>(mid, dntt, din_item, hk, acc, c->t.mod, nl, c->nq, c->nq,
+                                                                    items));
     }
     static void down(he_ctx *c, const KsOut &o, const uint64_t *src, size_t src_item, size_t src_poly, const uint64_t *lift,
                      int items, int nl, const uint64_t *inv, cudaStream_t s)
@@ -579,6 +737,45 @@ int helr_ks_fused(he_ctx *c, const uint64_t *dntt, const uint64_t *drow, uint64_
     case 14: return run_fused<7, 7>(c, dntt, drow, mid, key, acc, items, nl, s);
     case 15: return run_fused<7, 8>(c, dntt, drow, mid, key, acc, items, nl, s);
     case 16: return run_fused<8, 8>(c, dntt, drow, mid, key, acc, items, nl, s);
+    default: return helr_fail(c, HE_EINVAL, "log_n %d unsupported", c->logn);
+    }
+}
+
+template <int K1, int K2>
+int run_hoisted(he_ctx *c, const uint64_t *dntt, size_t din_item, const uint64_t *drow, uint64_t *mid, const HoistKeys &hk,
+                uint64_t *acc, int items, int nl, cudaStream_t s)
+{
+    static bool prepared = false;
+    if (!prepared) {
+        HELR_CUDA(c, (KsPlan<K1, K2>::prepare()));
+        prepared = true;
+    }
+    prof_start(c, PROF_MODUP, s);
+    const int l1 = KsPlan<K1, K2>::modup(c, drow, mid, items, nl, s);
+    prof_stop(c, PROF_MODUP, s, (double)items * nl * nl, l1, (double)items * nl, (double)items * nl * (nl + 1));
+    prof_start(c, PROF_KS_INNER, s);
+    KsPlan<K1, K2>::hoisted(c, dntt, din_item, mid, hk, acc, items, nl, s);
+    // row passes of the nl x nl lifted digits; products: rotations x 2 keys x nl digits x (nl + 1) targets;
+    // DRAM: digit rows read and written once, read once per rotation (gathers), keys once per launch, acc written
+    prof_stop(c, PROF_KS_INNER, s, (double)items * nl * nl, 2, (double)items * hk.n * 2 * nl * (nl + 1),
+              (double)items * nl * nl * 2 + (double)items * hk.n * nl * (nl + 1) + hk.n * 2.0 * nl * (nl + 1) +
+                  (double)items * 2 * (nl + 1));
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
+
+int helr_ks_hoisted(he_ctx *c, const uint64_t *dntt, size_t din_item, const uint64_t *drow, uint64_t *mid,
+                    const HoistKeys &hk, uint64_t *acc, int items, int nl, cudaStream_t s)
+{
+    if (hk.n < 1 || hk.n > HELR_MAX_HOIST) return helr_fail(c, HE_EINVAL, "%d rotations in one hoisted sum", hk.n);
+    switch (c->logn) {
+    case 10: return run_hoisted<5, 5>(c, dntt, din_item, drow, mid, hk, acc, items, nl, s);
+    case 11: return run_hoisted<5, 6>(c, dntt, din_item, drow, mid, hk, acc, items, nl, s);
+    case 12: return run_hoisted<6, 6>(c, dntt, din_item, drow, mid, hk, acc, items, nl, s);
+    case 13: return run_hoisted<6, 7>(c, dntt, din_item, drow, mid, hk, acc, items, nl, s);
+    case 14: return run_hoisted<7, 7>(c, dntt, din_item, drow, mid, hk, acc, items, nl, s);
+    case 15: return run_hoisted<7, 8>(c, dntt, din_item, drow, mid, hk, acc, items, nl, s);
+    case 16: return run_hoisted<8, 8>(c, dntt, din_item, drow, mid, hk, acc, items, nl, s);
     default: return helr_fail(c, HE_EINVAL, "log_n %d unsupported", c->logn);
     }
 }

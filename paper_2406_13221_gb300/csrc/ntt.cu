@@ -89,13 +89,13 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T) k_ntt_fwd_rows(uint64_t *__r
 
 // ---------------------------------------------------------------- inverse
 // pass A: rows (last forward stages undone first).  Input limb k is read at
-// in + (k / 2) in_item + (k % 2) in_poly (contiguous limbs: in_item = 2N,
-// in_poly = N); output limbs are contiguous.
+// in + (k / per_item) in_item + (k % per_item) in_poly (contiguous limbs:
+// in_item = per_item N, in_poly = N); output limbs are contiguous.
 template <int K1, int K2, int RPC>
 __global__ void __launch_bounds__(RPC * Geo<K2>::T) k_ntt_inv_rows(const uint64_t *__restrict__ in, size_t in_item,
                                                                    size_t in_poly, uint64_t *__restrict__ out,
                                                                    const uint64_t *__restrict__ twall, const ModQ *__restrict__ mods,
-                                                                   LimbMap lm)
+                                                                   LimbMap lm, int per_item)
 {
     using G = Geo<K2>;
     constexpr int R1 = 1 << K1, R2 = G::R, N = R1 * R2, NG = R1 / RPC;
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T) k_ntt_inv_rows(const uint64_
     const int pr = limb_prime(lm, limb);
     const uint64_t q = mods[pr].q, q2 = 2 * q;
     const uint64_t *tw = twall + (size_t)pr * N * 2;
-    const uint64_t *rin = in + (size_t)(limb >> 1) * in_item + (size_t)(limb & 1) * in_poly + (size_t)row * R2;
+    const uint64_t *rin = in + (size_t)(limb / per_item) * in_item + (size_t)(limb % per_item) * in_poly + (size_t)row * R2;
     uint64_t *rout = out + (size_t)limb * N + (size_t)row * R2;
     uint64_t *seg = smem + rl * G::SEG;
     uint64_t x[G::E];
@@ -172,22 +172,22 @@ struct NttPlan {
         HELR_LAUNCH(k_ntt_fwd_rows<K1, K2, RPC><<<(unsigned)(nlimbs * (R1 / RPC)), RPC * T2, SM2, s>>>(out, t.tw, t.mod, m));
     }
     static void inv_rows(const uint64_t *in, size_t in_item, size_t in_poly, uint64_t *out, size_t nlimbs, const DevTables &t,
-                         const LimbMap &m, cudaStream_t s)
+                         const LimbMap &m, cudaStream_t s, int per_item)
     {
         HELR_LAUNCH(k_ntt_inv_rows<K1, K2, RPC><<<(unsigned)(nlimbs * (R1 / RPC)), RPC * T2, SM2, s>>>(in, in_item, in_poly, out,
-                                                                                                 t.itw, t.mod, m));
+                                                                                                 t.itw, t.mod, m, per_item));
     }
     static void inv(const uint64_t *in, uint64_t *out, size_t nlimbs, const DevTables &t, const LimbMap &m, cudaStream_t s)
     {
         HELR_LAUNCH(k_ntt_inv_rows<K1, K2, RPC><<<(unsigned)(nlimbs * (R1 / RPC)), RPC * T2, SM2, s>>>(in, 2 * (size_t)N, N, out,
-                                                                                                 t.itw, t.mod, m));
+                                                                                                 t.itw, t.mod, m, 2));
         HELR_LAUNCH(k_ntt_inv_cols<K1, K2, C><<<(unsigned)(nlimbs * (R2 / C)), C * T1, SM1, s>>>(out, t.itw, t.mod, t.ninv, m));
     }
 };
 
 template <int K1, int K2>
 int run_inv_rows(he_ctx *c, const uint64_t *in, size_t in_item, size_t in_poly, uint64_t *out, size_t nlimbs,
-                 const LimbMap &m, cudaStream_t s)
+                 const LimbMap &m, cudaStream_t s, int per_item)
 {
     static bool prepared = false;
     if (!prepared) {
@@ -196,7 +196,7 @@ int run_inv_rows(he_ctx *c, const uint64_t *in, size_t in_item, size_t in_poly, 
     }
     if (nlimbs == 0) return HE_OK;
     prof_start(c, PROF_NTT_INV, s);
-    NttPlan<K1, K2>::inv_rows(in, in_item, in_poly, out, nlimbs, c->t, m, s);
+    NttPlan<K1, K2>::inv_rows(in, in_item, in_poly, out, nlimbs, c->t, m, s, per_item);
     prof_stop(c, PROF_NTT_INV, s, 0.5 * (double)nlimbs, 1);  // half of each transform
     HELR_CUDA(c, cudaGetLastError());
     return HE_OK;
@@ -290,19 +290,21 @@ int helr_ntt_inv_oop(he_ctx *c, const uint64_t *in, uint64_t *out, size_t nlimbs
 }
 // the row pass of the inverse transform only: the column pass (K1 stages, the
 // factor N^-1) is left to a consumer that reads whole columns.  Input limb k is
-// read at in + (k / 2) in_item + (k % 2) in_poly; output limbs are contiguous.
+// read at in + (k / per_item) in_item + (k % per_item) in_poly; output limbs
+// are contiguous.
 int helr_ntt_inv_rows(he_ctx *c, const uint64_t *in, size_t in_item, size_t in_poly, uint64_t *out, size_t nlimbs,
-                      const LimbMap &m, cudaStream_t s)
+                      const LimbMap &m, cudaStream_t s, int per_item)
 {
     if (nlimbs > (size_t)1 << 24) return helr_fail(c, HE_EINVAL, "too many limbs in one transform batch");
+    if (per_item < 1) return helr_fail(c, HE_EINVAL, "limbs per item %d", per_item);
     switch (c->logn) {
-    case 10: return run_inv_rows<5, 5>(c, in, in_item, in_poly, out, nlimbs, m, s);
-    case 11: return run_inv_rows<5, 6>(c, in, in_item, in_poly, out, nlimbs, m, s);
-    case 12: return run_inv_rows<6, 6>(c, in, in_item, in_poly, out, nlimbs, m, s);
-    case 13: return run_inv_rows<6, 7>(c, in, in_item, in_poly, out, nlimbs, m, s);
-    case 14: return run_inv_rows<7, 7>(c, in, in_item, in_poly, out, nlimbs, m, s);
-    case 15: return run_inv_rows<7, 8>(c, in, in_item, in_poly, out, nlimbs, m, s);
-    case 16: return run_inv_rows<8, 8>(c, in, in_item, in_poly, out, nlimbs, m, s);
+    case 10: return run_inv_rows<5, 5>(c, in, in_item, in_poly, out, nlimbs, m, s, per_item);
+    case 11: return run_inv_rows<5, 6>(c, in, in_item, in_poly, out, nlimbs, m, s, per_item);
+    case 12: return run_inv_rows<6, 6>(c, in, in_item, in_poly, out, nlimbs, m, s, per_item);
+    case 13: return run_inv_rows<6, 7>(c, in, in_item, in_poly, out, nlimbs, m, s, per_item);
+    case 14: return run_inv_rows<7, 7>(c, in, in_item, in_poly, out, nlimbs, m, s, per_item);
+    case 15: return run_inv_rows<7, 8>(c, in, in_item, in_poly, out, nlimbs, m, s, per_item);
+    case 16: return run_inv_rows<8, 8>(c, in, in_item, in_poly, out, nlimbs, m, s, per_item);
     default: return helr_fail(c, HE_EINVAL, "log_n %d unsupported", c->logn);
     }
 }

@@ -63,7 +63,11 @@ def test_ntt_matches_oracle(logn, nlimbs):
     assert np.array_equal(from_dev(dev).reshape(nlimbs, n), data)
 
 
+# rotations of the tests, plus those of the 16 x 256 training circuit with its
+# rotate-and-sum steps in hoisted groups of 2, 4 and 8 positions
 PAIR_ROTATIONS = [1, 2, 4, 8, -1, -2, -4, -8, 3, 100, -77] + [16 << k for k in range(8)]
+PAIR_ROTATIONS = sorted(set(PAIR_ROTATIONS) | {
+    r for rho in (1, 2, 3) for n, st in ((4, 1), (4, -1), (8, 16)) for rots in qgnag.rot_groups(n, st, rho) for r in rots})
 
 
 @pytest.fixture(scope="module")
@@ -158,6 +162,55 @@ def test_rotation_bitwise(pair, r):
     assert np.array_equal(ctx.rotate(a, r).export(), he.rotate(ra, r).data)
     a3 = ctx.moddrop(a, 3)
     assert np.array_equal(ctx.rotate(a3, r).export(), he.rotate(he.moddrop(ra, 3), r).data)
+
+
+@pytest.mark.parametrize("rots", [[3], [1, 2, 3], [-4, -8, -12], [16, 32, 48, 64, 80, 96, 112], [1, -1]])
+def test_hoisted_rotation_sum_bitwise(pair, rots):
+    """he_rotsum (one ModUp and one ModDown for all the rotations) equals the
+    oracle's hoisted rotation sum at levels 8 and 3; one rotation equals
+    add(a, rotate(a, r))."""
+    ctx, he = pair
+    a, ra = enc_pair(ctx, he, rand_slots(ctx.nslots, 31), 33)
+    for lv in (8, 3):
+        x, rx = (a, ra) if lv == 8 else (ctx.moddrop(a, lv), he.moddrop(ra, lv))
+        got = ctx.rotsum(x, rots).export()
+        assert np.array_equal(got, he.rotsum(rx, rots).data), lv
+        if len(rots) == 1:
+            assert np.array_equal(got, ctx.add(x, ctx.rotate(x, rots[0])).export())
+    with pytest.raises(binding.HeError) as e:
+        ctx.rotsum(a, [1, 9])  # no key for 9
+    assert e.value.code == binding.HE_EKEY
+    with pytest.raises(binding.HeError):
+        ctx.rotsum(a, list(range(1, 9)))  # more than 7 rotations
+
+
+@pytest.mark.parametrize("rho", [1, 3])
+def test_iteration_bitwise_other_rotation_radix(small_job_inputs, rho):
+    """The iteration with its rotate-and-sum steps in hoisted groups of 2 (the
+    plain log-step sum) and of 8 positions equals the oracle's circuit with the
+    same grouping."""
+    ctx, he, data, _ = small_job_inputs
+    L = 6
+    circ = qgnag.Circuit(he, 16, 256, D, start_level=L, rot_radix_log=rho)
+    Z = [he.encrypt(he.encode(data.blocks[b], L, D), 400 + b) for b in range(data.blocks.shape[0])]
+    B = he.encrypt(he.encode(np.tile(data.n * data.bbar_full, circ.m), L, D), 410)
+    rng = np.random.default_rng(13)
+    w0 = np.tile(np.r_[rng.uniform(-0.5, 0.5, data.f1), np.zeros(16 - data.f1)], circ.m)
+    W = he.encrypt(he.encode(w0, L, D), 411)
+    V = he.encrypt(he.encode(0.5 * w0, L, D), 412)
+    alpha, eta = qgnag.schedule(2), qgnag.nag_scalars(3)[2]
+    Wn, Vn = circ.iteration(Z, B, W, V, alpha, eta, 1.0 / data.n)
+    g = lambda c: ctx.import_ct(c.data, c.level, c.scale)  # noqa: E731
+    ctx.set_rotation_radix(rho)
+    try:
+        gW, gV = binding.lr_iteration(ctx, [g(z) for z in Z], g(B), g(W), g(V), 16, 256, alpha, eta,
+                                      1.0 / data.n, qgnag.G8)
+    finally:
+        ctx.set_rotation_radix(2)
+    assert np.array_equal(gW.export(), Wn.data)
+    assert np.array_equal(gV.export(), Vn.data)
+    with pytest.raises(binding.HeError):
+        ctx.set_rotation_radix(4)
 
 
 def test_constants_and_plaintext_product_bitwise(pair):
