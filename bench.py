@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-first-order", action="store_true")
     ap.add_argument("--no-bbar", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default key-switch waves (profiling runs)")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     ap.add_argument("--sweep-point", default="", help="log_n,limbs,batch: run only this NTT sweep point")
     ap.add_argument("--sweep", action="store_true",
                     help="HE primitive sweep: batched NTT and key switching vs N, limbs and batch (JSON line per point)")
@@ -175,12 +177,16 @@ def run_ours(args, rank, world):
     barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.profile_range:
+        torch.cuda.cudart().cudaProfilerStart()
     e0.record()
     for _ in range(args.steps):
         job.step(t, sched)
         t += 1
     e1.record()
     torch.cuda.synchronize()
+    if args.profile_range:
+        torch.cuda.cudart().cudaProfilerStop()
     barrier(world)
     clocks = clocks_stop(clk)
     launches = binding.launch_count() - l0

@@ -547,24 +547,41 @@ struct HoistGeo {
     static constexpr int RPC = (256 / TPR) < R1 ? (256 / TPR) : R1; // rows per CTA
     static constexpr int THREADS = RPC * TPR;
 };
-template <int K1, int K2>
-__global__ void __launch_bounds__(HoistGeo<K1, K2>::THREADS)
-    k_ks_hoist_ip(const uint64_t *__restrict__ mid, const uint64_t *__restrict__ dntt, size_t din_item, HoistKeys hk,
-                  uint64_t *__restrict__ acc, const ModQ *__restrict__ mods, int nl, int nq, int pidx, int items)
+// 128-bit sum of products x k for primes below 2^41 (x < 2^47, k < 2^41)
+// without 64 x 64-bit products: with x = xh 2^32 + xl and k = kh 2^32 + kl,
+// A (+ carries cA 2^64) sums xl kl and B sums xl kh + xh kl + xh kh 2^32 (each
+// term < 2^57, so B holds up to 64 terms); T = A + cA 2^64 + B 2^32.
+struct Acc40 {
+    uint64_t A, B;
+    uint32_t cA;
+};
+__device__ __forceinline__ void mac40(Acc40 &a, uint64_t x, uint64_t k)
+{
+    const uint32_t xl = (uint32_t)x, xh = (uint32_t)(x >> 32), kl = (uint32_t)k, kh = (uint32_t)(k >> 32);
+    const uint64_t p0 = (uint64_t)xl * kl;
+    a.A += p0;
+    a.cA += a.A < p0;
+    a.B += (uint64_t)xl * kh + (uint64_t)xh * kl + ((uint64_t)(xh * kh) << 32);
+}
+// T 2^-64 mod q for the sum held by a (keys in Montgomery form)
+__device__ __forceinline__ uint64_t redc40(const Acc40 &a, const ModQ &m)
+{
+    const uint64_t lo = a.A + (a.B << 32);
+    uint64_t hi = a.cA + (a.B >> 32) + (lo < a.A);
+    hi = hi >= m.q ? reduce64(hi, m) : hi;
+    return redc128(hi, lo, m);
+}
+
+template <int K1, int K2, bool F40>
+__device__ __forceinline__ void hoist_ip_body(const uint64_t *__restrict__ mid, const uint64_t *__restrict__ dntt,
+                                              size_t din_item, const HoistKeys &hk, uint64_t *__restrict__ acc,
+                                              const ModQ &m, int nl, int nq, int b, int t, int kl, int row)
 {
     using G = Geo<K2>;
     using H = HoistGeo<K1, K2>;
     constexpr int R1 = 1 << K1, R2 = 1 << K2, N = R1 * R2, LOGN = K1 + K2;
-    constexpr int TPR = H::TPR, PPT = H::PPT, RPC = H::RPC, NG = R1 / RPC;
-    int bid = blockIdx.x;
-    const int b = bid % items;
-    bid /= items;
-    const int grp = bid % NG;
-    const int t = bid / NG;  // target 0..nl (nl = P)
-    const int pt = t < nl ? t : pidx, kl = t < nl ? t : nq;
-    const ModQ m = mods[pt];
-    const int u = threadIdx.x % TPR, rl = threadIdx.x / TPR;
-    const int row = grp * RPC + rl;
+    constexpr int TPR = H::TPR, PPT = H::PPT;
+    const int u = threadIdx.x % TPR;
     const size_t roff = (size_t)row * R2;
     int col[PPT];
 #pragma unroll
@@ -572,11 +589,15 @@ __global__ void __launch_bounds__(HoistGeo<K1, K2>::THREADS)
         const int p = u + TPR * mm;
         col[mm] = G::E * (p % G::T) + p / G::T;
     }
+    // accumulators of both key polynomials: 32-bit products only (F40), else 64 x 64-bit
+    Acc40 f0[PPT], f1[PPT];
     uint32_t a0[PPT][4], a1[PPT][4];
 #pragma unroll
-    for (int mm = 0; mm < PPT; mm++)
+    for (int mm = 0; mm < PPT; mm++) {
+        f0[mm] = f1[mm] = Acc40{0, 0, 0};
 #pragma unroll
         for (int w = 0; w < 4; w++) a0[mm][w] = a1[mm][w] = 0;
+    }
     for (int j = 0; j < hk.n; j++) {
         // an unrolled select: a dynamic index into the parameter arrays would
         // move them into local memory
@@ -596,8 +617,13 @@ __global__ void __launch_bounds__(HoistGeo<K1, K2>::THREADS)
 #pragma unroll
             for (int mm = 0; mm < PPT; mm++) {
                 const uint64_t x = __ldg(src + ps[mm]);
-                mac128(a0[mm], x, ld_stream(k0 + TPR * mm));
-                mac128(a1[mm], x, ld_stream(k1 + TPR * mm));
+                if constexpr (F40) {
+                    mac40(f0[mm], x, ld_stream(k0 + TPR * mm));
+                    mac40(f1[mm], x, ld_stream(k1 + TPR * mm));
+                } else {
+                    mac128(a0[mm], x, ld_stream(k0 + TPR * mm));
+                    mac128(a1[mm], x, ld_stream(k1 + TPR * mm));
+                }
             }
         }
     }
@@ -605,13 +631,39 @@ __global__ void __launch_bounds__(HoistGeo<K1, K2>::THREADS)
     uint64_t *o1 = acc + (((size_t)b * 2 + 1) * (nl + 1) + t) * N + roff;
 #pragma unroll
     for (int mm = 0; mm < PPT; mm++) {
-        uint64_t h0 = ((uint64_t)a0[mm][3] << 32) | a0[mm][2];
-        uint64_t h1 = ((uint64_t)a1[mm][3] << 32) | a1[mm][2];
-        h0 = h0 >= m.q ? reduce64(h0, m) : h0;
-        h1 = h1 >= m.q ? reduce64(h1, m) : h1;
-        o0[col[mm]] = redc128(h0, ((uint64_t)a0[mm][1] << 32) | a0[mm][0], m);
-        o1[col[mm]] = redc128(h1, ((uint64_t)a1[mm][1] << 32) | a1[mm][0], m);
+        if constexpr (F40) {
+            o0[col[mm]] = redc40(f0[mm], m);
+            o1[col[mm]] = redc40(f1[mm], m);
+        } else {
+            uint64_t h0 = ((uint64_t)a0[mm][3] << 32) | a0[mm][2];
+            uint64_t h1 = ((uint64_t)a1[mm][3] << 32) | a1[mm][2];
+            h0 = h0 >= m.q ? reduce64(h0, m) : h0;
+            h1 = h1 >= m.q ? reduce64(h1, m) : h1;
+            o0[col[mm]] = redc128(h0, ((uint64_t)a0[mm][1] << 32) | a0[mm][0], m);
+            o1[col[mm]] = redc128(h1, ((uint64_t)a1[mm][1] << 32) | a1[mm][0], m);
+        }
     }
+}
+
+template <int K1, int K2>
+__global__ void __launch_bounds__(HoistGeo<K1, K2>::THREADS, 3)
+    k_ks_hoist_ip(const uint64_t *__restrict__ mid, const uint64_t *__restrict__ dntt, size_t din_item, HoistKeys hk,
+                  uint64_t *__restrict__ acc, const ModQ *__restrict__ mods, int nl, int nq, int pidx, int items)
+{
+    using H = HoistGeo<K1, K2>;
+    constexpr int R1 = 1 << K1, NG = R1 / H::RPC;
+    int bid = blockIdx.x;
+    const int b = bid % items;
+    bid /= items;
+    const int grp = bid % NG;
+    const int t = bid / NG;  // target 0..nl (nl = P)
+    const int pt = t < nl ? t : pidx, kl = t < nl ? t : nq;
+    const ModQ m = mods[pt];
+    const int row = grp * H::RPC + threadIdx.x / H::TPR;
+    if (m.q < (1ull << 41))  // the same for the whole CTA
+        hoist_ip_body<K1, K2, true>(mid, dntt, din_item, hk, acc, m, nl, nq, b, t, kl, row);
+    else
+        hoist_ip_body<K1, K2, false>(mid, dntt, din_item, hk, acc, m, nl, nq, b, t, kl, row);
 }
 
 template <int K1, int K2>

@@ -293,7 +293,7 @@ def test_errors_are_reported(pair):
         ctx.add(a, b)
     assert e.value.code == binding.HE_ESCALE
     with pytest.raises(binding.HeError) as e:
-        ctx.rotate(a, 5)  # no key for 5
+        ctx.rotate(a, 9)  # no key for 9
     assert e.value.code == binding.HE_EKEY
     low = ctx.moddrop(a, 0)
     with pytest.raises(binding.HeError) as e:
