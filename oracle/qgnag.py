@@ -168,7 +168,7 @@ class Circuit:
     iteration consumes 6 levels and ends at level L - 6.  With first_order=True
     the circuit is the first-order NAG baseline: no Bbar product, depth 5."""
 
-    def __init__(self, he: Ckks, g, m, scale, poly=G8, start_level=None, first_order=False, rot_radix_log=2):
+    def __init__(self, he: Ckks, g, m, scale, poly=G8, start_level=None, first_order=False, rot_radix_log=3):
         self.he, self.g, self.m, self.scale, self.poly = he, g, m, float(scale), poly
         self.first_order = first_order
         self.rho = rot_radix_log
