@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-first-order", action="store_true")
     ap.add_argument("--no-bbar", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default key-switch waves (profiling runs)")
+    ap.add_argument("--rot-radix", type=int, default=0,
+                    help="log2 of the hoisted rotation group (0 = library default)")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     ap.add_argument("--sweep-point", default="", help="log_n,limbs,batch: run only this NTT sweep point")
@@ -153,6 +155,8 @@ def run_ours(args, rank, world):
     t0 = time.time()
     X, y = synth.financial(seed=1, n=args.rows)
     ctx = binding.Context(LOGN, NQ)
+    if args.rot_radix:
+        ctx.set_rotation_radix(args.rot_radix)
     # key-switch wave per level from the library's autotuner (the relinearisation
     # key it times with comes from the same seed the job uses for its keys)
     ta = time.time()

@@ -237,7 +237,7 @@ int he_prof_keyswitches(he_ctx *ctx, double *by_limbs, size_t n);
  * positions: each group sums the rotations by m 2^e (0 < m < 2^r) of one
  * ciphertext with one ModUp and one ModDown (Sec. 2.1 key switching shared by
  * the rotations), so r = 1 is the plain log-step sum.  Sets r for later jobs
- * and iterations of ctx (default 2; 1..3, else HE_EINVAL).  A job must run
+ * and iterations of ctx (default 3; 1..3, else HE_EINVAL).  A job must run
  * with the r it was created with (its rotation keys depend on it). */
 int he_set_rotation_radix(he_ctx *ctx, int log2_radix);
 /* Galois element of a left rotation by r. */

@@ -711,10 +711,12 @@ int helr_rotsum(he_ctx *c, const uint64_t *a, size_t a_item, int batch, int leve
     const int nl = level + 1, nt = nl + 1;
     const size_t N = c->n, lw = (size_t)nl * N;
     if (hk.n < 1 || hk.n > HELR_MAX_HOIST) return helr_fail(c, HE_EINVAL, "%d rotations in one hoisted sum", hk.n);
-    // the summed 128-bit products must not overflow: hk.n * nl terms below q^2
+    // the summed 128-bit products must not overflow: hk.n * nl terms below q^2,
+    // or below 20 q^2 where the digits' row pass leaves its words unreduced
     for (int t = 0; t <= nl; t++) {
         const uint64_t q = t < nl ? c->q[t] : c->q[c->nq];
-        if ((u128)q * q > ~(u128)0 / ((unsigned)hk.n * (unsigned)nl))
+        const unsigned f = (unsigned)hk.n * (unsigned)nl * (q < HELR_LZ_QMAX ? 20u : 1u);
+        if ((u128)q * q > ~(u128)0 / f)
             return helr_fail(c, HE_EINVAL, "%d rotations x %d digits overflow the 128-bit sums", hk.n, nl);
     }
     cudaStream_t s = c->stream;

@@ -221,7 +221,7 @@ struct he_ctx {
     Prof prof;
     int ks_wave = 0;               // items per fused key-switch wave forced by HELR_KS_WAVE (0 = none)
     int ks_wave_tab[HELR_MAXQ + 1] = {};  // wave per limb count chosen by he_autotune (0 = default)
-    int rot_radix_log = 2;         // rotate-and-sum steps as hoisted groups of 2^rot_radix_log positions
+    int rot_radix_log = 3;         // rotate-and-sum steps as hoisted groups of 2^rot_radix_log positions
 };
 
 struct he_ct {

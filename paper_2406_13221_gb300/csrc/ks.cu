@@ -479,8 +479,10 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T)
 
 // Hoisted rotations, step 1: the forward row pass of every lifted digit
 // (column pass already applied by k_ks_modup_cols in ModUp mode), in place in
-// mid[b][i][t] for the targets t != i (t = nl standing for P), words reduced to
-// [0, q_t).  grid: items * nl digits * nl targets * (R1 / RPC).
+// mid[b][i][t] for the targets t != i (t = nl standing for P).  Words are
+// reduced to [0, q_t) for primes of 2^58 and above; below that the unreduced
+// butterflies leave them below 20 q_t.  grid: items * nl digits * nl targets
+// * (R1 / RPC).
 template <int K1, int K2, int RPC>
 __global__ void __launch_bounds__(RPC * Geo<K2>::T)
     k_ks_digit_rows(uint64_t *__restrict__ mid, const uint64_t *__restrict__ twall, const ModQ *__restrict__ mods, int nl,
@@ -508,14 +510,22 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T)
 #pragma unroll
     for (int r = 0; r < E; r++) x[r] = rowp[l + T * r];
     const int A = R1 + row;
-    fwd_strided<K2>(x, tw, A, q, q2);
-    to_contig<K2>(x, seg, l);
-    fwd_contig<K2, true>(x, tw, A, l, q, q2);
+    if (q < HELR_LZ_QMAX) {
+        // unreduced butterflies: the words stay below 20q (< 2^47 for the
+        // 40-bit primes), which the inner product accepts as they are
+        fwd_strided<K2, true>(x, tw, A, q, q2);
+        to_contig<K2>(x, seg, l);
+        fwd_contig<K2, true, true>(x, tw, A, l, q, q2);
+    } else {
+        fwd_strided<K2>(x, tw, A, q, q2);
+        to_contig<K2>(x, seg, l);
+        fwd_contig<K2, true>(x, tw, A, l, q, q2);
 #pragma unroll
-    for (int r = 0; r < E; r++) {
-        uint64_t v = x[r];
-        v = v >= q2 ? v - q2 : v;
-        x[r] = v >= q ? v - q : v;
+        for (int r = 0; r < E; r++) {
+            uint64_t v = x[r];
+            v = v >= q2 ? v - q2 : v;
+            x[r] = v >= q ? v - q : v;
+        }
     }
     __syncthreads();
     to_strided<K2>(x, seg, l);
@@ -534,9 +544,10 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T)
 // digit, which L1 keeps while the row's threads read it.  Keys are in
 // Montgomery form and in the row order of k_key_rows (word E l + r of a row
 // at r T + l): thread u takes key positions u, u + TPR, ..., coalesced, and
-// the columns they stand for.  Sums are exact in 128 bits (words below q,
-// at most HELR_MAX_HOIST * nl terms below q^2: < 2^128 for the chains the
-// context admits) and reduced once.
+// the columns they stand for.  Sums are exact in 128 bits and reduced once:
+// at most HELR_MAX_HOIST * nl terms x k with k < q and x < q (primes of 2^58
+// and above) or x < 20q (below 2^58; helr_rotsum refuses chains where that
+// could reach 2^128).
 // grid: items (fastest: the items of a wave share each key row through L2) *
 // (nl + 1) targets * (R1 / RPC).
 template <int K1, int K2>
@@ -550,7 +561,8 @@ struct HoistGeo {
 // 128-bit sum of products x k for primes below 2^41 (x < 2^47, k < 2^41)
 // without 64 x 64-bit products: with x = xh 2^32 + xl and k = kh 2^32 + kl,
 // A (+ carries cA 2^64) sums xl kl and B sums xl kh + xh kl + xh kh 2^32 (each
-// term < 2^57, so B holds up to 64 terms); T = A + cA 2^64 + B 2^32.
+// term < 2^57, and < 2^55 for x < 20q: B holds the 7 x 39 terms the context
+// admits at most); T = A + cA 2^64 + B 2^32.
 struct Acc40 {
     uint64_t A, B;
     uint32_t cA;
