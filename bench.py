@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     ap.add_argument("--sweep-point", default="", help="log_n,limbs,batch: run only this NTT sweep point")
+    ap.add_argument("--ks-point", default="",
+                    help="level,items,kind (kind relin or rot7): one batched key switch or hoisted rotation sum at "
+                         "N=2^16, the full chain, timed (profiling entry)")
     ap.add_argument("--sweep", action="store_true",
                     help="HE primitive sweep: batched NTT and key switching vs N, limbs and batch (JSON line per point)")
     return ap.parse_args()
@@ -478,6 +481,50 @@ def sweep(args):
             del din, dout
 
 
+def ks_primitive(ctx, level, items, kind, reps=3):
+    """Seconds per call and key switches per second of one batched primitive at
+    N = 2^16: a relinearisation key switch of `items` polynomials (relin) or a
+    hoisted sum of the seven rotations 1..7 of `items` ciphertexts (rot7),
+    uniformly random residues in evaluation form."""
+    import torch
+    n, nl = 1 << LOGN, level + 1
+    if kind == "relin":
+        din = torch.randint(0, 1 << 30, (items * nl * n,), dtype=torch.int64, device="cuda")
+        dout = torch.zeros(items * 2 * nl * n, dtype=torch.int64, device="cuda")
+        call = lambda: ctx.keyswitch_batch(din.data_ptr(), dout.data_ptr(), items, level, 0)  # noqa: E731
+        ks = items
+    else:
+        din = torch.randint(0, 1 << 30, (items * 2 * nl * n,), dtype=torch.int64, device="cuda")
+        dout = torch.zeros_like(din)
+        call = lambda: ctx.rotsum_batch(din.data_ptr(), dout.data_ptr(), items, level, list(range(1, 8)))  # noqa: E731
+        ks = 7 * items
+    call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1000.0 / reps
+    del din, dout
+    return sec, ks / sec
+
+
+def ks_point(args):
+    """One primitive point (profiling entry): prints its JSON line."""
+    from paper_2406_13221_gb300 import binding, build
+    build.build()
+    level, items, kind = args.ks_point.split(",")
+    level, items = int(level), int(items)
+    ctx = binding.Context(LOGN, NQ)
+    ctx.keygen(2, list(range(1, 8)))
+    sec, rate = ks_primitive(ctx, level, items, kind)
+    print(json.dumps({"ks_point": kind, "log_n": LOGN, "limbs": level + 1, "items": items, "s_per_call": round(sec, 6),
+                      "keyswitch_per_s": round(rate, 1)}), flush=True)
+    ctx.close()
+
+
 def ctw_bytes():
     return 2 * (ITER_LEVEL + 1) * (1 << LOGN) * 8
 
@@ -801,6 +848,9 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
+    if args.ks_point:
+        ks_point(args)
+        return
     if args.sweep or args.sweep_point:
         sweep(args)
         return

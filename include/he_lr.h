@@ -173,6 +173,13 @@ int he_ntt_inverse(he_ctx *ctx, uint64_t *d_limbs, size_t n_limbs, const int *pr
  * allocated by the call. */
 int he_keyswitch_batch(he_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int batch, int level,
                        uint64_t gal);
+/* Batched hoisted rotation sums of device ciphertexts (he_rotsum for every
+ * item): d_in and d_out [batch][2][level+1][N] NTT-form words, d_out[b] =
+ * d_in[b] + sum_j Rot(d_in[b], rots[j]) for 1 <= n_rot <= 7 rotations whose
+ * key switches share one ModUp and one ModDown per item.  d_out must not
+ * overlap d_in (HE_EINVAL).  Device scratch is allocated by the call. */
+int he_rotsum_batch(he_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int batch, int level,
+                    const int64_t *rots, size_t n_rot);
 /* Autotuning of the key-switch wave: the number of items whose ModUp and
  * inner product share one DRAM read of each key row (the run-time tile of the
  * fused key switch of Sec. 2.1; scratch [wave][level+1][level+2][N] words).

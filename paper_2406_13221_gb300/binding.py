@@ -100,6 +100,7 @@ SIGNATURES = {
     "he_prof_keyswitches": (_i, [_vp, _vp, _sz]),
     "he_set_rotation_radix": (_i, [_vp, _i]),
     "he_rotsum": (_i, [_vp, _vp, _vp, _sz, _pp]),
+    "he_rotsum_batch": (_i, [_vp, _vp, _vp, _i, _i, _vp, _sz]),
     "he_lr_job_free": (_i, [_vp]),
     "he_lr_multi_create": (_i, [_vp, _vp, _sz, _i, _pp]),
     "he_lr_multi_step": (_i, [_vp, _i, he_lr_sched]),
@@ -290,6 +291,10 @@ class Context:
         if w <= 0:
             self.check(-w)
         return w
+
+    def rotsum_batch(self, din, dout, batch, level, rots):
+        r = np.asarray(rots, np.int64)
+        self.check(self.L.he_rotsum_batch(self.h, din, dout, batch, level, _ptr(r), len(r)))
 
     def keyswitch_batch(self, din, dout, batch, level, gal):
         self.check(self.L.he_keyswitch_batch(self.h, din, dout, batch, level, gal))

@@ -791,6 +791,27 @@ extern "C" int he_keyswitch_batch(he_ctx *c, const uint64_t *d_in, uint64_t *d_o
     return helr_keyswitch(c, d_in, d_out, batch, level, key, nullptr);
 }
 
+extern "C" int he_rotsum_batch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, int level, const int64_t *rots,
+                               size_t n_rot)
+{
+    if (!c || !d_in || !d_out || !rots || batch <= 0 || level < 0 || level >= c->nq || n_rot < 1 ||
+        n_rot > HELR_MAX_HOIST || d_in == d_out)
+        return HE_EINVAL;
+    HoistKeys hk{};
+    hk.n = (int)n_rot;
+    for (size_t j = 0; j < n_rot; j++) {
+        hk.gal[j] = he_galois_elt(c, rots[j]);
+        hk.key[j] = helr_find_key(c, hk.gal[j]);
+        if (!hk.key[j]) return helr_fail(c, HE_EKEY, "no rotation key for %lld", (long long)rots[j]);
+    }
+    const size_t ct = 2 * (size_t)(level + 1) * c->n;
+    KsScratch ws;
+    HELR_TRY(helr_ks_scratch_alloc(c, batch, level, &ws));
+    const int rc = helr_rotsum(c, d_in, ct, batch, level, hk, &ws, Str{d_out, ct, (size_t)(level + 1) * c->n});
+    helr_ks_scratch_free(c, &ws);
+    return rc;
+}
+
 static int limbmap_from(const he_ctx *c, const int *prime_of, int period, LimbMap *m)
 {
     if (!prime_of || period <= 0 || period > HELR_MAXQ + 1) return HE_EINVAL;

@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T)
 // butterflies leave them below 20 q_t.  grid: items * nl digits * nl targets
 // * (R1 / RPC).
 template <int K1, int K2, int RPC>
-__global__ void __launch_bounds__(RPC * Geo<K2>::T)
+__global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
     k_ks_digit_rows(uint64_t *__restrict__ mid, const uint64_t *__restrict__ twall, const ModQ *__restrict__ mods, int nl,
                     int pidx)
 {
