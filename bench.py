@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-multi", action="store_true")
     ap.add_argument("--no-first-order", action="store_true")
     ap.add_argument("--no-bbar", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the compact primitive sweep and the tensor-core floor")
+    ap.add_argument("--no-images", action="store_true", help="skip the MNIST-shaped workload")
     ap.add_argument("--no-autotune", action="store_true", help="default key-switch waves (profiling runs)")
     ap.add_argument("--rot-radix", type=int, default=0,
                     help="log2 of the hoisted rotation group (0 = library default)")
@@ -206,9 +208,8 @@ def run_ours(args, rank, world):
     ks_per_iter = int(st.keyswitches)
     ms_max, sec_iter, rates = replica_rates(ms, args.steps, world,
                                             {"ks": ks_per_iter, "limbs": transform_limbs(prof) / args.steps})
-    err = None
-    if not args.no_twin:
-        err = twin_error(X, y, job, t, sched)
+    # decrypted weights (on the device) for the FP64-twin check of the CPU leg
+    main_w = {"iters": t, "sched": sched, "rows": {r: job.weights(r) for r in (0, 127)}}
     # ---------------- batched vs plain one-ciphertext-per-launch
     plain = None
     if not args.no_plain:
@@ -264,6 +265,19 @@ def run_ours(args, rank, world):
     roof = roofline(prof, ks_prof, ks_by_limbs, args.steps, ms_max / 1000.0 / args.steps, props.multi_processor_count,
                     sm_mhz)
     ntt = standalone_ntt(ctx)
+    psweep = k4 = images = None
+    if not args.no_sweep:
+        psweep = primitive_sweep(ctx)
+        k4 = k4_tensor_floor(ctx)
+    if world == 1 and not args.no_images:
+        images = image_pair_time(ctx, args)
+    # the CPU leg (rank 0 of a single-GPU run): FP64-twin checks of the decrypted weights
+    err = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_twin:
+        err = twin_checks(X, y, main_w, images)
+    elif images:
+        for name in ("full_batch", "mini_batch"):
+            images[name].pop("_w", None)
     out = {
         "metric": METRIC, "value": round(sec_iter, 5), "unit": "s/iter", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": False,
@@ -279,6 +293,9 @@ def run_ours(args, rank, world):
         "keyswitch_hbm_frac": roof["keyswitch_hbm_frac_of_iteration"],
         "ntt_standalone": ntt,
         "ntt_hbm_frac": ntt["hbm_frac"],
+        "primitive_sweep": psweep,
+        "k4_tensor_ntt": k4,
+        "image_pair_g16": images,
         "plain_one_ct_per_launch_s_per_iter": round(plain, 4) if plain else None,
         "mini_batch": mini,
         "multi_job": multi,
@@ -525,6 +542,168 @@ def ks_point(args):
     ctx.close()
 
 
+def k4_tensor_floor(ctx, limbs=64, reps=5):
+    """The tensor pipe's share of an exact four-step NTT at N = 2^16 = 256 x 256,
+    measured against the butterfly transforms of the same limbs.
+
+    Each pass of a four-step NTT multiplies every limb, as a 256 x 256 matrix,
+    by the 256 x 256 DFT matrix modulo q.  With 40-bit words cut into five
+    byte slices the exact product needs the 25 slice-by-slice GEMMs (each sum
+    of 256 products of bytes stays below 2^24, so FP32 accumulation is exact);
+    the twiddle product between the passes and the carry/modular recombination
+    come on top.  The GEMMs alone therefore bound a tensor-core pass from
+    below.  They are timed here with cuBLAS (the measured peak reference) as
+    one GEMM per pass over all limbs: [5*256 x 256] slices of the DFT matrix
+    times [256 x 5*256*limbs] slices of the data, for each exact input type
+    the installed PyTorch offers (INT8 -> INT32, FP16 -> FP32, TF32 -> FP32),
+    after checking one product against an integer matmul.  sm_103a has no
+    INT8 tcgen05.mma (ptxas: ".kind::i8 not supported on .target sm_103a"),
+    so cuBLAS's INT8 rate is whatever the part offers without it."""
+    import torch
+    n = 1 << LOGN
+    side = 256
+    out = {"n": n, "limbs": limbs, "slices_per_word": 5, "slice_gemms_per_pass": 25,
+           "tcgen05_kind_i8_on_sm_103a": "unsupported (ptxas: Feature '.kind::i8' not supported on .target 'sm_103a')"}
+    # butterfly reference: forward + inverse = four passes per limb
+    buf = torch.randint(0, 1 << 30, (limbs * n,), dtype=torch.int64, device="cuda")
+    prime_of = list(range(NQ))
+    for _ in range(2):
+        ctx.ntt_forward(buf.data_ptr(), limbs, prime_of)
+        ctx.ntt_inverse(buf.data_ptr(), limbs, prime_of)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        ctx.ntt_forward(buf.data_ptr(), limbs, prime_of)
+        ctx.ntt_inverse(buf.data_ptr(), limbs, prime_of)
+    e1.record()
+    torch.cuda.synchronize()
+    bfly_pass_us = e0.elapsed_time(e1) * 1000.0 / (reps * 4 * limbs)
+    out["butterfly_us_per_limb_pass"] = round(bfly_pass_us, 4)
+    del buf
+    g = torch.Generator(device="cuda").manual_seed(5)
+    M, K, Ncols = 5 * side, side, 5 * side * limbs
+    flops = 2.0 * M * K * Ncols
+    candidates = []
+    if hasattr(torch, "_int_mm"):
+        candidates.append(("int8_to_int32", lambda a, b: torch._int_mm(a, b), torch.int8, -128, 128))
+    try:
+        a = torch.ones(16, 16, dtype=torch.float16, device="cuda")
+        torch.mm(a, a, out_dtype=torch.float32)
+        candidates.append(("fp16_to_fp32", lambda a, b: torch.mm(a, b, out_dtype=torch.float32), torch.float16, 0, 256))
+    except (TypeError, RuntimeError):
+        out["fp16_to_fp32"] = "torch.mm has no out_dtype in this PyTorch"
+    candidates.append(("tf32_to_fp32", None, torch.float32, 0, 256))
+    for name, fn, dt, lo, hi in candidates:
+        A = torch.randint(lo, hi, (M, K), generator=g, device="cuda", dtype=torch.int32)
+        B = torch.randint(lo, hi, (K, Ncols), generator=g, device="cuda", dtype=torch.int32)
+        Ad, Bd = A.to(dt), B.to(dt)
+        if fn is None:
+            prev = torch.backends.cuda.matmul.allow_tf32
+            torch.backends.cuda.matmul.allow_tf32 = True
+            fn = lambda a, b: torch.mm(a, b)  # noqa: E731
+        try:
+            C = fn(Ad, Bd)
+            torch.cuda.synchronize()
+            cols = slice(0, 512)
+            ref = A.cpu().numpy().astype(np.int64) @ B[:, cols].cpu().numpy().astype(np.int64)
+            exact = bool(np.array_equal(C[:, cols].double().cpu().numpy().astype(np.int64), ref))
+            for _ in range(2):
+                fn(Ad, Bd)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                fn(Ad, Bd)
+            e1.record()
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1000.0 / reps
+            out[name] = {"exact": exact, "tops": round(flops / sec / 1e12, 1),
+                         "gemm_us_per_limb_pass": round(sec * 1e6 / limbs, 4),
+                         "vs_butterfly_pass": round(sec * 1e6 / limbs / bfly_pass_us, 2)}
+        except RuntimeError as e:
+            out[name] = "unavailable: %s" % str(e).splitlines()[0][:120]
+        finally:
+            if name == "tf32_to_fp32":
+                torch.backends.cuda.matmul.allow_tf32 = prev
+        del A, B, Ad, Bd
+    return out
+
+
+def primitive_sweep(ctx):
+    """A compact HE primitive sweep (N = 2^14..2^16 transforms, key switching
+    and hoisted rotation sums at two limb counts), each point with its HBM
+    fraction at the algorithmic bytes of the survey's measurement table: a
+    transform of one limb reads and writes it once (16N bytes); a key switch
+    at L limbs reads its input and writes two polynomials (3L limbs) and reads
+    its 2L(L+1) key limbs once per call; a hoisted sum of r rotations reads
+    and writes its ciphertext once and r keys."""
+    import torch
+    from paper_2406_13221_gb300 import binding
+    hbm = float(measured_peaks().get("hbm_gbs", 6800.0))
+    out = {"ntt": [], "keyswitch": []}
+    for logn in (14, 15, 16):
+        n = 1 << logn
+        c = ctx if logn == LOGN else binding.Context(logn, 8)
+        limbs = 512  # 64 ciphertexts of 8 limbs
+        buf = torch.randint(0, 1 << 30, (limbs * n,), dtype=torch.int64, device="cuda")
+        prime_of = list(range(8))
+        for _ in range(2):
+            c.ntt_forward(buf.data_ptr(), limbs, prime_of)
+            c.ntt_inverse(buf.data_ptr(), limbs, prime_of)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 4
+        e0.record()
+        for _ in range(reps):
+            c.ntt_forward(buf.data_ptr(), limbs, prime_of)
+            c.ntt_inverse(buf.data_ptr(), limbs, prime_of)
+        e1.record()
+        torch.cuda.synchronize()
+        rate = 2 * reps * limbs / (e0.elapsed_time(e1) / 1000.0)
+        out["ntt"].append({"log_n": logn, "limbs_per_launch": limbs, "ntt_limbs_per_s": round(rate, 1),
+                           "hbm_frac": round(rate * 16 * n / 1e9 / hbm, 4)})
+        del buf
+        if c is not ctx:
+            c.close()
+    n = 1 << LOGN
+    for kind, level in (("relin", 6), ("relin", 3), ("rot7", 5), ("rot7", 3)):
+        items, nl = 128, level + 1
+        sec, rate = ks_primitive(ctx, level, items, kind)
+        r = 1 if kind == "relin" else 7
+        alg = (3.0 * nl * items + r * 2.0 * nl * (nl + 1)) * 8 * n  # per call
+        out["keyswitch"].append({"kind": kind, "log_n": LOGN, "limbs": nl, "items": items,
+                                 "keyswitch_per_s": round(rate, 1), "hbm_frac": round(alg / sec / 1e9 / hbm, 4)})
+    return out
+
+
+def image_pair_time(ctx, args):
+    """The MNIST-shaped workload (Sec. 5.2, Table 2: 11,982 x 196, sigmoid
+    polynomial g16) on synthetic images: full batch and mini-batch (1,024
+    samples) seconds per iteration over 2 iterations after one warm-up, and
+    the decrypted weights against the FP64 twin."""
+    import torch
+    from paper_2406_13221_gb300 import binding, synth
+    X, y = synth.image_pair()
+    out = {"workload": "11,982 x 196 synthetic two-class images, g16, N=2^16, 128 x 256 packing"}
+    for mode, name, sched in ((binding.FULL_BATCH, "full_batch", (2.0, 1.0, 81.0, 2.5)),
+                              (binding.MINI_BATCH, "mini_batch", (1.0, 0.1, 81.0, 2.5))):
+        job = binding.Job(ctx, X, y, mode, 1024, binding.G16, LOG_SCALE, enc_seed=21, key_seed=2)
+        job.step(0, sched)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for t in (1, 2):
+            job.step(t, sched)
+        e1.record()
+        torch.cuda.synchronize()
+        res = {"s_per_iter": round(e0.elapsed_time(e1) / 2 / 1000.0, 5), "blocks": int(job.stats().n_blocks),
+               "keyswitches_per_iter": int(job.stats().keyswitches)}
+        res["_w"] = (job.weights(0), "full" if mode == binding.FULL_BATCH else "mini", sched)
+        out[name] = res
+        job.close()
+    return out
+
+
 def ctw_bytes():
     return 2 * (ITER_LEVEL + 1) * (1 << LOGN) * 8
 
@@ -678,12 +857,23 @@ def standalone_ntt(ctx, limbs=256, reps=10):
             "hbm_frac": round(rate * 16 * n / 1e9 / hbm, 4)}
 
 
-def twin_error(X, y, job, iters, sched):
-    """Decrypted W (rows 0 and m-1) against the FP64 plaintext run of the same iterations."""
+def twin_checks(X, y, main_w, images):
+    """Part of the CPU leg: the decrypted weights the GPU jobs produced (rows 0
+    and m-1 of the full-batch job; row 0 of each MNIST-shaped job) against the
+    FP64 plaintext run of the same iterations (oracle/plain.py); fills in the
+    image jobs' errors and returns the full-batch job's."""
     from oracle import plain, qgnag
     data = qgnag.TrainData(X, y, g=256, m=128, batch_rows=1024)
-    wp = plain.train(data, iters, sched=sched)
-    err = max(float(np.abs(job.weights(r) - wp).max()) for r in (0, 127))
+    wp = plain.train(data, main_w["iters"], sched=main_w["sched"])
+    err = max(float(np.abs(w - wp).max()) for w in main_w["rows"].values())
+    if images:
+        from paper_2406_13221_gb300 import synth
+        Xi, yi = synth.image_pair()
+        di = qgnag.TrainData(Xi, yi, g=256, m=128, batch_rows=1024)
+        for name in ("full_batch", "mini_batch"):
+            w, mode, sched = images[name].pop("_w")
+            wpi = plain.train(di, 3, mode=mode, sched=sched, poly=qgnag.G16)
+            images[name]["max_abs_err_vs_fp64_twin"] = float(np.abs(w - wpi).max())
     return err
 
 

@@ -12,6 +12,12 @@ shared by the tests, the benchmark and the CPU reference.
   weights ~ N(0, 1) plus a N(0, 1) bias.
 * ``job``       -- one job of the uneven multi-job workload: n samples, f
   features, generated like ``financial`` (three quarters Gaussian columns).
+* ``image_pair`` -- stands in for the paper's restructured MNIST task
+  (Sec. 5.2: 11,982 training images of two digit classes, 14 x 14 = 196
+  pixel features): two smooth random class templates on a 14 x 14 grid,
+  each sample its class template shifted by up to one pixel, scaled by a
+  random stroke intensity, plus Gaussian pixel noise, clipped to [0, 1] and
+  min-max scaled to [-1, 1]; labels +/-1 by class, classes balanced.
 """
 import numpy as np
 
@@ -54,6 +60,26 @@ def job(seed, n, f, n_gauss=None, nnz=20):
 
 def financial(seed=1, n=422108, f=200):
     return job(seed, n, f, n_gauss=150, nnz=20)
+
+
+def image_pair(seed=7, n=11982, side=14, noise=0.15):
+    rng = np.random.default_rng(seed)
+    yy, xx = np.mgrid[0:side, 0:side] / (side - 1.0)
+    templates = []
+    for _ in range(2):
+        t = np.zeros((side, side))
+        for _ in range(6):  # a few Gaussian strokes per class
+            cy, cx = rng.uniform(0.2, 0.8, 2)
+            sy, sx = rng.uniform(0.05, 0.2, 2)
+            t += np.exp(-((yy - cy) ** 2 / (2 * sy * sy) + (xx - cx) ** 2 / (2 * sx * sx)))
+        templates.append(t / t.max())
+    cls = rng.permutation(np.arange(n) % 2)
+    X = np.empty((n, side * side))
+    for k in range(n):
+        img = np.roll(templates[cls[k]], tuple(rng.integers(-1, 2, 2)), axis=(0, 1))
+        img = img * rng.uniform(0.7, 1.0) + noise * rng.standard_normal((side, side))
+        X[k] = np.clip(img, 0.0, 1.0).ravel()
+    return _scale_cols(X), np.where(cls == 1, 1.0, -1.0)
 
 
 def multijob_shapes(seed=5, njobs=16, lo=5000, hi=100000):
