@@ -167,7 +167,8 @@ def run_ours(args, rank, world):
     ta = time.time()
     ctx.keygen(2)
     tuned_levels = 0 if args.no_autotune else ctx.autotune(None, 256)
-    autotune = {"ks_wave_by_level": [ctx.ks_wave(lv) for lv in range(NQ)], "levels_measured": tuned_levels,
+    autotune = {"ks_wave_by_level": [ctx.ks_wave(lv) for lv in range(NQ)],
+                "ks_tile_by_level": [ctx.ks_tile(lv) for lv in range(NQ)], "levels_measured": tuned_levels,
                 "s": round(time.time() - ta, 2)}
     job = binding.Job(ctx, X, y, binding.FULL_BATCH, 1024, binding.G8, LOG_SCALE, enc_seed=3, key_seed=2,
                       batch_blocks=args.chunk)

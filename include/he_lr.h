@@ -180,13 +180,19 @@ int he_keyswitch_batch(he_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int b
  * overlap d_in (HE_EINVAL).  Device scratch is allocated by the call. */
 int he_rotsum_batch(he_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int batch, int level,
                     const int64_t *rots, size_t n_rot);
-/* Autotuning of the key-switch wave: the number of items whose ModUp and
- * inner product share one DRAM read of each key row (the run-time tile of the
- * fused key switch of Sec. 2.1; scratch [wave][level+1][level+2][N] words).
- * For every level it times `items` batched relinearisations (16 or more;
- * 0 = 256) with waves of 16, 32, 64, 128 and 256 items (those <= items) on the
- * context stream and keeps the smallest wave within 1% of the fastest; later
- * key switches of this context use it.
+/* Autotuning of the key switch (Sec. 2.1; the relinearisation inside every
+ * Mul and the key switch inside every rotation): per level it picks
+ *  - the wave: the number of items whose ModUp and inner product share one
+ *    DRAM read of each key row (scratch [wave][level+1][level+2][N] words),
+ *    timing `items` batched relinearisations (16 or more; 0 = 256) with waves
+ *    of 16, 32, 64, 128 and 256 items (those <= items) and keeping the
+ *    smallest wave within 1% of the fastest;
+ *  - the tile variant of the kernels at that wave: bit 0 halves the columns
+ *    per CTA of the ModUp/ModDown column kernel, bit 1 halves the rows per
+ *    CTA of the ModDown and hoisted-digit row kernels; a variant other than 0
+ *    is kept only when it is more than 1% faster.
+ * Later key switches of this context use the choices; results do not depend
+ * on them (the words are the same for every wave and tile).
  * table_path (may be NULL): a text table keyed by device, SM count, log N,
  * n_q and the primes; levels it already holds are loaded instead of measured,
  * and the file is rewritten when anything was measured.  *measured (may be
@@ -194,10 +200,15 @@ int he_rotsum_batch(he_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int batc
  * (HE_EKEY); device memory for the largest wave is allocated and freed by the
  * call (a wave that does not fit is skipped); HE_EINVAL when the table cannot
  * be written.  The environment variable HELR_KS_WAVE, when set, overrides
- * every table. */
+ * every wave. */
 int he_autotune(he_ctx *ctx, const char *table_path, int items, int *measured);
 /* The wave key switches at `level` use (> 0), or -HE_EINVAL. */
 int he_ks_wave(const he_ctx *ctx, int level);
+/* The tile variant key switches at `level` use (0..3), or -HE_EINVAL. */
+int he_ks_tile(const he_ctx *ctx, int level);
+/* Force the tile variant of every later key switch (0..3), or return to the
+ * autotuned choice (-1); HE_EINVAL otherwise. */
+int he_set_ks_tile(he_ctx *ctx, int tile);
 /* Rescale without allocating (no counterpart in the paper: it exists for
  * callers that may not allocate device memory, such as code running under a
  * device-memory budget fixed in advance or inside a framework that owns every

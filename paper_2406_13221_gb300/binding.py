@@ -101,6 +101,8 @@ SIGNATURES = {
     "he_set_rotation_radix": (_i, [_vp, _i]),
     "he_rotsum": (_i, [_vp, _vp, _vp, _sz, _pp]),
     "he_rotsum_batch": (_i, [_vp, _vp, _vp, _i, _i, _vp, _sz]),
+    "he_ks_tile": (_i, [_vp, _i]),
+    "he_set_ks_tile": (_i, [_vp, _i]),
     "he_lr_job_free": (_i, [_vp]),
     "he_lr_multi_create": (_i, [_vp, _vp, _sz, _i, _pp]),
     "he_lr_multi_step": (_i, [_vp, _i, he_lr_sched]),
@@ -285,6 +287,15 @@ class Context:
         n = ctypes.c_int()
         self.check(self.L.he_autotune(self.h, None if path is None else os.fsencode(path), int(items), ctypes.byref(n)))
         return n.value
+
+    def ks_tile(self, level):
+        v = self.L.he_ks_tile(self.h, level)
+        if v < 0:
+            raise HeError(-v, "he_ks_tile")
+        return v
+
+    def set_ks_tile(self, tile):
+        self.check(self.L.he_set_ks_tile(self.h, int(tile)))
 
     def ks_wave(self, level):
         w = self.L.he_ks_wave(self.h, int(level))

@@ -1,21 +1,27 @@
-// autotune.cu -- choice of the key-switch wave per (N, limbs), measured on the
-// device and kept in a table file.
+// autotune.cu -- choice of the key-switch wave and kernel tiles per (N, limbs),
+// measured on the device and kept in a table file.
 //
 // Hybrid key switching (Sec. 2.1: the relinearisation inside Mul and the key
 // switch inside every rotation) runs its ModUp and inner product in waves of
 // items that share one DRAM read of each key row.  The wave is the one tile of
 // the fused path that is chosen at run time: a larger wave amortises the key
 // read over more items but needs [wave][nl][nl+1][N] words of scratch and a
-// larger L2 footprint per key row.  The transform tiles themselves (16 words
-// per thread, 8 rows or 16 columns per CTA) are compile-time shapes.
+// larger L2 footprint per key row.  The kernel tiles come in four variants
+// (tile bit 0: the column kernel of ModUp and ModDown with half as many
+// columns per CTA; bit 1: the row kernels of ModDown and of the hoisted
+// digits with half as many rows per CTA); the words per thread of a pass
+// (2^ceil(K/2) of a row or column of 2^K words) are fixed by the transform's
+// register layout.
 //
-// he_autotune times batched key switches for every wave candidate at every
-// limb count nl = 1..n_q and keeps the smallest wave within 1% of the fastest;
-// helr_ks_wave consults the result.  The table file holds one header line naming the device and the
+// he_autotune times batched key switches at every limb count nl = 1..n_q:
+// first every wave candidate with tile 0, keeping the smallest wave within 1%
+// of the fastest, then the other tiles at that wave, keeping a variant only
+// when it beats tile 0 by more than 1%; helr_ks_wave and helr_ks_tile consult
+// the result.  The table file holds one header line naming the device and the
 // parameters, then one line per limb count:
-//     he_lr ks-wave table v1
+//     he_lr ks-wave table v2
 //     key <device> <SMs> <log N> <n_q> <hash of the primes>
-//     nl <nl> wave <items> us_per_keyswitch <time>
+//     nl <nl> wave <items> tile <variant> us_per_keyswitch <time>
 // A file whose header names another device or parameter set is measured anew
 // and overwritten.
 #include <stdio.h>
@@ -29,6 +35,7 @@
 namespace {
 
 constexpr int kWaves[] = {16, 32, 64, 128, 256};
+constexpr int kTiles = 4;
 
 // uniform words below q_j for limb j of every item (the values only need to be
 // valid residues; their distribution does not change the work)
@@ -73,38 +80,39 @@ TuneKey key_of(const he_ctx *c)
 }
 
 // entries of a table file whose header matches `k` (tab[nl] = wave, 0 = none)
-bool load_table(const char *path, const TuneKey &k, int *tab, double *us)
+bool load_table(const char *path, const TuneKey &k, int *tab, int *tiles, double *us)
 {
     FILE *f = fopen(path, "r");
     if (!f) return false;
     char line[512], dev[256];
-    int sms, logn, nq, nl, wave;
+    int sms, logn, nq, nl, wave, tile;
     unsigned long long qh;
     double t;
-    bool ok = fgets(line, sizeof line, f) && strncmp(line, "he_lr ks-wave table v1", 22) == 0 &&
+    bool ok = fgets(line, sizeof line, f) && strncmp(line, "he_lr ks-wave table v2", 22) == 0 &&
               fgets(line, sizeof line, f) &&
               sscanf(line, "key %255s %d %d %d %llx", dev, &sms, &logn, &nq, &qh) == 5 && strcmp(dev, k.dev) == 0 &&
               sms == k.sms && logn == k.logn && nq == k.nq && qh == k.qhash;
     while (ok && fgets(line, sizeof line, f))
-        if (sscanf(line, "nl %d wave %d us_per_keyswitch %lf", &nl, &wave, &t) == 3 && nl >= 1 && nl <= k.nq &&
-            wave > 0)
-            tab[nl] = wave, us[nl] = t;
+        if (sscanf(line, "nl %d wave %d tile %d us_per_keyswitch %lf", &nl, &wave, &tile, &t) == 4 && nl >= 1 &&
+            nl <= k.nq && wave > 0 && tile >= 0 && tile < kTiles)
+            tab[nl] = wave, tiles[nl] = tile, us[nl] = t;
     fclose(f);
     return ok;
 }
 
-bool save_table(const char *path, const TuneKey &k, const int *tab, const double *us)
+bool save_table(const char *path, const TuneKey &k, const int *tab, const int *tiles, const double *us)
 {
     FILE *f = fopen(path, "w");
     if (!f) return false;
-    fprintf(f, "he_lr ks-wave table v1\nkey %s %d %d %d %llx\n", k.dev, k.sms, k.logn, k.nq, k.qhash);
+    fprintf(f, "he_lr ks-wave table v2\nkey %s %d %d %d %llx\n", k.dev, k.sms, k.logn, k.nq, k.qhash);
     for (int nl = 1; nl <= k.nq; nl++)
-        if (tab[nl] > 0) fprintf(f, "nl %d wave %d us_per_keyswitch %.3f\n", nl, tab[nl], us[nl]);
+        if (tab[nl] > 0) fprintf(f, "nl %d wave %d tile %d us_per_keyswitch %.3f\n", nl, tab[nl], tiles[nl], us[nl]);
     return fclose(f) == 0;
 }
 
-// fastest wave for key switches of `items` inputs at nl limbs; *us = time per key switch
-int measure(he_ctx *c, const uint64_t *key, int items, int nl, int *best, double *us)
+// fastest wave, then fastest tile variant, for key switches of `items` inputs
+// at nl limbs; *us = time per key switch
+int measure(he_ctx *c, const uint64_t *key, int items, int nl, int *best, int *best_tile, double *us)
 {
     const size_t N = c->n;
     int maxw = 0;
@@ -116,7 +124,7 @@ int measure(he_ctx *c, const uint64_t *key, int items, int nl, int *best, double
     KsScratch ws{};
     ws.base = nullptr;
     // scratch sized for the largest candidate that fits
-    const int saved = c->ks_wave;
+    const int saved = c->ks_wave, saved_tile = c->ks_tile;
     while (rc == HE_OK) {
         c->ks_wave = maxw;
         rc = helr_ks_scratch_alloc(c, items, nl - 1, &ws);
@@ -134,31 +142,44 @@ int measure(he_ctx *c, const uint64_t *key, int items, int nl, int *best, double
             din, nw, c->logn, nl, c->t.mod, 0x5eedull + nl);
         if (cudaGetLastError() != cudaSuccess) rc = helr_fail(c, HE_ECUDA, "fill kernel launch failed");
     }
-    double msw[sizeof kWaves / sizeof kWaves[0]] = {};
-    int nw = 0;
-    for (int w : kWaves) {
-        if (rc != HE_OK || w > maxw) break;
+    // one warm-up, then the faster of two timed runs
+    auto time_ks = [&](int w, int tile, double *ms) {
         ws.wave = w;
-        double ms = 0;
-        for (int r = 0; r < 3 && rc == HE_OK; r++) {  // one warm-up, then the faster of two timed runs
+        c->ks_tile = tile;
+        for (int r = 0; r < 3 && rc == HE_OK; r++) {
             if (cudaEventRecord(e0, c->stream) != cudaSuccess) rc = helr_fail(c, HE_ECUDA, "event record failed");
             if (rc == HE_OK) rc = helr_keyswitch(c, din, dout, items, nl - 1, key, &ws, nullptr);
             float t = 0;
             if (rc == HE_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                                 cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
                 rc = helr_fail(c, HE_ECUDA, "event timing failed");
-            if (r == 1 || (r == 2 && t < ms)) ms = t;
+            if (r == 1 || (r == 2 && t < *ms)) *ms = t;
         }
+        c->ks_tile = saved_tile;
+    };
+    double msw[sizeof kWaves / sizeof kWaves[0]] = {};
+    int nw = 0;
+    for (int w : kWaves) {
+        if (rc != HE_OK || w > maxw) break;
+        double ms = 0;
+        time_ks(w, 0, &ms);
         if (rc == HE_OK) msw[nw++] = ms;
     }
     // the smallest wave within 1% of the fastest: less scratch, and timing noise
     // does not flip the choice between near-equal waves
     double best_ms = 0;
     *best = 0;
+    *best_tile = 0;
     for (int i = 0; i < nw; i++)
         if (i == 0 || msw[i] < best_ms) best_ms = msw[i];
     for (int i = 0; i < nw && !*best; i++)
         if (msw[i] <= 1.01 * best_ms) *best = kWaves[i], best_ms = msw[i];
+    // the other tile variants at that wave: kept only when more than 1% faster
+    for (int tile = 1; tile < kTiles && rc == HE_OK && *best; tile++) {
+        double ms = 0;
+        time_ks(*best, tile, &ms);
+        if (rc == HE_OK && ms < best_ms / 1.01) *best_tile = tile, best_ms = ms;
+    }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (ws.base) helr_ks_scratch_free(c, &ws);
@@ -180,6 +201,13 @@ int helr_ks_wave(const he_ctx *c, int nl)
     return 128;
 }
 
+int helr_ks_tile(const he_ctx *c, int nl)
+{
+    if (c->ks_tile >= 0) return c->ks_tile;
+    if (nl >= 1 && nl <= HELR_MAXQ) return c->ks_tile_tab[nl];
+    return 0;
+}
+
 extern "C" int he_autotune(he_ctx *c, const char *path, int items, int *measured)
 {
     if (!c || items < 0 || (items > 0 && items < kWaves[0])) return HE_EINVAL;
@@ -187,17 +215,17 @@ extern "C" int he_autotune(he_ctx *c, const char *path, int items, int *measured
     const uint64_t *key = helr_find_key(c, 0);
     if (!key) return helr_fail(c, HE_EKEY, "autotuning needs the relinearisation key (he_keygen first)");
     const TuneKey k = key_of(c);
-    int tab[HELR_MAXQ + 1] = {};
+    int tab[HELR_MAXQ + 1] = {}, tiles[HELR_MAXQ + 1] = {};
     double us[HELR_MAXQ + 1] = {};
-    if (path) load_table(path, k, tab, us);
+    if (path) load_table(path, k, tab, tiles, us);
     int n = 0;
     for (int nl = 1; nl <= c->nq; nl++) {
         if (tab[nl] > 0) continue;
-        HELR_TRY(measure(c, key, items, nl, &tab[nl], &us[nl]));
+        HELR_TRY(measure(c, key, items, nl, &tab[nl], &tiles[nl], &us[nl]));
         n++;
     }
-    for (int nl = 1; nl <= c->nq; nl++) c->ks_wave_tab[nl] = tab[nl];
-    if (path && n && !save_table(path, k, tab, us)) return helr_fail(c, HE_EINVAL, "cannot write %s", path);
+    for (int nl = 1; nl <= c->nq; nl++) c->ks_wave_tab[nl] = tab[nl], c->ks_tile_tab[nl] = tiles[nl];
+    if (path && n && !save_table(path, k, tab, tiles, us)) return helr_fail(c, HE_EINVAL, "cannot write %s", path);
     if (measured) *measured = n;
     return HE_OK;
 }
@@ -206,4 +234,18 @@ extern "C" int he_ks_wave(const he_ctx *c, int level)
 {
     if (!c || level < 0 || level >= c->nq) return -HE_EINVAL;
     return helr_ks_wave(c, level + 1);
+}
+
+extern "C" int he_ks_tile(const he_ctx *c, int level)
+{
+    if (!c || level < 0 || level >= c->nq) return -HE_EINVAL;
+    return helr_ks_tile(c, level + 1);
+}
+
+extern "C" int he_set_ks_tile(he_ctx *c, int tile)
+{
+    if (!c || tile < -1 || tile >= kTiles) return c ? helr_fail(c, HE_EINVAL, "tile variant %d (0..3, -1 = tuned)", tile)
+                                                     : HE_EINVAL;
+    c->ks_tile = tile;
+    return HE_OK;
 }

@@ -221,6 +221,8 @@ struct he_ctx {
     Prof prof;
     int ks_wave = 0;               // items per fused key-switch wave forced by HELR_KS_WAVE (0 = none)
     int ks_wave_tab[HELR_MAXQ + 1] = {};  // wave per limb count chosen by he_autotune (0 = default)
+    int ks_tile = -1;              // tile variant forced by he_set_ks_tile (-1 = none)
+    int ks_tile_tab[HELR_MAXQ + 1] = {};  // tile variant per limb count chosen by he_autotune
     int rot_radix_log = 3;         // rotate-and-sum steps as hoisted groups of 2^rot_radix_log positions
 };
 
@@ -339,6 +341,10 @@ int helr_ks_fused(he_ctx *c, const uint64_t *dntt, const uint64_t *drow, uint64_
 // items per fused key-switch wave at nl limbs: HELR_KS_WAVE, else the
 // he_autotune table, else 128 (autotune.cu)
 int helr_ks_wave(const he_ctx *c, int nl);
+// tile variant of the key-switch kernels at nl limbs (bit 0: narrower column
+// CTAs, bit 1: fewer rows per row CTA): he_set_ks_tile, else the he_autotune
+// table, else 0 (autotune.cu)
+int helr_ks_tile(const he_ctx *c, int nl);
 int helr_ks_scratch_alloc(he_ctx *c, int batch, int level, KsScratch *ws);
 void helr_ks_scratch_free(he_ctx *c, KsScratch *ws);
 // Output stage of a key switch (ModDown combined with the operation around it):

@@ -685,8 +685,15 @@ struct KsPlan {
     static constexpr int C = (256 / T1) < R2 ? (256 / T1) : R2;
     static constexpr int RPC = (128 / T2) < R1 ? (128 / T2) : R1;
     static constexpr int RPCD = (256 / T2) < R1 ? (256 / T2) : R1;
-    static constexpr size_t SMD = (size_t)RPCD * Geo<K2>::SEG * 8;
-    static constexpr size_t SM1 = (size_t)C * Geo<K1>::SEG * 8 + (size_t)C * R1 * 8;
+    // tile variants chosen per limb count by he_autotune (tile bit 0: half as
+    // many columns per CTA in the column kernel; bit 1: half as many rows per
+    // CTA in the row kernels of ModDown and of the hoisted digits)
+    static constexpr int CB = C / 2 > 0 ? C / 2 : 1;
+    static constexpr int RB = RPCD / 2 > 0 ? RPCD / 2 : 1;
+    static constexpr size_t smd(int rr) { return (size_t)rr * Geo<K2>::SEG * 8; }
+    static constexpr size_t sm1(int cc) { return (size_t)cc * Geo<K1>::SEG * 8 + (size_t)cc * R1 * 8; }
+    static constexpr size_t SMD = smd(RPCD);
+    static constexpr size_t SM1 = sm1(C);
     // one digit's rows, the row twiddle pairs, the TMEM address slot
     static constexpr size_t SM2 = (size_t)RPC * R2 * 8 + (size_t)RPC * R2 * 16 + 16;
     static cudaError_t prepare()
@@ -698,14 +705,30 @@ struct KsPlan {
         if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_down_rows<K1, K2, RPCD>, RPCD * T2, SMD);
         if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_digit_rows<K1, K2, RPCD>, RPCD * T2, SMD);
         if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_hoist_ip<K1, K2>, HoistGeo<K1, K2>::THREADS, 0);
+        if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_modup_cols<K1, K2, CB, false>, CB * T1, sm1(CB));
+        if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_modup_cols<K1, K2, CB, true>, CB * T1, sm1(CB));
+        if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_down_rows<K1, K2, RB>, RB * T2, smd(RB));
+        if (e == cudaSuccess) e = helr_fit_carveout((const void *)k_ks_digit_rows<K1, K2, RB>, RB * T2, smd(RB));
         return e;
+    }
+    template <int CC, bool DOWN>
+    static void cols(he_ctx *c, const uint64_t *drow, uint64_t *out, size_t nsrc, int nl, int src_prime, cudaStream_t s)
+    {
+        const unsigned grid = (unsigned)(nsrc * (R2 / CC));
+        HELR_LAUNCH(k_ks_modup_cols<K1, K2, CC, DOWN><<<grid, CC * T1, sm1(CC), s>>>(drow, out, c->t.tw, c->t.itw, c->t.mod,
+                                                                                      c->t.ninv, nl, c->nq, src_prime));
     }
     // hoisted rotations: row passes of the lifted digits, then the summed inner products
     static void hoisted(he_ctx *c, const uint64_t *dntt, size_t din_item, uint64_t *mid, const HoistKeys &hk, uint64_t *acc,
                         int items, int nl, cudaStream_t s)
     {
-        const unsigned g1 = (unsigned)((size_t)items * nl * nl * (R1 / RPCD));
-        HELR_LAUNCH(k_ks_digit_rows<K1, K2, RPCD><<<g1, RPCD * T2, SMD, s>>>(mid, c->t.tw, c->t.mod, nl, c->nq));
+        if (helr_ks_tile(c, nl) & 2) {
+            const unsigned g1 = (unsigned)((size_t)items * nl * nl * (R1 / RB));
+            HELR_LAUNCH(k_ks_digit_rows<K1, K2, RB><<<g1, RB * T2, smd(RB), s>>>(mid, c->t.tw, c->t.mod, nl, c->nq));
+        } else {
+            const unsigned g1 = (unsigned)((size_t)items * nl * nl * (R1 / RPCD));
+            HELR_LAUNCH(k_ks_digit_rows<K1, K2, RPCD><<<g1, RPCD * T2, SMD, s>>>(mid, c->t.tw, c->t.mod, nl, c->nq));
+        }
         using H = HoistGeo<K1, K2>;
         const unsigned g2 = (unsigned)((size_t)items * (nl + 1) * (R1 / H::RPC));
         HELR_LAUNCH(k_ks_hoist_ip<K1, K2><<<g2, H::THREADS, 0, s>>>(mid, dntt, din_item, hk, acc, c->t.mod, nl, c->nq, c->nq,
@@ -714,15 +737,22 @@ struct KsPlan {
     static void down(he_ctx *c, const KsOut &o, const uint64_t *src, size_t src_item, size_t src_poly, const uint64_t *lift,
                      int items, int nl, const uint64_t *inv, cudaStream_t s)
     {
-        const unsigned grid = (unsigned)((size_t)items * 2 * nl * (R1 / RPCD));
-        HELR_LAUNCH(k_ks_down_rows<K1, K2, RPCD><<<grid, RPCD * T2, SMD, s>>>(o, src, src_item, src_poly, lift, c->t.tw,
-                                                                              c->t.mod, inv, nl));
+        if (helr_ks_tile(c, nl) & 2) {
+            const unsigned grid = (unsigned)((size_t)items * 2 * nl * (R1 / RB));
+            HELR_LAUNCH(k_ks_down_rows<K1, K2, RB><<<grid, RB * T2, smd(RB), s>>>(o, src, src_item, src_poly, lift, c->t.tw,
+                                                                                  c->t.mod, inv, nl));
+        } else {
+            const unsigned grid = (unsigned)((size_t)items * 2 * nl * (R1 / RPCD));
+            HELR_LAUNCH(k_ks_down_rows<K1, K2, RPCD><<<grid, RPCD * T2, SMD, s>>>(o, src, src_item, src_poly, lift, c->t.tw,
+                                                                                  c->t.mod, inv, nl));
+        }
     }
     static void down_cols(he_ctx *c, const uint64_t *drow, size_t nsrc, int src_prime, uint64_t *out, int nl, cudaStream_t s)
     {
-        const unsigned grid = (unsigned)(nsrc * (R2 / C));
-        HELR_LAUNCH(k_ks_modup_cols<K1, K2, C, true><<<grid, C * T1, SM1, s>>>(drow, out, c->t.tw, c->t.itw, c->t.mod,
-                                                                                c->t.ninv, nl, c->nq, src_prime));
+        if (helr_ks_tile(c, nl) & 1)
+            cols<CB, true>(c, drow, out, nsrc, nl, src_prime, s);
+        else
+            cols<C, true>(c, drow, out, nsrc, nl, src_prime, s);
     }
     // targets 0..nl of a key switch at nl limbs (nl = P) whose prime takes (lz) or
     // does not take the unreduced forward butterfly
@@ -735,9 +765,10 @@ struct KsPlan {
     }
     static int modup(he_ctx *c, const uint64_t *drow, uint64_t *mid, int items, int nl, cudaStream_t s)
     {
-        unsigned grid = (unsigned)((size_t)items * nl * (R2 / C));
-        HELR_LAUNCH(k_ks_modup_cols<K1, K2, C, false><<<grid, C * T1, SM1, s>>>(drow, mid, c->t.tw, c->t.itw, c->t.mod,
-                                                                                 c->t.ninv, nl, c->nq, 0));
+        if (helr_ks_tile(c, nl) & 1)
+            cols<CB, false>(c, drow, mid, (size_t)items * nl, nl, 0, s);
+        else
+            cols<C, false>(c, drow, mid, (size_t)items * nl, nl, 0, s);
         return 1;
     }
     static int inner(he_ctx *c, const uint64_t *mid, const uint64_t *dntt, const uint64_t *key, uint64_t *acc, int items,

@@ -251,24 +251,30 @@ def test_batched_keyswitch_bitwise(pair):
 
 
 def test_autotune_table_and_parity(pair, tmp_path):
-    """he_autotune measures every level once and writes its table; a second
-    context with the same parameters loads the table without measuring; key
-    switches of more than one wave with the chosen waves equal the oracle's."""
+    """he_autotune measures every level once and writes its table (wave and
+    tile variant per limb count); a second context with the same parameters
+    loads the table without measuring; key switches of more than one wave with
+    the chosen waves and tiles equal the oracle's."""
     _, he = pair
     path = tmp_path / "ks_wave.txt"
     ctx = binding.Context(13, 9)
     ctx.keygen(2, [3])
     assert ctx.autotune(str(path), items=40) == 9
     lines = path.read_text().splitlines()
-    assert lines[0] == "he_lr ks-wave table v1" and lines[1].startswith("key ")
-    waves = {int(f[1]): int(f[3]) for f in (ln.split() for ln in lines[2:])}
+    assert lines[0] == "he_lr ks-wave table v2" and lines[1].startswith("key ")
+    rows = [ln.split() for ln in lines[2:]]
+    waves = {int(f[1]): int(f[3]) for f in rows}
+    tiles = {int(f[1]): int(f[5]) for f in rows}
     assert sorted(waves) == list(range(1, 10))
     assert set(waves.values()) <= {16, 32}  # the candidates up to 40 items
+    assert set(tiles.values()) <= {0, 1, 2, 3}
     assert [ctx.ks_wave(lv) for lv in range(9)] == [waves[nl] for nl in range(1, 10)]
+    assert [ctx.ks_tile(lv) for lv in range(9)] == [tiles[nl] for nl in range(1, 10)]
     ctx2 = binding.Context(13, 9)
     ctx2.keygen(2, [3])
     assert ctx2.autotune(str(path), items=40) == 0
     assert [ctx2.ks_wave(lv) for lv in range(9)] == [waves[nl] for nl in range(1, 10)]
+    assert [ctx2.ks_tile(lv) for lv in range(9)] == [tiles[nl] for nl in range(1, 10)]
     level, batch = 5, 40
     rng = np.random.default_rng(14)
     n = ctx2.n
@@ -283,6 +289,24 @@ def test_autotune_table_and_parity(pair, tmp_path):
     got = from_dev(out).reshape(batch, 2, level + 1, n)
     for b in (0, 17, batch - 1):  # first wave, a later wave, the ragged last one
         assert np.array_equal(got[b], he.keyswitch(level, gal, polys[b]))
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2, 3])
+def test_every_tile_variant_bitwise(pair, tile):
+    """Each tile variant of the key-switch kernels (narrower column CTAs, fewer
+    rows per row CTA, both) gives the oracle's words: a batched key switch
+    with a rescale, and a hoisted rotation sum."""
+    ctx, he = pair
+    ctx.set_ks_tile(tile)
+    try:
+        a, ra = enc_pair(ctx, he, rand_slots(ctx.nslots, 60 + tile), 61)
+        b, rb = enc_pair(ctx, he, rand_slots(ctx.nslots, 62 + tile), 63)
+        assert np.array_equal(ctx.rescale(ctx.mul(a, b)).export(), he.rescale(he.mul(ra, rb)).data)
+        assert np.array_equal(ctx.rotsum(a, [1, 2, 3]).export(), he.rotsum(ra, [1, 2, 3]).data)
+    finally:
+        ctx.set_ks_tile(-1)
+    with pytest.raises(binding.HeError):
+        ctx.set_ks_tile(4)
 
 
 def test_errors_are_reported(pair):
