@@ -753,29 +753,36 @@ def class_butterflies(name, units, units2):
 
 def recorded_keyswitch_traffic(by_limbs):
     """Measured DRAM bytes per key switch (ncu, profiles/traffic.txt lines
-    `keyswitch <code-sha> nl=<L> <bytes per key switch>`) weighted by the key
-    switches of each limb count; None unless every limb count issued has a
-    record for the current kernel sources."""
+    `keyswitch <code-sha> nl=<L> <bytes per key switch>`), valid for the
+    current kernel sources only.  A record `nl=all` (the DRAM bytes of every
+    kernel of a whole iteration over the key switches it issued) serves any
+    mix; otherwise the per-limb-count records are weighted by the key
+    switches of each limb count, and None unless every limb count has one."""
     h = kernel_sources_hash()
     rec = {}
     try:
         for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
             p = line.split()
             if len(p) >= 4 and not line.startswith("#") and p[0] == "keyswitch" and p[1] == h and p[2].startswith("nl="):
-                rec[int(p[2][3:])] = float(p[3])
+                rec[p[2][3:]] = float(p[3])
     except OSError:
         return None
     tot = sum(by_limbs.values())
-    if not tot or any(nl not in rec for nl in by_limbs):
+    if not tot:
         return None
-    return sum(rec[nl] * k for nl, k in by_limbs.items()) / tot
+    if "all" in rec:
+        return rec["all"]
+    if any(str(nl) not in rec for nl in by_limbs):
+        return None
+    return sum(rec[str(nl)] * k for nl, k in by_limbs.items()) / tot
 
 
 def recorded_fmaheavy(kernel):
-    """Integer-multiply-pipe (fmaheavy) warp instructions per butterfly of
-    `kernel` from an ncu capture (profiles/traffic.txt lines `fmaheavy
-    <kernel> <code-sha> <instr per butterfly>`), valid for the current kernel
-    sources only."""
+    """Integer-multiply-pipe (fmaheavy) warp instructions per warp-wide step of
+    32 butterflies of `kernel`, from an ncu capture (profiles/traffic.txt lines
+    `fmaheavy <kernel> <code-sha> <value>`: the pipe's busy cycles x 2 warp
+    instructions per SM cycle over the butterflies / 32), valid for the
+    current kernel sources only."""
     h = kernel_sources_hash()
     try:
         for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
@@ -792,9 +799,11 @@ def roofline(prof, ks, ks_by_limbs, steps, sec_iter, sms, sm_mhz):
     run as one pipeline): algorithmic bytes of every key switch the timed steps
     issued (3L limbs per item, 2L(L+1) key limbs per wave) over the time spent
     inside key switches, against the measured HBM copy bandwidth.  Beside it:
-    the same bytes over the whole iteration, and the dominant kernel class on
-    the integer multiply pipe (its butterflies per second times the measured
-    instructions per butterfly, against SMs x 64 lanes x clock)."""
+    the same bytes over the whole iteration, and the column kernel of ModUp and
+    ModDown (k_ks_modup_cols, the kernel with the largest share) on the
+    integer multiply pipe: its butterflies per second times the measured
+    instructions per 32 butterflies, against SMs x 2 warp instructions per
+    clock (16 lanes per sub-partition)."""
     peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     n = 1 << LOGN
@@ -804,21 +813,24 @@ def roofline(prof, ks, ks_by_limbs, steps, sec_iter, sms, sm_mhz):
     achieved = alg / sec / 1e9 if sec else 0.0
     traffic = recorded_keyswitch_traffic(ks_by_limbs)
     best = max(CLASSES, key=lambda k: prof[k][0])
-    ms, units, launches, units2, _ = prof[best]
-    bf = class_butterflies(best, units, units2)
-    ipb = recorded_fmaheavy(KERNEL_OF_CLASS[best])
+    ms, units, launches, units2, _ = prof["modup"]
+    bf = class_butterflies("modup", units, units2)
+    ipb = recorded_fmaheavy("k_ks_modup_cols")
     pipe_peak = sms * FMAHEAVY_LANES_PER_SM * sm_mhz * 1e6 / 32.0  # warp instructions per second
     issue = None
     if ipb is not None and ms:
-        ach = bf * ipb / (ms / 1000.0)
-        issue = {"kernel": KERNEL_OF_CLASS[best], "pipe": "fmaheavy (integer multiply)",
-                 "instr_per_butterfly": ipb, "achieved": round(ach / 1e12, 4), "peak": round(pipe_peak / 1e12, 4),
-                 "unit": "T warp-instr/s", "frac": round(ach / pipe_peak, 4), "sms": sms, "sm_mhz": sm_mhz}
+        ach = bf / 32.0 * ipb / (ms / 1000.0)
+        issue = {"kernel": "k_ks_modup_cols", "pipe": "fmaheavy (integer multiply)",
+                 "warp_instr_per_32_butterflies": ipb, "achieved": round(ach / 1e12, 4),
+                 "peak": round(pipe_peak / 1e12, 4), "unit": "T warp-instr/s", "frac": round(ach / pipe_peak, 4),
+                 "sms": sms, "sm_mhz": sm_mhz}
     ts = sum(prof[k][0] for k in CLASSES)
     return {"kernel": "key switch (k_ntt_inv_rows + k_ks_modup_cols + k_ks_inner_rows + k_ks_down_rows)",
             "unit_of_work": "one key switch", "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
             "unit": "GB/s", "frac": round(achieved / hbm, 4),
             "traffic": round(traffic) if traffic is not None else None,
+            "traffic_scope": "DRAM bytes of every kernel of an iteration per key switch issued (ncu, 256-block "
+                             "iteration scaled per key switch)",
             "alg_bytes_per_unit": round(alg / ks_n) if ks_n else None, "units": int(ks_n),
             "avg_unit_us": round(1000.0 * ks_ms / ks_n, 3) if ks_n else None,
             "keyswitches_by_limbs": {str(k): int(v / steps) for k, v in sorted(ks_by_limbs.items())},

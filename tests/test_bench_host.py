@@ -81,12 +81,16 @@ def test_keyswitch_traffic_and_pipe_records(tmp_path, monkeypatch):
     assert bench.recorded_keyswitch_traffic({}) is None
     assert bench.recorded_fmaheavy("k_ks_modup_cols") == pytest.approx(15.9)
     assert bench.recorded_fmaheavy("k_ks_inner_rows") is None
+    # a whole-iteration record serves any mix of limb counts
+    _traffic_file(tmp_path, "keyswitch %s nl=all 36.0e6\nkeyswitch %s nl=7 1.0\n" % (h, h))
+    assert bench.recorded_keyswitch_traffic({7: 1, 5: 2}) == pytest.approx(36.0e6)
 
 
 def test_roofline_of_the_key_switch(monkeypatch):
     monkeypatch.setattr(bench, "measured_peaks", lambda: {"hbm_gbs": 7000.0})
     monkeypatch.setattr(bench, "recorded_keyswitch_traffic", lambda by: 2.0e6)
-    monkeypatch.setattr(bench, "recorded_fmaheavy", lambda k: 16.0 if k == "k_ks_modup_cols" else None)
+    rec = {"k_ks_modup_cols": 16.0}
+    monkeypatch.setattr(bench, "recorded_fmaheavy", lambda k: rec.get(k))
     n = 1 << bench.LOGN
     # (ms, units, launches, units2, dram_limbs) per class over 2 steps
     prof = {"ntt_fwd": (100.0, 10, 4, 0, 0), "ntt_inv": (50.0, 5, 2, 0, 0),
@@ -105,10 +109,11 @@ def test_roofline_of_the_key_switch(monkeypatch):
     iv = r["issue_view"]
     bf = bench.class_butterflies("modup", 100, 20)
     peak = 152 * 64 * 2070e6 / 32
-    assert iv["frac"] == pytest.approx(bf * 16.0 / 0.4 / peak, abs=1e-4) and iv["sms"] == 152
+    assert iv["kernel"] == "k_ks_modup_cols"
+    assert iv["frac"] == pytest.approx(bf / 32 * 16.0 / 0.4 / peak, abs=1e-4) and iv["sms"] == 152
     assert r["classes_ms_per_step"] == {"ntt_fwd": 50.0, "ntt_inv": 25.0, "modup": 200.0, "ks_inner": 150.0}
-    # without an instruction record for the dominant kernel there is no issue view
-    prof["ks_inner"] = (500.0, 90, 8, 500, 200)
+    # without an instruction record for the column kernel there is no issue view
+    rec.clear()
     assert bench.roofline(prof, ks, {5: 40}, 2, 0.5, 152, 2070.0)["issue_view"] is None
 
 
