@@ -58,6 +58,9 @@ def _declare(L):
         "orc_cdt_table": (i32, [dbl, vp, i32]),
         "orc_sample": (None, [u64, u64, i32, u64, dbl, i64, vp]),
         "orc_ctx_new": (vp, [i32, i32, i32, i32, i32, dbl]),
+        "orc_ctx_new_bits": (vp, [i32, i32, vp, i32, dbl]),
+        "orc_gen_primes_bits": (i32, [i32, i32, vp, i32, vp]),
+        "orc_set_secret_weight": (i32, [vp, i32]),
         "orc_ctx_free": (None, [vp]),
         "orc_get_primes": (None, [vp, vp]),
         "orc_get_psi": (None, [vp, vp]),

@@ -60,11 +60,22 @@ class Ckks:
     """One parameter set: ring degree 2^logn, ciphertext primes q_0..q_{nq-1},
     one special prime P, error width sigma."""
 
-    def __init__(self, logn, nq, q0_bits=60, qi_bits=40, p_bits=60, sigma=3.2):
+    def __init__(self, logn, nq, q0_bits=60, qi_bits=40, p_bits=60, sigma=3.2, bits=None, secret_weight=0):
+        """bits: one bit width per ciphertext prime q_0..q_{nq-1} (default: q0_bits,
+        then qi_bits); secret_weight: h > 0 gives the secret exactly h nonzero
+        ternary coefficients (0: every coefficient uniform in {-1, 0, 1})."""
         self.L = lib()
-        self.ctx = self.L.orc_ctx_new(logn, nq, q0_bits, qi_bits, p_bits, sigma)
+        if bits is None:
+            self.ctx = self.L.orc_ctx_new(logn, nq, q0_bits, qi_bits, p_bits, sigma)
+        else:
+            if len(bits) != nq:
+                raise ValueError("one bit width per ciphertext prime")
+            b = np.asarray(bits, np.int32)
+            self.ctx = self.L.orc_ctx_new_bits(logn, nq, _p(b), p_bits, sigma)
         if not self.ctx:
             raise ValueError("no prime chain for these parameters")
+        if self.L.orc_set_secret_weight(self.ctx, int(secret_weight)):
+            raise ValueError("secret weight out of range")
         self.logn, self.n, self.nslots, self.nq = logn, 1 << logn, 1 << (logn - 1), nq
         self.max_level = nq - 1
         pr = np.zeros(nq + 1, np.uint64)
@@ -83,8 +94,11 @@ class Ckks:
     def galois_elt(self, r):
         return int(self.L.orc_galois_elt(self.ctx, int(r)))
 
-    def keygen(self, seed, rotations=()):
-        gals = np.array([self.galois_elt(r) for r in rotations], np.uint64)
+    def keygen(self, seed, rotations=(), extra_gals=()):
+        """Secret, public key, relinearisation key and one key-switching key per
+        rotation amount (and per raw Galois element in extra_gals, e.g. 2N - 1
+        for the conjugation X -> X^-1)."""
+        gals = np.array([self.galois_elt(r) for r in rotations] + [int(g) for g in extra_gals], np.uint64)
         rc = self.L.orc_keygen(self.ctx, seed, _p(gals), len(gals))
         if rc:
             raise RuntimeError("keygen failed")
@@ -200,6 +214,14 @@ class Ckks:
         out = np.zeros_like(ct.data)
         if self.L.orc_rotsum_gal(self.ctx, ct.level, _p(gals), len(gals), _p(ct.data), _p(out)):
             raise KeyError("no rotation key for one of %s" % (list(rots),))
+        return Ct(out, ct.level, ct.scale)
+
+    def rotate_gal(self, ct, gal):
+        """The automorphism X -> X^gal on both polynomials, then the key switch
+        of the second back to s (gal = 2N - 1: slot-wise complex conjugation)."""
+        out = np.zeros_like(ct.data)
+        if self.L.orc_rotate_gal(self.ctx, ct.level, int(gal), _p(ct.data), _p(out)):
+            raise KeyError("no key-switching key for galois element %d" % gal)
         return Ct(out, ct.level, ct.scale)
 
     def rescale(self, ct):

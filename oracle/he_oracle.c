@@ -112,6 +112,21 @@ int orc_gen_primes(int logn, int nq, int q0_bits, int qi_bits, int p_bits, uint6
     return 0;
 }
 
+/* The same with a bit width per ciphertext prime: q_i the largest unused prime
+ * below 2^bits[i] that is 1 mod 2N, taken in the order i = 0..nq-1, then P. */
+int orc_gen_primes_bits(int logn, int nq, const int *bits, int p_bits, uint64_t *out)
+{
+    uint64_t m = 2ull << logn;
+    if (nq < 1 || nq >= ORC_MAXQ) return -1;
+    for (int k = 0; k < nq; k++) {
+        if (bits[k] < 20 || bits[k] > 60) return -1;
+        out[k] = prime_below(bits[k], m, out, k);
+        if (!out[k]) return -2;
+    }
+    out[nq] = prime_below(p_bits, m, out, nq);
+    return out[nq] ? 0 : -2;
+}
+
 /* psi = h^((q-1)/2N) for the smallest h >= 2 with psi^N = -1 (a primitive 2N-th root) */
 uint64_t orc_find_psi(uint64_t q, int logn)
 {
@@ -255,6 +270,7 @@ uint64_t orc_splitmix64_next(uint64_t *state)
 
 /* stream identifiers */
 #define ST_SK 1ull
+#define ST_SK_SPARSE 7ull
 #define ST_PK_A 2ull
 #define ST_PK_E 3ull
 #define ST_ENC_V 4ull
@@ -305,6 +321,7 @@ typedef struct {
     double *zre, *zim; /* zeta^k = exp(i pi k / N), k < 2N */
     int *sidx;         /* slot j -> DFT index (5^j mod 2N - 1)/4 */
     /* keys */
+    int secret_hw;     /* 0: every coefficient of s uniform in {-1,0,1}; h > 0: exactly h nonzeros */
     int have_sk;
     int64_t *sk;       /* ternary secret, N */
     uint64_t *pk;      /* [2][nq][N] (b, a) */
@@ -337,11 +354,23 @@ void orc_sample(uint64_t seed, uint64_t stream, int kind, uint64_t q, double sig
 /* ------------------------------------------------------------------ */
 /* context                                                            */
 /* ------------------------------------------------------------------ */
+static orc_ctx *ctx_from_primes(int logn, int nq, orc_ctx *c, double sigma);
 orc_ctx *orc_ctx_new(int logn, int nq, int q0_bits, int qi_bits, int p_bits, double sigma)
 {
     orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
-    c->logn = logn; c->n = 1 << logn; c->nslots = c->n / 2; c->nq = nq;
     if (orc_gen_primes(logn, nq, q0_bits, qi_bits, p_bits, c->q)) { free(c); return NULL; }
+    return ctx_from_primes(logn, nq, c, sigma);
+}
+/* a context whose ciphertext primes have the bit widths bits[0..nq-1] */
+orc_ctx *orc_ctx_new_bits(int logn, int nq, const int *bits, int p_bits, double sigma)
+{
+    orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
+    if (orc_gen_primes_bits(logn, nq, bits, p_bits, c->q)) { free(c); return NULL; }
+    return ctx_from_primes(logn, nq, c, sigma);
+}
+static orc_ctx *ctx_from_primes(int logn, int nq, orc_ctx *c, double sigma)
+{
+    c->logn = logn; c->n = 1 << logn; c->nslots = c->n / 2; c->nq = nq;
     for (int i = 0; i <= nq; i++) tab_init(&c->tab[i], c->q[i], orc_find_psi(c->q[i], logn), c->n);
     c->sigma = sigma;
     c->cdt_len = orc_cdt_table(sigma, c->cdt, 64);
@@ -357,6 +386,14 @@ orc_ctx *orc_ctx_new(int logn, int nq, int q0_bits, int qi_bits, int p_bits, dou
     uint64_t g = 1, twon = 2ull * n;
     for (int j = 0; j < c->nslots; j++) { c->sidx[j] = (int)((g - 1) / 4); g = (g * 5) % twon; }
     return c;
+}
+
+/* secret with exactly h nonzero coefficients at the next orc_keygen (0 = dense ternary) */
+int orc_set_secret_weight(orc_ctx *c, int h)
+{
+    if (h < 0 || h > c->n) return -1;
+    c->secret_hw = h;
+    return 0;
 }
 
 void orc_ctx_free(orc_ctx *c)
@@ -590,7 +627,20 @@ int orc_keygen(orc_ctx *c, uint64_t seed, const uint64_t *gals, int ngal)
     for (int i = 0; i < c->nksk; i++) free(c->ksk[i]);
     c->nksk = 0;
     c->sk = (int64_t *)malloc(sizeof(int64_t) * n);
-    for (int i = 0; i < n; i++) c->sk[i] = sample_ternary(seed, ST_SK, (uint64_t)i);
+    if (c->secret_hw > 0) {
+        /* exactly h nonzero coefficients: word k of the stream picks position
+         * word % N (skipped when already taken) and the sign from bit 32 */
+        memset(c->sk, 0, sizeof(int64_t) * n);
+        for (uint64_t k = 0, placed = 0; placed < (uint64_t)c->secret_hw; k++) {
+            uint64_t w = orc_rand_word(seed, ST_SK_SPARSE, k);
+            uint64_t pos = w % (uint64_t)n;
+            if (c->sk[pos]) continue;
+            c->sk[pos] = (w >> 32) & 1 ? 1 : -1;
+            placed++;
+        }
+    } else {
+        for (int i = 0; i < n; i++) c->sk[i] = sample_ternary(seed, ST_SK, (uint64_t)i);
+    }
     c->have_sk = 1;
     c->pk = (uint64_t *)malloc(sizeof(uint64_t) * 2 * (size_t)nq * n);
     int64_t *e = (int64_t *)malloc(sizeof(int64_t) * n);
