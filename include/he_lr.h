@@ -57,8 +57,15 @@ typedef struct he_pt he_pt;
 
 /* Scheme parameters (Sec. 5: the paper's runs use N = 2^16; the chain here is
  * one q0_bits prime, n_q - 1 primes of qi_bits, one special prime of p_bits,
- * all = 1 mod 2N; the secret is ternary and errors are discrete Gaussians of
- * width sigma). log_n in [10, 16], 2 <= n_q <= 39, bit widths in [30, 60]. */
+ * all = 1 mod 2N, each the largest unused such prime below 2^bits; the secret
+ * is ternary and errors are discrete Gaussians of width sigma). log_n in
+ * [10, 16], 2 <= n_q <= 39, bit widths in [30, 60].
+ * bits (may be NULL): a width for each ciphertext prime q_0..q_(n_q-1) in
+ * place of q0_bits / qi_bits (chains that bootstrap mix widths); the array is
+ * read during he_ctx_create only.
+ * secret_hw: 0 = every secret coefficient uniform in {-1, 0, 1}; h > 0 =
+ * exactly h nonzero coefficients (a sparse secret keeps the integer overflow
+ * of a bootstrap's ModRaise small). */
 typedef struct {
     int log_n;
     int n_q;
@@ -66,6 +73,8 @@ typedef struct {
     int qi_bits;
     int p_bits;
     double sigma;
+    const int *bits;
+    int secret_hw;
 } he_params;
 
 /* Create a context: generates the prime chain, transform tables and the
@@ -94,6 +103,11 @@ int he_zeta_table(int log_n, double *re, double *im);
  * right) switches s(X^(5^r)) -> s.  Randomness is the splitmix64 stream of
  * `seed`.  May be called again to add rotation keys (same seed). */
 int he_keygen(he_ctx *ctx, uint64_t seed, const int64_t *rotations, size_t n_rot);
+/* Keys for raw Galois elements (odd residues below 2N; 2N - 1 is the slot-wise
+ * complex conjugation X -> X^-1 the bootstrap uses), from the seed of the
+ * last he_keygen (HE_EKEY before it, HE_EINVAL for an even or out-of-range
+ * element). */
+int he_keygen_galois(he_ctx *ctx, const uint64_t *gals, size_t n);
 
 /* Encode n_slots <= N/2 complex values (re, im; im may be NULL) at `level`
  * with `scale`: the coefficients are round_half_away(scale * tau^-1(z)). */
@@ -258,6 +272,45 @@ int he_prof_keyswitches(he_ctx *ctx, double *by_limbs, size_t n);
  * and iterations of ctx (default 3; 1..3, else HE_EINVAL).  A job must run
  * with the r it was created with (its rotation keys depend on it). */
 int he_set_rotation_radix(he_ctx *ctx, int log2_radix);
+/* ------------------------------------------------------------------ bootstrapping
+ * The refresh of the weight ciphertexts by bootstrapping (Sec. 2.1, Sec. 4.3
+ * Step 7): a ciphertext at level 0 whose slot vector repeats with period
+ * `slots` (W and V repeat the g weights in every row) comes back at
+ * `level_out` with scale `scale_out` holding the same slots:
+ *   ModRaise (the q0 words as centred integers modulo every prime), SubSum
+ *   (the trace to Z[X^(N / 2 slots)] by hoisted rotations), CoeffToSlot
+ *   (E^H / slots by baby-step/giant-step diagonals, real and imaginary parts
+ *   split with the conjugation and X^(N/2)), EvalMod (the degree-`degree`
+ *   Taylor polynomial of cos(2 pi (v - 1/4) / 2^double_angles) on
+ *   |v| <= K + 1/2, then `double_angles` steps y -> 2y^2 - 1: sin(2 pi v)),
+ *   SlotToCoeff (q0 E / (2 pi scale_out)).
+ * It consumes 1 + ceil(log2 degree) + 1 + double_angles + 1 levels from the
+ * top of the chain and needs: a sparse secret (he_params.secret_hw, so that
+ * the ModRaise overflow |I| stays below K), a scale_out well below q0 (the
+ * refreshed value carries a relative error of about (2 pi scale_out |m| /
+ * q0)^2 / 6 from sin against its argument), the rotation keys he_boot_keys
+ * lists and the conjugation key (he_keygen_galois, element 2N - 1).
+ * HE_ELEVEL when the chain is too short for level_out, HE_EKEY for a missing
+ * key, HE_EINVAL for parameters out of range. */
+typedef struct {
+    int slots;          /* period of the slot vector (a power of two <= N/2) */
+    int K;              /* bound on the ModRaise overflow |I| */
+    int double_angles;  /* r */
+    int degree;         /* degree of the cosine polynomial, 2..63 */
+    double scale_out;
+    int level_out;
+} he_boot_params;
+/* The rotation amounts a bootstrap with these parameters needs (written to
+ * rots[0..cap), the count to *n_rots). */
+int he_boot_keys(he_ctx *ctx, const he_boot_params *p, int64_t *rots, size_t cap, size_t *n_rots);
+/* Bootstrap one ciphertext into a new one (scratch allocated by the call). */
+int he_bootstrap(he_ctx *ctx, const he_ct *in, const he_boot_params *p, he_ct **out);
+/* Bootstrap `batch` device ciphertexts [batch][2][in_level+1][N] (NTT form)
+ * into d_out [batch][2][level_out+1][N]; the slots are refreshed together
+ * (every key switch of the bootstrap runs over the whole batch). */
+int he_bootstrap_batch(he_ctx *ctx, const uint64_t *d_in, int in_level, uint64_t *d_out, int batch,
+                       const he_boot_params *p);
+
 /* Galois element of a left rotation by r. */
 uint64_t he_galois_elt(const he_ctx *ctx, int64_t r);
 

@@ -29,7 +29,13 @@ class HeError(RuntimeError):
 
 class he_params(ctypes.Structure):
     _fields_ = [("log_n", ctypes.c_int), ("n_q", ctypes.c_int), ("q0_bits", ctypes.c_int),
-                ("qi_bits", ctypes.c_int), ("p_bits", ctypes.c_int), ("sigma", ctypes.c_double)]
+                ("qi_bits", ctypes.c_int), ("p_bits", ctypes.c_int), ("sigma", ctypes.c_double),
+                ("bits", ctypes.POINTER(ctypes.c_int)), ("secret_hw", ctypes.c_int)]
+
+
+class he_boot_params(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("K", ctypes.c_int), ("double_angles", ctypes.c_int),
+                ("degree", ctypes.c_int), ("scale_out", ctypes.c_double), ("level_out", ctypes.c_int)]
 
 
 class he_lr_sched(ctypes.Structure):
@@ -99,6 +105,10 @@ SIGNATURES = {
     "he_prof_read2": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "he_prof_keyswitches": (_i, [_vp, _vp, _sz]),
     "he_set_rotation_radix": (_i, [_vp, _i]),
+    "he_keygen_galois": (_i, [_vp, _vp, _sz]),
+    "he_boot_keys": (_i, [_vp, ctypes.POINTER(he_boot_params), _vp, _sz, ctypes.POINTER(_sz)]),
+    "he_bootstrap": (_i, [_vp, _vp, ctypes.POINTER(he_boot_params), _pp]),
+    "he_bootstrap_batch": (_i, [_vp, _vp, _i, _vp, _i, ctypes.POINTER(he_boot_params)]),
     "he_rotsum": (_i, [_vp, _vp, _vp, _sz, _pp]),
     "he_rotsum_batch": (_i, [_vp, _vp, _vp, _i, _i, _vp, _sz]),
     "he_ks_tile": (_i, [_vp, _i]),
@@ -139,9 +149,15 @@ def _ptr(a):
 class Context:
     """One he_ctx: parameter set, tables, keys; kernels run on `stream`."""
 
-    def __init__(self, log_n=13, n_q=9, q0_bits=60, qi_bits=40, p_bits=60, sigma=3.2, stream=None):
+    def __init__(self, log_n=13, n_q=9, q0_bits=60, qi_bits=40, p_bits=60, sigma=3.2, stream=None, bits=None,
+                 secret_weight=0):
         self.L = load()
-        p = he_params(log_n, n_q, q0_bits, qi_bits, p_bits, sigma)
+        barr = None
+        if bits is not None:
+            if len(bits) != n_q:
+                raise ValueError("one bit width per ciphertext prime")
+            barr = (ctypes.c_int * n_q)(*bits)
+        p = he_params(log_n, n_q, q0_bits, qi_bits, p_bits, sigma, barr, int(secret_weight))
         h = ctypes.c_void_p()
         rc = self.L.he_ctx_create(ctypes.byref(p), stream, ctypes.byref(h))
         if rc:
@@ -174,6 +190,29 @@ class Context:
     def keygen(self, seed, rotations=()):
         r = np.asarray(list(rotations), np.int64)
         self.check(self.L.he_keygen(self.h, seed, _ptr(r) if len(r) else None, len(r)))
+
+    def keygen_galois(self, gals):
+        g = np.asarray(gals, np.uint64)
+        self.check(self.L.he_keygen_galois(self.h, _ptr(g), len(g)))
+
+    def boot_keys(self, slots, K, r, deg, scale_out, level_out):
+        """rotation amounts a bootstrap needs"""
+        p = he_boot_params(slots, K, r, deg, scale_out, level_out)
+        n = ctypes.c_size_t()
+        self.check(self.L.he_boot_keys(self.h, ctypes.byref(p), None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value, np.int64)
+        self.check(self.L.he_boot_keys(self.h, ctypes.byref(p), _ptr(out), n.value, ctypes.byref(n)))
+        return [int(x) for x in out]
+
+    def bootstrap(self, ct, slots, K, r, deg, scale_out, level_out):
+        p = he_boot_params(slots, K, r, deg, scale_out, level_out)
+        o = ctypes.c_void_p()
+        self.check(self.L.he_bootstrap(self.h, ct.h, ctypes.byref(p), ctypes.byref(o)))
+        return Ct(self, o)
+
+    def bootstrap_batch(self, din, in_level, dout, batch, slots, K, r, deg, scale_out, level_out):
+        p = he_boot_params(slots, K, r, deg, scale_out, level_out)
+        self.check(self.L.he_bootstrap_batch(self.h, din, in_level, dout, batch, ctypes.byref(p)))
 
     def galois_elt(self, r):
         return int(self.L.he_galois_elt(self.h, int(r)))

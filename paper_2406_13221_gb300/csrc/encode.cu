@@ -310,7 +310,28 @@ int helr_keygen_base(he_ctx *c, uint64_t seed)
     LimbMap all;
     all.period = np;
     for (int j = 0; j < np; j++) all.p[j] = (unsigned char)j;
-    HELR_TRY(helr_sample(c, c->d_sk, np, all, seed, 1, 0));
+    if (c->secret_hw > 0) {
+        // exactly h nonzero coefficients: word k of stream 7 picks position
+        // word mod N (skipped when taken) and the sign from bit 32
+        std::vector<int64_t> sk((size_t)n, 0);
+        const uint64_t seedm = mix64(seed);
+        for (uint64_t k = 0, placed = 0; placed < (uint64_t)c->secret_hw; k++) {
+            const uint64_t w = mix64(seedm + ((7ull << 40) + k + 1) * 0x9E3779B97F4A7C15ull);
+            const uint64_t pos = w % (uint64_t)n;
+            if (sk[pos]) continue;
+            sk[pos] = (w >> 32) & 1 ? 1 : -1;
+            placed++;
+        }
+        std::vector<uint64_t> limbs((size_t)np * n);
+        for (int j = 0; j < np; j++)
+            for (int i = 0; i < n; i++)
+                limbs[(size_t)j * n + i] = sk[i] >= 0 ? (uint64_t)sk[i] : c->q[j] - 1;
+        HELR_CUDA(c, cudaMemcpyAsync(c->d_sk, limbs.data(), sizeof(uint64_t) * limbs.size(), cudaMemcpyHostToDevice,
+                                     c->stream));
+        HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    } else {
+        HELR_TRY(helr_sample(c, c->d_sk, np, all, seed, 1, 0));
+    }
     // host copy of the ternary secret: limb 0 in coefficient form, centred
     std::vector<uint64_t> h((size_t)n);
     HELR_CUDA(c, cudaMemcpyAsync(h.data(), c->d_sk, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, c->stream));

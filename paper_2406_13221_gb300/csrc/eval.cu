@@ -165,10 +165,20 @@ int ev_rescale(Eval *ev, const CtB &a, CtB &out)
 int ev_rotate_acc(Eval *ev, const CtB &a, int64_t r, CtB &out, int accumulate)
 {
     he_ctx *c = ev->c;
-    HELR_TRY(check_batch(ev, a));
     const uint64_t gal = he_galois_elt(c, r);
+    if (!helr_find_key(c, gal)) return helr_fail(c, HE_EKEY, "no rotation key for %lld", (long long)r);
+    return ev_rotate_gal(ev, a, gal, out, accumulate);
+}
+
+// the automorphism X -> X^gal of both polynomials and the key switch of the
+// second back to s (gal = 5^r mod 2N: rotation by r slots; gal = 2N - 1: the
+// slot-wise complex conjugation); accumulate: out = a + sigma_gal(a)
+int ev_rotate_gal(Eval *ev, const CtB &a, uint64_t gal, CtB &out, int accumulate)
+{
+    he_ctx *c = ev->c;
+    HELR_TRY(check_batch(ev, a));
     const uint64_t *key = helr_find_key(c, gal);
-    if (!key) return helr_fail(c, HE_EKEY, "no rotation key for %lld", (long long)r);
+    if (!key) return helr_fail(c, HE_EKEY, "no key-switching key for galois element %llu", (unsigned long long)gal);
     const int B = a.batch, lv = a.level, nl = lv + 1;
     const size_t N = c->n, lw = (size_t)nl * N;
     cudaStream_t s = c->stream;

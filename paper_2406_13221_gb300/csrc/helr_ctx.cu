@@ -254,14 +254,14 @@ static int ctx_init(he_ctx *c, const he_params *p)
     c->sigma = p->sigma;
     const uint64_t twon = 2ull * c->n;
     std::vector<uint64_t> used;
-    uint64_t v = h_next_prime(p->q0_bits, twon, used);
-    if (!v) return helr_fail(c, HE_EINVAL, "no %d-bit prime = 1 mod 2N", p->q0_bits);
-    used.push_back(v);
-    for (int i = 1; i < c->nq; i++) {
-        v = h_next_prime(p->qi_bits, twon, used);
-        if (!v) return helr_fail(c, HE_EINVAL, "not enough %d-bit primes", p->qi_bits);
+    uint64_t v;
+    for (int i = 0; i < c->nq; i++) {
+        const int b = p->bits ? p->bits[i] : (i ? p->qi_bits : p->q0_bits);
+        v = h_next_prime(b, twon, used);
+        if (!v) return helr_fail(c, HE_EINVAL, "not enough %d-bit primes = 1 mod 2N", b);
         used.push_back(v);
     }
+    c->secret_hw = p->secret_hw;
     v = h_next_prime(p->p_bits, twon, used);
     if (!v) return helr_fail(c, HE_EINVAL, "no special prime");
     used.push_back(v);
@@ -368,8 +368,11 @@ extern "C" int he_ctx_create(const he_params *p, void *stream, he_ctx **out)
     *out = nullptr;
     if (!p || p->log_n < HELR_MIN_LOGN || p->log_n > HELR_MAX_LOGN || p->n_q < 2 || p->n_q + 1 > HELR_MAXQ ||
         p->q0_bits < 30 || p->q0_bits > 60 || p->qi_bits < 30 || p->qi_bits > 60 || p->p_bits < 30 || p->p_bits > 60 ||
-        !(p->sigma > 0.0))
+        !(p->sigma > 0.0) || p->secret_hw < 0 || p->secret_hw > (1 << p->log_n))
         return HE_EINVAL;
+    if (p->bits)
+        for (int i = 0; i < p->n_q; i++)
+            if (p->bits[i] < 30 || p->bits[i] > 60) return HE_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -479,6 +482,19 @@ extern "C" int he_keygen(he_ctx *c, uint64_t seed, const int64_t *rot, size_t nr
         HELR_TRY(helr_add_key(c, 0));
     }
     for (size_t i = 0; i < nrot; i++) HELR_TRY(helr_add_key(c, he_galois_elt(c, rot[i])));
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HE_OK;
+}
+
+extern "C" int he_keygen_galois(he_ctx *c, const uint64_t *gals, size_t n)
+{
+    if (!c || (n && !gals)) return HE_EINVAL;
+    if (!c->have_keys) return helr_fail(c, HE_EKEY, "he_keygen first");
+    for (size_t i = 0; i < n; i++)
+        if (!(gals[i] & 1) || gals[i] >= 2ull * c->n)
+            return helr_fail(c, HE_EINVAL, "galois element %llu is not an odd residue below 2N",
+                             (unsigned long long)gals[i]);
+    for (size_t i = 0; i < n; i++) HELR_TRY(helr_add_key(c, gals[i]));
     HELR_CUDA(c, cudaStreamSynchronize(c->stream));
     return HE_OK;
 }

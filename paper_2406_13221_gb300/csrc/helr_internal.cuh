@@ -224,6 +224,7 @@ struct he_ctx {
     int ks_tile = -1;              // tile variant forced by he_set_ks_tile (-1 = none)
     int ks_tile_tab[HELR_MAXQ + 1] = {};  // tile variant per limb count chosen by he_autotune
     int rot_radix_log = 3;         // rotate-and-sum steps as hoisted groups of 2^rot_radix_log positions
+    int secret_hw = 0;             // 0: dense ternary secret; h > 0: exactly h nonzero coefficients
 };
 
 struct he_ct {
@@ -436,6 +437,7 @@ int ev_mul_relin_seg(Eval *ev, const CtB &a, const uint64_t *const *bptr, const 
 int ev_rotate(Eval *ev, const CtB &a, int64_t r, CtB &out);
 int ev_rotate_acc(Eval *ev, const CtB &a, int64_t r, CtB &out, int accumulate);
 int ev_rotsum(Eval *ev, const CtB &a, const int64_t *rots, int nrot, CtB &out);
+int ev_rotate_gal(Eval *ev, const CtB &a, uint64_t gal, CtB &out, int accumulate);
 // Rotate-and-sum over 2^nbits positions spaced `step` slots apart as hoisted
 // groups of 2^rho positions: group e (e = 0, rho, 2 rho, ...) of width
 // w = min(rho, nbits - e) sums the rotations by m 2^e step, 0 < m < 2^w.
