@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-bbar", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip the compact primitive sweep and the tensor-core floor")
     ap.add_argument("--no-images", action="store_true", help="skip the MNIST-shaped workload")
+    ap.add_argument("--no-boot", action="store_true", help="skip the workload refreshed by bootstrapping")
     ap.add_argument("--no-autotune", action="store_true", help="default key-switch waves (profiling runs)")
     ap.add_argument("--rot-radix", type=int, default=0,
                     help="log2 of the hoisted rotation group (0 = library default)")
@@ -272,13 +273,20 @@ def run_ours(args, rank, world):
         k4 = k4_tensor_floor(ctx)
     if world == 1 and not args.no_images:
         images = image_pair_time(ctx, args)
+    booted = None
+    if world == 1 and not args.no_boot:
+        ctx.close()
+        booted = boot_refresh_time(X, y, args)
     # the CPU leg (rank 0 of a single-GPU run): FP64-twin checks of the decrypted weights
     err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_twin:
-        err = twin_checks(X, y, main_w, images)
-    elif images:
+        err = twin_checks(X, y, main_w, images, booted)
+    else:
         for name in ("full_batch", "mini_batch"):
-            images[name].pop("_w", None)
+            if images:
+                images[name].pop("_w", None)
+        if booted:
+            booted.pop("_w", None)
     out = {
         "metric": METRIC, "value": round(sec_iter, 5), "unit": "s/iter", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": False,
@@ -297,6 +305,7 @@ def run_ours(args, rank, world):
         "primitive_sweep": psweep,
         "k4_tensor_ntt": k4,
         "image_pair_g16": images,
+        "bootstrapped_refresh": booted,
         "plain_one_ct_per_launch_s_per_iter": round(plain, 4) if plain else None,
         "mini_batch": mini,
         "multi_job": multi,
@@ -705,6 +714,57 @@ def image_pair_time(ctx, args):
     return out
 
 
+BOOT_BITS = [50] + [40] * 6 + [55] * 14  # q0, the iteration's six levels, the bootstrap's fourteen
+BOOT_PARAMS = dict(slots=256, K=16, r=6, deg=19, scale_out=2.0 ** LOG_SCALE, level_out=ITER_LEVEL)
+
+
+def boot_refresh_time(X, y, args, iters=2):
+    """The full-batch workload with W and V refreshed by bootstrapping (Sec. 4.3
+    Step 7 as the paper runs it, no client round trip) on the bootstrappable
+    chain (q0 50 bits, six 40-bit levels for the iteration, fourteen 55-bit
+    levels for the bootstrap; a secret of 64 nonzero coefficients): seconds per
+    iteration over `iters` iterations after one warm-up, the bootstrap's share,
+    and the decrypted weights for the FP64-twin check of the CPU leg."""
+    import torch
+    from paper_2406_13221_gb300 import binding
+    t0 = time.time()
+    ctx = binding.Context(LOGN, len(BOOT_BITS), bits=BOOT_BITS, secret_weight=64)
+    job = binding.Job(ctx, X, y, binding.FULL_BATCH, 1024, binding.G8, LOG_SCALE, enc_seed=3, key_seed=2,
+                      batch_blocks=args.chunk)
+    job.set_refresh(BOOT_PARAMS)
+    setup = time.time() - t0
+    sched = (2.0, 1.0, 81.0, 2.5)
+    job.step(0, sched)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for t in range(1, 1 + iters):
+        job.step(t, sched)
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1000.0 / iters
+    st = job.stats()
+    # a bootstrap of W and V alone (the refresh), timed on its own
+    n = 1 << LOGN
+    din = torch.randint(0, 1 << 30, (2 * 2 * n,), dtype=torch.int64, device="cuda")
+    dout = torch.zeros(2 * 2 * (ITER_LEVEL + 1) * n, dtype=torch.int64, device="cuda")
+    ctx.bootstrap_batch(din.data_ptr(), 0, dout.data_ptr(), 2, **BOOT_PARAMS)
+    torch.cuda.synchronize()
+    e0.record()
+    ctx.bootstrap_batch(din.data_ptr(), 0, dout.data_ptr(), 2, **BOOT_PARAMS)
+    e1.record()
+    torch.cuda.synchronize()
+    boot_s = e0.elapsed_time(e1) / 1000.0
+    out = {"workload": "full-batch QG-NAG at %d x %d, W and V refreshed by bootstrapping" % X.shape,
+           "chain_bits": BOOT_BITS, "secret_nonzeros": 64, "bootstrap": BOOT_PARAMS,
+           "s_per_iter": round(sec, 5), "bootstrap_of_w_and_v_s": round(boot_s, 5),
+           "update_share": round(st.sec_update_avg / st.sec_iter_avg, 3) if st.sec_iter_avg else None,
+           "setup_s": round(setup, 1), "_w": (job.weights(0), 1 + iters, sched)}
+    job.close()
+    ctx.close()
+    return out
+
+
 def ctw_bytes():
     return 2 * (ITER_LEVEL + 1) * (1 << LOGN) * 8
 
@@ -870,7 +930,7 @@ def standalone_ntt(ctx, limbs=256, reps=10):
             "hbm_frac": round(rate * 16 * n / 1e9 / hbm, 4)}
 
 
-def twin_checks(X, y, main_w, images):
+def twin_checks(X, y, main_w, images, booted=None):
     """Part of the CPU leg: the decrypted weights the GPU jobs produced (rows 0
     and m-1 of the full-batch job; row 0 of each MNIST-shaped job) against the
     FP64 plaintext run of the same iterations (oracle/plain.py); fills in the
@@ -887,6 +947,9 @@ def twin_checks(X, y, main_w, images):
             w, mode, sched = images[name].pop("_w")
             wpi = plain.train(di, 3, mode=mode, sched=sched, poly=qgnag.G16)
             images[name]["max_abs_err_vs_fp64_twin"] = float(np.abs(w - wpi).max())
+    if booted:
+        w, iters, sched = booted.pop("_w")
+        booted["max_abs_err_vs_fp64_twin"] = float(np.abs(w - plain.train(data, iters, sched=sched)).max())
     return err
 
 

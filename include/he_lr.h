@@ -376,6 +376,14 @@ int he_lr_job_set_graph(he_lr_job *job, int on);
 /* Data blocks per kernel launch for later steps: 1 = the plain
  * one-ciphertext-per-launch form; at most the value the job was created with. */
 int he_lr_job_set_batch(he_lr_job *job, int blocks_per_launch);
+/* Refresh W and V after every later step by bootstrapping (Sec. 4.3 Step 7)
+ * instead of decrypting and re-encrypting them: one he_bootstrap_batch over
+ * both.  p must return slots of period g at the job's start level with its
+ * scale (HE_EINVAL otherwise); the context needs the chain and the sparse
+ * secret the bootstrap requires; the rotation and conjugation keys are
+ * generated here from the context's key seed.  p = NULL returns to
+ * decryption and re-encryption. */
+int he_lr_job_set_refresh(he_lr_job *job, const he_boot_params *p);
 /* Decrypted weights W (slots of row `row`, g values; padded columns are 0). */
 int he_lr_job_weights(he_lr_job *job, int row, double *w, size_t len);
 /* Access to the job's current W and V ciphertexts (owned by the job). */

@@ -106,6 +106,7 @@ SIGNATURES = {
     "he_prof_keyswitches": (_i, [_vp, _vp, _sz]),
     "he_set_rotation_radix": (_i, [_vp, _i]),
     "he_keygen_galois": (_i, [_vp, _vp, _sz]),
+    "he_lr_job_set_refresh": (_i, [_vp, ctypes.POINTER(he_boot_params)]),
     "he_boot_keys": (_i, [_vp, ctypes.POINTER(he_boot_params), _vp, _sz, ctypes.POINTER(_sz)]),
     "he_bootstrap": (_i, [_vp, _vp, ctypes.POINTER(he_boot_params), _pp]),
     "he_bootstrap_batch": (_i, [_vp, _vp, _i, _vp, _i, ctypes.POINTER(he_boot_params)]),
@@ -430,6 +431,15 @@ class Job:
 
     def set_graph(self, on=True):
         self.ctx.check(self.ctx.L.he_lr_job_set_graph(self.h, int(on)))
+
+    def set_refresh(self, boot=None):
+        """Refresh W and V by bootstrapping with the parameters dict boot (slots,
+        K, r, deg, scale_out, level_out), or by decryption and re-encryption (None)."""
+        if boot is None:
+            self.ctx.check(self.ctx.L.he_lr_job_set_refresh(self.h, None))
+        else:
+            p = he_boot_params(boot["slots"], boot["K"], boot["r"], boot["deg"], boot["scale_out"], boot["level_out"])
+            self.ctx.check(self.ctx.L.he_lr_job_set_refresh(self.h, ctypes.byref(p)))
 
     def set_batch(self, blocks_per_launch):
         self.ctx.check(self.ctx.L.he_lr_job_set_batch(self.h, int(blocks_per_launch)))

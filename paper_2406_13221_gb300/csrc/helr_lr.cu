@@ -179,6 +179,10 @@ struct he_lr_job {
     int graph;
     cudaStream_t gstream;
     cudaGraphExec_t gexec;
+    // refresh by bootstrapping (optional; otherwise decrypt and re-encrypt)
+    int boot;
+    he_boot_params bp;
+    uint64_t *boot_buf;         // [2][2][L+1][N] in, then out
 };
 
 static double f2(const he_lr_sched &s, double t) { return s.max - (s.max - s.min) * pow(t / s.T, s.power); }
@@ -281,6 +285,7 @@ extern "C" int he_lr_job_free(he_lr_job *j)
     if (j->V) he_ct_free(j->V);
     helr_free(c, j->sig);
     helr_free(c, j->buf);
+    helr_free(c, j->boot_buf);
     ev_free(&j->ev);
     cudaStreamSynchronize(c->stream);
     if (j->gexec) cudaGraphExecDestroy(j->gexec);
@@ -761,6 +766,58 @@ extern "C" int he_lr_job_set_graph(he_lr_job *j, int on)
     return HE_OK;
 }
 
+// The refresh of W' and V' (Sec. 4.3 Step 7): one bootstrap over both when the
+// job refreshes by bootstrapping, else decryption and re-encryption with the
+// seeds of iteration t.
+static int job_refresh(he_lr_job *j, int t, const CtB &Wn, const CtB &Vn)
+{
+    he_ctx *c = j->c;
+    if (!j->boot) {
+        HELR_TRY(refresh_dev(c, Wn.d, Wn.level, Wn.scale, j->L, j->scale0, obj_seed(j->enc_seed, 5, t), j->W->d));
+        HELR_TRY(refresh_dev(c, Vn.d, Vn.level, Vn.scale, j->L, j->scale0, obj_seed(j->enc_seed, 6, t), j->V->d));
+        j->W->scale = j->scale0;
+        j->V->scale = j->scale0;
+        return HE_OK;
+    }
+    if (Wn.level != 0 || Vn.level != 0) return helr_fail(c, HE_EINTERNAL, "the iteration should end at level 0");
+    const size_t N = c->n, win = 2 * N, wout = 2 * (size_t)(j->L + 1) * N;
+    HELR_CUDA(c, cudaMemcpyAsync(j->boot_buf, Wn.d, win * 8, cudaMemcpyDeviceToDevice, c->stream));
+    HELR_CUDA(c, cudaMemcpyAsync(j->boot_buf + win, Vn.d, win * 8, cudaMemcpyDeviceToDevice, c->stream));
+    uint64_t *out = j->boot_buf + 2 * win;
+    HELR_TRY(he_bootstrap_batch(c, j->boot_buf, Wn.level, out, 2, &j->bp));
+    HELR_CUDA(c, cudaMemcpyAsync(j->W->d, out, wout * 8, cudaMemcpyDeviceToDevice, c->stream));
+    HELR_CUDA(c, cudaMemcpyAsync(j->V->d, out + wout, wout * 8, cudaMemcpyDeviceToDevice, c->stream));
+    j->W->scale = j->V->scale = j->scale0;
+    return HE_OK;
+}
+
+extern "C" int he_lr_job_set_refresh(he_lr_job *j, const he_boot_params *p)
+{
+    if (!j) return HE_EINVAL;
+    he_ctx *c = j->c;
+    if (!p) {
+        j->boot = 0;
+        return HE_OK;
+    }
+    if (p->level_out != j->L || p->scale_out != j->scale0 || p->slots != j->g)
+        return helr_fail(c, HE_EINVAL, "the bootstrap must return slots of period g = %d at level %d, scale 2^%g", j->g,
+                         j->L, log2(j->scale0));
+    size_t nr = 0;
+    HELR_TRY(he_boot_keys(c, p, nullptr, 0, &nr));
+    std::vector<int64_t> rots(nr);
+    HELR_TRY(he_boot_keys(c, p, rots.data(), nr, &nr));
+    HELR_TRY(he_keygen(c, c->key_seed, rots.data(), nr));
+    const uint64_t conj = 2ull * c->n - 1;
+    HELR_TRY(he_keygen_galois(c, &conj, 1));
+    if (!j->boot_buf) {
+        const size_t N = c->n;
+        HELR_TRY(helr_alloc(c, (void **)&j->boot_buf, 8 * (4 * (size_t)(j->L + 1) * N + 4 * N)));
+    }
+    j->bp = *p;
+    j->boot = 1;
+    return HE_OK;
+}
+
 extern "C" int he_lr_job_step(he_lr_job *j, int t, he_lr_sched sched)
 {
     if (!j || t < 0 || !(sched.T > 0)) return HE_EINVAL;
@@ -772,10 +829,7 @@ extern "C" int he_lr_job_step(he_lr_job *j, int t, he_lr_sched sched)
     HELR_CUDA(c, cudaStreamSynchronize(c->stream));
     auto t1 = std::chrono::steady_clock::now();
     // Step 7: refresh W and V
-    HELR_TRY(refresh_dev(c, Wn.d, Wn.level, Wn.scale, j->L, j->scale0, obj_seed(j->enc_seed, 5, t), j->W->d));
-    HELR_TRY(refresh_dev(c, Vn.d, Vn.level, Vn.scale, j->L, j->scale0, obj_seed(j->enc_seed, 6, t), j->V->d));
-    j->W->scale = j->scale0;
-    j->V->scale = j->scale0;
+    HELR_TRY(job_refresh(j, t, Wn, Vn));
     HELR_CUDA(c, cudaStreamSynchronize(c->stream));
     auto t2 = std::chrono::steady_clock::now();
     j->upd_total += std::chrono::duration<double>(t1 - t0).count();

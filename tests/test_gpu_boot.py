@@ -116,3 +116,42 @@ def test_bootstrap_full_size_refreshes_weights():
     got = ctx.decode(ctx.decrypt(out))
     assert np.abs(got.real - z).max() < 1e-4
     assert np.abs(got.imag).max() < 1e-4
+
+
+def test_job_refreshed_by_bootstrapping_bitwise():
+    """A full-batch job refreshing W and V by bootstrapping on a bootstrappable
+    chain at N = 2^12 (16-column blocks, 8 blocks): after each of two steps the
+    state equals, word for word, the oracle's iteration followed by the
+    oracle's bootstrap of W' and V'; the weights track the FP64 twin."""
+    from oracle import plain, qgnag
+    from paper_2406_13221_gb300 import synth
+    bits = [50] + [40] * 6 + [55] * 13
+    ctx = binding.Context(12, len(bits), bits=bits, secret_weight=32)
+    he = Ckks(12, len(bits), bits=bits, secret_weight=32)
+    X, y = synth.small(seed=17, n=1024, f=15)
+    data = qgnag.TrainData(X, y, g=16, m=128, batch_rows=1024)
+    circ = qgnag.Circuit(he, 16, 128, D)
+    L = circ.L
+    prm = dict(slots=16, K=12, r=5, deg=23, scale_out=D, level_out=L)
+    job = binding.Job(ctx, X, y, binding.FULL_BATCH, 1024, binding.G8, 40.0, enc_seed=19, key_seed=2)
+    job.set_refresh(prm)
+    p = boot.BootParams(n=16, K=12, r=5, deg=23, delta_out=D, out_level=L)
+    rots, gals = boot.key_rotations(he, p)
+    he.keygen(2, sorted(set(circ.rotations()) | set(rots)), gals)
+    nb = data.blocks.shape[0]
+    Z = [OCt(job.input(0, b).export(), L, D) for b in range(nb)]
+    B = OCt(job.input(1, 0).export(), L, D)
+    (Ww, _, _), (Vw, _, _) = job.state_words()
+    W, V = OCt(Ww, L, D), OCt(Vw, L, D)
+    etas = qgnag.nag_scalars(2)
+    for t in range(2):
+        job.step(t)
+        Wn, Vn = circ.iteration(Z, B, W, V, qgnag.schedule(t), etas[t], 1.0 / data.n)
+        W, V = boot.bootstrap(he, Wn, p), boot.bootstrap(he, Vn, p)
+        (Ww, lw, sw), (Vw, _, _) = job.state_words()
+        assert (lw, sw) == (L, D)
+        assert np.array_equal(Ww, W.data), t
+        assert np.array_equal(Vw, V.data), t
+    wp = plain.train(data, 2)
+    assert np.abs(job.weights(0) - wp).max() < 1e-3
+    job.set_refresh(None)

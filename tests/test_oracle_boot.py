@@ -158,3 +158,35 @@ def test_bootstrap_refreshes_the_message(setup, amp):
     # and the refreshed ciphertext computes: one more product at level 1
     sq = he.rescale(he.mul(out, out))
     assert np.abs(he.decode(he.decrypt(sq)).real - z * z).max() < 2 * amp * tol + 1e-6 * amp * amp
+
+
+def test_training_with_bootstrapped_refresh_tracks_the_twin():
+    """The encrypted QG-NAG iteration with W and V refreshed by bootstrapping
+    (no decryption between iterations) on a bootstrappable chain at N = 2^12
+    (q0 50 bits, six 40-bit levels for the iteration, thirteen 55-bit levels
+    for the bootstrap): the decrypted weights after two iterations within
+    1e-3 of the FP64 plaintext run."""
+    from oracle import plain, qgnag
+    from paper_2406_13221_gb300 import synth
+    bits = [50] + [40] * 6 + [55] * 13
+    he = Ckks(12, len(bits), bits=bits, secret_weight=32)
+    X, y = synth.small(seed=17, n=1024, f=15)
+    data = qgnag.TrainData(X, y, g=16, m=128, batch_rows=1024)
+    circ = qgnag.Circuit(he, 16, 128, D)
+    p = boot.BootParams(n=16, K=12, r=5, deg=23, delta_out=D, out_level=circ.L)
+    rots, gals = boot.key_rotations(he, p)
+    he.keygen(2, sorted(set(circ.rotations()) | set(rots)), gals)
+    L = circ.L
+    Z = [he.encrypt(he.encode(data.blocks[b], L, D), 100 + b) for b in range(data.blocks.shape[0])]
+    B = he.encrypt(he.encode(np.tile(data.n * data.bbar_full, circ.m), L, D), 200)
+    W = he.encrypt(he.encode(np.zeros(he.nslots), L, D), 201)
+    V = he.encrypt(he.encode(np.zeros(he.nslots), L, D), 202)
+    etas = qgnag.nag_scalars(2)
+    for t in range(2):
+        Wn, Vn = circ.iteration(Z, B, W, V, qgnag.schedule(t), etas[t], 1.0 / data.n)
+        assert Wn.level == 0
+        W, V = boot.bootstrap(he, Wn, p), boot.bootstrap(he, Vn, p)
+        assert (W.level, W.scale) == (L, D)
+    w = he.decode(he.decrypt(W)).real.reshape(circ.m, circ.g)
+    wp = plain.train(data, 2)
+    assert np.abs(w[0] - wp).max() < 1e-3 and np.abs(w[-1] - wp).max() < 1e-3
