@@ -223,6 +223,23 @@ int he_ks_tile(const he_ctx *ctx, int level);
 /* Force the tile variant of every later key switch (0..3), or return to the
  * autotuned choice (-1); HE_EINVAL otherwise. */
 int he_set_ks_tile(he_ctx *ctx, int tile);
+/* Form of the hoisted inner product of rotation groups (he_rotsum,
+ * he_rotsum_batch and the rotate-and-sum steps of a training iteration,
+ * Sec. 2.2 / 3.3): 0 = CUDA cores (default); 1 = tensor cores (tcgen05.mma on
+ * FP16 byte slices of the digits and keys, exact: the sum over the group's
+ * rotations and digits is formed in 128 bits from the integer diagonal sums
+ * the MMA accumulates).  Form 1 applies at a key switch whose target primes
+ * q_0..q_(nl-1) are below 2^40, with rotations x limbs <= 51 and nl <= 8; the
+ * special prime's target and every other case keep the CUDA-core form.  Both
+ * forms give the same words.  HE_EINVAL for other values. */
+int he_set_hoist_form(he_ctx *ctx, int form);
+/* Launches of the tensor-core form made by ctx so far. */
+unsigned long long he_hoist_tensor_launches(const he_ctx *ctx);
+/* Synchronise the context stream and read the device status word: HE_OK, or
+ * HE_ETIMEOUT when a bounded device-side wait (the mbarrier waits of the
+ * tensor-core form, 1 s each) expired since the last call; the word is then
+ * cleared. */
+int he_check_device(he_ctx *ctx);
 /* Rescale without allocating (no counterpart in the paper: it exists for
  * callers that may not allocate device memory, such as code running under a
  * device-memory budget fixed in advance or inside a framework that owns every

@@ -114,6 +114,9 @@ SIGNATURES = {
     "he_rotsum_batch": (_i, [_vp, _vp, _vp, _i, _i, _vp, _sz]),
     "he_ks_tile": (_i, [_vp, _i]),
     "he_set_ks_tile": (_i, [_vp, _i]),
+    "he_set_hoist_form": (_i, [_vp, _i]),
+    "he_hoist_tensor_launches": (ctypes.c_ulonglong, [_vp]),
+    "he_check_device": (_i, [_vp]),
     "he_lr_job_free": (_i, [_vp]),
     "he_lr_multi_create": (_i, [_vp, _vp, _sz, _i, _pp]),
     "he_lr_multi_step": (_i, [_vp, _i, he_lr_sched]),
@@ -336,6 +339,17 @@ class Context:
 
     def set_ks_tile(self, tile):
         self.check(self.L.he_set_ks_tile(self.h, int(tile)))
+
+    def set_hoist_form(self, form):
+        """0: hoisted inner products on the CUDA cores; 1: on the tensor cores where they apply."""
+        self.check(self.L.he_set_hoist_form(self.h, int(form)))
+
+    def hoist_tensor_launches(self):
+        return int(self.L.he_hoist_tensor_launches(self.h))
+
+    def check_device(self):
+        """Raise HeError(HE_ETIMEOUT) if a bounded device-side wait expired."""
+        self.check(self.L.he_check_device(self.h))
 
     def ks_wave(self, level):
         w = self.L.he_ks_wave(self.h, int(level))

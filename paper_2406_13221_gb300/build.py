@@ -14,8 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhelr.so")
-UNITS = ["ntt.cu", "ks.cu", "ops.cu", "encode.cu", "eval.cu", "helr_ctx.cu", "helr_lr.cu", "noalloc.cu", "autotune.cu",
-         "boot.cu"]
+UNITS = ["ntt.cu", "ks.cu", "ks_tensor.cu", "ops.cu", "encode.cu", "eval.cu", "helr_ctx.cu", "helr_lr.cu", "noalloc.cu",
+         "autotune.cu", "boot.cu"]
 HEADERS = ["helr_internal.cuh", "ntt_core.cuh", os.path.join("..", "..", "include", "he_lr.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",

@@ -58,6 +58,27 @@ extern "C" int he_set_rotation_radix(he_ctx *c, int log2_radix)
     return HE_OK;
 }
 
+extern "C" int he_set_hoist_form(he_ctx *c, int form)
+{
+    if (!c) return HE_EINVAL;
+    if (form != 0 && form != 1) return helr_fail(c, HE_EINVAL, "hoisted inner-product form %d (0 or 1)", form);
+    c->hoist_form = form;
+    return HE_OK;
+}
+
+extern "C" unsigned long long he_hoist_tensor_launches(const he_ctx *c) { return c ? c->hoist_tensor_launches : 0; }
+
+extern "C" int he_check_device(he_ctx *c)
+{
+    if (!c) return HE_EINVAL;
+    int st = 0;
+    HELR_CUDA(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    HELR_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (st == 0) return HE_OK;
+    HELR_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    return helr_fail(c, HE_ETIMEOUT, "a bounded device-side wait expired (status %#x)", st);
+}
+
 extern "C" int he_prof_keyswitches(he_ctx *c, double *by_limbs, size_t n)
 {
     if (!c || !by_limbs) return HE_EINVAL;
@@ -357,6 +378,8 @@ static int ctx_init(he_ctx *c, const he_params *p)
     HELR_TRY(upload(c, (void **)&c->d_pinv, pinv.data(), pinv.size() * 8));
     HELR_TRY(helr_alloc(c, (void **)&c->d_sk, sizeof(uint64_t) * np * n));
     HELR_TRY(helr_alloc(c, (void **)&c->d_pk, sizeof(uint64_t) * 2 * nq * n));
+    HELR_TRY(helr_alloc(c, (void **)&c->d_status, sizeof(int)));
+    HELR_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
     c->h_sk = (int64_t *)calloc(n, sizeof(int64_t));
     HELR_CUDA(c, cudaStreamSynchronize(c->stream));
     return HE_OK;
@@ -404,7 +427,8 @@ extern "C" int he_ctx_destroy(he_ctx *c)
     cudaStreamSynchronize(c->stream);
     for (auto &p : c->prof.cls)
         for (auto e : p.ev) cudaEventDestroy(e);
-    void *ptrs[] = {c->t.mod, c->t.tw, c->t.itw, c->t.ninv, c->t.zeta, c->t.sidx, c->t.cdt, c->d_qinv, c->d_pinv, c->d_sk, c->d_pk};
+    void *ptrs[] = {c->t.mod, c->t.tw, c->t.itw, c->t.ninv, c->t.zeta, c->t.sidx, c->t.cdt, c->d_qinv, c->d_pinv, c->d_sk, c->d_pk,
+                    c->d_status};
     for (void *p : ptrs) helr_free(c, p);
     for (auto &k : c->ksk) helr_free(c, k.d);
     cudaStreamSynchronize(c->stream);

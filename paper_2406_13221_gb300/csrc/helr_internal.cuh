@@ -225,6 +225,9 @@ struct he_ctx {
     int ks_tile_tab[HELR_MAXQ + 1] = {};  // tile variant per limb count chosen by he_autotune
     int rot_radix_log = 3;         // rotate-and-sum steps as hoisted groups of 2^rot_radix_log positions
     int secret_hw = 0;             // 0: dense ternary secret; h > 0: exactly h nonzero coefficients
+    int hoist_form = 0;            // hoisted inner product: 0 CUDA cores, 1 tensor cores where it applies
+    unsigned long long hoist_tensor_launches = 0;
+    int *d_status = nullptr;       // device failure bits (bit 0: a bounded wait expired), he_check_device
 };
 
 struct he_ct {
@@ -381,6 +384,13 @@ int helr_keyswitch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, 
 // item (helr_ctx.cu); hk lists the keys and Galois elements.
 int helr_rotsum(he_ctx *c, const uint64_t *a, size_t a_item, int batch, int level, const HoistKeys &hk, KsScratch *ws,
                 Str out);
+// The hoisted inner product of a group on the tensor cores (ks_tensor.cu):
+// whether it applies at nl limbs with nrot rotations and to which targets
+// [t_lo, t_hi) (a run of primes below 2^40), and its launch for them (acc as
+// for k_ks_hoist_ip).
+bool helr_hoist_tensor_range(const he_ctx *c, int nl, int nrot, int *t_lo, int *t_hi);
+int helr_hoist_ip_tensor(he_ctx *c, const uint64_t *mid, const uint64_t *dntt, size_t din_item, const HoistKeys &hk,
+                         uint64_t *acc, int items, int nl, int t_lo, int t_hi, cudaStream_t s);
 // ModUp of the input's digits, their full forward transforms and the summed
 // inner products of every rotation of hk (ks.cu): dntt = second polynomials in
 // evaluation form (item stride din_item), drow = the same after the inverse row

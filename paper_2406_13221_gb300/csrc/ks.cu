@@ -110,17 +110,6 @@ __global__ void __launch_bounds__(C * Geo<K1>::T, 3)
     }
 }
 
-// sigma_gal on the evaluation form: position k holds the evaluation at
-// psi^(2 bitrev(k) + 1), so sigma_gal(x) takes at k the value x holds at the
-// position of psi^((2 bitrev(k) + 1) gal).  The product is needed modulo 2N
-// only, so 32-bit arithmetic suffices.
-template <int LOGN>
-__device__ __forceinline__ uint32_t auto_pos(uint32_t k, uint64_t gal)
-{
-    const uint32_t kk = __brev(k) >> (32 - LOGN);
-    const uint32_t e = ((2u * kk + 1u) * (uint32_t)gal) & ((2u << LOGN) - 1u);
-    return __brev((e - 1u) >> 1) >> (32 - LOGN);
-}
 
 // bulk prefetch of `bytes` (a multiple of 16) from a 16-byte aligned global
 // address into L2 (no data returned to the thread)
@@ -228,12 +217,6 @@ __device__ __forceinline__ void set128(uint32_t *acc, uint64_t x, uint64_t k)
     acc[1] = (uint32_t)(lo >> 32);
     acc[2] = (uint32_t)hi;
     acc[3] = (uint32_t)(hi >> 32);
-}
-// Montgomery reduction of T = hi 2^64 + lo: T 2^-64 mod q, for hi < q.
-__device__ __forceinline__ uint64_t redc128(uint64_t hi, uint64_t lo, const ModQ &m)
-{
-    const uint64_t mh = __umul64hi(lo * m.qinv, m.q);
-    return hi >= mh ? hi - mh : hi - mh + m.q;
 }
 
 // One launch per butterfly form: `tl` lists the targets t (0..nl, nl standing
@@ -549,7 +532,7 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
 // and above) or x < 20q (below 2^58; helr_rotsum refuses chains where that
 // could reach 2^128).
 // grid: items (fastest: the items of a wave share each key row through L2) *
-// (nl + 1) targets * (R1 / RPC).
+// (nl + 1 - t0) targets t0..nl * (R1 / RPC).
 template <int K1, int K2>
 struct HoistGeo {
     static constexpr int R1 = 1 << K1, R2 = 1 << K2;
@@ -660,7 +643,7 @@ __device__ __forceinline__ void hoist_ip_body(const uint64_t *__restrict__ mid, 
 template <int K1, int K2>
 __global__ void __launch_bounds__(HoistGeo<K1, K2>::THREADS, 3)
     k_ks_hoist_ip(const uint64_t *__restrict__ mid, const uint64_t *__restrict__ dntt, size_t din_item, HoistKeys hk,
-                  uint64_t *__restrict__ acc, const ModQ *__restrict__ mods, int nl, int nq, int pidx, int items)
+                  uint64_t *__restrict__ acc, const ModQ *__restrict__ mods, int nl, int nq, int pidx, int items, int t0)
 {
     using H = HoistGeo<K1, K2>;
     constexpr int R1 = 1 << K1, NG = R1 / H::RPC;
@@ -668,7 +651,7 @@ __global__ void __launch_bounds__(HoistGeo<K1, K2>::THREADS, 3)
     const int b = bid % items;
     bid /= items;
     const int grp = bid % NG;
-    const int t = bid / NG;  // target 0..nl (nl = P)
+    const int t = t0 + bid / NG;  // target t0..nl (nl = P)
     const int pt = t < nl ? t : pidx, kl = t < nl ? t : nq;
     const ModQ m = mods[pt];
     const int row = grp * H::RPC + threadIdx.x / H::TPR;
@@ -719,8 +702,8 @@ struct KsPlan {
                                                                                       c->t.ninv, nl, c->nq, src_prime));
     }
     // hoisted rotations: row passes of the lifted digits, then the summed inner products
-    static void hoisted(he_ctx *c, const uint64_t *dntt, size_t din_item, uint64_t *mid, const HoistKeys &hk, uint64_t *acc,
-                        int items, int nl, cudaStream_t s)
+    static int hoisted(he_ctx *c, const uint64_t *dntt, size_t din_item, uint64_t *mid, const HoistKeys &hk, uint64_t *acc,
+                       int items, int nl, cudaStream_t s)
     {
         if (helr_ks_tile(c, nl) & 2) {
             const unsigned g1 = (unsigned)((size_t)items * nl * nl * (R1 / RB));
@@ -729,10 +712,20 @@ struct KsPlan {
             const unsigned g1 = (unsigned)((size_t)items * nl * nl * (R1 / RPCD));
             HELR_LAUNCH(k_ks_digit_rows<K1, K2, RPCD><<<g1, RPCD * T2, SMD, s>>>(mid, c->t.tw, c->t.mod, nl, c->nq));
         }
+        // the tensor-core form takes the run of 40-bit targets [a, b) where it
+        // applies; the CUDA cores take targets [0, a) and [b, nl] (nl = P)
         using H = HoistGeo<K1, K2>;
-        const unsigned g2 = (unsigned)((size_t)items * (nl + 1) * (R1 / H::RPC));
-        HELR_LAUNCH(k_ks_hoist_ip<K1, K2><<<g2, H::THREADS, 0, s>>>(mid, dntt, din_item, hk, acc, c->t.mod, nl, c->nq, c->nq,
-                                                                    items));
+        int a = nl + 1, b = nl + 1;
+        if (c->hoist_form == 1 && helr_hoist_tensor_range(c, nl, hk.n, &a, &b))
+            HELR_TRY(helr_hoist_ip_tensor(c, mid, dntt, din_item, hk, acc, items, nl, a, b, s));
+        const int runs[2][2] = {{0, a}, {b, nl + 1}};
+        for (const auto &r : runs)
+            if (r[1] > r[0]) {
+                const unsigned g2 = (unsigned)((size_t)items * (r[1] - r[0]) * (R1 / H::RPC));
+                HELR_LAUNCH(k_ks_hoist_ip<K1, K2><<<g2, H::THREADS, 0, s>>>(mid, dntt, din_item, hk, acc, c->t.mod, nl,
+                                                                            c->nq, c->nq, items, r[0]));
+            }
+        return HE_OK;
     }
     static void down(he_ctx *c, const KsOut &o, const uint64_t *src, size_t src_item, size_t src_poly, const uint64_t *lift,
                      int items, int nl, const uint64_t *inv, cudaStream_t s)
@@ -849,7 +842,7 @@ int run_hoisted(he_ctx *c, const uint64_t *dntt, size_t din_item, const uint64_t
     const int l1 = KsPlan<K1, K2>::modup(c, drow, mid, items, nl, s);
     prof_stop(c, PROF_MODUP, s, (double)items * nl * nl, l1, (double)items * nl, (double)items * nl * (nl + 1));
     prof_start(c, PROF_KS_INNER, s);
-    KsPlan<K1, K2>::hoisted(c, dntt, din_item, mid, hk, acc, items, nl, s);
+    HELR_TRY((KsPlan<K1, K2>::hoisted(c, dntt, din_item, mid, hk, acc, items, nl, s)));
     // row passes of the nl x nl lifted digits; products: rotations x 2 keys x nl digits x (nl + 1) targets;
     // DRAM: digit rows read and written once, read once per rotation (gathers), keys once per launch, acc written
     prof_stop(c, PROF_KS_INNER, s, (double)items * nl * nl, 2, (double)items * hk.n * 2 * nl * (nl + 1),

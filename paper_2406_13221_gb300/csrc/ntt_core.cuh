@@ -193,3 +193,22 @@ __device__ __forceinline__ void to_contig_swz(uint64_t (&x)[Geo<K>::E], uint64_t
 }
 
 }  // namespace nttc
+
+// sigma_gal on the evaluation form: position k holds the evaluation at
+// psi^(2 bitrev(k) + 1), so sigma_gal(x) takes at k the value x holds at the
+// position of psi^((2 bitrev(k) + 1) gal).  The product is needed modulo 2N
+// only, so 32-bit arithmetic suffices.
+template <int LOGN>
+__device__ __forceinline__ uint32_t auto_pos(uint32_t k, uint64_t gal)
+{
+    const uint32_t kk = __brev(k) >> (32 - LOGN);
+    const uint32_t e = ((2u * kk + 1u) * (uint32_t)gal) & ((2u << LOGN) - 1u);
+    return __brev((e - 1u) >> 1) >> (32 - LOGN);
+}
+
+// Montgomery reduction of T = hi 2^64 + lo: T 2^-64 mod q, for hi < q.
+__device__ __forceinline__ uint64_t redc128(uint64_t hi, uint64_t lo, const ModQ &m)
+{
+    const uint64_t mh = __umul64hi(lo * m.qinv, m.q);
+    return hi >= mh ? hi - mh : hi - mh + m.q;
+}

@@ -88,6 +88,36 @@ def test_hoisted_rotation_sums_256_items(bench_pair):
         assert np.array_equal(got[b], ref.data), (b, wave)
 
 
+def test_hoisted_rotation_sums_256_items_tensor_form(bench_pair):
+    """The same sums with the inner product on the tensor cores
+    (he_set_hoist_form(1)): items at both ends of each 128-item tile of the
+    first wave and the last item equal the oracle's hoisted rotation sum."""
+    ctx, he = bench_pair
+    batch, n, level = 256, ctx.n, 5
+    rots = list(range(1, 8))
+    rng = np.random.default_rng(78)
+    cts = np.empty((batch, 2, level + 1, n), np.uint64)
+    for j in range(level + 1):
+        cts[:, :, j, :] = rng.integers(0, he.q[j], (batch, 2, n), dtype=np.uint64)
+    dev = torch.from_numpy(cts.reshape(-1).view(np.int64)).cuda()
+    ctx.ntt_forward(dev.data_ptr(), batch * 2 * (level + 1), list(range(level + 1)))
+    out = torch.zeros_like(dev)
+    n0 = ctx.hoist_tensor_launches()
+    ctx.set_hoist_form(1)
+    try:
+        ctx.rotsum_batch(dev.data_ptr(), out.data_ptr(), batch, level, rots)
+    finally:
+        ctx.set_hoist_form(0)
+    ctx.check_device()
+    assert ctx.hoist_tensor_launches() > n0
+    ctx.ntt_inverse(out.data_ptr(), batch * 2 * (level + 1), list(range(level + 1)))
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint64).reshape(batch, 2, level + 1, n)
+    for b in (0, 127, 128, batch - 1):
+        ref = he.rotsum(OCt(cts[b], level, D), rots)
+        assert np.array_equal(got[b], ref.data), b
+
+
 def test_block_gradients_300_blocks_256_per_launch(bench_pair):
     """A 300-block job at 256 blocks per launch (a full chunk, then a ragged
     chunk of 44): the gradient ciphertexts of Steps 1-6 for blocks 0, 128, 255
