@@ -63,8 +63,9 @@ def parse():
                     help="bracket the timed steps with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     ap.add_argument("--sweep-point", default="", help="log_n,limbs,batch: run only this NTT sweep point")
     ap.add_argument("--ks-point", default="",
-                    help="level,items,kind (kind relin or rot7): one batched key switch or hoisted rotation sum at "
-                         "N=2^16, the full chain, timed (profiling entry)")
+                    help="level,items,kind (kind relin, rot7, or rot7tc with the inner product on the tensor "
+                         "cores): one batched key switch or hoisted rotation sum at N=2^16, the full chain, timed "
+                         "(profiling entry)")
     ap.add_argument("--sweep", action="store_true",
                     help="HE primitive sweep: batched NTT and key switching vs N, limbs and batch (JSON line per point)")
     return ap.parse_args()
@@ -267,10 +268,11 @@ def run_ours(args, rank, world):
     roof = roofline(prof, ks_prof, ks_by_limbs, args.steps, ms_max / 1000.0 / args.steps, props.multi_processor_count,
                     sm_mhz)
     ntt = standalone_ntt(ctx)
-    psweep = k4 = images = None
+    psweep = k4 = hoist_tc = images = None
     if not args.no_sweep:
         psweep = primitive_sweep(ctx)
         k4 = k4_tensor_floor(ctx)
+        hoist_tc = hoist_forms(ctx)
     if world == 1 and not args.no_images:
         images = image_pair_time(ctx, args)
     booted = None
@@ -304,6 +306,7 @@ def run_ours(args, rank, world):
         "ntt_hbm_frac": ntt["hbm_frac"],
         "primitive_sweep": psweep,
         "k4_tensor_ntt": k4,
+        "hoist_ip_tensor_cores": hoist_tc,
         "image_pair_g16": images,
         "bootstrapped_refresh": booted,
         "plain_one_ct_per_launch_s_per_iter": round(plain, 4) if plain else None,
@@ -546,7 +549,11 @@ def ks_point(args):
     level, items = int(level), int(items)
     ctx = binding.Context(LOGN, NQ)
     ctx.keygen(2, list(range(1, 8)))
+    if kind.endswith("tc"):  # hoisted inner product on the tensor cores
+        kind = kind[:-2]
+        ctx.set_hoist_form(1)
     sec, rate = ks_primitive(ctx, level, items, kind)
+    ctx.check_device()
     print(json.dumps({"ks_point": kind, "log_n": LOGN, "limbs": level + 1, "items": items, "s_per_call": round(sec, 6),
                       "keyswitch_per_s": round(rate, 1)}), flush=True)
     ctx.close()
@@ -636,6 +643,51 @@ def k4_tensor_floor(ctx, limbs=64, reps=5):
             if name == "tf32_to_fp32":
                 torch.backends.cuda.matmul.allow_tf32 = prev
         del A, B, Ad, Bd
+    return out
+
+
+def hoist_forms(ctx, items=128, reps=5):
+    """The two forms of the hoisted inner product on the bench's rotation
+    groups: he_rotsum_batch of `items` ciphertexts with the 7 rotations of one
+    hoisted group (1..7) at 6 and at 4 limbs, with the inner product on the CUDA
+    cores (the default) and on the tensor cores (he_set_hoist_form(1):
+    tcgen05.mma on FP16 byte slices of digits and keys, exact, for the 40-bit
+    targets).  Seconds per call of each, whether their output words are equal,
+    and whether the tensor-core kernel ran."""
+    import torch
+    n = 1 << LOGN
+    rots = list(range(1, 8))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    for level in (5, 3):
+        nl = level + 1
+        din = torch.randint(0, 1 << 30, (items * 2 * nl * n,), dtype=torch.int64, device="cuda")
+        rec = {"limbs": nl, "items": items, "rotations": len(rots)}
+        res = []
+        for form, name in ((0, "cuda_cores"), (1, "tensor_cores")):
+            dout = torch.zeros_like(din)
+            ctx.set_hoist_form(form)
+            try:
+                n0 = ctx.hoist_tensor_launches()
+                ctx.rotsum_batch(din.data_ptr(), dout.data_ptr(), items, level, rots)
+                torch.cuda.synchronize()
+                ran = ctx.hoist_tensor_launches() > n0
+                e0.record()
+                for _ in range(reps):
+                    ctx.rotsum_batch(din.data_ptr(), dout.data_ptr(), items, level, rots)
+                e1.record()
+                torch.cuda.synchronize()
+            finally:
+                ctx.set_hoist_form(0)
+            ctx.check_device()
+            rec[name + "_s_per_call"] = round(e0.elapsed_time(e1) / 1000.0 / reps, 6)
+            if form == 1:
+                rec["tensor_kernel_ran"] = bool(ran)
+            res.append(dout)
+        rec["words_equal"] = bool(torch.equal(res[0], res[1]))
+        rec["tensor_vs_cuda_cores"] = round(rec["tensor_cores_s_per_call"] / rec["cuda_cores_s_per_call"], 3)
+        out.append(rec)
+        del din, res
     return out
 
 
