@@ -236,11 +236,14 @@ __device__ __forceinline__ void set128(uint32_t *acc, uint64_t x, uint64_t k)
 // copies those of its rows into shared memory once and serves every digit from
 // there.  One digit buffer (the next digit's rows are requested as soon as the
 // exchange has read the current ones) keeps the CTA at 48 KB, 4 CTAs per SM.
+// A digit's rows are one contiguous tile, copied by the TMA engine
+// (cp.async.bulk, one thread, completion counted in bytes on an mbarrier);
+// the wait for it is bounded (1 s) and sets bit 1 of *status when it expires.
 template <int K1, int K2, int RPC, bool LZ>
 __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
     k_ks_inner_rows(const uint64_t *__restrict__ mid, const uint64_t *__restrict__ dntt, const uint64_t *__restrict__ key,
                     uint64_t *__restrict__ acc, const uint64_t *__restrict__ twall, const ModQ *__restrict__ mods, int nl,
-                    int nq, int pidx, int items, PosList tl)
+                    int nq, int pidx, int items, PosList tl, int *status)
 {
     using G = Geo<K2>;
     constexpr int R1 = 1 << K1, R2 = G::R, N = R1 * R2, NG = R1 / RPC, E = G::E, NT = RPC * G::T;
@@ -270,16 +273,25 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
     auto src_of = [&](int i) -> const uint64_t * {
         return i == t ? dntt + ((size_t)b * nl + i) * N + toff : mid + (((size_t)b * nl + i) * (nl + 1) + t) * N + toff;
     };
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tws + 2 * RPC * R2);
+    const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(tws + 2 * RPC * R2 + 1);
+    // the whole tile of digit i (TILE words, 16-byte aligned on both sides)
     auto prefetch = [&](int i, uint64_t *dst) {
-        const uint64_t *src = src_of(i);
-#pragma unroll
-        for (int k = 0; k < TILE / 2 / NT; k++) {
-            const int w = 2 * (threadIdx.x + k * NT);
-            cp_async16(dst + w, src + w);
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(TILE * 8)
+                         : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             (uint32_t)__cvta_generic_to_shared(dst)),
+                         "l"(src_of(i)), "r"(TILE * 8), "r"(mbar)
+                         : "memory");
         }
     };
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tws + 2 * RPC * R2);
     if (warp == 0) tmem_alloc(tmem_slot, TCOLS);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     prefetch(0, buf);
     // pair j of stage block m of row r sits at m (R1 + r) + j in the table
     for (int k = threadIdx.x; k < RPC * R2; k += NT) {
@@ -298,8 +310,10 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
     const uint64_t *twr = tws + 2 * (rl * R2 - 1);
     uint64_t *o0 = acc + (((size_t)b * 2 + 0) * (nl + 1) + t) * N + roff + E * l;
     uint64_t *o1 = acc + (((size_t)b * 2 + 1) * (nl + 1) + t) * N + roff + E * l;
+    bool ok = true;
     for (int i = 0; i < nl; i++) {
-        cp_async_wait<0>();  // digit i (and, for i = 0, the twiddles) have landed
+        if (i == 0) cp_async_wait<0>();          // the twiddles have landed
+        ok &= mbar_wait_bounded(mbar, i & 1);  // and digit i
         __syncthreads();
         uint64_t x[E];
         uint64_t *rows = buf + rl * R2;
@@ -315,7 +329,6 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
         }
         __syncthreads();  // the buffer is read: it takes the next digit
         if (i + 1 < nl) prefetch(i + 1, buf);
-        cp_async_commit();
         if (i != t) {
             fwd_contig<K2, true, LZ, true>(x, twr, 1, l, q, q2);
             // words stay unreduced: below 4q, or below 20q with LZ (the column
@@ -381,6 +394,7 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
             }
         }
     }
+    if (!ok) atomicOr(status, 2);
     tmem_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -398,7 +412,7 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
 // src limb j of polynomial p of item b: src + b src_item + p src_poly + j N.
 // grid: items * 2 polys * nl limbs * (R1 / RPC).
 template <int K1, int K2, int RPC>
-__global__ void __launch_bounds__(RPC * Geo<K2>::T)
+__global__ void __launch_bounds__(RPC * Geo<K2>::T, 768 / (RPC * Geo<K2>::T))
     k_ks_down_rows(KsOut o, const uint64_t *__restrict__ srcp, size_t src_item, size_t src_poly,
                    const uint64_t *__restrict__ lift, const uint64_t *__restrict__ twall, const ModQ *__restrict__ mods,
                    const uint64_t *__restrict__ inv, int nl)
@@ -444,19 +458,31 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T)
     // Harvey's butterflies), the Shoup product < 2q, each added term < q (rel,
     // acc and up to HELR_MAX_HOIST rotation terms): the sum stays below
     // (4 + 7) q < 2^64 for primes below 2^60
+    const size_t rowk = (size_t)j * N + (size_t)row * R2 + l;
 #pragma unroll
     for (int r = 0; r < E; r++) {
-        const int k = row * R2 + l + T * r;
-        const size_t lk = (size_t)j * N + k;
-        uint64_t v = shoup_lazy(sv[lk] + (q4 - x[r]), pv, pvp, q);
-        if (o.rel) v += o.rel[bt * o.rel_item + p * o.rel_poly + lk];
-        if (o.rot && p == 0) {
+        uint64_t v = shoup_lazy(sv[rowk + T * r] + (q4 - x[r]), pv, pvp, q);
+        if (o.rel) v += o.rel[bt * o.rel_item + p * o.rel_poly + rowk + T * r];
+        x[r] = v;
+    }
+    if (o.rot && p == 0) {
+        // one rotation at a time: the CTA's reads of a rotation stay within the
+        // source rows of its own rows, so L1 serves the repeated lines
+        const uint64_t *rot = o.rot + bt * o.rot_item + (size_t)j * N;
+        for (int g = 0; g < o.ngal; g++) {
+            uint64_t gal = o.gals[0];
 #pragma unroll
-            for (int g = 0; g < HELR_MAX_HOIST; g++)
-                if (g < o.ngal) v += o.rot[bt * o.rot_item + (size_t)j * N + auto_pos<LOGN>((uint32_t)k, o.gals[g])];
+            for (int x2 = 1; x2 < HELR_MAX_HOIST; x2++)
+                if (x2 == g) gal = o.gals[x2];
+#pragma unroll
+            for (int r = 0; r < E; r++) x[r] += rot[auto_pos<LOGN>((uint32_t)(row * R2 + l + T * r), gal)];
         }
-        if (o.acc) v += o.acc[bt * o.acc_item + p * o.acc_poly + lk];
-        o.out.p[bt * o.out.item + p * o.out.poly + lk] = reduce64(v, mq);
+    }
+#pragma unroll
+    for (int r = 0; r < E; r++) {
+        uint64_t v = x[r];
+        if (o.acc) v += o.acc[bt * o.acc_item + p * o.acc_poly + rowk + T * r];
+        o.out.p[bt * o.out.item + p * o.out.poly + rowk + T * r] = reduce64(v, mq);
     }
 }
 
@@ -774,10 +800,10 @@ struct KsPlan {
             const unsigned grid = (unsigned)((size_t)items * tl.n * (R1 / RPC));
             if (lz)
                 HELR_LAUNCH(k_ks_inner_rows<K1, K2, RPC, true><<<grid, RPC * T2, SM2, s>>>(mid, dntt, key, acc, c->t.tw, c->t.mod,
-                                                                                        nl, c->nq, c->nq, items, tl));
+                                                                                        nl, c->nq, c->nq, items, tl, c->d_status));
             else
                 HELR_LAUNCH(k_ks_inner_rows<K1, K2, RPC, false><<<grid, RPC * T2, SM2, s>>>(mid, dntt, key, acc, c->t.tw, c->t.mod,
-                                                                                         nl, c->nq, c->nq, items, tl));
+                                                                                         nl, c->nq, c->nq, items, tl, c->d_status));
             launches++;
         }
         return launches;

@@ -92,23 +92,6 @@ __device__ __forceinline__ void cp16(uint32_t dst, const void *src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity)
-{
-    uint64_t t0;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-    for (;;) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done)
-                     : "r"(mb), "r"(parity)
-                     : "memory");
-        if (done) return true;
-        uint64_t t1;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
-        if (t1 - t0 > 1000000000ull) return false;
-    }
-}
 __device__ __forceinline__ void tmem_st4(uint32_t ta, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
 {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta), "r"(a), "r"(b), "r"(c),
@@ -289,7 +272,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (r >= 2) {
             // the MMAs of round r - 2 have read buffers rb; a group whose last
             // rotation that was is complete in TMEM
-            ok &= mbar_wait(mb0 + 8 * rb, (uint32_t)((r - 2) >> 1) & 1u);
+            ok &= mbar_wait_bounded(mb0 + 8 * rb, (uint32_t)((r - 2) >> 1) & 1u);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if ((r - 2) % nrot == nrot - 1) epilogue((r - 2) / nrot);
         }
@@ -375,7 +358,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     }
     for (int r = R >= 2 ? R - 2 : 0; r < R; r++) {
-        ok &= mbar_wait(mb0 + 8 * (r & 1), (uint32_t)(r >> 1) & 1u);
+        ok &= mbar_wait_bounded(mb0 + 8 * (r & 1), (uint32_t)(r >> 1) & 1u);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (r % nrot == nrot - 1) epilogue(r / nrot);
     }

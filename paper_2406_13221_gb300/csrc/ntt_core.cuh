@@ -212,3 +212,23 @@ __device__ __forceinline__ uint64_t redc128(uint64_t hi, uint64_t lo, const ModQ
     const uint64_t mh = __umul64hi(lo * m.qinv, m.q);
     return hi >= mh ? hi - mh : hi - mh + m.q;
 }
+
+// Wait for phase `parity` of the mbarrier at shared address mb, for at most
+// one second of the global timer; false when the wait expired.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mb, uint32_t parity)
+{
+    uint64_t t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(mb), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        uint64_t t1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+        if (t1 - t0 > 1000000000ull) return false;
+    }
+}
