@@ -556,17 +556,9 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 3)
 // the columns they stand for.  Sums are exact in 128 bits and reduced once:
 // at most HELR_MAX_HOIST * nl terms x k with k < q and x < q (primes of 2^58
 // and above) or x < 20q (below 2^58; helr_rotsum refuses chains where that
-// could reach 2^128).
-// grid: items (fastest: the items of a wave share each key row through L2) *
-// (nl + 1 - t0) targets t0..nl * (R1 / RPC).
-template <int K1, int K2>
-struct HoistGeo {
-    static constexpr int R1 = 1 << K1, R2 = 1 << K2;
-    static constexpr int TPR = R2 < 64 ? R2 : 64;                   // threads per row
-    static constexpr int PPT = R2 / TPR;                            // positions per thread
-    static constexpr int RPC = (256 / TPR) < R1 ? (256 / TPR) : R1; // rows per CTA
-    static constexpr int THREADS = RPC * TPR;
-};
+// could reach 2^128).  A thread computes items b and b + 1 at the same
+// positions, so every key word it loads serves both items.
+//
 // 128-bit sum of products x k for primes below 2^41 (x < 2^47, k < 2^41)
 // without 64 x 64-bit products: with x = xh 2^32 + xl and k = kh 2^32 + kl,
 // A (+ carries cA 2^64) sums xl kl and B sums xl kh + xh kl + xh kh 2^32 (each
@@ -593,10 +585,20 @@ __device__ __forceinline__ uint64_t redc40(const Acc40 &a, const ModQ &m)
     return redc128(hi, lo, m);
 }
 
+// grid: ceil(items / 2) item pairs (fastest: the items of a wave share each
+// key row through L2) * (nl + 1 - t0) targets t0..nl * (R1 / RPC).
+template <int K1, int K2>
+struct HoistGeo {
+    static constexpr int R1 = 1 << K1, R2 = 1 << K2;
+    static constexpr int TPR = R2 / 2 < 128 ? R2 / 2 : 128;          // threads per row
+    static constexpr int PPT = R2 / TPR;                             // positions per thread and item
+    static constexpr int RPC = (256 / TPR) < R1 ? (256 / TPR) : R1;  // rows per CTA
+    static constexpr int THREADS = RPC * TPR;
+};
 template <int K1, int K2, bool F40>
 __device__ __forceinline__ void hoist_ip_body(const uint64_t *__restrict__ mid, const uint64_t *__restrict__ dntt,
-                                              size_t din_item, const HoistKeys &hk, uint64_t *__restrict__ acc,
-                                              const ModQ &m, int nl, int nq, int b, int t, int kl, int row)
+                                               size_t din_item, const HoistKeys &hk, uint64_t *__restrict__ acc,
+                                               const ModQ &m, int nl, int nq, int b0, bool two, int t, int kl, int row)
 {
     using G = Geo<K2>;
     using H = HoistGeo<K1, K2>;
@@ -604,24 +606,24 @@ __device__ __forceinline__ void hoist_ip_body(const uint64_t *__restrict__ mid, 
     constexpr int TPR = H::TPR, PPT = H::PPT;
     const int u = threadIdx.x % TPR;
     const size_t roff = (size_t)row * R2;
+    const int b1 = two ? b0 + 1 : b0;
     int col[PPT];
 #pragma unroll
     for (int mm = 0; mm < PPT; mm++) {
         const int p = u + TPR * mm;
         col[mm] = G::E * (p % G::T) + p / G::T;
     }
-    // accumulators of both key polynomials: 32-bit products only (F40), else 64 x 64-bit
-    Acc40 f0[PPT], f1[PPT];
-    uint32_t a0[PPT][4], a1[PPT][4];
+    Acc40 f0[2][PPT], f1[2][PPT];
+    uint32_t a0[2][PPT][4], a1[2][PPT][4];
 #pragma unroll
-    for (int mm = 0; mm < PPT; mm++) {
-        f0[mm] = f1[mm] = Acc40{0, 0, 0};
+    for (int it = 0; it < 2; it++)
 #pragma unroll
-        for (int w = 0; w < 4; w++) a0[mm][w] = a1[mm][w] = 0;
-    }
+        for (int mm = 0; mm < PPT; mm++) {
+            f0[it][mm] = f1[it][mm] = Acc40{0, 0, 0};
+#pragma unroll
+            for (int w = 0; w < 4; w++) a0[it][mm][w] = a1[it][mm][w] = 0;
+        }
     for (int j = 0; j < hk.n; j++) {
-        // an unrolled select: a dynamic index into the parameter arrays would
-        // move them into local memory
         const uint64_t *key = hk.key[0];
         uint64_t gal = hk.gal[0];
 #pragma unroll
@@ -631,37 +633,49 @@ __device__ __forceinline__ void hoist_ip_body(const uint64_t *__restrict__ mid, 
 #pragma unroll
         for (int mm = 0; mm < PPT; mm++) ps[mm] = auto_pos<LOGN>((uint32_t)(roff + col[mm]), gal);
         for (int i = 0; i < nl; i++) {
-            const uint64_t *src = i == t ? dntt + (size_t)b * din_item + (size_t)i * N
-                                         : mid + (((size_t)b * nl + i) * (nl + 1) + t) * N;
+            const uint64_t *s0 = i == t ? dntt + (size_t)b0 * din_item + (size_t)i * N
+                                        : mid + (((size_t)b0 * nl + i) * (nl + 1) + t) * N;
+            const uint64_t *s1 = i == t ? dntt + (size_t)b1 * din_item + (size_t)i * N
+                                        : mid + (((size_t)b1 * nl + i) * (nl + 1) + t) * N;
             const uint64_t *k0 = key + (((size_t)i * 2 + 0) * (nq + 1) + kl) * N + roff + u;
             const uint64_t *k1 = key + (((size_t)i * 2 + 1) * (nq + 1) + kl) * N + roff + u;
 #pragma unroll
             for (int mm = 0; mm < PPT; mm++) {
-                const uint64_t x = __ldg(src + ps[mm]);
+                const uint64_t x0 = __ldg(s0 + ps[mm]), x1 = __ldg(s1 + ps[mm]);
+                const uint64_t ka = ld_stream(k0 + TPR * mm), kb = ld_stream(k1 + TPR * mm);
                 if constexpr (F40) {
-                    mac40(f0[mm], x, ld_stream(k0 + TPR * mm));
-                    mac40(f1[mm], x, ld_stream(k1 + TPR * mm));
+                    mac40(f0[0][mm], x0, ka);
+                    mac40(f1[0][mm], x0, kb);
+                    mac40(f0[1][mm], x1, ka);
+                    mac40(f1[1][mm], x1, kb);
                 } else {
-                    mac128(a0[mm], x, ld_stream(k0 + TPR * mm));
-                    mac128(a1[mm], x, ld_stream(k1 + TPR * mm));
+                    mac128(a0[0][mm], x0, ka);
+                    mac128(a1[0][mm], x0, kb);
+                    mac128(a0[1][mm], x1, ka);
+                    mac128(a1[1][mm], x1, kb);
                 }
             }
         }
     }
-    uint64_t *o0 = acc + (((size_t)b * 2 + 0) * (nl + 1) + t) * N + roff;
-    uint64_t *o1 = acc + (((size_t)b * 2 + 1) * (nl + 1) + t) * N + roff;
 #pragma unroll
-    for (int mm = 0; mm < PPT; mm++) {
-        if constexpr (F40) {
-            o0[col[mm]] = redc40(f0[mm], m);
-            o1[col[mm]] = redc40(f1[mm], m);
-        } else {
-            uint64_t h0 = ((uint64_t)a0[mm][3] << 32) | a0[mm][2];
-            uint64_t h1 = ((uint64_t)a1[mm][3] << 32) | a1[mm][2];
-            h0 = h0 >= m.q ? reduce64(h0, m) : h0;
-            h1 = h1 >= m.q ? reduce64(h1, m) : h1;
-            o0[col[mm]] = redc128(h0, ((uint64_t)a0[mm][1] << 32) | a0[mm][0], m);
-            o1[col[mm]] = redc128(h1, ((uint64_t)a1[mm][1] << 32) | a1[mm][0], m);
+    for (int it = 0; it < 2; it++) {
+        if (it == 1 && !two) break;
+        const int b = b0 + it;
+        uint64_t *o0 = acc + (((size_t)b * 2 + 0) * (nl + 1) + t) * N + roff;
+        uint64_t *o1 = acc + (((size_t)b * 2 + 1) * (nl + 1) + t) * N + roff;
+#pragma unroll
+        for (int mm = 0; mm < PPT; mm++) {
+            if constexpr (F40) {
+                o0[col[mm]] = redc40(f0[it][mm], m);
+                o1[col[mm]] = redc40(f1[it][mm], m);
+            } else {
+                uint64_t h0 = ((uint64_t)a0[it][mm][3] << 32) | a0[it][mm][2];
+                uint64_t h1 = ((uint64_t)a1[it][mm][3] << 32) | a1[it][mm][2];
+                h0 = h0 >= m.q ? reduce64(h0, m) : h0;
+                h1 = h1 >= m.q ? reduce64(h1, m) : h1;
+                o0[col[mm]] = redc128(h0, ((uint64_t)a0[it][mm][1] << 32) | a0[it][mm][0], m);
+                o1[col[mm]] = redc128(h1, ((uint64_t)a1[it][mm][1] << 32) | a1[it][mm][0], m);
+            }
         }
     }
 }
@@ -669,22 +683,24 @@ __device__ __forceinline__ void hoist_ip_body(const uint64_t *__restrict__ mid, 
 template <int K1, int K2>
 __global__ void __launch_bounds__(HoistGeo<K1, K2>::THREADS, 3)
     k_ks_hoist_ip(const uint64_t *__restrict__ mid, const uint64_t *__restrict__ dntt, size_t din_item, HoistKeys hk,
-                  uint64_t *__restrict__ acc, const ModQ *__restrict__ mods, int nl, int nq, int pidx, int items, int t0)
+                   uint64_t *__restrict__ acc, const ModQ *__restrict__ mods, int nl, int nq, int pidx, int items, int t0)
 {
     using H = HoistGeo<K1, K2>;
     constexpr int R1 = 1 << K1, NG = R1 / H::RPC;
+    const int npair = (items + 1) / 2;
     int bid = blockIdx.x;
-    const int b = bid % items;
-    bid /= items;
+    const int b0 = 2 * (bid % npair);
+    bid /= npair;
     const int grp = bid % NG;
-    const int t = t0 + bid / NG;  // target t0..nl (nl = P)
+    const int t = t0 + bid / NG;
     const int pt = t < nl ? t : pidx, kl = t < nl ? t : nq;
     const ModQ m = mods[pt];
     const int row = grp * H::RPC + threadIdx.x / H::TPR;
-    if (m.q < (1ull << 41))  // the same for the whole CTA
-        hoist_ip_body<K1, K2, true>(mid, dntt, din_item, hk, acc, m, nl, nq, b, t, kl, row);
+    const bool two = b0 + 1 < items;
+    if (m.q < (1ull << 41))
+        hoist_ip_body<K1, K2, true>(mid, dntt, din_item, hk, acc, m, nl, nq, b0, two, t, kl, row);
     else
-        hoist_ip_body<K1, K2, false>(mid, dntt, din_item, hk, acc, m, nl, nq, b, t, kl, row);
+        hoist_ip_body<K1, K2, false>(mid, dntt, din_item, hk, acc, m, nl, nq, b0, two, t, kl, row);
 }
 
 template <int K1, int K2>
@@ -747,9 +763,9 @@ struct KsPlan {
         const int runs[2][2] = {{0, a}, {b, nl + 1}};
         for (const auto &r : runs)
             if (r[1] > r[0]) {
-                const unsigned g2 = (unsigned)((size_t)items * (r[1] - r[0]) * (R1 / H::RPC));
+                const unsigned g2 = (unsigned)((size_t)((items + 1) / 2) * (r[1] - r[0]) * (R1 / H::RPC));
                 HELR_LAUNCH(k_ks_hoist_ip<K1, K2><<<g2, H::THREADS, 0, s>>>(mid, dntt, din_item, hk, acc, c->t.mod, nl,
-                                                                            c->nq, c->nq, items, r[0]));
+                                                                              c->nq, c->nq, items, r[0]));
             }
         return HE_OK;
     }
