@@ -490,6 +490,8 @@ def sweep(args):
                                   "hbm_frac_of_alg_bytes": round(2 * reps * nl * 16 * n / sec / 1e9 /
                                                                  measured_peaks().get("hbm_gbs", 6800.0), 4)}), flush=True)
                 del buf
+            if not point:
+                sweep_ct_ops(ctx, logn, limbs)
             ctx.close()
     if point:
         return
@@ -515,6 +517,52 @@ def sweep(args):
             print(json.dumps({"sweep": "keyswitch", "log_n": LOGN, "limbs": nl, "batch": batch,
                               "keyswitch_per_s": round(reps * batch / sec, 1)}), flush=True)
             del din, dout
+
+
+def sweep_ct_ops(ctx, logn, limbs, rot=4):
+    """The ciphertext operations of the primitive sweep at the full chain of
+    `limbs` primes: ct x ct multiply with relinearisation, rotation by `rot`
+    slots and rescale, each batched over 1, 8, 64 and 512 ciphertexts
+    (he_mul_relin_batch, he_rotate_batch, he_rescale_batch) on uniform random
+    residues.  Algorithmic bytes at L limbs (8N bytes a limb, keys once per
+    call): Mul 2 ciphertexts in and 1 out plus the 2L(L+1) key limbs; rotation
+    1 in, 1 out plus the key; rescale 2L limbs in, 2(L-1) out.  Points whose
+    working set (operands, evaluator and key-switch scratch) would pass
+    120 GB are skipped."""
+    import torch
+    nl = min(limbs, 38)  # the sweep's contexts hold at most 38 ciphertext primes
+    n, level = 1 << logn, nl - 1
+    ctx.keygen(2, [rot])
+    hbm = float(measured_peaks().get("hbm_gbs", 6800.0))
+    for batch in (1, 8, 64, 512):
+        words = batch * nl * n * (6 + 8 + 4) + min(128, batch) * nl * (nl + 1) * n
+        if words * 8 > 120 << 30:
+            continue
+        a = torch.randint(0, 1 << 30, (batch * 2 * nl * n,), dtype=torch.int64, device="cuda")
+        b = torch.randint(0, 1 << 30, (batch * 2 * nl * n,), dtype=torch.int64, device="cuda")
+        o = torch.zeros_like(a)
+        keyb = 2 * nl * (nl + 1)
+        ops = (("mul_relin", lambda: ctx.mul_relin_batch(a.data_ptr(), b.data_ptr(), o.data_ptr(), batch, level),
+                batch * 6 * nl + keyb),
+               ("rotate", lambda: ctx.rotate_batch(a.data_ptr(), o.data_ptr(), batch, level, rot),
+                batch * 4 * nl + keyb),
+               ("rescale", lambda: ctx.rescale_batch(a.data_ptr(), o.data_ptr(), batch, level),
+                batch * (4 * nl - 2)))
+        for name, call, limbs_moved in ops:
+            call()
+            torch.cuda.synchronize()
+            reps = max(2, min(20, 256 // batch))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                call()
+            e1.record()
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1000.0 / reps
+            print(json.dumps({"sweep": name, "log_n": logn, "limbs": nl, "ciphertexts_per_launch": batch,
+                              "ciphertexts_per_s": round(batch / sec, 1),
+                              "hbm_frac_of_alg_bytes": round(limbs_moved * 8 * n / sec / 1e9 / hbm, 4)}), flush=True)
+        del a, b, o
 
 
 def ks_primitive(ctx, level, items, kind, reps=3):

@@ -194,6 +194,21 @@ int he_keyswitch_batch(he_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int b
  * overlap d_in (HE_EINVAL).  Device scratch is allocated by the call. */
 int he_rotsum_batch(he_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int batch, int level,
                     const int64_t *rots, size_t n_rot);
+/* Batched Mul, Rescale and Rotation (Sec. 2.1) on device ciphertexts: `batch`
+ * items of [2][level+1][N] NTT-form words each, stored contiguously; the
+ * output buffer must not overlap an input (HE_EINVAL).  Scales are the
+ * caller's (the words are those of he_mul, he_rescale and he_rotate on each
+ * item).  Device scratch is allocated by the call; each runs on the context
+ * stream without synchronising.
+ * he_mul_relin_batch: d_out[b] = Relin(d_a[b] (x) d_b[b]) at the same level
+ *   (HE_EKEY without a relinearisation key).
+ * he_rescale_batch: d_out[b] = d_in[b] divided by q_level with rounding, at
+ *   level - 1 ([batch][2][level][N]); HE_ELEVEL at level 0.
+ * he_rotate_batch: d_out[b] = Rot(d_in[b], r), a left rotation of the slots
+ *   by r (HE_EKEY without its key). */
+int he_mul_relin_batch(he_ctx *ctx, const uint64_t *d_a, const uint64_t *d_b, uint64_t *d_out, int batch, int level);
+int he_rescale_batch(he_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int batch, int level);
+int he_rotate_batch(he_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int batch, int level, int64_t r);
 /* Autotuning of the key switch (Sec. 2.1; the relinearisation inside every
  * Mul and the key switch inside every rotation): per level it picks
  *  - the wave: the number of items whose ModUp and inner product share one

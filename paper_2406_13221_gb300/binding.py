@@ -112,6 +112,9 @@ SIGNATURES = {
     "he_bootstrap_batch": (_i, [_vp, _vp, _i, _vp, _i, ctypes.POINTER(he_boot_params)]),
     "he_rotsum": (_i, [_vp, _vp, _vp, _sz, _pp]),
     "he_rotsum_batch": (_i, [_vp, _vp, _vp, _i, _i, _vp, _sz]),
+    "he_mul_relin_batch": (_i, [_vp, _vp, _vp, _vp, _i, _i]),
+    "he_rescale_batch": (_i, [_vp, _vp, _vp, _i, _i]),
+    "he_rotate_batch": (_i, [_vp, _vp, _vp, _i, _i, ctypes.c_int64]),
     "he_ks_tile": (_i, [_vp, _i]),
     "he_set_ks_tile": (_i, [_vp, _i]),
     "he_set_hoist_form": (_i, [_vp, _i]),
@@ -363,6 +366,15 @@ class Context:
 
     def keyswitch_batch(self, din, dout, batch, level, gal):
         self.check(self.L.he_keyswitch_batch(self.h, din, dout, batch, level, gal))
+
+    def mul_relin_batch(self, da, db, dout, batch, level):
+        self.check(self.L.he_mul_relin_batch(self.h, da, db, dout, batch, level))
+
+    def rescale_batch(self, din, dout, batch, level):
+        self.check(self.L.he_rescale_batch(self.h, din, dout, batch, level))
+
+    def rotate_batch(self, din, dout, batch, level, r):
+        self.check(self.L.he_rotate_batch(self.h, din, dout, batch, level, int(r)))
 
 
 class Ct:

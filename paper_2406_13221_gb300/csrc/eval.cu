@@ -424,6 +424,58 @@ extern "C" int he_rotsum(he_ctx *c, const he_ct *a, const int64_t *rots, size_t 
     return HE_OK;
 }
 
+// Batched Mul (with relinearisation), Rescale and Rotation on device buffers:
+// `batch` ciphertexts [batch][2][level+1][N] of NTT-form words, the output
+// in its own buffer (no overlap with an operand).  The scale is the caller's:
+// these calls move words only.
+static int batch_args(he_ctx *c, const void *in, const void *out, int batch, int level)
+{
+    if (!c || !in || !out || batch <= 0 || level < 0 || level >= c->nq) return HE_EINVAL;
+    if (in == out) return helr_fail(c, HE_EINVAL, "the output must not overlap the input");
+    return HE_OK;
+}
+
+extern "C" int he_mul_relin_batch(he_ctx *c, const uint64_t *d_a, const uint64_t *d_b, uint64_t *d_out, int batch,
+                                  int level)
+{
+    HELR_TRY(batch_args(c, d_a, d_out, batch, level));
+    if (!d_b || d_b == d_out) return HE_EINVAL;
+    Eval ev{};
+    HELR_TRY(ev_init(c, &ev, batch, level));
+    const size_t item = 2 * (size_t)(level + 1) * c->n;
+    CtB a{const_cast<uint64_t *>(d_a), batch, level, 1.0, item}, b{const_cast<uint64_t *>(d_b), batch, level, 1.0, item};
+    CtB o{d_out, batch, level, 0, item};
+    const int rc = ev_mul_relin(&ev, a, b, o);
+    ev_free(&ev);
+    return rc;
+}
+
+extern "C" int he_rescale_batch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, int level)
+{
+    HELR_TRY(batch_args(c, d_in, d_out, batch, level));
+    if (level < 1) return helr_fail(c, HE_ELEVEL, "Rescale: no level left");
+    Eval ev{};
+    HELR_TRY(ev_init(c, &ev, batch, level));
+    const size_t N = c->n;
+    CtB a{const_cast<uint64_t *>(d_in), batch, level, 1.0, 2 * (size_t)(level + 1) * N};
+    CtB o{d_out, batch, level - 1, 0, 2 * (size_t)level * N};
+    const int rc = ev_rescale(&ev, a, o);
+    ev_free(&ev);
+    return rc;
+}
+
+extern "C" int he_rotate_batch(he_ctx *c, const uint64_t *d_in, uint64_t *d_out, int batch, int level, int64_t r)
+{
+    HELR_TRY(batch_args(c, d_in, d_out, batch, level));
+    Eval ev{};
+    HELR_TRY(ev_init(c, &ev, batch, level));
+    const size_t item = 2 * (size_t)(level + 1) * c->n;
+    CtB a{const_cast<uint64_t *>(d_in), batch, level, 1.0, item}, o{d_out, batch, level, 1.0, item};
+    const int rc = ev_rotate(&ev, a, r, o);
+    ev_free(&ev);
+    return rc;
+}
+
 extern "C" int he_cmul(he_ctx *c, const he_ct *a, double v, double const_scale, he_ct **out)
 {
     if (!c || !a || !out || !(const_scale > 0)) return HE_EINVAL;

@@ -184,6 +184,53 @@ def test_hoisted_rotation_sum_bitwise(pair, rots):
         ctx.rotsum(a, list(range(1, 9)))  # more than 7 rotations
 
 
+def test_batched_mul_rescale_rotate_bitwise(pair):
+    """he_mul_relin_batch, he_rescale_batch and he_rotate_batch on five device
+    ciphertexts equal the oracle's Mul, Rescale and Rotate of every item; the
+    calls refuse an output that overlaps the input, a missing key and a
+    rescale at level 0."""
+    ctx, he = pair
+    n, level, batch = ctx.n, 8, 5
+    A = [enc_pair(ctx, he, rand_slots(ctx.nslots, 70 + i), 80 + i)[1] for i in range(batch)]
+    B = [enc_pair(ctx, he, rand_slots(ctx.nslots, 90 + i), 100 + i)[1] for i in range(batch)]
+    primes = list(range(level + 1))
+
+    def dev(cts):
+        t = torch.from_numpy(np.stack([c.data for c in cts]).reshape(-1).view(np.int64)).cuda()
+        ctx.ntt_forward(t.data_ptr(), batch * 2 * (level + 1), primes)
+        return t
+
+    def host(t, lv):
+        ctx.ntt_inverse(t.data_ptr(), batch * 2 * (lv + 1), list(range(lv + 1)))
+        torch.cuda.synchronize()
+        return t.cpu().numpy().view(np.uint64).reshape(batch, 2, lv + 1, n)
+
+    da, db = dev(A), dev(B)
+    prod = torch.zeros_like(da)
+    ctx.mul_relin_batch(da.data_ptr(), db.data_ptr(), prod.data_ptr(), batch, level)
+    resc = torch.zeros(batch * 2 * level * n, dtype=torch.int64, device="cuda")
+    ctx.rescale_batch(prod.data_ptr(), resc.data_ptr(), batch, level)
+    rot = torch.zeros_like(da)
+    ctx.rotate_batch(da.data_ptr(), rot.data_ptr(), batch, level, 4)
+    got_p, got_r, got_s = host(prod, level), host(rot, level), host(resc, level - 1)
+    for i in range(batch):
+        ref = he.mul(A[i], B[i])
+        assert np.array_equal(got_p[i], ref.data), i
+        assert np.array_equal(got_s[i], he.rescale(ref).data), i
+        assert np.array_equal(got_r[i], he.rotate(A[i], 4).data), i
+    for call in (lambda: ctx.rescale_batch(da.data_ptr(), da.data_ptr(), batch, level),
+                 lambda: ctx.mul_relin_batch(da.data_ptr(), db.data_ptr(), db.data_ptr(), batch, level)):
+        with pytest.raises(binding.HeError) as e:
+            call()
+        assert e.value.code == binding.HE_EINVAL
+    with pytest.raises(binding.HeError) as e:
+        ctx.rotate_batch(da.data_ptr(), rot.data_ptr(), batch, level, 9)  # no key for 9
+    assert e.value.code == binding.HE_EKEY
+    with pytest.raises(binding.HeError) as e:
+        ctx.rescale_batch(da.data_ptr(), resc.data_ptr(), batch, 0)
+    assert e.value.code == binding.HE_ELEVEL
+
+
 @pytest.mark.parametrize("rho", [1, 2])
 def test_iteration_bitwise_other_rotation_radix(small_job_inputs, rho):
     """The iteration with its rotate-and-sum steps in hoisted groups of 2 (the
