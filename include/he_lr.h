@@ -255,6 +255,11 @@ unsigned long long he_hoist_tensor_launches(const he_ctx *ctx);
  * tensor-core form, 1 s each) expired since the last call; the word is then
  * cleared. */
 int he_check_device(he_ctx *ctx);
+/* Self-test of that path: one thread waits on a barrier with the kernels'
+ * bounded wait.  arrive = 1: the thread arrives first and the wait ends at
+ * once; arrive = 0: nothing arrives, the wait runs out after one second and
+ * the next he_check_device returns HE_ETIMEOUT.  The context stays usable. */
+int he_selftest_bounded_wait(he_ctx *ctx, int arrive);
 /* Rescale without allocating (no counterpart in the paper: it exists for
  * callers that may not allocate device memory, such as code running under a
  * device-memory budget fixed in advance or inside a framework that owns every

@@ -120,6 +120,7 @@ SIGNATURES = {
     "he_set_hoist_form": (_i, [_vp, _i]),
     "he_hoist_tensor_launches": (ctypes.c_ulonglong, [_vp]),
     "he_check_device": (_i, [_vp]),
+    "he_selftest_bounded_wait": (_i, [_vp, _i]),
     "he_lr_job_free": (_i, [_vp]),
     "he_lr_multi_create": (_i, [_vp, _vp, _sz, _i, _pp]),
     "he_lr_multi_step": (_i, [_vp, _i, he_lr_sched]),
@@ -353,6 +354,9 @@ class Context:
     def check_device(self):
         """Raise HeError(HE_ETIMEOUT) if a bounded device-side wait expired."""
         self.check(self.L.he_check_device(self.h))
+
+    def selftest_bounded_wait(self, arrive):
+        self.check(self.L.he_selftest_bounded_wait(self.h, int(arrive)))
 
     def ks_wave(self, level):
         w = self.L.he_ks_wave(self.h, int(level))

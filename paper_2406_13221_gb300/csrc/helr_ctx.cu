@@ -8,6 +8,7 @@
 #include <stdlib.h>
 
 #include "helr_internal.cuh"
+#include "ntt_core.cuh"
 
 typedef unsigned __int128 u128;
 
@@ -67,6 +68,26 @@ extern "C" int he_set_hoist_form(he_ctx *c, int form)
 }
 
 extern "C" unsigned long long he_hoist_tensor_launches(const he_ctx *c) { return c ? c->hoist_tensor_launches : 0; }
+
+// One thread waits on an mbarrier of expected count 1 with the kernels' bounded
+// wait; when `arrive` is 0 nothing arrives, the wait runs out after one second
+// and bit 0 of the status word is set.
+__global__ void k_selftest_wait(int arrive, int *status)
+{
+    __shared__ uint64_t bar;
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
+    if (!mbar_wait_bounded(mb, 0)) atomicOr(status, 1);
+}
+
+extern "C" int he_selftest_bounded_wait(he_ctx *c, int arrive)
+{
+    if (!c) return HE_EINVAL;
+    HELR_LAUNCH(k_selftest_wait<<<1, 1, 0, c->stream>>>(arrive ? 1 : 0, c->d_status));
+    HELR_CUDA(c, cudaGetLastError());
+    return HE_OK;
+}
 
 extern "C" int he_check_device(he_ctx *c)
 {
