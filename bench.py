@@ -171,7 +171,8 @@ def run_ours(args, rank, world):
     ctx.keygen(2)
     tuned_levels = 0 if args.no_autotune else ctx.autotune(None, 256)
     autotune = {"ks_wave_by_level": [ctx.ks_wave(lv) for lv in range(NQ)],
-                "ks_tile_by_level": [ctx.ks_tile(lv) for lv in range(NQ)], "levels_measured": tuned_levels,
+                "ks_tile_by_level": [ctx.ks_tile(lv) for lv in range(NQ)],
+                "hoist_form_by_level": [ctx.hoist_form(lv) for lv in range(NQ)], "levels_measured": tuned_levels,
                 "s": round(time.time() - ta, 2)}
     job = binding.Job(ctx, X, y, binding.FULL_BATCH, 1024, binding.G8, LOG_SCALE, enc_seed=3, key_seed=2,
                       batch_blocks=args.chunk)
@@ -753,7 +754,7 @@ def hoist_forms(ctx, items=128, reps=5):
                 e1.record()
                 torch.cuda.synchronize()
             finally:
-                ctx.set_hoist_form(0)
+                ctx.set_hoist_form(-1)
             ctx.check_device()
             rec[name + "_s_per_call"] = round(e0.elapsed_time(e1) / 1000.0 / reps, 6)
             if form == 1:

@@ -219,9 +219,12 @@ int he_rotate_batch(he_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int batc
  *  - the tile variant of the kernels at that wave: bit 0 halves the columns
  *    per CTA of the ModUp/ModDown column kernel, bit 1 halves the rows per
  *    CTA of the ModDown and hoisted-digit row kernels; a variant other than 0
- *    is kept only when it is more than 1% faster.
+ *    is kept only when it is more than 1% faster;
+ *  - where the tensor-core form of the hoisted inner product applies
+ *    (he_set_hoist_form), its time against the CUDA-core form on a hoisted
+ *    sum of seven rotations; it is kept only when more than 1% faster.
  * Later key switches of this context use the choices; results do not depend
- * on them (the words are the same for every wave and tile).
+ * on them (the words are the same for every wave, tile and form).
  * table_path (may be NULL): a text table keyed by device, SM count, log N,
  * n_q and the primes; levels it already holds are loaded instead of measured,
  * and the file is rewritten when anything was measured.  *measured (may be
@@ -240,7 +243,9 @@ int he_ks_tile(const he_ctx *ctx, int level);
 int he_set_ks_tile(he_ctx *ctx, int tile);
 /* Form of the hoisted inner product of rotation groups (he_rotsum,
  * he_rotsum_batch and the rotate-and-sum steps of a training iteration,
- * Sec. 2.2 / 3.3): 0 = CUDA cores (default); 1 = tensor cores (tcgen05.mma on
+ * Sec. 2.2 / 3.3): -1 = the form he_autotune chose per limb count (the
+ * default; the CUDA-core form until he_autotune has measured both);
+ * 0 = CUDA cores; 1 = tensor cores (tcgen05.mma on
  * FP16 byte slices of the digits and keys, exact: the sum over the group's
  * rotations and digits is formed in 128 bits from the integer diagonal sums
  * the MMA accumulates).  Form 1 applies at a key switch whose target primes
@@ -248,6 +253,9 @@ int he_set_ks_tile(he_ctx *ctx, int tile);
  * special prime's target and every other case keep the CUDA-core form.  Both
  * forms give the same words.  HE_EINVAL for other values. */
 int he_set_hoist_form(he_ctx *ctx, int form);
+/* The form hoisted sums at `level` use (0 or 1; he_autotune's choice unless
+ * he_set_hoist_form forced one), or -HE_EINVAL. */
+int he_hoist_form(const he_ctx *ctx, int level);
 /* Launches of the tensor-core form made by ctx so far. */
 unsigned long long he_hoist_tensor_launches(const he_ctx *ctx);
 /* Synchronise the context stream and read the device status word: HE_OK, or

@@ -118,6 +118,7 @@ SIGNATURES = {
     "he_ks_tile": (_i, [_vp, _i]),
     "he_set_ks_tile": (_i, [_vp, _i]),
     "he_set_hoist_form": (_i, [_vp, _i]),
+    "he_hoist_form": (_i, [_vp, _i]),
     "he_hoist_tensor_launches": (ctypes.c_ulonglong, [_vp]),
     "he_check_device": (_i, [_vp]),
     "he_selftest_bounded_wait": (_i, [_vp, _i]),
@@ -345,8 +346,15 @@ class Context:
         self.check(self.L.he_set_ks_tile(self.h, int(tile)))
 
     def set_hoist_form(self, form):
-        """0: hoisted inner products on the CUDA cores; 1: on the tensor cores where they apply."""
+        """0: hoisted inner products on the CUDA cores; 1: on the tensor cores where they
+        apply; -1: the form he_autotune chose per limb count."""
         self.check(self.L.he_set_hoist_form(self.h, int(form)))
+
+    def hoist_form(self, level):
+        v = self.L.he_hoist_form(self.h, int(level))
+        if v < 0:
+            raise HeError(-v, "he_hoist_form")
+        return v
 
     def hoist_tensor_launches(self):
         return int(self.L.he_hoist_tensor_launches(self.h))

@@ -62,7 +62,7 @@ extern "C" int he_set_rotation_radix(he_ctx *c, int log2_radix)
 extern "C" int he_set_hoist_form(he_ctx *c, int form)
 {
     if (!c) return HE_EINVAL;
-    if (form != 0 && form != 1) return helr_fail(c, HE_EINVAL, "hoisted inner-product form %d (0 or 1)", form);
+    if (form < -1 || form > 1) return helr_fail(c, HE_EINVAL, "hoisted inner-product form %d (0, 1, -1 = tuned)", form);
     c->hoist_form = form;
     return HE_OK;
 }

@@ -225,7 +225,8 @@ struct he_ctx {
     int ks_tile_tab[HELR_MAXQ + 1] = {};  // tile variant per limb count chosen by he_autotune
     int rot_radix_log = 3;         // rotate-and-sum steps as hoisted groups of 2^rot_radix_log positions
     int secret_hw = 0;             // 0: dense ternary secret; h > 0: exactly h nonzero coefficients
-    int hoist_form = 0;            // hoisted inner product: 0 CUDA cores, 1 tensor cores where it applies
+    int hoist_form = -1;           // hoisted inner product forced: 0 CUDA cores, 1 tensor cores; -1 tuned
+    int hoist_form_tab[HELR_MAXQ + 1] = {};  // the form per limb count chosen by he_autotune (0 by default)
     unsigned long long hoist_tensor_launches = 0;
     int *d_status = nullptr;       // device failure bits (bit 0: a bounded wait expired), he_check_device
 };
@@ -349,6 +350,8 @@ int helr_ks_wave(const he_ctx *c, int nl);
 // CTAs, bit 1: fewer rows per row CTA): he_set_ks_tile, else the he_autotune
 // table, else 0 (autotune.cu)
 int helr_ks_tile(const he_ctx *c, int nl);
+// the hoisted inner product's form at nl limbs (0 CUDA cores, 1 tensor cores)
+int helr_hoist_form(const he_ctx *c, int nl);
 int helr_ks_scratch_alloc(he_ctx *c, int batch, int level, KsScratch *ws);
 void helr_ks_scratch_free(he_ctx *c, KsScratch *ws);
 // Output stage of a key switch (ModDown combined with the operation around it):

@@ -758,7 +758,7 @@ struct KsPlan {
         // applies; the CUDA cores take targets [0, a) and [b, nl] (nl = P)
         using H = HoistGeo<K1, K2>;
         int a = nl + 1, b = nl + 1;
-        if (c->hoist_form == 1 && helr_hoist_tensor_range(c, nl, hk.n, &a, &b))
+        if (helr_hoist_form(c, nl) == 1 && helr_hoist_tensor_range(c, nl, hk.n, &a, &b))
             HELR_TRY(helr_hoist_ip_tensor(c, mid, dntt, din_item, hk, acc, items, nl, a, b, s));
         const int runs[2][2] = {{0, a}, {b, nl + 1}};
         for (const auto &r : runs)

@@ -107,7 +107,7 @@ def test_hoisted_rotation_sums_256_items_tensor_form(bench_pair):
     try:
         ctx.rotsum_batch(dev.data_ptr(), out.data_ptr(), batch, level, rots)
     finally:
-        ctx.set_hoist_form(0)
+        ctx.set_hoist_form(-1)
     ctx.check_device()
     assert ctx.hoist_tensor_launches() > n0
     ctx.ntt_inverse(out.data_ptr(), batch * 2 * (level + 1), list(range(level + 1)))

@@ -49,7 +49,7 @@ def rotsum_batch(ctx, he, batch, level, rots, seed, form):
     try:
         ctx.rotsum_batch(dev.data_ptr(), out.data_ptr(), batch, level, rots)
     finally:
-        ctx.set_hoist_form(0)
+        ctx.set_hoist_form(-1)
     ctx.ntt_inverse(out.data_ptr(), batch * 2 * (level + 1), list(range(level + 1)))
     torch.cuda.synchronize()
     return out.cpu().numpy().view(np.uint64).reshape(batch, 2, level + 1, n), cts
@@ -110,7 +110,7 @@ def test_iteration_with_tensor_form_bitwise(pair):
         gW, gV = binding.lr_iteration(ctx, [g(z) for z in Z], g(B), g(W), g(V), 16, 256, alpha, eta,
                                       1.0 / data.n, qgnag.G8)
     finally:
-        ctx.set_hoist_form(0)
+        ctx.set_hoist_form(-1)
     ctx.check_device()
     assert ctx.hoist_tensor_launches() > n0
     assert np.array_equal(gW.export(), Wn.data)

@@ -298,30 +298,42 @@ def test_batched_keyswitch_bitwise(pair):
 
 
 def test_autotune_table_and_parity(pair, tmp_path):
-    """he_autotune measures every level once and writes its table (wave and
-    tile variant per limb count); a second context with the same parameters
-    loads the table without measuring; key switches of more than one wave with
-    the chosen waves and tiles equal the oracle's."""
+    """he_autotune measures every level once and writes its table (wave, tile
+    variant and hoisted inner-product form per limb count); a second context
+    with the same parameters loads the table without measuring; key switches of
+    more than one wave with the chosen waves and tiles, and a hoisted sum with
+    the chosen form, equal the oracle's."""
     _, he = pair
     path = tmp_path / "ks_wave.txt"
     ctx = binding.Context(13, 9)
     ctx.keygen(2, [3])
     assert ctx.autotune(str(path), items=40) == 9
     lines = path.read_text().splitlines()
-    assert lines[0] == "he_lr ks-wave table v2" and lines[1].startswith("key ")
+    assert lines[0] == "he_lr ks-wave table v3" and lines[1].startswith("key ")
     rows = [ln.split() for ln in lines[2:]]
+    assert all(len(f) == 12 and f[8] == "hoist" for f in rows)
     waves = {int(f[1]): int(f[3]) for f in rows}
     tiles = {int(f[1]): int(f[5]) for f in rows}
+    forms = {int(f[1]): int(f[9]) for f in rows}
     assert sorted(waves) == list(range(1, 10))
     assert set(waves.values()) <= {16, 32}  # the candidates up to 40 items
     assert set(tiles.values()) <= {0, 1, 2, 3}
+    assert set(forms.values()) <= {0, 1}
+    # the tensor-core form applies from 2 limbs (a 40-bit target) to 7 (7 x 7 <= 51 pairs)
+    assert forms[1] == 0 and forms[8] == 0 and forms[9] == 0
+    assert all(float(f[11]) > 0 for f in rows if 2 <= int(f[1]) <= 7)
     assert [ctx.ks_wave(lv) for lv in range(9)] == [waves[nl] for nl in range(1, 10)]
     assert [ctx.ks_tile(lv) for lv in range(9)] == [tiles[nl] for nl in range(1, 10)]
+    assert [ctx.hoist_form(lv) for lv in range(9)] == [forms[nl] for nl in range(1, 10)]
     ctx2 = binding.Context(13, 9)
     ctx2.keygen(2, [3])
     assert ctx2.autotune(str(path), items=40) == 0
     assert [ctx2.ks_wave(lv) for lv in range(9)] == [waves[nl] for nl in range(1, 10)]
     assert [ctx2.ks_tile(lv) for lv in range(9)] == [tiles[nl] for nl in range(1, 10)]
+    assert [ctx2.hoist_form(lv) for lv in range(9)] == [forms[nl] for nl in range(1, 10)]
+    ctx2.keygen(2, PAIR_ROTATIONS)
+    a, ra = enc_pair(ctx2, he, rand_slots(ctx2.nslots, 44), 45, level=5)
+    assert np.array_equal(ctx2.rotsum(a, [1, 2, 3]).export(), he.rotsum(ra, [1, 2, 3]).data)
     level, batch = 5, 40
     rng = np.random.default_rng(14)
     n = ctx2.n
