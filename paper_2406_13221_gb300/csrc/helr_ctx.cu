@@ -294,6 +294,12 @@ static int ctx_init(he_ctx *c, const he_params *p)
     c->nq = p->n_q;
     c->nprime = p->n_q + 1;
     c->sigma = p->sigma;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            c->sms = sms;
+    }
     const uint64_t twon = 2ull * c->n;
     std::vector<uint64_t> used;
     uint64_t v;

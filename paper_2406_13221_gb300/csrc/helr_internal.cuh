@@ -225,6 +225,7 @@ struct he_ctx {
     int ks_tile_tab[HELR_MAXQ + 1] = {};  // tile variant per limb count chosen by he_autotune
     int rot_radix_log = 3;         // rotate-and-sum steps as hoisted groups of 2^rot_radix_log positions
     int secret_hw = 0;             // 0: dense ternary secret; h > 0: exactly h nonzero coefficients
+    int sms = 152;                 // SMs of the device (grid sizing)
     int hoist_form = -1;           // hoisted inner product forced: 0 CUDA cores, 1 tensor cores; -1 tuned
     int hoist_form_tab[HELR_MAXQ + 1] = {};  // the form per limb count chosen by he_autotune (0 by default)
     unsigned long long hoist_tensor_launches = 0;

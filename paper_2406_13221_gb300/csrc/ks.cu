@@ -715,6 +715,9 @@ struct KsPlan {
     // CTA in the row kernels of ModDown and of the hoisted digits)
     static constexpr int CB = C / 2 > 0 ? C / 2 : 1;
     static constexpr int RB = RPCD / 2 > 0 ? RPCD / 2 : 1;
+    // a launch of fewer than two CTAs per SM (a wave of one or a few items)
+    // takes the narrower tile, with twice the CTAs
+    static bool small(const he_ctx *c, size_t ctas) { return ctas < 2 * (size_t)c->sms; }
     static constexpr size_t smd(int rr) { return (size_t)rr * Geo<K2>::SEG * 8; }
     static constexpr size_t sm1(int cc) { return (size_t)cc * Geo<K1>::SEG * 8 + (size_t)cc * R1 * 8; }
     static constexpr size_t SMD = smd(RPCD);
@@ -747,7 +750,7 @@ struct KsPlan {
     static int hoisted(he_ctx *c, const uint64_t *dntt, size_t din_item, uint64_t *mid, const HoistKeys &hk, uint64_t *acc,
                        int items, int nl, cudaStream_t s)
     {
-        if (helr_ks_tile(c, nl) & 2) {
+        if ((helr_ks_tile(c, nl) & 2) || small(c, (size_t)items * nl * nl * (R1 / RPCD))) {
             const unsigned g1 = (unsigned)((size_t)items * nl * nl * (R1 / RB));
             HELR_LAUNCH(k_ks_digit_rows<K1, K2, RB><<<g1, RB * T2, smd(RB), s>>>(mid, c->t.tw, c->t.mod, nl, c->nq));
         } else {
@@ -772,7 +775,7 @@ struct KsPlan {
     static void down(he_ctx *c, const KsOut &o, const uint64_t *src, size_t src_item, size_t src_poly, const uint64_t *lift,
                      int items, int nl, const uint64_t *inv, cudaStream_t s)
     {
-        if (helr_ks_tile(c, nl) & 2) {
+        if ((helr_ks_tile(c, nl) & 2) || small(c, (size_t)items * 2 * nl * (R1 / RPCD))) {
             const unsigned grid = (unsigned)((size_t)items * 2 * nl * (R1 / RB));
             HELR_LAUNCH(k_ks_down_rows<K1, K2, RB><<<grid, RB * T2, smd(RB), s>>>(o, src, src_item, src_poly, lift, c->t.tw,
                                                                                   c->t.mod, inv, nl));
@@ -784,7 +787,7 @@ struct KsPlan {
     }
     static void down_cols(he_ctx *c, const uint64_t *drow, size_t nsrc, int src_prime, uint64_t *out, int nl, cudaStream_t s)
     {
-        if (helr_ks_tile(c, nl) & 1)
+        if ((helr_ks_tile(c, nl) & 1) || small(c, nsrc * (R2 / C)))
             cols<CB, true>(c, drow, out, nsrc, nl, src_prime, s);
         else
             cols<C, true>(c, drow, out, nsrc, nl, src_prime, s);
@@ -800,7 +803,7 @@ struct KsPlan {
     }
     static int modup(he_ctx *c, const uint64_t *drow, uint64_t *mid, int items, int nl, cudaStream_t s)
     {
-        if (helr_ks_tile(c, nl) & 1)
+        if ((helr_ks_tile(c, nl) & 1) || small(c, (size_t)items * nl * (R2 / C)))
             cols<CB, false>(c, drow, mid, (size_t)items * nl, nl, 0, s);
         else
             cols<C, false>(c, drow, mid, (size_t)items * nl, nl, 0, s);
