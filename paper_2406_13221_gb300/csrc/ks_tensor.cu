@@ -44,11 +44,12 @@
 // returns and frees its tensor memory.
 //
 // Measured on GB300 (7 rotations, 6 limbs, 128 items at N = 2^16) it is slower
-// than the CUDA-core form, 27.7 against 12.7 ms per rotation sum.  The tensor
+// than the CUDA-core form, 27.2 against 11.8 ms per rotation sum.  The tensor
 // pipe is active 4% of the time.  Splitting digit words into bytes, the
 // Toeplitz key layout and two barriers per round of 4 positions cost more than
 // the 32-bit partial products they replace.  The per-item sector gathers also
-// read about 1.8 times the DRAM bytes.  So form 0 stays the default.
+// read about 1.8 times the DRAM bytes.  he_autotune measures both forms and keeps
+// this one only where it is faster.
 #include <stdint.h>
 
 #include "ntt_core.cuh"
