@@ -118,6 +118,44 @@ def test_hoisted_rotation_sums_256_items_tensor_form(bench_pair):
         assert np.array_equal(got[b], ref.data), b
 
 
+def test_batched_mul_rescale_rotate_64_items(bench_pair):
+    """he_mul_relin_batch, he_rescale_batch and he_rotate_batch on 64 ciphertexts at
+    the Step 1 level (7 limbs) with the bench's keys: items 0, 31 and 63 equal the
+    oracle's Mul, Rescale and Rotate (by 1 slot)."""
+    ctx, he = bench_pair
+    batch, n, level = 64, ctx.n, 6
+    rng = np.random.default_rng(91)
+    A = np.empty((batch, 2, level + 1, n), np.uint64)
+    B = np.empty_like(A)
+    for j in range(level + 1):
+        A[:, :, j, :] = rng.integers(0, he.q[j], (batch, 2, n), dtype=np.uint64)
+        B[:, :, j, :] = rng.integers(0, he.q[j], (batch, 2, n), dtype=np.uint64)
+    primes = list(range(level + 1))
+
+    def dev(x):
+        t = torch.from_numpy(x.reshape(-1).view(np.int64)).cuda()
+        ctx.ntt_forward(t.data_ptr(), batch * 2 * (level + 1), primes)
+        return t
+
+    def host(t, lv):
+        ctx.ntt_inverse(t.data_ptr(), batch * 2 * (lv + 1), list(range(lv + 1)))
+        torch.cuda.synchronize()
+        return t.cpu().numpy().view(np.uint64).reshape(batch, 2, lv + 1, n)
+
+    da, db = dev(A), dev(B)
+    prod, rot = torch.zeros_like(da), torch.zeros_like(da)
+    resc = torch.zeros(batch * 2 * level * n, dtype=torch.int64, device="cuda")
+    ctx.mul_relin_batch(da.data_ptr(), db.data_ptr(), prod.data_ptr(), batch, level)
+    ctx.rescale_batch(prod.data_ptr(), resc.data_ptr(), batch, level)
+    ctx.rotate_batch(da.data_ptr(), rot.data_ptr(), batch, level, 1)
+    got_p, got_s, got_r = host(prod, level), host(resc, level - 1), host(rot, level)
+    for b in (0, 31, batch - 1):
+        ref = he.mul(OCt(A[b], level, D), OCt(B[b], level, D))
+        assert np.array_equal(got_p[b], ref.data), b
+        assert np.array_equal(got_s[b], he.rescale(ref).data), b
+        assert np.array_equal(got_r[b], he.rotate(OCt(A[b], level, D), 1).data), b
+
+
 def test_block_gradients_300_blocks_256_per_launch(bench_pair):
     """A 300-block job at 256 blocks per launch (a full chunk, then a ragged
     chunk of 44): the gradient ciphertexts of Steps 1-6 for blocks 0, 128, 255
