@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(RPC * Geo<K2>::T, 4)
 // src limb j of polynomial p of item b: src + b src_item + p src_poly + j N.
 // grid: items * 2 polys * nl limbs * (R1 / RPC).
 template <int K1, int K2, int RPC>
-__global__ void __launch_bounds__(RPC * Geo<K2>::T, 768 / (RPC * Geo<K2>::T))
+__global__ void __launch_bounds__(RPC * Geo<K2>::T, 1024 / (RPC * Geo<K2>::T))
     k_ks_down_rows(KsOut o, const uint64_t *__restrict__ srcp, size_t src_item, size_t src_poly,
                    const uint64_t *__restrict__ lift, const uint64_t *__restrict__ twall, const ModQ *__restrict__ mods,
                    const uint64_t *__restrict__ inv, int nl)
