@@ -132,26 +132,48 @@ int linear_transform(Eval *ev, Pool &pool, const CtB &a, int n, const std::vecto
     const int nb = 31 - __builtin_clz((unsigned)n);
     const int n1 = 1 << ((nb + 1) / 2), n2 = n / n1, ns = c->nslots, nl = a.level + 1;
     const size_t N = c->n;
-    // every diagonal, encoded at once
-    std::vector<double> re((size_t)n * ns), im((size_t)n * ns);
-    for (int g = 0; g < n2; g++)
-        for (int b = 0; b < n1; b++) {
-            const int r = g * n1 + b;
-            double *zr = re.data() + (size_t)r * ns, *zi = im.data() + (size_t)r * ns;
-            for (int s = 0; s < ns; s++) {
-                const int k = ((s % n) - g * n1 + n) % n;
-                zr[s] = Mre[(size_t)k * n + (k + r) % n];
-                zi[s] = Mim[(size_t)k * n + (k + r) % n];
-            }
-        }
-    double *dz = nullptr;
+    // every diagonal, encoded at once; the plaintexts depend on the matrix, the
+    // level and the scale only, so a context encodes each set once and keeps it
+    uint64_t key = 1469598103934665603ull;  // FNV-1a
+    auto mix = [&key](const void *p, size_t bytes) {
+        const unsigned char *u = (const unsigned char *)p;
+        for (size_t i = 0; i < bytes; i++) key = (key ^ u[i]) * 1099511628211ull;
+    };
+    mix(Mre.data(), sizeof(double) * Mre.size());
+    mix(Mim.data(), sizeof(double) * Mim.size());
+    mix(&pt_scale, sizeof pt_scale);
+    mix(&n, sizeof n);
+    mix(&nl, sizeof nl);
     uint64_t *pts = nullptr;
-    HELR_TRY(helr_alloc(c, (void **)&dz, sizeof(double) * 2 * re.size()));
-    int rc = helr_alloc(c, (void **)&pts, sizeof(uint64_t) * (size_t)n * nl * N);
-    if (!rc) {
-        cudaMemcpyAsync(dz, re.data(), sizeof(double) * re.size(), cudaMemcpyHostToDevice, c->stream);
-        cudaMemcpyAsync(dz + re.size(), im.data(), sizeof(double) * im.size(), cudaMemcpyHostToDevice, c->stream);
-        rc = helr_encode_dev(c, dz, dz + re.size(), n, (size_t)ns, a.level, pt_scale, pts, (size_t)nl * N);
+    for (const auto &d : c->boot_diag)
+        if (d.first == key) pts = d.second;
+    int rc = HE_OK;
+    if (!pts) {
+        std::vector<double> re((size_t)n * ns), im((size_t)n * ns);
+        for (int g = 0; g < n2; g++)
+            for (int b = 0; b < n1; b++) {
+                const int r = g * n1 + b;
+                double *zr = re.data() + (size_t)r * ns, *zi = im.data() + (size_t)r * ns;
+                for (int s = 0; s < ns; s++) {
+                    const int k = ((s % n) - g * n1 + n) % n;
+                    zr[s] = Mre[(size_t)k * n + (k + r) % n];
+                    zi[s] = Mim[(size_t)k * n + (k + r) % n];
+                }
+            }
+        double *dz = nullptr;
+        HELR_TRY(helr_alloc(c, (void **)&dz, sizeof(double) * 2 * re.size()));
+        rc = helr_alloc(c, (void **)&pts, sizeof(uint64_t) * (size_t)n * nl * N);
+        if (!rc) {
+            cudaMemcpyAsync(dz, re.data(), sizeof(double) * re.size(), cudaMemcpyHostToDevice, c->stream);
+            cudaMemcpyAsync(dz + re.size(), im.data(), sizeof(double) * im.size(), cudaMemcpyHostToDevice, c->stream);
+            rc = helr_encode_dev(c, dz, dz + re.size(), n, (size_t)ns, a.level, pt_scale, pts, (size_t)nl * N);
+        }
+        helr_free(c, dz);
+        if (rc) {
+            helr_free(c, pts);
+            return rc;
+        }
+        c->boot_diag.push_back({key, pts});
     }
     // baby steps
     std::vector<CtB> baby(n1, a);
@@ -189,8 +211,6 @@ int linear_transform(Eval *ev, Pool &pool, const CtB &a, int n, const std::vecto
         if (!rc) rc = g ? ev_add(ev, acc, *part, acc, 0) : ev_moddrop(ev, *part, part->level, acc);
     }
     if (!rc) rc = ev_rescale(ev, acc, out);
-    helr_free(c, pts);
-    helr_free(c, dz);
     return rc;
 }
 

@@ -458,6 +458,7 @@ extern "C" int he_ctx_destroy(he_ctx *c)
                     c->d_status};
     for (void *p : ptrs) helr_free(c, p);
     for (auto &k : c->ksk) helr_free(c, k.d);
+    for (auto &d : c->boot_diag) helr_free(c, d.second);
     cudaStreamSynchronize(c->stream);
     free(c->h_sk);
     delete c;
@@ -528,6 +529,7 @@ extern "C" int he_keygen(he_ctx *c, uint64_t seed, const int64_t *rot, size_t nr
     if (!c || (nrot && !rot)) return HE_EINVAL;
     if (!c->have_keys || c->key_seed != seed) {
         for (auto &k : c->ksk) helr_free(c, k.d);
+    for (auto &d : c->boot_diag) helr_free(c, d.second);
         c->ksk.clear();
         HELR_TRY(helr_keygen_base(c, seed));
         HELR_TRY(helr_add_key(c, 0));

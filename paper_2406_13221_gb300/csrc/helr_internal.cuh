@@ -230,6 +230,9 @@ struct he_ctx {
     int hoist_form_tab[HELR_MAXQ + 1] = {};  // the form per limb count chosen by he_autotune (0 by default)
     unsigned long long hoist_tensor_launches = 0;
     int *d_status = nullptr;       // device failure bits (bit 0: a bounded wait expired), he_check_device
+    // encoded diagonal plaintexts of the bootstrap's linear transforms, keyed by
+    // a hash of the matrix, the level, the plaintext scale and the slot period
+    std::vector<std::pair<uint64_t, uint64_t *>> boot_diag;
 };
 
 struct he_ct {
